@@ -1,0 +1,170 @@
+"""Pins for the oracle's ABMC blocking, greedy block coloring and ordering.
+
+ABMC (Sec. 3; block size s = ceil(n/n_b), Sec. 5.1) is pinned by closed forms
+(path graph, block sizes), the Table 6 ABMC rows and a hand-worked 4x4 grid;
+greedy coloring (Sec. 3, Sec. 5.1) by networkx's independent greedy_color and
+the invariant that same-color blocks share no edge.
+"""
+import math
+import os
+
+import networkx as nx
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import gen
+import oracle
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _path_graph(n):
+    m = sp.diags([np.ones(n - 1), np.ones(n), np.ones(n - 1)], [-1, 0, 1], format="csr")
+    return gen.from_scipy(m)
+
+
+def _truncated_grid(n, w):
+    """n nodes of a w-wide 2D grid, numbered row-major."""
+    i = np.arange(n)
+    right = i[(i % w != w - 1) & (i + 1 < n)]
+    down = i[i + w < n]
+    r = np.concatenate([right, down])
+    c = np.concatenate([right + 1, down + w])
+    m = sp.csr_matrix((np.ones(r.size), (r, c)), shape=(n, n))
+    return gen.from_scipy(m + m.T + sp.identity(n))
+
+
+@pytest.mark.parametrize("n,s", [(1, 1), (10, 3), (100, 7), (257, 16), (64, 64), (5, 10)])
+def test_abmc_path_graph_is_contiguous_segments(n, s):
+    a = _path_graph(n)
+    gptr, gadj = oracle.graph(a.n, a.rowptr, a.colind)
+    block_of, nb = oracle.abmc(n, gptr, gadj, s)
+    assert nb == math.ceil(n / s)
+    assert np.array_equal(block_of, np.arange(n) // s)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_abmc_block_sizes_closed_form(seed):
+    rng = np.random.default_rng(seed)
+    a = gen.random_spd_small(int(rng.integers(50, 400)), 0.03, seed)
+    s = int(rng.integers(1, 40))
+    gptr, gadj = oracle.graph(a.n, a.rowptr, a.colind)
+    block_of, nb = oracle.abmc(a.n, gptr, gadj, s)
+    sizes = np.bincount(block_of, minlength=nb)
+    assert nb == math.ceil(a.n / s)
+    assert np.all(sizes[:-1] == s)
+    assert sizes[-1] == a.n - (nb - 1) * s
+
+
+def test_abmc_table6_rows():
+    """Table 6: ABMC has B_max = ceil(n/n_b), G = 0.00, B_max/B_avg = 1.00."""
+    rows = [l.split() for l in open(os.path.join(GOLD, "table6_abmc.txt")) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 8
+    for name, n, nb_paper, bmax, g, ratio in rows:
+        n, nb_paper, bmax = int(n), int(nb_paper), int(bmax)
+        s = math.ceil(n / nb_paper)
+        a = _truncated_grid(n, 1024)
+        gptr, gadj = oracle.graph(a.n, a.rowptr, a.colind)
+        block_of, nb = oracle.abmc(n, gptr, gadj, s)
+        sizes = np.bincount(block_of)
+        assert nb == nb_paper, name
+        assert sizes.max() == bmax, name
+        assert f"{oracle.gini(sizes):.2f}" == g, name
+        assert f"{sizes.max() / sizes.mean():.2f}" == ratio, name
+
+
+def _read_gold(name):
+    d = {}
+    for l in open(os.path.join(GOLD, name)):
+        if l.strip() and not l.startswith("#"):
+            k, *v = l.split()
+            d[k] = np.array([int(x) for x in v])
+    return d
+
+
+def test_abmc_hand_worked_grid():
+    g = _read_gold("grid4x4_abmc4.txt")
+    a = gen.poisson2d_5pt(4)
+    bl = oracle.blocking(a, "abmc", 4)
+    assert np.array_equal(bl["block_of"], g["block_of"])
+    assert np.array_equal(bl["color_of"], g["color_of"])
+    assert np.array_equal(bl["perm"], g["perm"])
+    assert np.array_equal(bl["block_ptr"], g["block_ptr"])
+    assert np.array_equal(bl["color_ptr"], g["color_ptr"])
+
+
+def _block_graph(n, gptr, gadj, block_of, nb):
+    src = np.repeat(np.arange(n), np.diff(gptr))
+    bs, bd = block_of[src], block_of[gadj]
+    keep = bs != bd
+    G = nx.Graph()
+    G.add_nodes_from(range(nb))
+    G.add_edges_from(zip(bs[keep].tolist(), bd[keep].tolist()))
+    return G
+
+
+@pytest.mark.parametrize("case", ["grid2d", "grid3d", "rspd", "rgg"])
+@pytest.mark.parametrize("s", [1, 4, 16])
+def test_greedy_coloring_matches_networkx(case, s):
+    a = {"grid2d": lambda: gen.poisson2d_5pt(20), "grid3d": lambda: gen.poisson3d_7pt(8),
+         "rspd": lambda: gen.random_spd_small(300, 0.02, 5),
+         "rgg": lambda: gen.rgg_laplacian(500, 10.0, 3)}[case]()
+    gptr, gadj = oracle.graph(a.n, a.rowptr, a.colind)
+    block_of, nb = oracle.abmc(a.n, gptr, gadj, s)
+    color_of, nc = oracle.color_blocks(a.n, gptr, gadj, nb, block_of)
+    G = _block_graph(a.n, gptr, gadj, block_of, nb)
+    ref = nx.greedy_color(G, strategy=lambda g, colors: list(range(nb)))
+    assert all(color_of[b] == ref[b] for b in range(nb))
+    assert nc == max(ref.values()) + 1
+    # invariant: no edge joins two blocks of one color
+    for u, v in G.edges():
+        assert color_of[u] != color_of[v]
+    maxdeg = max((d for _, d in G.degree()), default=0)
+    assert nc <= maxdeg + 1
+
+
+def test_path_of_blocks_needs_two_colors():
+    a = _path_graph(100)
+    bl = oracle.blocking(a, "abmc", 10)
+    assert bl["n_c"] == 2
+    assert np.array_equal(bl["color_of"], np.arange(10) % 2)
+
+
+@pytest.mark.parametrize("method,kw", [("abmc", {"block_size": 8}), ("leiden_cpm", {"gamma": 0.1}),
+                                       ("leiden_md", {"gamma": 1.0})])
+def test_ordering_is_color_block_row_major(method, kw):
+    a = gen.poisson2d_5pt(24)
+    bl = oracle.blocking(a, method, **kw)
+    perm, bp, cp = bl["perm"], bl["block_ptr"], bl["color_ptr"]
+    assert np.array_equal(np.sort(perm), np.arange(a.n))
+    assert bp[0] == 0 and bp[-1] == a.n and np.all(np.diff(bp) > 0)
+    assert cp[0] == 0 and cp[-1] == bl["n_b"] and np.all(np.diff(cp) > 0)
+    # rows ascending inside each block; one block id and one color per block
+    for j in range(bl["n_b"]):
+        rows = perm[bp[j]:bp[j + 1]]
+        assert np.all(np.diff(rows) > 0)
+        assert len(set(bl["block_of"][rows])) == 1
+    # same-color blocks share no edge (checked on the permuted matrix)
+    ah = oracle.permute(a, perm)
+    blk = np.repeat(np.arange(bl["n_b"]), np.diff(bp))
+    col = np.repeat(np.arange(bl["n_c"]), np.diff(cp))[blk]
+    coo = ah.tocoo()
+    other = blk[coo.row] != blk[coo.col]
+    assert not np.any(col[coo.row][other] == col[coo.col][other])
+
+
+def test_leiden_block_sort_descending():
+    a = gen.poisson2d_5pt(30)
+    gptr, gadj = oracle.graph(a.n, a.rowptr, a.colind)
+    memb, k = oracle.leiden(a.n, gptr, gadj, "cpm", 0.05)
+    b = oracle.sort_blocks_desc(a.n, k, memb)
+    sizes = np.bincount(b, minlength=k)
+    assert np.all(np.diff(sizes) <= 0)
+    # ties broken by the smallest original row, ascending
+    first = np.array([np.nonzero(b == j)[0].min() for j in range(k)])
+    for j in range(k - 1):
+        if sizes[j] == sizes[j + 1]:
+            assert first[j] < first[j + 1]
+    # same partition, relabelled
+    assert len(set(zip(memb.tolist(), b.tolist()))) == k
