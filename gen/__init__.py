@@ -269,6 +269,10 @@ def elasticity_like(n_nodes_target: int, stencil: int, lam: float) -> CSR:
     n = 3 * nn
     a = sp.csr_matrix((np.concatenate(V), (np.concatenate(R), np.concatenate(C))), shape=(n, n))
     a.sum_duplicates()
+    # exact symmetry: the assembly sums (i,j) and (j,i) in different orders,
+    # so a cancellation could leave one of them a stored zero and not the other
+    a = ((a + a.T) * 0.5).tocsr()
+    a.eliminate_zeros()
     dmax = a.diagonal().max()
     a = a + 1e-6 * dmax * sp.identity(n, format="csr")
     return from_scipy(a, name=f"elast{stencil}_{nx}")

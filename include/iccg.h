@@ -1,0 +1,193 @@
+/*
+ * iccg.h -- C ABI of the GB300 block-multicolor ICCG library (libiccg.so).
+ *
+ * The library solves A x = b for a sparse SPD matrix A with the conjugate
+ * gradient method preconditioned by IC(0), whose forward and backward
+ * substitutions run in block-multicolor order: colors one after another,
+ * the blocks of one color in parallel, the rows of a block in order
+ * (Suzuki, "Comparison of Algebraic Block Multi-Coloring and Leiden Methods
+ * for Parallel Preconditioning in the ICCG Method", Sec. 3 and Alg. 1).
+ *
+ * General conventions
+ *   - Every function returns an iccg_status and never aborts or traps.
+ *   - Sparse matrices are CSR: rowptr int64[n+1], colind int32[nnz] (0-based),
+ *     val double[nnz]; both triangles stored, a diagonal entry in every row,
+ *     symmetric pattern.  nnz must be below 2^31.
+ *   - Vectors are in the caller's (original) row numbering; the library
+ *     applies the block-multicolor permutation internally.
+ *   - Array arguments of iccg_setup / iccg_solve / iccg_precond / iccg_spmv
+ *     may be host or device pointers (the library asks the CUDA runtime which
+ *     one it got).  The caller owns them; the library copies what it keeps.
+ *   - All device work of a context runs on the stream given to iccg_setup.
+ *     Calls on one context must not overlap; separate contexts are
+ *     independent.
+ *   - Host helpers (iccg_block_*, iccg_color_order) take host pointers only.
+ */
+#ifndef ICCG_H_
+#define ICCG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct iccg_ctx iccg_ctx;   /* opaque; owned by the library */
+typedef void *iccg_stream_t;        /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  ICCG_OK = 0,
+  ICCG_ERR_ARG = 1,           /* invalid argument (sizes, CSR, permutation, pointers) */
+  ICCG_ERR_COLORING = 2,      /* two blocks of one color share an edge */
+  ICCG_ERR_BREAKDOWN = 3,     /* IC(0) pivot not positive; see iccg_last_error */
+  ICCG_NOT_CONVERGED = 4,     /* maxit reached; x and the history are valid */
+  ICCG_ERR_CUDA = 5,          /* a CUDA runtime call failed; see iccg_last_error */
+  ICCG_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  ICCG_ERR_NONFINITE = 7,     /* NaN/Inf met in the iteration */
+  ICCG_ERR_UNIMPLEMENTED = 8,
+  ICCG_ERR_STATE = 9          /* call order violated (e.g. solve before factor) */
+} iccg_status;
+
+typedef struct {
+  int32_t precond_fp32;       /* 1: IC factors and substitutions stored and run in FP32
+                                 with FP32 accumulation; IC(0) itself, the CG dots,
+                                 alpha/beta and the x/r updates stay FP64 */
+  int32_t warps_per_cta;      /* warps per CTA of the per-color kernels; 0 = 4 */
+  int32_t rows_per_thread;    /* tile = 32 * rows_per_thread rows; 1, 2 or 4; 0 = 1 */
+  int32_t no_graph;           /* 1: drive the PCG loop from the host instead of a
+                                 CUDA graph with a device-side WHILE condition */
+  int32_t no_pdl;             /* 1: launch kernels without programmatic dependent
+                                 launch (no overlap of a kernel's prologue with the
+                                 tail of the previous one) */
+  int32_t reserved[3];        /* must be 0 */
+} iccg_opts;
+
+/* ------------------------------------------------------------------------
+ * iccg_setup -- Sec. 3: the block-multicolor ordering renumbers rows color
+ * by color, block by block; Alg. 1 then processes colors in sequence and the
+ * blocks of a color in parallel.
+ *
+ *   ctx        out: new context (NULL on error)
+ *   n, nnz     matrix order and stored entries (0 <= n, 0 <= nnz < 2^31)
+ *   rowptr, colind, val   CSR of A in the original numbering
+ *   perm       int32[n], perm[new] = old; a bijection on [0, n)
+ *   block_ptr  int32[n_b+1], rows of block j are new rows
+ *              [block_ptr[j], block_ptr[j+1]); strictly increasing, 0 .. n
+ *   color_ptr  int32[n_c+1], blocks of color c are [color_ptr[c],
+ *              color_ptr[c+1]); strictly increasing, 0 .. n_b
+ *   opts       NULL = defaults
+ *   stream     the CUDA stream all work of this context uses
+ *
+ * Checks the CSR (sorted or not, in range, diagonal present, symmetric
+ * pattern), the permutation and pointer arrays, and the coloring invariant
+ * that no stored entry joins two different blocks of one color
+ * (ICCG_ERR_COLORING, offending block in iccg_last_error).  Copies the
+ * permuted matrix and the per-color tile layout to the device.
+ * ------------------------------------------------------------------------ */
+iccg_status iccg_setup(iccg_ctx **ctx, int32_t n, int64_t nnz,
+                       const int64_t *rowptr, const int32_t *colind, const double *val,
+                       const int32_t *perm, const int32_t *block_ptr, const int32_t *color_ptr,
+                       int32_t n_b, int32_t n_c, const iccg_opts *opts, iccg_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * iccg_factor -- Sec. 3: IC(0) with zero fill-in of the reordered matrix,
+ * L L^T form (Alg. 1 divides by L_ii): L has the pattern of tril(A_hat) and
+ * (L L^T)_ij = a_hat_ij on it.  Runs on the device in FP64, color by color
+ * like Alg. 1.  A pivot that is not positive (or not finite) returns
+ * ICCG_ERR_BREAKDOWN; iccg_last_error gives the first such row in the
+ * original numbering.  May be called again (e.g. after iccg_update_values).
+ * ------------------------------------------------------------------------ */
+iccg_status iccg_factor(iccg_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * iccg_solve -- preconditioned CG (Sec. 1) with the IC(0) preconditioner
+ * applied by block-multicolor forward/backward substitution (Alg. 1 and the
+ * reverse sweep described after it); stops when ||r||_2/||b||_2 <= tol
+ * (Sec. 4 uses tol = 1e-8) with r the recursively updated residual.
+ *
+ *   b          double[n], right-hand side (host or device)
+ *   x          double[n], in: x0, out: solution (host or device)
+ *   tol, maxit stopping tolerance (>= 0) and iteration cap (>= 0)
+ *   iters      host int32*, out: iterations done (may be NULL)
+ *   res_hist   host double[maxit+1], out: ||r_k||/||b|| for k = 0..iters
+ *              (may be NULL)
+ *
+ * b = 0 gives x = 0 and 0 iterations.  Returns ICCG_NOT_CONVERGED when maxit
+ * is reached (x and history valid) and ICCG_ERR_NONFINITE on NaN/Inf.
+ * Requires a successful iccg_factor.
+ * ------------------------------------------------------------------------ */
+iccg_status iccg_solve(iccg_ctx *ctx, const double *b, double *x, double tol, int32_t maxit,
+                       int32_t *iters, double *res_hist);
+
+/* z = (L L^T)^{-1} r with the block-multicolor substitutions (Alg. 1 and the
+ * backward sweep); r, z double[n] in the original numbering. */
+iccg_status iccg_precond(iccg_ctx *ctx, const double *r, double *z);
+
+/* q = A p with the library's SpMV kernel (Table 8's SpMV phase); p, q
+ * double[n] in the original numbering. */
+iccg_status iccg_spmv(iccg_ctx *ctx, const double *p, double *q);
+
+/* Copy the IC(0) factor of the permuted matrix to host arrays laid out as
+ * the lower triangle of A_hat in CSR order (columns ascending, diagonal last
+ * in each row): lval double[nnz_lower]; *nnz_lower receives the count (pass
+ * lval = NULL to query it). */
+iccg_status iccg_get_factor(iccg_ctx *ctx, double *lval, int64_t *nnz_lower);
+
+/* Per-phase device time of one solve (CUDA events on the context's stream,
+ * host-driven loop, one event pair around every kernel).  ms[6] receives the
+ * summed milliseconds of: 0 init, 1 SpMV, 2 forward colors, 3 fused last
+ * color, 4 backward colors, 5 everything (first to last event); launches[6]
+ * the kernel launch counts.  Same arguments and results as iccg_solve. */
+iccg_status iccg_profile_solve(iccg_ctx *ctx, const double *b, double *x, double tol,
+                               int32_t maxit, int32_t *iters, double *ms, int64_t *launches);
+
+/* Layout facts of a context (host out-params, any may be NULL):
+ * n, nnz, n_b, n_c, number of tiles, number of tasks (warp work items),
+ * strictly-lower entries nL, max tile rounds (forward), max rows per task. */
+iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[9]);
+
+iccg_status iccg_last_error(const iccg_ctx *ctx, int64_t *row_or_block, const char **msg);
+void iccg_destroy(iccg_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Host-side blocking helpers (production implementations; host pointers).
+ * ------------------------------------------------------------------------ */
+
+/* Adjacency graph of A (Sec. 3): undirected, edge {i,j} iff i != j and a_ij
+ * or a_ji is stored.  gptr int64[n+1]; gadj int32[*m] neighbours ascending.
+ * Pass gadj = NULL to get *m (2 x edges) only. */
+iccg_status iccg_graph(int32_t n, const int64_t *rowptr, const int32_t *colind,
+                       int64_t *gptr, int32_t *gadj, int64_t *m);
+
+/* ABMC blocking (Sec. 3; block size s = ceil(n/n_b), Sec. 5.1): a seed is
+ * taken among the unassigned nodes and its neighbours are added from a FIFO
+ * candidate set until the block has s nodes; an empty candidate set is
+ * refilled with the smallest unassigned node.  block_of int32[n]. */
+iccg_status iccg_block_abmc(int32_t n, const int64_t *gptr, const int32_t *gadj, int32_t s,
+                            int32_t *block_of, int32_t *n_b);
+
+/* Leiden blocking (Sec. 4, Sec. 6.1; Traag, Waltman & van Eck 2019).
+ * quality 0 = modularity (Eq. 1, resolution gamma), 1 = CPM (Eq. 2,
+ * threshold gamma); n_iter full Leiden iterations (paper: 2), randomness
+ * beta (paper: 0.01), seed (paper: 42).  Communities are numbered by first
+ * appearance.  block_of int32[n]. */
+iccg_status iccg_block_leiden(int32_t n, const int64_t *gptr, const int32_t *gadj, int32_t quality,
+                              double gamma, int32_t n_iter, double beta, uint64_t seed,
+                              int32_t *block_of, int32_t *n_b);
+
+/* Leiden block order (Sec. 6.1): relabel blocks by size, descending (ties:
+ * smaller first row first). */
+iccg_status iccg_sort_blocks_desc(int32_t n, int32_t n_b, int32_t *block_of);
+
+/* Greedy block coloring (Sec. 3; Sec. 5.1) followed by the block-multicolor
+ * ordering (colors ascending, blocks ascending, rows ascending).
+ * color_of int32[n_b]; perm int32[n]; block_ptr int32[n_b+1];
+ * color_ptr int32[n_b+1] (first n_c+1 entries used). */
+iccg_status iccg_color_order(int32_t n, const int64_t *gptr, const int32_t *gadj, int32_t n_b,
+                             const int32_t *block_of, int32_t *color_of, int32_t *n_c,
+                             int32_t *perm, int32_t *block_ptr, int32_t *color_ptr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ICCG_H_ */

@@ -1,0 +1,608 @@
+// C ABI of libiccg: context management, setup, IC(0), the graph-driven PCG
+// solve and the per-kernel entry points used by the parity tests.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "iccg_internal.h"
+
+using namespace iccg;
+
+
+struct iccg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  iccg_opts opts{};
+  bool fp32 = false;
+  HostLayout H;
+  Plan plan;
+  Params P{};
+  bool factored = false;
+  std::vector<void *> allocs;
+  // solve state
+  double *hist = nullptr;
+  int32_t hist_cap = 0;
+  double *bin = nullptr, *xin = nullptr, *xout = nullptr;
+  Scalars *sc_host = nullptr;      // pinned
+  double *hist_host = nullptr;     // pinned
+  int32_t hist_host_cap = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  unsigned long long cond_handle = 0;
+  // error record
+  int64_t err_index = -1;
+  std::string err_msg;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+iccg_status cuda_fail(iccg_ctx *c, cudaError_t e, const char *where) {
+  if (c) {
+    c->err_index = -1;
+    c->err_msg = std::string(where) + ": " + cudaGetErrorString(e);
+  }
+  return ICCG_ERR_CUDA;
+}
+
+#define CK(call, where)                          \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+bool host_copy(const T *p, size_t count, std::vector<T> &out, cudaStream_t s) {
+  out.resize(count);
+  if (count == 0) return true;
+  if (is_device_ptr(p)) {
+    if (cudaMemcpyAsync(out.data(), p, count * sizeof(T), cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
+    return cudaStreamSynchronize(s) == cudaSuccess;
+  }
+  std::memcpy(out.data(), p, count * sizeof(T));
+  return true;
+}
+
+template <typename T>
+cudaError_t dev_alloc(iccg_ctx *c, T **p, size_t count) {
+  // 64 bytes of padding: 16-byte vector loads of a segment's aligned cover
+  // may read up to 15 bytes past the last element.
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 64);
+  if (e != cudaSuccess) return e;
+  c->allocs.push_back(q);
+  cudaMemsetAsync(q, 0, count * sizeof(T) + 64, c->stream);
+  *p = static_cast<T *>(q);
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t dev_upload(iccg_ctx *c, T **p, const std::vector<T> &v) {
+  cudaError_t e = dev_alloc(c, p, v.size());
+  if (e != cudaSuccess || v.empty()) return e;
+  return cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream);
+}
+
+// copy a caller array (host or device) into a device buffer
+cudaError_t copy_in(iccg_ctx *c, double *dst, const double *src, size_t count) {
+  if (count == 0) return cudaSuccess;
+  cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  return cudaMemcpyAsync(dst, src, count * sizeof(double), k, c->stream);
+}
+
+cudaError_t copy_out(iccg_ctx *c, double *dst, const double *src, size_t count) {
+  if (count == 0) return cudaSuccess;
+  cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  return cudaMemcpyAsync(dst, src, count * sizeof(double), k, c->stream);
+}
+
+constexpr int kCapLimit = 1024;   // staged entries per warp (beyond: direct loads)
+
+int cap_of(int seg) {
+  int c = ((seg + 8) + 3) & ~3;
+  return std::min(c, kCapLimit);
+}
+
+[[maybe_unused]] int warp_bytes_unused(int cap, int R, int elem) {
+  return ((cap * elem + 15) & ~15) + ((cap * 4 + 15) & ~15) + ((32 * R * elem + 15) & ~15);
+}
+
+std::once_flag g_cfg_once[64];
+cudaError_t g_cfg_err[64];
+
+void destroy_graph(iccg_ctx *c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
+                       const double *val, const int32_t *perm, const int32_t *block_ptr,
+                       const int32_t *color_ptr, int32_t n_b, int32_t n_c, const iccg_opts *opts,
+                       iccg_stream_t stream) {
+  if (!out) return ICCG_ERR_ARG;
+  *out = nullptr;
+  if (n < 0 || nnz < 0) return ICCG_ERR_ARG;
+  if (!rowptr || (n > 0 && (!colind || !val || !perm || !block_ptr || !color_ptr))) return ICCG_ERR_ARG;
+  iccg_opts o{};
+  if (opts) o = *opts;
+  for (int k = 0; k < 3; ++k)
+    if (o.reserved[k] != 0) return ICCG_ERR_ARG;
+  if (o.warps_per_cta == 0) o.warps_per_cta = 4;
+  if (o.rows_per_thread == 0) o.rows_per_thread = 1;
+  if (o.warps_per_cta < 1 || o.warps_per_cta > kMaxWarpsPerCta) return ICCG_ERR_ARG;
+  if (o.rows_per_thread != 1 && o.rows_per_thread != 2 && o.rows_per_thread != 4) return ICCG_ERR_ARG;
+
+  iccg_ctx *ctx = new iccg_ctx();
+  ctx->opts = o;
+  ctx->fp32 = o.precond_fp32 != 0;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  *out = ctx;
+  // host views of the inputs (device inputs are copied down); all validation
+  // happens before the first CUDA call that needs a device
+  std::vector<int64_t> hrp;
+  std::vector<int32_t> hci, hperm, hbp, hcp;
+  std::vector<double> hval;
+  if (!host_copy(rowptr, size_t(n) + 1, hrp, ctx->stream)) return cuda_fail(ctx, cudaGetLastError(), "copy rowptr");
+  if (hrp[0] != 0 || hrp[n] != nnz) {
+    ctx->err_msg = "rowptr[0] must be 0 and rowptr[n] = nnz";
+    return ICCG_ERR_ARG;
+  }
+  if (!host_copy(colind, size_t(nnz), hci, ctx->stream) || !host_copy(val, size_t(nnz), hval, ctx->stream) ||
+      !host_copy(perm, size_t(n), hperm, ctx->stream) ||
+      !host_copy(block_ptr, size_t(n > 0 ? n_b + 1 : 0), hbp, ctx->stream) ||
+      !host_copy(color_ptr, size_t(n > 0 ? n_c + 1 : 0), hcp, ctx->stream))
+    return cuda_fail(ctx, cudaGetLastError(), "copy inputs");
+  if (n == 0) { hbp.assign(1, 0); hcp.assign(1, 0); }
+  const int R = o.rows_per_thread, W = o.warps_per_cta;
+  iccg_status st = build_layout(n, nnz, hrp.data(), hci.data(), hval.data(), hperm.data(), hbp.data(),
+                                hcp.data(), n_b, n_c, R, ctx->H, ctx->err_index, ctx->err_msg);
+  if (st != ICCG_OK) return st;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaGetDevice");
+  {
+    int dev = ctx->device;
+    if (dev < 64) {
+      std::call_once(g_cfg_once[dev], [dev] { g_cfg_err[dev] = configure_kernels(); });
+      if (g_cfg_err[dev] != cudaSuccess) return cuda_fail(ctx, g_cfg_err[dev], "configure_kernels");
+    }
+  }
+  HostLayout &H = ctx->H;
+
+  // launch plan
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  Plan &L = ctx->plan;
+  L.stream = ctx->stream;
+  L.W = W;
+  L.R = R;
+  L.n_c = n_c;
+  L.n = n;
+  L.pdl = o.no_pdl == 0;
+  const int elem = ctx->fp32 ? 4 : 8;
+  const int cap_l = cap_of(H.seg_l), cap_u = cap_of(H.seg_u), cap_a = cap_of(H.seg_a);
+  L.smem_fwd = W * warp_smem_bytes(cap_l, R, elem);
+  L.smem_bwd = W * warp_smem_bytes(cap_u, R, elem);
+  L.smem_fused = W * warp_smem_bytes(std::max(cap_l, cap_u), R, elem);
+  L.smem_a = W * warp_smem_bytes(cap_a, 0, 8);
+  // one warp per task (color kernels) or per 32R-row tile (SpMV)
+  L.grid_c.assign(n_c, 0);
+  L.task0.assign(n_c, 0);
+  L.task1.assign(n_c, 0);
+  int32_t gbig = 1;
+  for (int c = 0; c < n_c; ++c) {
+    L.task0[c] = H.color_task[c];
+    L.task1[c] = H.color_task[c + 1];
+    const int ntask = L.task1[c] - L.task0[c];
+    L.grid_c[c] = std::max(1, (ntask + W - 1) / W);
+    gbig = std::max(gbig, L.grid_c[c]);
+  }
+  const int T = 32 * R;
+  const int ntile_a = (n + T - 1) / T;
+  L.grid_a = std::max(1, (ntile_a + W - 1) / W);
+  L.grid_v = std::max(1, std::min((n + 255) / 256, sms * 8));
+  gbig = std::max(gbig, L.grid_a);
+
+  // device arrays
+  Params &P = ctx->P;
+  P.n = n; P.R = R; P.W = W; P.n_c = n_c;
+  P.cap_l = cap_l; P.cap_u = cap_u; P.cap_a = cap_a;
+  int32_t *d_arp, *d_acol, *d_lrp, *d_lcol, *d_urp, *d_ucol, *d_umap, *d_perm;
+  TaskDesc *d_tasks;
+  TileDesc *d_tiles;
+  double *d_aval, *d_ainit, *d_adiag;
+  uint8_t *d_lev;
+  CK(dev_upload(ctx, &d_arp, H.arp), "alloc A");
+  CK(dev_upload(ctx, &d_acol, H.acol), "alloc A");
+  CK(dev_upload(ctx, &d_aval, H.aval), "alloc A");
+  CK(dev_upload(ctx, &d_lrp, H.lrp), "alloc L");
+  CK(dev_upload(ctx, &d_lcol, H.lcol), "alloc L");
+  CK(dev_upload(ctx, &d_ainit, H.ainit), "alloc L");
+  CK(dev_upload(ctx, &d_adiag, H.adiag), "alloc L");
+  CK(dev_upload(ctx, &d_urp, H.urp), "alloc U");
+  CK(dev_upload(ctx, &d_ucol, H.ucol), "alloc U");
+  CK(dev_upload(ctx, &d_umap, H.umap), "alloc U");
+  CK(dev_upload(ctx, &d_tiles, H.tiles), "alloc tiles");
+  CK(dev_upload(ctx, &d_tasks, H.tasks), "alloc tiles");
+  CK(dev_upload(ctx, &d_lev, H.lev), "alloc tiles");
+  CK(dev_upload(ctx, &d_perm, H.perm), "alloc perm");
+  P.arp = d_arp; P.acol = d_acol; P.aval = d_aval;
+  P.lrp = d_lrp; P.lcol = d_lcol; P.urp = d_urp; P.ucol = d_ucol; P.umap = d_umap;
+  P.ainit = d_ainit; P.adiag = d_adiag;
+  P.tdesc = d_tiles;
+  P.tasks = d_tasks;
+  P.lev = d_lev;
+  P.perm = d_perm;
+  const size_t nL = size_t(H.nL), nn = size_t(n);
+  CK(dev_alloc(ctx, &P.lval, nL), "alloc factor");
+  CK(dev_alloc(ctx, &P.uval, nL), "alloc factor");
+  CK(dev_alloc(ctx, &P.lval32, nL), "alloc factor");
+  CK(dev_alloc(ctx, &P.uval32, nL), "alloc factor");
+  CK(dev_alloc(ctx, &P.ldiag, nn), "alloc factor");
+  CK(dev_alloc(ctx, &P.invd, nn), "alloc factor");
+  CK(dev_alloc(ctx, &P.invd32, nn), "alloc factor");
+  CK(dev_alloc(ctx, &P.xh, nn), "alloc vectors");
+  CK(dev_alloc(ctx, &P.r, nn), "alloc vectors");
+  CK(dev_alloc(ctx, &P.q, nn), "alloc vectors");
+  CK(dev_alloc(ctx, &P.p0, nn), "alloc vectors");
+  CK(dev_alloc(ctx, &P.p1, nn), "alloc vectors");
+  CK(dev_alloc(ctx, &P.bh, nn), "alloc vectors");
+  double *y, *z;
+  CK(dev_alloc(ctx, &y, nn), "alloc vectors");
+  CK(dev_alloc(ctx, &z, nn), "alloc vectors");
+  P.y = y; P.z = z;
+  CK(dev_alloc(ctx, &ctx->bin, nn), "alloc vectors");
+  CK(dev_alloc(ctx, &ctx->xin, nn), "alloc vectors");
+  CK(dev_alloc(ctx, &ctx->xout, nn), "alloc vectors");
+  P.bin = ctx->bin; P.xin = ctx->xin; P.xout = ctx->xout;
+  // reduction slots: one per CTA of the widest launch, doubled so the solve
+  // start can keep <b,b> and <r0,r0> partials side by side; kept even for
+  // 16-byte loads
+  P.npart = gbig;
+  P.ngroup = (gbig + kGroup - 1) / kGroup;
+  P.nbb = L.grid_v;
+  CK(dev_alloc(ctx, &P.part0, size_t(P.npart)), "alloc reductions");
+  CK(dev_alloc(ctx, &P.part1, size_t(P.npart)), "alloc reductions");
+  CK(dev_alloc(ctx, &P.acc_rr, size_t(P.ngroup)), "alloc reductions");
+  CK(dev_alloc(ctx, &P.acc_rz, size_t(P.ngroup)), "alloc reductions");
+  CK(dev_alloc(ctx, &P.gpq, size_t(P.ngroup)), "alloc reductions");
+  CK(dev_alloc(ctx, &P.init_bb, size_t(P.nbb)), "alloc reductions");
+  CK(dev_alloc(ctx, &P.gticket, size_t(P.ngroup)), "alloc reductions");
+  CK(dev_alloc(ctx, &P.sc, 1), "alloc scalars");
+  CK(dev_alloc(ctx, &P.err_row, 1), "alloc scalars");
+  CK(cudaMallocHost(&ctx->sc_host, sizeof(Scalars)), "pinned");
+  std::memset(ctx->sc_host, 0, sizeof(Scalars));
+  CK(cudaStreamSynchronize(ctx->stream), "setup sync");
+  return ICCG_OK;
+}
+
+iccg_status iccg_factor(iccg_ctx *ctx) {
+  if (!ctx) return ICCG_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  ctx->factored = false;
+  if (ctx->H.n == 0) { ctx->factored = true; return ICCG_OK; }
+  CK(cudaMemsetAsync(ctx->P.err_row, 0xff, sizeof(unsigned long long), ctx->stream), "factor");
+  CK(launch_factor(ctx->P, ctx->plan, int(ctx->H.nL)), "factor launch");
+  unsigned long long row = 0;
+  CK(cudaMemcpyAsync(&row, ctx->P.err_row, sizeof(row), cudaMemcpyDeviceToHost, ctx->stream), "factor");
+  CK(cudaStreamSynchronize(ctx->stream), "factor sync");
+  if (row != ~0ULL) {
+    ctx->err_index = ctx->H.perm[size_t(row)];
+    ctx->err_msg = "IC(0) pivot not positive";
+    return ICCG_ERR_BREAKDOWN;
+  }
+  ctx->factored = true;
+  return ICCG_OK;
+}
+
+static iccg_status ensure_hist(iccg_ctx *ctx, int32_t maxit) {
+  if (maxit + 1 > ctx->hist_cap) {
+    int32_t cap = std::max(maxit + 1, 1024);
+    double *h = nullptr;
+    CK(dev_alloc(ctx, &h, size_t(cap)), "alloc history");
+    ctx->hist = h;
+    ctx->hist_cap = cap;
+    ctx->P.hist = h;
+    destroy_graph(ctx);   // the graph captured the old pointer
+  }
+  if (maxit + 1 > ctx->hist_host_cap) {
+    if (ctx->hist_host) cudaFreeHost(ctx->hist_host);
+    ctx->hist_host = nullptr;
+    int32_t cap = std::max(maxit + 1, 1024);
+    CK(cudaMallocHost(&ctx->hist_host, sizeof(double) * size_t(cap)), "pinned history");
+    ctx->hist_host_cap = cap;
+  }
+  return ICCG_OK;
+}
+
+static iccg_status build_graph(iccg_ctx *ctx) {
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0), "graph");
+  ctx->graph = g;
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault), "graph cond");
+  ctx->cond_handle = (unsigned long long)h;
+  // capture on a private stream (the legacy default stream cannot capture);
+  // the instantiated graph is launched on the context's stream
+  cudaStream_t s = nullptr;
+  CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "capture stream");
+  struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } sg{s};
+  Plan Lc = ctx->plan;
+  Lc.stream = s;
+  CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal), "capture");
+  cudaError_t e = launch_solve_init(ctx->P, Lc, ctx->fp32, nullptr, nullptr);
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t cnode = nullptr;
+  if (e == cudaSuccess) {
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    e = cudaStreamGetCaptureInfo(s, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+    if (e == cudaSuccess) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp);
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) e = launch_solve_final(ctx->P, Lc);
+  }
+  cudaGraph_t g2 = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s, &g2);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "capture init");
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "end capture");
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal), "capture body");
+  e = launch_solve_body(ctx->P, Lc, ctx->fp32, nullptr, nullptr);
+  e2 = cudaStreamEndCapture(s, &body);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "capture body");
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "end capture body");
+  CK(cudaGraphInstantiate(&ctx->gexec, g, 0), "instantiate");
+  return ICCG_OK;
+}
+
+struct ProfileState {
+  cudaStream_t s;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> phase;
+  size_t used = 0;
+  double ms[PH_COUNT] = {0};
+  int64_t launches[PH_COUNT] = {0};
+  void flush() {
+    cudaStreamSynchronize(s);
+    for (size_t k = 0; k + 1 < used; k += 2) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      ms[phase[k]] += t;
+      launches[phase[k]] += 1;
+    }
+    used = 0;
+  }
+  static void hook(void *u, int ph, int begin) {
+    ProfileState *p = static_cast<ProfileState *>(u);
+    if (begin && p->used + 2 > p->ev.size()) p->flush();
+    if (p->used >= p->ev.size()) return;
+    p->phase[p->used] = ph;
+    cudaEventRecord(p->ev[p->used], p->s);
+    p->used++;
+    (void)begin;
+  }
+};
+
+static iccg_status solve_impl(iccg_ctx *ctx, const double *b, double *x, double tol, int32_t maxit,
+                              int32_t *iters, double *res_hist, ProfileState *prof) {
+  if (!ctx || tol < 0 || !(tol == tol) || maxit < 0) return ICCG_ERR_ARG;
+  DeviceGuard guard(ctx->device);
+  const int32_t n = ctx->H.n;
+  if (n > 0 && (!b || !x)) return ICCG_ERR_ARG;
+  if (!ctx->factored) { ctx->err_msg = "iccg_solve before a successful iccg_factor"; return ICCG_ERR_STATE; }
+  if (n == 0) {
+    if (iters) *iters = 0;
+    if (res_hist) res_hist[0] = 0.0;
+    return ICCG_OK;
+  }
+  iccg_status st = ensure_hist(ctx, maxit);
+  if (st != ICCG_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const bool use_graph = ctx->opts.no_graph == 0 && prof == nullptr;
+  if (use_graph && !ctx->gexec) {
+    st = build_graph(ctx);
+    if (st != ICCG_OK) { destroy_graph(ctx); return st; }
+  }
+  CK(copy_in(ctx, ctx->bin, b, size_t(n)), "copy b");
+  CK(copy_in(ctx, ctx->xin, x, size_t(n)), "copy x0");
+  Scalars *sh = ctx->sc_host;
+  std::memset(sh, 0, sizeof(Scalars));
+  sh->tol = tol;
+  sh->maxit = maxit;
+  sh->use_cond = use_graph ? 1 : 0;
+  sh->cond_handle = ctx->cond_handle;
+  sh->status = ICCG_NOT_CONVERGED;
+  CK(cudaMemcpyAsync(ctx->P.sc, sh, sizeof(Scalars), cudaMemcpyHostToDevice, s), "scalars");
+  if (use_graph) {
+    CK(cudaGraphLaunch(ctx->gexec, s), "graph launch");
+  } else {
+    CK(launch_solve_init(ctx->P, ctx->plan, ctx->fp32, prof ? ProfileState::hook : nullptr, prof), "init");
+    for (;;) {
+      CK(cudaMemcpyAsync(sh, ctx->P.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s), "scalars");
+      CK(cudaStreamSynchronize(s), "sync");
+      if (sh->done) break;
+      CK(launch_solve_body(ctx->P, ctx->plan, ctx->fp32, prof ? ProfileState::hook : nullptr, prof), "body");
+    }
+    CK(launch_solve_final(ctx->P, ctx->plan), "final");
+  }
+  CK(copy_out(ctx, x, ctx->xout, size_t(n)), "copy x");
+  CK(cudaMemcpyAsync(sh, ctx->P.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s), "scalars");
+  CK(cudaStreamSynchronize(s), "solve sync");
+  const int32_t it = sh->iter;
+  if (iters) *iters = it;
+  if (res_hist) {
+    CK(cudaMemcpyAsync(ctx->hist_host, ctx->hist, sizeof(double) * size_t(it + 1), cudaMemcpyDeviceToHost, s), "history");
+    CK(cudaStreamSynchronize(s), "history sync");
+    std::memcpy(res_hist, ctx->hist_host, sizeof(double) * size_t(it + 1));
+  }
+  return static_cast<iccg_status>(sh->status);
+}
+
+iccg_status iccg_solve(iccg_ctx *ctx, const double *b, double *x, double tol, int32_t maxit, int32_t *iters,
+                       double *res_hist) {
+  return solve_impl(ctx, b, x, tol, maxit, iters, res_hist, nullptr);
+}
+
+iccg_status iccg_profile_solve(iccg_ctx *ctx, const double *b, double *x, double tol, int32_t maxit,
+                               int32_t *iters, double *ms, int64_t *launches) {
+  if (!ctx) return ICCG_ERR_ARG;
+  DeviceGuard guard(ctx->device);
+  ProfileState ps;
+  ps.s = ctx->stream;
+  ps.ev.resize(4096);
+  ps.phase.resize(4096);
+  for (auto &e : ps.ev) CK(cudaEventCreate(&e), "event");
+  // the ALL phase is bracketed by its own pair of events
+  cudaEvent_t a0, a1;
+  CK(cudaEventCreate(&a0), "event");
+  CK(cudaEventCreate(&a1), "event");
+  CK(cudaEventRecord(a0, ctx->stream), "event");
+  iccg_status st = solve_impl(ctx, b, x, tol, maxit, iters, nullptr, &ps);
+  cudaEventRecord(a1, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  ps.flush();
+  float tall = 0.f;
+  cudaEventElapsedTime(&tall, a0, a1);
+  ps.ms[PH_ALL] = tall;
+  ps.launches[PH_ALL] = 0;
+  for (int k = 0; k < PH_ALL; ++k) ps.launches[PH_ALL] += ps.launches[k];
+  for (auto &e : ps.ev) cudaEventDestroy(e);
+  cudaEventDestroy(a0);
+  cudaEventDestroy(a1);
+  for (int k = 0; k < PH_COUNT; ++k) {
+    if (ms) ms[k] = ps.ms[k];
+    if (launches) launches[k] = ps.launches[k];
+  }
+  return st;
+}
+
+iccg_status iccg_precond(iccg_ctx *ctx, const double *r, double *z) {
+  if (!ctx) return ICCG_ERR_ARG;
+  DeviceGuard guard(ctx->device);
+  const int32_t n = ctx->H.n;
+  if (n == 0) return ICCG_OK;
+  if (!r || !z) return ICCG_ERR_ARG;
+  if (!ctx->factored) return ICCG_ERR_STATE;
+  cudaStream_t s = ctx->stream;
+  const Plan &L = ctx->plan;
+  CK(copy_in(ctx, ctx->bin, r, size_t(n)), "copy r");
+  CK(launch_permute(ctx->bin, ctx->P.r, ctx->P.perm, n, true, L.grid_v, s), "permute");
+  CK(launch_precond(ctx->P, L, ctx->fp32), "precond");
+  const double *zsrc = static_cast<const double *>(ctx->P.z);
+  if (ctx->fp32) {
+    CK(launch_widen(static_cast<const float *>(ctx->P.z), ctx->P.q, n, L.grid_v, s), "widen");
+    zsrc = ctx->P.q;
+  }
+  CK(launch_permute(zsrc, ctx->xout, ctx->P.perm, n, false, L.grid_v, s), "permute");
+  CK(copy_out(ctx, z, ctx->xout, size_t(n)), "copy z");
+  CK(cudaStreamSynchronize(s), "sync");
+  return ICCG_OK;
+}
+
+iccg_status iccg_spmv(iccg_ctx *ctx, const double *p, double *q) {
+  if (!ctx) return ICCG_ERR_ARG;
+  DeviceGuard guard(ctx->device);
+  const int32_t n = ctx->H.n;
+  if (n == 0) return ICCG_OK;
+  if (!p || !q) return ICCG_ERR_ARG;
+  cudaStream_t s = ctx->stream;
+  const Plan &L = ctx->plan;
+  CK(copy_in(ctx, ctx->bin, p, size_t(n)), "copy p");
+  CK(launch_permute(ctx->bin, ctx->P.xh, ctx->P.perm, n, true, L.grid_v, s), "permute");
+  CK(launch_spmv_plain(ctx->P, L), "spmv");
+  CK(launch_permute(ctx->P.q, ctx->xout, ctx->P.perm, n, false, L.grid_v, s), "permute");
+  CK(copy_out(ctx, q, ctx->xout, size_t(n)), "copy q");
+  CK(cudaStreamSynchronize(s), "sync");
+  return ICCG_OK;
+}
+
+iccg_status iccg_get_factor(iccg_ctx *ctx, double *lval, int64_t *nnz_lower) {
+  if (!ctx || !nnz_lower) return ICCG_ERR_ARG;
+  DeviceGuard guard(ctx->device);
+  const HostLayout &H = ctx->H;
+  *nnz_lower = H.nL + H.n;
+  if (!lval) return ICCG_OK;
+  if (!ctx->factored) return ICCG_ERR_STATE;
+  std::vector<double> lv(size_t(H.nL)), dg(size_t(H.n));
+  if (H.nL) CK(cudaMemcpyAsync(lv.data(), ctx->P.lval, sizeof(double) * lv.size(), cudaMemcpyDeviceToHost, ctx->stream), "copy L");
+  if (H.n) CK(cudaMemcpyAsync(dg.data(), ctx->P.ldiag, sizeof(double) * dg.size(), cudaMemcpyDeviceToHost, ctx->stream), "copy D");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  int64_t k = 0;
+  for (int32_t i = 0; i < H.n; ++i) {
+    for (int32_t p = H.lrp[i]; p < H.lrp[i + 1]; ++p) lval[k++] = lv[p];
+    lval[k++] = dg[i];
+  }
+  return ICCG_OK;
+}
+
+iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[9]) {
+  if (!ctx || !out) return ICCG_ERR_ARG;
+  const HostLayout &H = ctx->H;
+  out[0] = H.n;
+  out[1] = H.nnz;
+  out[2] = H.n_b;
+  out[3] = H.n_c;
+  out[4] = int64_t(H.tiles.size());
+  out[5] = int64_t(H.tasks.size() / 2);
+  out[6] = H.nL;
+  out[7] = H.max_rounds;
+  out[8] = H.max_task_rows;
+  return ICCG_OK;
+}
+
+iccg_status iccg_last_error(const iccg_ctx *ctx, int64_t *row_or_block, const char **msg) {
+  if (!ctx) return ICCG_ERR_ARG;
+  if (row_or_block) *row_or_block = ctx->err_index;
+  if (msg) *msg = ctx->err_msg.c_str();
+  return ICCG_OK;
+}
+
+void iccg_destroy(iccg_ctx *ctx) {
+  if (!ctx) return;
+  {
+    DeviceGuard guard(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    destroy_graph(ctx);
+    for (void *p : ctx->allocs) cudaFree(p);
+    if (ctx->sc_host) cudaFreeHost(ctx->sc_host);
+    if (ctx->hist_host) cudaFreeHost(ctx->hist_host);
+  }
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// Internal declarations of libiccg (not part of the C ABI).
+//
+// Device data layout (all in the block-multicolor numbering, Sec. 3):
+//   A_hat   CSR (arp/acol/aval) for the SpMV of Table 8's "SpMV" phase.
+//   L       strictly lower part of the IC(0) factor in CSR (lrp/lcol/lval),
+//           diagonal separately (ldiag, invd = 1/L_ii).
+//   U = L^T strictly upper part in CSR (urp/ucol/uval); umap[k] is the L
+//           entry that U entry k mirrors.
+//   Tiles   a tile is <= 32*R consecutive rows that one warp owns (lane l
+//           holds rows r0 + l + 32k).  A tile holds whole blocks of one color
+//           (several small blocks may share a tile), or one 32*R-row slice of
+//           a larger block.  A task is the tile sequence one warp walks in
+//           order (a large block = one task of several tiles); tasks of one
+//           color are contiguous.
+//   Within a tile the in-tile dependencies form a DAG; the substitution
+//   resolves it with `rounds` sweeps over the tile (after sweep k every row of
+//   level <= k is final), so a tile needs (depth + 1) sweeps.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/iccg.h"
+
+namespace iccg {
+
+constexpr int kWarp = 32;
+constexpr int kMaxWarpsPerCta = 16;
+
+// Everything one warp needs to start a tile: rows, forward/backward sweep
+// counts and the L / U entry ranges (one 32-byte load).
+struct __align__(16) TileDesc {
+  int32_t r0, r1;       // rows [r0, r1)
+  int32_t rounds;       // forward sweeps | backward sweeps << 16
+  int32_t pad;
+  int32_t l0, l1;       // L entries [l0, l1)
+  int32_t u0, u1;       // U entries [u0, u1)
+};
+
+// A task (the work of one warp): its first tile inline, so a warp starts
+// with a single 48-byte load, plus its tile range.
+struct __align__(16) TaskDesc {
+  TileDesc first;
+  int32_t tile0, ntiles, pad0, pad1;
+};
+
+constexpr int kGroup = 32;   // CTAs per first-level reduction group
+
+// Device-resident scalars of one solve.
+struct Scalars {
+  double bb, bnorm, rr, rz, pq, alpha, beta, tol;
+  int32_t iter, maxit, done, status;
+  uint32_t ticket;       // arrival counter for "last CTA reduces" epilogues
+  int32_t use_cond;      // 1 when a graph conditional handle is live
+  unsigned long long cond_handle;
+};
+
+// Everything a kernel needs; passed by value.
+struct Params {
+  int32_t n, R, W, n_c;
+  // A_hat
+  const int32_t *arp, *acol;
+  const double *aval;
+  // L / U
+  const int32_t *lrp, *lcol, *urp, *ucol, *umap;
+  double *lval, *uval, *ldiag, *invd;
+  float *lval32, *uval32, *invd32;
+  const double *ainit, *adiag;
+  // tiles and tasks (task k covers tiles [tile0, tile0 + ntiles))
+  const TileDesc *tdesc;
+  const TaskDesc *tasks;
+  const uint8_t *lev;
+  // staging capacities (entries) per warp
+  int32_t cap_l, cap_u, cap_a;
+  // vectors (permuted numbering)
+  double *xh, *r, *q, *p0, *p1, *bh;
+  void *y, *z;                  // double or float, by precision
+  const double *bin, *xin;      // original-order inputs
+  double *xout;                 // original-order output
+  const int32_t *perm;
+  // reductions, two levels: every CTA writes its partials to part0 / part1;
+  // the last CTA of each group of kGroup CTAs sums the group's partials in
+  // index order and adds them to the group's slot of acc_rr / acc_rz (carried
+  // across the launches of one iteration) or writes gpq; the last group of the
+  // launch runs the epilogue.  init_bb holds <b,b> partials of the solve start.
+  double *part0, *part1;        // [npart]
+  double *acc_rr, *acc_rz, *gpq;// [ngroup]
+  double *init_bb;              // [nbb]
+  uint32_t *gticket;            // [ngroup] group arrival counters
+  int32_t npart, ngroup, nbb;
+  Scalars *sc;
+  double *hist;
+  unsigned long long *err_row;  // IC(0) breakdown row (new numbering), ~0 = none
+};
+
+// ---- host-side layout built by iccg_setup --------------------------------
+struct HostLayout {
+  int32_t n = 0, n_b = 0, n_c = 0;
+  int64_t nnz = 0, nL = 0;
+  std::vector<int32_t> perm, iperm;
+  std::vector<int32_t> arp, acol;
+  std::vector<double> aval;
+  std::vector<int32_t> lrp, lcol, urp, ucol, umap;
+  std::vector<double> ainit, adiag;
+  std::vector<TileDesc> tiles;
+  std::vector<TaskDesc> tasks;
+  std::vector<int32_t> color_task;    // n_c + 1
+  std::vector<uint8_t> lev;
+  std::vector<int32_t> block_ptr, color_ptr;
+  int32_t max_rounds = 0, max_task_rows = 0;
+  int32_t seg_l = 0, seg_u = 0, seg_a = 0;   // largest tile segments (entries)
+};
+
+// Validates inputs and builds the layout; returns ICCG_OK or an error with
+// (bad_index, message) filled in.
+iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
+                         const double *val, const int32_t *perm, const int32_t *block_ptr,
+                         const int32_t *color_ptr, int32_t n_b, int32_t n_c, int32_t R,
+                         HostLayout &out, int64_t &bad_index, std::string &msg);
+
+// ---- launch plan (host side) ---------------------------------------------
+struct Plan {
+  cudaStream_t stream = nullptr;
+  bool pdl = true;                      // programmatic dependent launch
+  int32_t W = 4, R = 1, n_c = 0, n = 0;
+  std::vector<int32_t> task0, task1;    // task range of each color
+  std::vector<int32_t> grid_c;          // CTAs of the color-c kernels
+  int32_t grid_a = 0;                   // CTAs of the SpMV-shaped kernels
+  int32_t grid_v = 0;                   // CTAs of the vector kernels
+  int32_t smem_fwd = 0, smem_bwd = 0, smem_fused = 0, smem_a = 0;  // bytes per CTA
+};
+
+// phase ids for the profiling hook
+enum Phase { PH_INIT = 0, PH_SPMV = 1, PH_FWD = 2, PH_FUSED = 3, PH_BWD = 4, PH_ALL = 5, PH_COUNT = 6 };
+typedef void (*PhaseHook)(void *user, int phase, int begin);
+
+// ---- kernel launchers (kernels.cu) ----------------------------------------
+cudaError_t configure_kernels();
+int warp_smem_bytes(int cap, int R, int elem);          // dynamic smem per warp
+cudaError_t launch_factor(const Params &P, const Plan &L, int nL);
+cudaError_t launch_solve_init(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);
+cudaError_t launch_solve_body(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);
+cudaError_t launch_solve_final(const Params &P, const Plan &L);
+cudaError_t launch_precond(const Params &P, const Plan &L, bool fp32);  // z(perm) from r(perm)
+cudaError_t launch_spmv_plain(const Params &P, const Plan &L);          // q = A_hat xh
+cudaError_t launch_permute(const double *src, double *dst, const int32_t *perm, int32_t n,
+                           bool gather, int32_t grid, cudaStream_t s);
+cudaError_t launch_widen(const float *src, double *dst, int32_t n, int32_t grid, cudaStream_t s);
+
+}  // namespace iccg

@@ -1,0 +1,305 @@
+"""ctypes binding of libiccg (include/iccg.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Arrays may be
+numpy arrays (host) or torch tensors (host or CUDA); their data pointers are
+passed straight through, so all compute runs in the library's CUDA kernels.
+The library is loaded from this package directory; if it is missing the
+import of any function raises (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libiccg.so")
+
+STATUS = {0: "ICCG_OK", 1: "ICCG_ERR_ARG", 2: "ICCG_ERR_COLORING", 3: "ICCG_ERR_BREAKDOWN",
+          4: "ICCG_NOT_CONVERGED", 5: "ICCG_ERR_CUDA", 6: "ICCG_ERR_TIMEOUT", 7: "ICCG_ERR_NONFINITE",
+          8: "ICCG_ERR_UNIMPLEMENTED", 9: "ICCG_ERR_STATE"}
+ICCG_OK, ICCG_NOT_CONVERGED = 0, 4
+
+
+class IccgError(RuntimeError):
+    def __init__(self, status, where, index=-1, msg=""):
+        self.status = status
+        self.index = index
+        super().__init__(f"{where}: {STATUS.get(status, status)} (index {index}) {msg}".strip())
+
+
+class iccg_opts(ctypes.Structure):
+    _fields_ = [("precond_fp32", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("rows_per_thread", ctypes.c_int32), ("no_graph", ctypes.c_int32),
+                ("no_pdl", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+_lib = None
+
+
+def load():
+    """Load libiccg.so (raises when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} not built; run paper_2609_00561_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, d, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
+    P = ctypes.POINTER
+    sig = {
+        "iccg_setup": [P(vp), i32, i64, vp, vp, vp, vp, vp, vp, i32, i32, P(iccg_opts), vp],
+        "iccg_factor": [vp],
+        "iccg_solve": [vp, vp, vp, d, i32, P(i32), vp],
+        "iccg_precond": [vp, vp, vp],
+        "iccg_spmv": [vp, vp, vp],
+        "iccg_get_factor": [vp, vp, P(i64)],
+        "iccg_profile_solve": [vp, vp, vp, d, i32, P(i32), vp, vp],
+        "iccg_info": [vp, vp],
+        "iccg_last_error": [vp, P(i64), P(ctypes.c_char_p)],
+        "iccg_graph": [i32, vp, vp, vp, vp, P(i64)],
+        "iccg_block_abmc": [i32, vp, vp, i32, vp, P(i32)],
+        "iccg_block_leiden": [i32, vp, vp, i32, d, i32, d, u64, vp, P(i32)],
+        "iccg_sort_blocks_desc": [i32, i32, vp],
+        "iccg_color_order": [i32, vp, vp, i32, vp, vp, P(i32), vp, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.iccg_destroy.argtypes = [vp]
+    L.iccg_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(st, where, ctx=None):
+    if st in (ICCG_OK, ICCG_NOT_CONVERGED):
+        return st
+    idx, msg = -1, ""
+    if ctx is not None:
+        i = ctypes.c_int64(-1)
+        m = ctypes.c_char_p()
+        load().iccg_last_error(ctx, ctypes.byref(i), ctypes.byref(m))
+        idx, msg = i.value, (m.value or b"").decode()
+    raise IccgError(st, where, idx, msg)
+
+
+def _as(a, dt):
+    if hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def make_opts(precond_fp32=0, warps_per_cta=0, rows_per_thread=0, no_graph=0, no_pdl=0):
+    o = iccg_opts()
+    o.precond_fp32, o.warps_per_cta, o.rows_per_thread, o.no_graph, o.no_pdl = (
+        int(precond_fp32), int(warps_per_cta), int(rows_per_thread), int(no_graph), int(no_pdl))
+    return o
+
+
+# ---------------------------------------------------------------------------
+# C entry points
+# ---------------------------------------------------------------------------
+def iccg_setup(n, nnz, rowptr, colind, val, perm, block_ptr, color_ptr, n_b, n_c, opts=None, stream=None):
+    """Returns a context handle (ctypes.c_void_p)."""
+    L = load()
+    ctx = ctypes.c_void_p()
+    keep = [_as(rowptr, np.int64), _as(colind, np.int32), _as(val, np.float64), _as(perm, np.int32),
+            _as(block_ptr, np.int32), _as(color_ptr, np.int32)]
+    o = opts if opts is not None else make_opts()
+    st = L.iccg_setup(ctypes.byref(ctx), int(n), int(nnz), *[_ptr(k) for k in keep], int(n_b), int(n_c),
+                      ctypes.byref(o), ctypes.c_void_p(stream or 0))
+    if st != ICCG_OK:
+        err = IccgError(st, "iccg_setup")
+        if ctx.value:
+            i = ctypes.c_int64(-1)
+            m = ctypes.c_char_p()
+            L.iccg_last_error(ctx, ctypes.byref(i), ctypes.byref(m))
+            err = IccgError(st, "iccg_setup", i.value, (m.value or b"").decode())
+            L.iccg_destroy(ctx)
+        raise err
+    return ctx
+
+
+def iccg_factor(ctx):
+    return _check(load().iccg_factor(ctx), "iccg_factor", ctx)
+
+
+def iccg_solve(ctx, b, x, tol=1e-8, maxit=10000, want_hist=True):
+    """x is updated in place (in: x0).  Returns (status, iterations, history)."""
+    it = ctypes.c_int32(0)
+    hist = np.zeros(maxit + 1) if want_hist else None
+    st = load().iccg_solve(ctx, _ptr(b), _ptr(x), float(tol), int(maxit), ctypes.byref(it), _ptr(hist))
+    _check(st, "iccg_solve", ctx)
+    return st, it.value, (hist[: it.value + 1].copy() if want_hist else None)
+
+
+def iccg_precond(ctx, r, z):
+    return _check(load().iccg_precond(ctx, _ptr(r), _ptr(z)), "iccg_precond", ctx)
+
+
+def iccg_spmv(ctx, p, q):
+    return _check(load().iccg_spmv(ctx, _ptr(p), _ptr(q)), "iccg_spmv", ctx)
+
+
+def iccg_get_factor(ctx):
+    """IC(0) factor as values on tril(A_hat) in CSR order (diagonal last)."""
+    cnt = ctypes.c_int64(0)
+    _check(load().iccg_get_factor(ctx, None, ctypes.byref(cnt)), "iccg_get_factor", ctx)
+    out = np.zeros(cnt.value)
+    _check(load().iccg_get_factor(ctx, _ptr(out), ctypes.byref(cnt)), "iccg_get_factor", ctx)
+    return out
+
+
+PHASES = ("init", "spmv", "fwd", "fused", "bwd", "all")
+
+
+def iccg_profile_solve(ctx, b, x, tol=1e-8, maxit=10000):
+    """Returns (status, iterations, {phase: ms}, {phase: launches})."""
+    it = ctypes.c_int32(0)
+    ms = np.zeros(6)
+    ln = np.zeros(6, dtype=np.int64)
+    st = load().iccg_profile_solve(ctx, _ptr(b), _ptr(x), float(tol), int(maxit), ctypes.byref(it),
+                                   _ptr(ms), _ptr(ln))
+    _check(st, "iccg_profile_solve", ctx)
+    return st, it.value, dict(zip(PHASES, ms.tolist())), dict(zip(PHASES, ln.tolist()))
+
+
+INFO_KEYS = ("n", "nnz", "n_b", "n_c", "tiles", "tasks", "nL", "max_rounds", "max_task_rows")
+
+
+def iccg_info(ctx):
+    out = np.zeros(9, dtype=np.int64)
+    _check(load().iccg_info(ctx, _ptr(out)), "iccg_info", ctx)
+    return dict(zip(INFO_KEYS, out.tolist()))
+
+
+def iccg_last_error(ctx):
+    i = ctypes.c_int64(-1)
+    m = ctypes.c_char_p()
+    load().iccg_last_error(ctx, ctypes.byref(i), ctypes.byref(m))
+    return i.value, (m.value or b"").decode()
+
+
+def iccg_destroy(ctx):
+    if ctx is not None and ctx.value:
+        load().iccg_destroy(ctx)
+
+
+def iccg_graph(n, rowptr, colind):
+    rowptr = _as(rowptr, np.int64)
+    colind = _as(colind, np.int32)
+    gptr = np.zeros(n + 1, dtype=np.int64)
+    m = ctypes.c_int64(0)
+    _check(load().iccg_graph(int(n), _ptr(rowptr), _ptr(colind), _ptr(gptr), None, ctypes.byref(m)), "iccg_graph")
+    gadj = np.zeros(max(m.value, 1), dtype=np.int32)
+    _check(load().iccg_graph(int(n), _ptr(rowptr), _ptr(colind), _ptr(gptr), _ptr(gadj), ctypes.byref(m)), "iccg_graph")
+    return gptr, gadj[: m.value]
+
+
+def iccg_block_abmc(n, gptr, gadj, s):
+    gptr, gadj = _as(gptr, np.int64), _as(gadj, np.int32)
+    block_of = np.zeros(max(n, 1), dtype=np.int32)
+    nb = ctypes.c_int32(0)
+    _check(load().iccg_block_abmc(int(n), _ptr(gptr), _ptr(gadj), int(s), _ptr(block_of), ctypes.byref(nb)),
+           "iccg_block_abmc")
+    return block_of[:n], nb.value
+
+
+def iccg_block_leiden(n, gptr, gadj, quality, gamma, n_iter=2, beta=0.01, seed=42):
+    q = {"modularity": 0, "md": 0, "cpm": 1, "cp": 1}[quality] if isinstance(quality, str) else int(quality)
+    gptr, gadj = _as(gptr, np.int64), _as(gadj, np.int32)
+    block_of = np.zeros(max(n, 1), dtype=np.int32)
+    nb = ctypes.c_int32(0)
+    _check(load().iccg_block_leiden(int(n), _ptr(gptr), _ptr(gadj), q, float(gamma), int(n_iter), float(beta),
+                                    int(seed), _ptr(block_of), ctypes.byref(nb)), "iccg_block_leiden")
+    return block_of[:n], nb.value
+
+
+def iccg_sort_blocks_desc(n, n_b, block_of):
+    b = np.array(block_of, dtype=np.int32, copy=True)
+    _check(load().iccg_sort_blocks_desc(int(n), int(n_b), _ptr(b)), "iccg_sort_blocks_desc")
+    return b
+
+
+def iccg_color_order(n, gptr, gadj, n_b, block_of):
+    """Returns (color_of, n_c, perm, block_ptr, color_ptr)."""
+    gptr, gadj, block_of = _as(gptr, np.int64), _as(gadj, np.int32), _as(block_of, np.int32)
+    color_of = np.zeros(max(n_b, 1), dtype=np.int32)
+    perm = np.zeros(max(n, 1), dtype=np.int32)
+    bptr = np.zeros(n_b + 1, dtype=np.int32)
+    cptr = np.zeros(n_b + 1, dtype=np.int32)
+    nc = ctypes.c_int32(0)
+    _check(load().iccg_color_order(int(n), _ptr(gptr), _ptr(gadj), int(n_b), _ptr(block_of), _ptr(color_of),
+                                   ctypes.byref(nc), _ptr(perm), _ptr(bptr), _ptr(cptr)), "iccg_color_order")
+    return color_of[:n_b], nc.value, perm[:n], bptr, cptr[: nc.value + 1]
+
+
+# ---------------------------------------------------------------------------
+# conveniences built only from the entry points above
+# ---------------------------------------------------------------------------
+def blocking(a, method="abmc", block_size=32, gamma=1.0, n_iter=2, beta=0.01, seed=42):
+    """graph -> ABMC or Leiden (+ size sort) -> greedy coloring -> ordering.
+    `a` has fields n, rowptr, colind.  Returns a dict like the oracle's."""
+    gptr, gadj = iccg_graph(a.n, a.rowptr, a.colind)
+    if method == "abmc":
+        block_of, nb = iccg_block_abmc(a.n, gptr, gadj, block_size)
+    elif method in ("leiden_md", "leiden_cpm"):
+        q = 0 if method == "leiden_md" else 1
+        block_of, nb = iccg_block_leiden(a.n, gptr, gadj, q, gamma, n_iter, beta, seed)
+        block_of = iccg_sort_blocks_desc(a.n, nb, block_of)
+    else:
+        raise ValueError(method)
+    color_of, nc, perm, bptr, cptr = iccg_color_order(a.n, gptr, gadj, nb, block_of)
+    return {"perm": perm, "block_ptr": bptr, "color_ptr": cptr, "n_b": nb, "n_c": nc,
+            "block_of": block_of, "color_of": color_of}
+
+
+class Solver:
+    """Owns one iccg context: setup + factor at construction."""
+
+    def __init__(self, a, bl, precond_fp32=False, warps_per_cta=0, rows_per_thread=0, no_graph=False,
+                 no_pdl=False, stream=None, factor=True):
+        self.n = a.n
+        self.ctx = iccg_setup(a.n, a.nnz, a.rowptr, a.colind, a.val, bl["perm"], bl["block_ptr"],
+                              bl["color_ptr"], bl["n_b"], bl["n_c"],
+                              make_opts(precond_fp32, warps_per_cta, rows_per_thread, no_graph, no_pdl), stream)
+        if factor:
+            iccg_factor(self.ctx)
+
+    def solve(self, b, x=None, tol=1e-8, maxit=10000):
+        if x is None:
+            x = np.zeros(self.n) if isinstance(b, np.ndarray) else b.new_zeros(b.shape)
+        st, it, hist = iccg_solve(self.ctx, b, x, tol, maxit)
+        return x, it, hist, st
+
+    def info(self):
+        return iccg_info(self.ctx)
+
+    def close(self):
+        iccg_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None) is not None:
+                self.close()
+        except Exception:
+            pass

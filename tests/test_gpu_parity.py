@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars (element by element on the same seeded inputs):
+  * IC(0) factor, SpMV, preconditioner apply: relative max difference
+    <= 1e-12 (FP64; only the summation order differs);
+  * FP64 ICCG solve: ||x_gpu - x_orc|| / ||x_orc|| <= 1e-10 and iteration
+    counts within +-1;
+  * blockings / permutations are inputs and bit-exact by construction.
+Cases span several tiles, ragged tails, multi-tile blocks (ABMC s > 32R,
+Leiden modularity blocks of hundreds of rows), one-color and one-row systems,
+and every launch shape (rows per thread, warps per CTA, graph or host loop,
+with or without programmatic dependent launch).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import gen
+import oracle
+from paper_2609_00561_gb300 import build as libbuild
+from paper_2609_00561_gb300 import iccg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    libbuild.build()
+
+
+def _tri(n):
+    return gen.from_scipy(sp.diags([-np.ones(n - 1), 2.5 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]))
+
+
+CASES = {
+    "c1_abmc16": (lambda: gen.config1(), "abmc", {"block_size": 16}),
+    "grid3d_abmc8": (lambda: (gen.poisson3d_7pt(20), gen.rhs_uniform(8000, 3), None), "abmc", {"block_size": 8}),
+    "grid3d_abmc32": (lambda: (gen.poisson3d_7pt(20), gen.rhs_uniform(8000, 3), None), "abmc", {"block_size": 32}),
+    "grid3d_abmc100": (lambda: (gen.poisson3d_7pt(20), gen.rhs_uniform(8000, 3), None), "abmc", {"block_size": 100}),
+    "grid2d_leiden_md": (lambda: (gen.poisson2d_5pt(45), gen.rhs_uniform(2025, 4), None), "leiden_md", {"gamma": 1.0}),
+    "grid3d_leiden_cpm": (lambda: (gen.poisson3d_7pt(15), gen.rhs_uniform(3375, 5), None), "leiden_cpm", {"gamma": 0.1}),
+    "rspd_777": (lambda: (gen.random_spd_small(777, 0.01, 7), gen.rhs_uniform(777, 6), None), "abmc", {"block_size": 13}),
+    "aniso27": (lambda: (gen.stencil_aniso("27pt", 3375, 4.0), gen.rhs_uniform(3375, 8), None), "abmc", {"block_size": 32}),
+    "elast27": (lambda: (gen.elasticity_like(700, 27, 3.0), gen.rhs_uniform(2187, 9), None), "abmc", {"block_size": 24}),
+    "diff27": (lambda: (gen.diffusion3d_27pt(14, seed=2), gen.rhs_uniform(2744, 10), None), "abmc", {"block_size": 32}),
+}
+
+_cache = {}
+
+
+def _case(name):
+    if name not in _cache:
+        mk, method, kw = CASES[name]
+        a, b, _ = mk()
+        bl = oracle.blocking(a, method, **kw)
+        ref = oracle.iccg(a, b, bl["perm"], tol=1e-8, maxit=20000)
+        _cache[name] = (a, b, bl, ref)
+    return _cache[name]
+
+
+def _rel(x, y):
+    return float(np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300))
+
+
+SHAPES = [dict(), dict(rows_per_thread=2), dict(rows_per_thread=4, warps_per_cta=8),
+          dict(warps_per_cta=1), dict(warps_per_cta=16), dict(no_graph=1), dict(no_pdl=1)]
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_factor_spmv_precond_match_oracle(name):
+    a, b, bl, ref = _case(name)
+    S = iccg.Solver(a, bl)
+    ah = oracle.permute(a, bl["perm"])
+    lptr, lcol, aval = oracle.tril_csr(ah)
+    lref, brow = oracle.ic0(lptr, lcol, aval)
+    assert brow == -1
+    lgpu = iccg.iccg_get_factor(S.ctx)
+    assert np.max(np.abs(lgpu - lref)) <= 1e-12 * np.max(np.abs(lref))
+    rng = np.random.default_rng(11)
+    p = rng.uniform(-1, 1, a.n)
+    q = np.zeros(a.n)
+    iccg.iccg_spmv(S.ctx, p, q)
+    qref = a.to_scipy() @ p
+    assert np.max(np.abs(q - qref)) <= 1e-13 * np.max(np.abs(qref))
+    z = np.zeros(a.n)
+    iccg.iccg_precond(S.ctx, p, z)
+    perm = bl["perm"]
+    zref_h = oracle.backward(lptr, lcol, lref, oracle.forward(lptr, lcol, lref, p[perm]))
+    zref = np.zeros(a.n)
+    zref[perm] = zref_h
+    assert np.max(np.abs(z - zref)) <= 1e-12 * np.max(np.abs(zref))
+    S.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("shape", range(len(SHAPES)))
+def test_solve_fp64_matches_oracle(name, shape):
+    a, b, bl, ref = _case(name)
+    S = iccg.Solver(a, bl, **SHAPES[shape])
+    x = np.zeros(a.n)
+    st, it, hist = iccg.iccg_solve(S.ctx, b, x, 1e-8, 20000)
+    assert st == iccg.ICCG_OK
+    assert abs(it - ref["iterations"]) <= 1
+    assert _rel(x, ref["x"]) <= 1e-10
+    assert hist[-1] <= 1e-8
+    # the recursive residual history is a property check, not the parity bar:
+    # its late entries carry rounding-order differences amplified by the
+    # condition number (observed up to 6e-6 relative on the elasticity case)
+    k = min(len(hist), len(ref["hist"]))
+    assert np.allclose(hist[:k], ref["hist"][:k], rtol=1e-3, atol=0)
+    S.close()
+
+
+@pytest.mark.parametrize("name", ["c1_abmc16", "grid3d_abmc100", "grid2d_leiden_md", "diff27", "elast27"])
+def test_solve_fp32_preconditioner(name):
+    """Extension 1: FP32 factors/substitutions, FP64 CG; reaches the same
+    recursive residual; its error against the FP64 oracle is reported."""
+    a, b, bl, ref = _case(name)
+    S = iccg.Solver(a, bl, precond_fp32=True)
+    x = np.zeros(a.n)
+    st, it, hist = iccg.iccg_solve(S.ctx, b, x, 1e-8, 20000)
+    assert st == iccg.ICCG_OK and hist[-1] <= 1e-8
+    true_rel = np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)
+    assert true_rel <= 1e-7
+    err = _rel(x, ref["x"])
+    kappa_proxy = max(1.0, ref["iterations"] / 10.0)
+    assert err <= 1e-6 * kappa_proxy, err
+    # FP32 factors perturb the preconditioner; on the nearly singular
+    # elasticity case this costs a few iterations (61 -> 65 observed)
+    assert abs(it - ref["iterations"]) <= 3 + ref["iterations"] // 10
+    S.close()
+
+
+def test_device_and_host_pointers_agree_and_are_deterministic():
+    a, b, bl, ref = _case("grid3d_abmc32")
+    S = iccg.Solver(a, bl)
+    xh = np.zeros(a.n)
+    iccg.iccg_solve(S.ctx, b, xh)
+    bd = torch.tensor(b, device="cuda")
+    xd = torch.zeros_like(bd)
+    iccg.iccg_solve(S.ctx, bd, xd)
+    assert np.array_equal(xd.cpu().numpy(), xh)
+    xh2 = np.zeros(a.n)
+    iccg.iccg_solve(S.ctx, b, xh2)
+    assert np.array_equal(xh, xh2)
+    S.close()
+
+
+def test_edge_cases():
+    a, b, bl, ref = _case("c1_abmc16")
+    S = iccg.Solver(a, bl)
+    # b = 0 -> x = 0, 0 iterations
+    x = np.full(a.n, 3.0)
+    st, it, hist = iccg.iccg_solve(S.ctx, np.zeros(a.n), x)
+    assert st == iccg.ICCG_OK and it == 0 and np.all(x == 0)
+    # x0 = exact solution (to rounding) -> converged at k = 0
+    x = ref["x"].copy()
+    st, it, hist = iccg.iccg_solve(S.ctx, b, x, 1e-6)
+    assert st == iccg.ICCG_OK and it == 0
+    # maxit = 0 and maxit reached
+    x = np.zeros(a.n)
+    st, it, hist = iccg.iccg_solve(S.ctx, b, x, 1e-8, 0)
+    assert st == iccg.ICCG_NOT_CONVERGED and it == 0 and len(hist) == 1
+    x = np.zeros(a.n)
+    st, it, hist = iccg.iccg_solve(S.ctx, b, x, 1e-8, 5)
+    assert st == iccg.ICCG_NOT_CONVERGED and it == 5
+    xo, ito, _, sto = oracle.pcg(oracle.permute(a, bl["perm"]), *_factor_of(a, bl), b[bl["perm"]], tol=1e-8, maxit=5)
+    xr = np.zeros(a.n); xr[bl["perm"]] = xo
+    assert _rel(x, xr) <= 1e-12
+    # a non-zero x0
+    x0 = np.random.default_rng(1).uniform(-1, 1, a.n)
+    x = x0.copy()
+    st, it, hist = iccg.iccg_solve(S.ctx, b, x)
+    r2 = oracle.iccg(a, b, bl["perm"], x0=x0)
+    assert abs(it - r2["iterations"]) <= 1 and _rel(x, r2["x"]) <= 1e-10
+    S.close()
+
+
+def _factor_of(a, bl):
+    ah = oracle.permute(a, bl["perm"])
+    lptr, lcol, aval = oracle.tril_csr(ah)
+    lval, _ = oracle.ic0(lptr, lcol, aval)
+    return lptr, lcol, lval
+
+
+def test_single_block_tridiagonal_converges_in_one_iteration():
+    a = _tri(300)
+    bl = {"perm": np.arange(300, dtype=np.int32), "block_ptr": np.array([0, 300], dtype=np.int32),
+          "color_ptr": np.array([0, 1], dtype=np.int32), "n_b": 1, "n_c": 1}
+    S = iccg.Solver(a, bl)
+    b = gen.rhs_uniform(300, 2)
+    x = np.zeros(300)
+    st, it, hist = iccg.iccg_solve(S.ctx, b, x, 1e-12)
+    assert st == iccg.ICCG_OK and it == 1
+    assert np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b) < 1e-12
+    S.close()
+
+
+def test_one_row_system():
+    a = gen.from_scipy(sp.csr_matrix(np.array([[4.0]])))
+    bl = {"perm": np.array([0], dtype=np.int32), "block_ptr": np.array([0, 1], dtype=np.int32),
+          "color_ptr": np.array([0, 1], dtype=np.int32), "n_b": 1, "n_c": 1}
+    S = iccg.Solver(a, bl)
+    x = np.zeros(1)
+    st, it, hist = iccg.iccg_solve(S.ctx, np.array([2.0]), x)
+    assert st == iccg.ICCG_OK and it == 1 and abs(x[0] - 0.5) < 1e-15
+    S.close()
+
+
+def test_breakdown_reports_oracle_row():
+    m = sp.diags([np.full(39, 1.2), np.ones(40), np.full(39, 1.2)], [-1, 0, 1], format="csr")
+    a = gen.from_scipy(m)
+    bl = oracle.blocking(a, "abmc", 4)
+    r = oracle.iccg(a, np.ones(40), bl["perm"])
+    assert r["status"] == "breakdown"
+    S = iccg.Solver(a, bl, factor=False)
+    with pytest.raises(iccg.IccgError) as ei:
+        iccg.iccg_factor(S.ctx)
+    assert ei.value.status == 3 and ei.value.index == r["breakdown_row"]
+    # solving without a successful factor is a state error
+    with pytest.raises(iccg.IccgError) as ei2:
+        iccg.iccg_solve(S.ctx, np.ones(40), np.zeros(40))
+    assert ei2.value.status == 9
+    S.close()
+
+
+def test_production_blocking_drives_the_same_solve():
+    a, b, _ = gen.config1()
+    bp = iccg.blocking(a, "leiden_cpm", gamma=0.2)
+    bo = oracle.blocking(a, "leiden_cpm", gamma=0.2)
+    assert np.array_equal(bp["perm"], bo["perm"])
+    S = iccg.Solver(a, bp)
+    x = np.zeros(a.n)
+    st, it, hist = iccg.iccg_solve(S.ctx, b, x)
+    ref = oracle.iccg(a, b, bo["perm"])
+    assert abs(it - ref["iterations"]) <= 1 and _rel(x, ref["x"]) <= 1e-10
+    S.close()
