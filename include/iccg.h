@@ -150,6 +150,33 @@ iccg_status iccg_last_error(const iccg_ctx *ctx, int64_t *row_or_block, const ch
 void iccg_destroy(iccg_ctx *ctx);
 
 /* ------------------------------------------------------------------------
+ * iccg_spmv_dot_noalloc -- q = A p and *pq = <p, q> with no device
+ * allocation at all.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory where they need the
+ * product (code recorded inside a CUDA stream capture, latency-critical loops
+ * that must not meet the allocator's implicit synchronisation, host
+ * frameworks that own all device memory through their own pool).
+ *
+ *   n                       rows, 0 <= n <= ICCG_NOALLOC_MAX_ROWS (else ICCG_ERR_ARG)
+ *   rowptr, colind, val     CSR of A (int64 rowptr, int32 colind, FP64), DEVICE pointers
+ *   p                       double[n] device input;  q  double[n] device output
+ *   pq                      one double, device output
+ *   stream                  the CUDA stream to run on
+ *
+ * Scratch (one partial per CTA and the reduction's arrival counters, about
+ * 137 KB) is a fixed array in the library's device image, held by every GPU
+ * that loads the library until the process exits.  All calls share it: the
+ * counters are cleared at the start of every call, and two calls whose work
+ * overlaps on the GPU race and give wrong results.  The first call on each
+ * device looks up the array's address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  The sum is deterministic (fixed order).
+ * ------------------------------------------------------------------------ */
+#define ICCG_NOALLOC_MAX_ROWS 4194304
+iccg_status iccg_spmv_dot_noalloc(int32_t n, const int64_t *rowptr, const int32_t *colind,
+                                  const double *val, const double *p, double *q, double *pq,
+                                  iccg_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Host-side blocking helpers (production implementations; host pointers).
  * ------------------------------------------------------------------------ */
 

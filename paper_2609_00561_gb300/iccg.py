@@ -63,6 +63,7 @@ def load():
         "iccg_block_leiden": [i32, vp, vp, i32, d, i32, d, u64, vp, P(i32)],
         "iccg_sort_blocks_desc": [i32, i32, vp],
         "iccg_color_order": [i32, vp, vp, i32, vp, vp, P(i32), vp, vp, vp],
+        "iccg_spmv_dot_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -250,6 +251,17 @@ def iccg_color_order(n, gptr, gadj, n_b, block_of):
     _check(load().iccg_color_order(int(n), _ptr(gptr), _ptr(gadj), int(n_b), _ptr(block_of), _ptr(color_of),
                                    ctypes.byref(nc), _ptr(perm), _ptr(bptr), _ptr(cptr)), "iccg_color_order")
     return color_of[:n_b], nc.value, perm[:n], bptr, cptr[: nc.value + 1]
+
+
+NOALLOC_MAX_ROWS = 4194304
+
+
+def iccg_spmv_dot_noalloc(n, rowptr, colind, val, p, q, pq, stream=None):
+    """q = A p and pq[0] = <p, q> through the allocation-free entry point.
+    All arrays are device tensors owned by the caller (rowptr int64, colind
+    int32, val / p / q / pq float64); returns the status code."""
+    return load().iccg_spmv_dot_noalloc(int(n), _ptr(rowptr), _ptr(colind), _ptr(val), _ptr(p), _ptr(q),
+                                        _ptr(pq), ctypes.c_void_p(stream or 0))
 
 
 # ---------------------------------------------------------------------------
