@@ -53,7 +53,8 @@ typedef struct {
                                  with FP32 accumulation; IC(0) itself, the CG dots,
                                  alpha/beta and the x/r updates stay FP64 */
   int32_t warps_per_cta;      /* warps per CTA of the per-color kernels; 0 = 4 */
-  int32_t rows_per_thread;    /* tile = 32 * rows_per_thread rows; 1, 2 or 4; 0 = 1 */
+  int32_t rows_per_thread;    /* a warp's group holds up to 32 * rows_per_thread rows of
+                                 whole blocks; 1, 2, 4, 8, 16 or 32; 0 = 8 */
   int32_t no_graph;           /* 1: drive the PCG loop from the host instead of a
                                  CUDA graph with a device-side WHILE condition */
   int32_t no_pdl;             /* 1: launch kernels without programmatic dependent
@@ -141,9 +142,11 @@ iccg_status iccg_get_factor(iccg_ctx *ctx, double *lval, int64_t *nnz_lower);
 iccg_status iccg_profile_solve(iccg_ctx *ctx, const double *b, double *x, double tol,
                                int32_t maxit, int32_t *iters, double *ms, int64_t *launches);
 
-/* Layout facts of a context (host out-params, any may be NULL):
- * n, nnz, n_b, n_c, number of tiles, number of tasks (warp work items),
- * strictly-lower entries nL, max tile rounds (forward), max rows per task. */
+/* Layout facts of a context, out[9]: n, nnz, n_b, n_c, number of groups (a
+ * group = consecutive whole blocks of one color, at most 32 * rows_per_thread
+ * rows, or one larger block; one warp each), number of groups too large for
+ * the shared-memory plan, strictly-lower entries nL, deepest in-block level
+ * count, largest group (rows). */
 iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[9]);
 
 iccg_status iccg_last_error(const iccg_ctx *ctx, int64_t *row_or_block, const char **msg);

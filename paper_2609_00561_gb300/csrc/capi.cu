@@ -120,15 +120,12 @@ cudaError_t copy_out(iccg_ctx *c, double *dst, const double *src, size_t count) 
   return cudaMemcpyAsync(dst, src, count * sizeof(double), k, c->stream);
 }
 
-constexpr int kCapLimit = 1024;   // staged entries per warp (beyond: direct loads)
+constexpr int kCapLimit = 4096;          // staged entries per warp (beyond: global reads)
+constexpr int kCtaSmemBudget = 64 * 1024;    // per-CTA shared-memory plan, bytes
 
 int cap_of(int seg) {
-  int c = ((seg + 8) + 3) & ~3;
-  return std::min(c, kCapLimit);
-}
-
-[[maybe_unused]] int warp_bytes_unused(int cap, int R, int elem) {
-  return ((cap * elem + 15) & ~15) + ((cap * 4 + 15) & ~15) + ((32 * R * elem + 15) & ~15);
+  int c = (seg + 3) & ~3;
+  return std::min(std::max(c, 4), kCapLimit);
 }
 
 std::once_flag g_cfg_once[64];
@@ -157,10 +154,11 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   if (opts) o = *opts;
   for (int k = 0; k < 3; ++k)
     if (o.reserved[k] != 0) return ICCG_ERR_ARG;
-  if (o.warps_per_cta == 0) o.warps_per_cta = 4;
+  if (o.warps_per_cta == 0) o.warps_per_cta = 8;
   if (o.rows_per_thread == 0) o.rows_per_thread = 1;
   if (o.warps_per_cta < 1 || o.warps_per_cta > kMaxWarpsPerCta) return ICCG_ERR_ARG;
-  if (o.rows_per_thread != 1 && o.rows_per_thread != 2 && o.rows_per_thread != 4) return ICCG_ERR_ARG;
+  if (o.rows_per_thread < 1 || o.rows_per_thread > 32 || (o.rows_per_thread & (o.rows_per_thread - 1)))
+    return ICCG_ERR_ARG;
 
   iccg_ctx *ctx = new iccg_ctx();
   ctx->opts = o;
@@ -184,8 +182,9 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     return cuda_fail(ctx, cudaGetLastError(), "copy inputs");
   if (n == 0) { hbp.assign(1, 0); hcp.assign(1, 0); }
   const int R = o.rows_per_thread, W = o.warps_per_cta;
+  const int G = 32 * W * R;   // rows of a group (one CTA of W warps)
   iccg_status st = build_layout(n, nnz, hrp.data(), hci.data(), hval.data(), hperm.data(), hbp.data(),
-                                hcp.data(), n_b, n_c, R, ctx->H, ctx->err_index, ctx->err_msg);
+                                hcp.data(), n_b, n_c, G, ctx->H, ctx->err_index, ctx->err_msg);
   if (st != ICCG_OK) return st;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaGetDevice");
   {
@@ -208,38 +207,54 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   L.n = n;
   L.pdl = o.no_pdl == 0;
   const int elem = ctx->fp32 ? 4 : 8;
-  const int cap_l = cap_of(H.seg_l), cap_u = cap_of(H.seg_u), cap_a = cap_of(H.seg_a);
-  L.smem_fwd = W * warp_smem_bytes(cap_l, R, elem);
-  L.smem_bwd = W * warp_smem_bytes(cap_u, R, elem);
-  L.smem_fused = W * warp_smem_bytes(std::max(cap_l, cap_u), R, elem);
-  L.smem_a = W * warp_smem_bytes(cap_a, 0, 8);
-  // one warp per task (color kernels) or per 32R-row tile (SpMV)
+  // per-CTA shared-memory plan for groups of at most G rows; shrink the entry
+  // capacity until the plan fits the budget, then mark the groups that fit it
+  // (the others read their data from global memory)
+  int cap_l = cap_of(H.seg_l), cap_u = cap_of(H.seg_u);
+  const int cap_rows = std::max(H.fit_rows, 1), cap_lev = std::max(H.fit_levels, 1);
+  while (group_smem_bytes(std::max(cap_l, cap_u), cap_rows, cap_lev, elem) > kCtaSmemBudget &&
+         std::max(cap_l, cap_u) > 64) {
+    cap_l = std::min(cap_l, std::max(cap_l, cap_u) / 2);
+    cap_u = std::min(cap_u, std::max(cap_l, cap_u) / 2);
+  }
+  for (GroupDesc &d : H.groups) {
+    const int rows = d.r1 - d.r0;
+    d.fit = (rows <= std::min(cap_rows, G) && d.l1 - d.l0 <= cap_l && d.u1 - d.u0 <= cap_u &&
+             std::max(d.nlf, d.nlb) <= cap_lev) ? 1 : 0;
+  }
+  const int cap_a = cap_of(H.seg_a);
+  const int Wc = W;   // warps per CTA of the color kernels (one CTA per group)
+  const int Wa = 4;   // warps per CTA of the SpMV (one warp per 32 rows)
+  L.W = Wc;
+  L.Wa = Wa;
+  L.smem_fwd = group_smem_bytes(cap_l, cap_rows, cap_lev, elem);
+  L.smem_bwd = group_smem_bytes(cap_u, cap_rows, cap_lev, elem);
+  L.smem_fused = group_smem_bytes(std::max(cap_l, cap_u), cap_rows, cap_lev, elem);
+  L.smem_a = Wa * spmv_smem_bytes(cap_a);
+  // one CTA per group (color kernels), one warp per 32-row tile (SpMV)
   L.grid_c.assign(n_c, 0);
   L.task0.assign(n_c, 0);
   L.task1.assign(n_c, 0);
   int32_t gbig = 1;
   for (int c = 0; c < n_c; ++c) {
-    L.task0[c] = H.color_task[c];
-    L.task1[c] = H.color_task[c + 1];
-    const int ntask = L.task1[c] - L.task0[c];
-    L.grid_c[c] = std::max(1, (ntask + W - 1) / W);
+    L.task0[c] = H.color_group[c];
+    L.task1[c] = H.color_group[c + 1];
+    L.grid_c[c] = std::max(1, L.task1[c] - L.task0[c]);
     gbig = std::max(gbig, L.grid_c[c]);
   }
-  const int T = 32 * R;
-  const int ntile_a = (n + T - 1) / T;
-  L.grid_a = std::max(1, (ntile_a + W - 1) / W);
+  const int ntile_a = (n + 31) / 32;
+  L.grid_a = std::max(1, (ntile_a + Wa - 1) / Wa);
   L.grid_v = std::max(1, std::min((n + 255) / 256, sms * 8));
   gbig = std::max(gbig, L.grid_a);
 
   // device arrays
   Params &P = ctx->P;
-  P.n = n; P.R = R; P.W = W; P.n_c = n_c;
+  P.n = n; P.R = R; P.W = Wc; P.n_c = n_c;
   P.cap_l = cap_l; P.cap_u = cap_u; P.cap_a = cap_a;
-  int32_t *d_arp, *d_acol, *d_lrp, *d_lcol, *d_urp, *d_ucol, *d_umap, *d_perm;
-  TaskDesc *d_tasks;
-  TileDesc *d_tiles;
+  P.cap_rows = cap_rows; P.cap_lev = cap_lev;
+  int32_t *d_arp, *d_acol, *d_lrp, *d_lcol, *d_urp, *d_ucol, *d_umap, *d_perm, *d_sf, *d_sb, *d_levp;
+  GroupDesc *d_groups;
   double *d_aval, *d_ainit, *d_adiag;
-  uint8_t *d_lev;
   CK(dev_upload(ctx, &d_arp, H.arp), "alloc A");
   CK(dev_upload(ctx, &d_acol, H.acol), "alloc A");
   CK(dev_upload(ctx, &d_aval, H.aval), "alloc A");
@@ -250,16 +265,18 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   CK(dev_upload(ctx, &d_urp, H.urp), "alloc U");
   CK(dev_upload(ctx, &d_ucol, H.ucol), "alloc U");
   CK(dev_upload(ctx, &d_umap, H.umap), "alloc U");
-  CK(dev_upload(ctx, &d_tiles, H.tiles), "alloc tiles");
-  CK(dev_upload(ctx, &d_tasks, H.tasks), "alloc tiles");
-  CK(dev_upload(ctx, &d_lev, H.lev), "alloc tiles");
+  CK(dev_upload(ctx, &d_groups, H.groups), "alloc groups");
+  CK(dev_upload(ctx, &d_sf, H.sched_f), "alloc groups");
+  CK(dev_upload(ctx, &d_sb, H.sched_b), "alloc groups");
+  CK(dev_upload(ctx, &d_levp, H.levp), "alloc groups");
   CK(dev_upload(ctx, &d_perm, H.perm), "alloc perm");
   P.arp = d_arp; P.acol = d_acol; P.aval = d_aval;
   P.lrp = d_lrp; P.lcol = d_lcol; P.urp = d_urp; P.ucol = d_ucol; P.umap = d_umap;
   P.ainit = d_ainit; P.adiag = d_adiag;
-  P.tdesc = d_tiles;
-  P.tasks = d_tasks;
-  P.lev = d_lev;
+  P.groups = d_groups;
+  P.sched_f = d_sf;
+  P.sched_b = d_sb;
+  P.levp = d_levp;
   P.perm = d_perm;
   const size_t nL = size_t(H.nL), nn = size_t(n);
   CK(dev_alloc(ctx, &P.lval, nL), "alloc factor");
@@ -577,11 +594,12 @@ iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[9]) {
   out[1] = H.nnz;
   out[2] = H.n_b;
   out[3] = H.n_c;
-  out[4] = int64_t(H.tiles.size());
-  out[5] = int64_t(H.tasks.size() / 2);
+  out[4] = int64_t(H.groups.size());
+  out[5] = 0;
+  for (const GroupDesc &d : H.groups) out[5] += d.fit ? 0 : 1;
   out[6] = H.nL;
-  out[7] = H.max_rounds;
-  out[8] = H.max_task_rows;
+  out[7] = H.max_levels;
+  out[8] = H.max_group_rows;
   return ICCG_OK;
 }
 

@@ -24,7 +24,7 @@ iccg_status fail(iccg_status st, int64_t idx, const char *what, int64_t &bad, st
 
 iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
                          const double *val, const int32_t *perm, const int32_t *block_ptr,
-                         const int32_t *color_ptr, int32_t n_b, int32_t n_c, int32_t R,
+                         const int32_t *color_ptr, int32_t n_b, int32_t n_c, int32_t group_rows,
                          HostLayout &H, int64_t &bad, std::string &msg) {
   bad = -1;
   if (n < 0 || nnz < 0 || nnz >= (int64_t(1) << 31)) return fail(ICCG_ERR_ARG, -1, "n or nnz out of range", bad, msg);
@@ -158,81 +158,100 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
     }
   }
 
-  // tiles and tasks per color
-  const int32_t T = kWarp * R;
-  std::vector<int32_t> tile_row(1, 0), task_tile(1, 0);
-  H.color_task.assign(n_c + 1, 0);
-  H.max_task_rows = 0;
+  // groups: consecutive whole blocks of one color, at most G rows (a larger
+  // block is a group of its own); one CTA per group
+  const int32_t G = std::max(group_rows, 1);
+  std::vector<int32_t> grow(1, 0);
+  H.color_group.assign(n_c + 1, 0);
   for (int32_t c = 0; c < n_c; ++c) {
-    H.color_task[c] = int32_t(task_tile.size()) - 1;
+    H.color_group[c] = int32_t(grow.size()) - 1;
     int32_t j = color_ptr[c];
     while (j < color_ptr[c + 1]) {
-      int32_t size = block_ptr[j + 1] - block_ptr[j];
-      if (size > T) {
-        for (int32_t r0 = block_ptr[j] + T; r0 < block_ptr[j + 1]; r0 += T) tile_row.push_back(r0);
-        tile_row.push_back(block_ptr[j + 1]);
-        H.max_task_rows = std::max(H.max_task_rows, size);
-        ++j;
-      } else {
-        int32_t end = j + 1;
-        while (end < color_ptr[c + 1] && block_ptr[end + 1] - block_ptr[j] <= T) ++end;
-        tile_row.push_back(block_ptr[end]);
-        H.max_task_rows = std::max(H.max_task_rows, block_ptr[end] - block_ptr[j]);
-        j = end;
-      }
-      task_tile.push_back(int32_t(tile_row.size()) - 1);
+      int32_t end = j + 1;
+      while (end < color_ptr[c + 1] && block_ptr[end + 1] - block_ptr[j] <= G) ++end;
+      grow.push_back(block_ptr[end]);
+      j = end;
     }
   }
-  H.color_task[n_c] = int32_t(task_tile.size()) - 1;
-  const int32_t ntiles = int32_t(tile_row.size()) - 1;
-  const int32_t ntasks = int32_t(task_tile.size()) - 1;
+  H.color_group[n_c] = int32_t(grow.size()) - 1;
+  const int32_t ngroups = int32_t(grow.size()) - 1;
 
-  // in-tile dependency depth: forward over L (rows ascending), backward over U
-  H.lev.assign(n, 0);
-  H.tiles.assign(ntiles, TileDesc{});
-  std::vector<uint8_t> ulev(n, 0);
-  int32_t maxr = 0, seg_l = 0, seg_u = 0;
-#pragma omp parallel for schedule(dynamic, 64) reduction(max : maxr, seg_l, seg_u)
-  for (int32_t t = 0; t < ntiles; ++t) {
-    const int32_t t0 = tile_row[t], t1 = tile_row[t + 1];
+  // in-group levels: forward over L (rows ascending), backward over U (rows
+  // descending); the schedule of a group lists its rows level by level
+  // (ascending row inside a level) and is stored at the group's row offset
+  std::vector<int32_t> levf(n, 0), levb(n, 0), nlf(ngroups), nlb(ngroups);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int32_t g = 0; g < ngroups; ++g) {
+    const int32_t r0 = grow[g], r1 = grow[g + 1];
     int32_t df = 0, db = 0;
-    for (int32_t i = t0; i < t1; ++i) {
+    for (int32_t i = r0; i < r1; ++i) {
       int32_t lv = 0;
       for (int32_t e = H.lrp[i]; e < H.lrp[i + 1]; ++e)
-        if (H.lcol[e] >= t0) lv = std::max(lv, H.lev[H.lcol[e]] + 1);
-      H.lev[i] = uint8_t(lv);
+        if (H.lcol[e] >= r0) lv = std::max(lv, levf[H.lcol[e]] + 1);
+      levf[i] = lv;
       df = std::max(df, lv);
     }
-    for (int32_t i = t1 - 1; i >= t0; --i) {
+    for (int32_t i = r1 - 1; i >= r0; --i) {
       int32_t lv = 0;
       for (int32_t e = H.urp[i]; e < H.urp[i + 1]; ++e)
-        if (H.ucol[e] < t1) lv = std::max(lv, ulev[H.ucol[e]] + 1);
-      ulev[i] = uint8_t(lv);
+        if (H.ucol[e] < r1) lv = std::max(lv, levb[H.ucol[e]] + 1);
+      levb[i] = lv;
       db = std::max(db, lv);
     }
-    TileDesc &d = H.tiles[t];
-    d.r0 = t0; d.r1 = t1;
-    d.rounds = (df + 1) | ((db + 1) << 16);
-    d.pad = 0;
-    d.l0 = H.lrp[t0]; d.l1 = H.lrp[t1];
-    d.u0 = H.urp[t0]; d.u1 = H.urp[t1];
-    maxr = std::max(maxr, std::max(df, db) + 1);
+    nlf[g] = df + 1;
+    nlb[g] = db + 1;
+  }
+  H.groups.assign(ngroups, GroupDesc{});
+  int32_t off = 0;
+  for (int32_t g = 0; g < ngroups; ++g) {
+    GroupDesc &d = H.groups[g];
+    d.r0 = grow[g]; d.r1 = grow[g + 1];
+    d.l0 = H.lrp[d.r0]; d.l1 = H.lrp[d.r1];
+    d.u0 = H.urp[d.r0]; d.u1 = H.urp[d.r1];
+    d.nlf = nlf[g]; d.nlb = nlb[g];
+    d.lf = off; off += d.nlf + 1;
+    d.lb = off; off += d.nlb + 1;
+    d.fit = 0; d.pad0 = d.pad1 = d.pad2 = 0;
+  }
+  H.sched_f.assign(n, 0);
+  H.sched_b.assign(n, 0);
+  H.levp.assign(off, 0);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int32_t g = 0; g < ngroups; ++g) {
+    const GroupDesc &d = H.groups[g];
+    for (int pass = 0; pass < 2; ++pass) {
+      const std::vector<int32_t> &lev = pass == 0 ? levf : levb;
+      const int32_t nl = pass == 0 ? d.nlf : d.nlb;
+      int32_t *lp = H.levp.data() + (pass == 0 ? d.lf : d.lb);
+      int32_t *sc = (pass == 0 ? H.sched_f.data() : H.sched_b.data()) + d.r0;
+      for (int32_t l = 0; l <= nl; ++l) lp[l] = 0;
+      for (int32_t i = d.r0; i < d.r1; ++i) lp[lev[i] + 1]++;
+      for (int32_t l = 0; l < nl; ++l) lp[l + 1] += lp[l];
+      std::vector<int32_t> fill(lp, lp + nl);
+      for (int32_t i = d.r0; i < d.r1; ++i) sc[fill[lev[i]]++] = i - d.r0;
+    }
+  }
+  // the shared-memory plan covers groups of at most G rows; a larger group
+  // (one big block) reads its data from global memory
+  int32_t seg_l = 0, seg_u = 0, maxlev = 1, maxrows = 1;
+  H.max_group_rows = 0;
+  H.max_levels = 0;
+  for (int32_t g = 0; g < ngroups; ++g) {
+    const GroupDesc &d = H.groups[g];
+    H.max_group_rows = std::max(H.max_group_rows, d.r1 - d.r0);
+    H.max_levels = std::max(H.max_levels, std::max(d.nlf, d.nlb));
+    if (d.r1 - d.r0 > G) continue;
     seg_l = std::max(seg_l, d.l1 - d.l0);
     seg_u = std::max(seg_u, d.u1 - d.u0);
+    maxlev = std::max(maxlev, std::max(d.nlf, d.nlb));
+    maxrows = std::max(maxrows, d.r1 - d.r0);
   }
-  H.max_rounds = maxr;
   H.seg_l = seg_l;
   H.seg_u = seg_u;
-  H.tasks.assign(ntasks, TaskDesc{});
-  for (int32_t k = 0; k < ntasks; ++k) {
-    TaskDesc &td = H.tasks[k];
-    td.tile0 = task_tile[k];
-    td.ntiles = task_tile[k + 1] - task_tile[k];
-    td.first = H.tiles[td.tile0];
-    td.pad0 = td.pad1 = 0;
-  }
+  H.fit_levels = maxlev;
+  H.fit_rows = maxrows;
   int32_t seg_a = 0;
-  for (int32_t r0 = 0; r0 < n; r0 += T) seg_a = std::max(seg_a, H.arp[std::min(n, r0 + T)] - H.arp[r0]);
+  for (int32_t r0 = 0; r0 < n; r0 += kWarp) seg_a = std::max(seg_a, H.arp[std::min(n, r0 + kWarp)] - H.arp[r0]);
   H.seg_a = seg_a;
   return ICCG_OK;
 }

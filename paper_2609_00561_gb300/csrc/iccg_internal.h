@@ -29,21 +29,18 @@ namespace iccg {
 constexpr int kWarp = 32;
 constexpr int kMaxWarpsPerCta = 16;
 
-// Everything one warp needs to start a tile: rows, forward/backward sweep
-// counts and the L / U entry ranges (one 32-byte load).
-struct __align__(16) TileDesc {
-  int32_t r0, r1;       // rows [r0, r1)
-  int32_t rounds;       // forward sweeps | backward sweeps << 16
-  int32_t pad;
-  int32_t l0, l1;       // L entries [l0, l1)
-  int32_t u0, u1;       // U entries [u0, u1)
-};
-
-// A task (the work of one warp): its first tile inline, so a warp starts
-// with a single 48-byte load, plus its tile range.
-struct __align__(16) TaskDesc {
-  TileDesc first;
-  int32_t tile0, ntiles, pad0, pad1;
+// A group: consecutive whole blocks of one color (or one big block), the
+// work of one warp.  Its forward / backward schedules list the group's rows
+// (as offsets from r0) level by level; they are stored at sched_f[r0 ..],
+// sched_b[r0 ..], with level pointers at levp[lf ..] / levp[lb ..].
+struct __align__(16) GroupDesc {
+  int32_t r0, r1;      // rows [r0, r1)
+  int32_t l0, l1;      // L entries [l0, l1)
+  int32_t u0, u1;      // U entries [u0, u1)
+  int32_t lf, lb;      // level-pointer offsets (forward, backward)
+  int32_t nlf, nlb;    // level counts
+  int32_t fit;         // 1: the group fits the per-warp shared-memory plan
+  int32_t pad0, pad1, pad2, pad3, pad4;
 };
 
 constexpr int kGroup = 32;   // CTAs per first-level reduction group
@@ -68,12 +65,12 @@ struct Params {
   double *lval, *uval, *ldiag, *invd;
   float *lval32, *uval32, *invd32;
   const double *ainit, *adiag;
-  // tiles and tasks (task k covers tiles [tile0, tile0 + ntiles))
-  const TileDesc *tdesc;
-  const TaskDesc *tasks;
-  const uint8_t *lev;
-  // staging capacities (entries) per warp
-  int32_t cap_l, cap_u, cap_a;
+  // groups and their level schedules
+  const GroupDesc *groups;
+  const int32_t *sched_f, *sched_b, *levp;
+  // per-warp shared-memory plan: entries of the staged L / U segment, rows
+  // and levels of a fitting group
+  int32_t cap_l, cap_u, cap_a, cap_rows, cap_lev;
   // vectors (permuted numbering)
   double *xh, *r, *q, *p0, *p1, *bh;
   void *y, *z;                  // double or float, by precision
@@ -104,28 +101,29 @@ struct HostLayout {
   std::vector<double> aval;
   std::vector<int32_t> lrp, lcol, urp, ucol, umap;
   std::vector<double> ainit, adiag;
-  std::vector<TileDesc> tiles;
-  std::vector<TaskDesc> tasks;
-  std::vector<int32_t> color_task;    // n_c + 1
-  std::vector<uint8_t> lev;
+  std::vector<GroupDesc> groups;
+  std::vector<int32_t> sched_f, sched_b, levp;
+  std::vector<int32_t> color_group;   // n_c + 1
   std::vector<int32_t> block_ptr, color_ptr;
-  int32_t max_rounds = 0, max_task_rows = 0;
-  int32_t seg_l = 0, seg_u = 0, seg_a = 0;   // largest tile segments (entries)
+  int32_t max_group_rows = 0, max_levels = 0;   // over all groups
+  int32_t fit_rows = 0, fit_levels = 0;         // over groups of at most 32R rows
+  int32_t seg_l = 0, seg_u = 0, seg_a = 0;      // largest segments (entries)
 };
 
-// Validates inputs and builds the layout; returns ICCG_OK or an error with
-// (bad_index, message) filled in.
+// Validates inputs and builds the layout (groups of at most group_rows rows);
+// returns ICCG_OK or an error with (bad_index, message) filled in.
 iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
                          const double *val, const int32_t *perm, const int32_t *block_ptr,
-                         const int32_t *color_ptr, int32_t n_b, int32_t n_c, int32_t R,
+                         const int32_t *color_ptr, int32_t n_b, int32_t n_c, int32_t group_rows,
                          HostLayout &out, int64_t &bad_index, std::string &msg);
 
 // ---- launch plan (host side) ---------------------------------------------
 struct Plan {
   cudaStream_t stream = nullptr;
   bool pdl = true;                      // programmatic dependent launch
-  int32_t W = 4, R = 1, n_c = 0, n = 0;
-  std::vector<int32_t> task0, task1;    // task range of each color
+  int32_t W = 8, R = 1, n_c = 0, n = 0;
+  int32_t Wa = 4;                       // warps per CTA of the SpMV
+  std::vector<int32_t> task0, task1;    // group range of each color
   std::vector<int32_t> grid_c;          // CTAs of the color-c kernels
   int32_t grid_a = 0;                   // CTAs of the SpMV-shaped kernels
   int32_t grid_v = 0;                   // CTAs of the vector kernels
@@ -138,7 +136,8 @@ typedef void (*PhaseHook)(void *user, int phase, int begin);
 
 // ---- kernel launchers (kernels.cu) ----------------------------------------
 cudaError_t configure_kernels();
-int warp_smem_bytes(int cap, int R, int elem);          // dynamic smem per warp
+int group_smem_bytes(int cap, int rows, int levs, int elem);  // per-warp plan of the color kernels
+int spmv_smem_bytes(int cap);                                // per-warp staging of the SpMV
 cudaError_t launch_factor(const Params &P, const Plan &L, int nL);
 cudaError_t launch_solve_init(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);
 cudaError_t launch_solve_body(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);

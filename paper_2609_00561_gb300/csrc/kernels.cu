@@ -1,8 +1,8 @@
 // Device kernels of block-multicolor ICCG for sm_103a.
 //
-// One PCG iteration is 2*n_c launches (n_c = number of block colors):
-//   spmv                 q = A (z + beta p_old), p_new = z + beta p_old, <p,q>;
-//                        its last group sets alpha = (r,z)/(p,q)
+// One PCG iteration is 2*n_c + 1 launches (n_c = number of block colors):
+//   p update             p = z + beta p
+//   spmv                 q = A p, <p,q>; its last group sets alpha = (r,z)/(p,q)
 //   fwd color 0..n_c-2   x += alpha p, r -= alpha q, <r,r>, then the forward
 //                        substitution L y = r for the rows of that color
 //                        (Alg. 1: colors in sequence, blocks of a color in
@@ -16,24 +16,27 @@
 //                        residual history, tests ||r||/||b|| <= tol and sets
 //                        the CUDA-graph WHILE condition.
 //
-// Work mapping: one warp per task (a run of whole small blocks of one color,
-// or one large block walked tile by tile); every launch has one warp per task
-// or per 32R-row SpMV tile, so latency is hidden by the number of resident
-// warps.  A tile's CSR segment of L, U or A (values and column indices) is
-// copied into the warp's shared memory with cp.async (16-byte, L2 only, all
-// copies in flight at once) while the row pointers and 1/L_ii load into
-// registers.  Kernels are launched with programmatic dependent launch: each
-// lets its successor start at once (griddepcontrol.launch_dependents), and
-// every kernel issues these static loads before it waits
-// (griddepcontrol.wait) for data its predecessor produces (r, q, x, p, y, z,
-// scalars, reduction slots).
+// Substitution work mapping.  One warp owns a group: consecutive whole blocks
+// of one color (at most 32R rows), or one block larger than that.  Blocks of
+// one color share no edge, so the group's rows depend on earlier colors and
+// on earlier rows of their own block only.  The warp works in two phases:
+//   A  every row at once, one row per lane: the entries that point to earlier
+//      colors (y or z gathers) and the fused x / r update;
+//   B  the in-block dependencies, level by level: the rows of all the group's
+//      blocks are listed by their depth in their block's dependency DAG, and
+//      each level is processed with the rows packed across lanes, so every row
+//      is computed exactly once and the FP64 lanes are mostly busy.  The
+//      per-row arithmetic is the row of Alg. 1 (earlier-color terms first).
+// GB300's FP64 FMA rate is 2 lanes/cycle/SM, so a DFMA issued with idle lanes
+// costs as much as a full one; this packing is what keeps the FP64 pipe from
+// becoming the bound.
 //
-// Within a tile every lane owns rows r0 + lane + 32k.  The entries that point
-// outside the tile are gathered first (y or z written by earlier colors or
-// earlier tiles); the in-tile entries (a contiguous run of each CSR row,
-// since columns are sorted) are cached in registers and the in-tile
-// dependencies are resolved by repeated sweeps over the tile (depth + 1
-// sweeps; after sweep k every row of level <= k is final).
+// Memory: a fitting group's CSR segment of L or U, its row pointers, 1/L_ii,
+// schedule and level pointers are copied into the warp's shared memory with
+// cp.async (16-byte, L2 only, all in flight at once) before the kernel waits
+// on its predecessor (programmatic dependent launch: griddepcontrol.wait), so
+// this static traffic overlaps the previous launch.  A group too large for the
+// shared-memory plan reads the same data from global memory.
 //
 // Reductions are deterministic and two-level: every CTA writes its partial;
 // the last CTA of each group of kGroup CTAs (arrival ticket) sums the group's
@@ -49,7 +52,6 @@ namespace {
 
 constexpr int kVecThreads = 256;
 constexpr int kChunk = 4;    // row entries processed per predicated batch
-constexpr int kCacheInt = 4; // in-tile entries per row kept in registers
 enum StepMode { M_FWD = 0, M_BWD = 1, M_FUSED = 2 };
 
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
@@ -137,9 +139,8 @@ __device__ __forceinline__ bool launch_last(const Params &P, int *flag) {
   return arrive_last(&P.sc->ticket, ng, flag);
 }
 
-// A CSR segment [e0, e1): staged in shared memory (entry e at sv[e - bv],
-// sc[e - bc]) when its 16-byte-aligned cover fits the buffer, else read from
-// global memory.
+// A CSR segment: staged in shared memory (entry e at sv[e - bv], sc[e - bc])
+// or read from global memory.
 template <typename VT>
 struct Seg {
   const VT *sv;
@@ -152,32 +153,29 @@ struct Seg {
   __device__ __forceinline__ int32_t c(int e) const { return staged ? sc[e - bc] : __ldg(gc + e); }
 };
 
-// Start the asynchronous copy of a segment into (sv, sc) and commit it as one
-// cp.async group.  Device arrays carry 64 bytes of padding, so the aligned
-// cover stays inside the allocation.
-template <typename VT>
-__device__ __forceinline__ Seg<VT> stage_async(const VT *gv, const int32_t *gc, int e0, int e1, VT *sv,
-                                               int32_t *sc, int cap, int lane) {
-  Seg<VT> s;
-  s.sv = sv; s.sc = sc; s.gv = gv; s.gc = gc;
-  constexpr int EV = 16 / sizeof(VT);
-  const int a0v = e0 & ~(EV - 1), a1v = (e1 + EV - 1) & ~(EV - 1);
-  const int a0c = e0 & ~3, a1c = (e1 + 3) & ~3;
-  s.bv = a0v; s.bc = a0c;
-  s.staged = (a1v - a0v <= cap) && (a1c - a0c <= cap);
-  if (s.staged) {
-    const int nv = (a1v - a0v) / EV;
-    for (int k = lane; k < nv; k += kWarp) cp_async16(sv + k * EV, gv + a0v + k * EV);
-    const int nc = (a1c - a0c) / 4;
-    for (int k = lane; k < nc; k += kWarp) cp_async16(sc + k * 4, gc + a0c + k * 4);
-  }
-  cp_commit();
-  return s;
+// Issue the cp.async copies of the 16-byte-aligned cover of g[a, b) into s;
+// returns the index of s[0] in g.  Device arrays carry 64 bytes of padding,
+// so the cover stays inside the allocation; s needs (b - a) + 2 * (16 /
+// sizeof(T)) elements.
+template <typename T>
+__device__ __forceinline__ int stage_cover(const T *g, int a, int b, T *s, int tid, int nthr) {
+  constexpr int EV = 16 / sizeof(T);
+  const int a0 = a & ~(EV - 1), a1 = (b + EV - 1) & ~(EV - 1);
+  const int nv = (a1 - a0) / EV;
+  for (int k = tid; k < nv; k += nthr) cp_async16(s + k * EV, g + a0 + k * EV);
+  return a0;
 }
 
-// acc -= sum of v_e * x(c_e) over the entries e in [rb, re); entries in
-// ascending order, kChunk at a time with predicated loads so a chunk's loads
-// are in flight together.
+// count of entries of [rb, re) whose column is below `bound` (columns sorted)
+template <typename VT>
+__device__ __forceinline__ int count_below(const Seg<VT> &S, int rb, int re, int bound) {
+  int n = 0;
+  for (int e = rb; e < re; ++e) n += S.c(e) < bound ? 1 : 0;
+  return n;
+}
+
+// acc -= sum of v_e * x(c_e) over the entries e in [rb, re), ascending;
+// loads in predicated batches of kChunk, then the FMAs of the batch.
 template <typename VT, typename AT, typename Load>
 __device__ __forceinline__ AT row_sub(const Seg<VT> &S, int rb, int re, AT acc, Load x) {
   for (int e0 = rb; e0 < re; e0 += kChunk) {
@@ -193,17 +191,10 @@ __device__ __forceinline__ AT row_sub(const Seg<VT> &S, int rb, int re, AT acc, 
 #pragma unroll
     for (int j = 0; j < kChunk; ++j) xx[j] = cc[j] >= 0 ? AT(x(cc[j])) : AT(0);
 #pragma unroll
-    for (int j = 0; j < kChunk; ++j) acc -= AT(vv[j]) * xx[j];
+    for (int j = 0; j < kChunk; ++j)
+      if (cc[j] >= 0) acc -= AT(vv[j]) * xx[j];
   }
   return acc;
-}
-
-// number of entries of [rb, re) whose column is below `bound` (columns sorted)
-template <typename VT>
-__device__ __forceinline__ int count_below(const Seg<VT> &S, int rb, int re, int bound) {
-  int n = 0;
-  for (int e = rb; e < re; ++e) n += S.c(e) < bound ? 1 : 0;
-  return n;
 }
 
 template <typename PT> __device__ __forceinline__ const PT *lvals(const Params &P);
@@ -216,151 +207,192 @@ template <typename PT> __device__ __forceinline__ const PT *invds(const Params &
 template <> __device__ __forceinline__ const double *invds<double>(const Params &P) { return P.invd; }
 template <> __device__ __forceinline__ const float *invds<float>(const Params &P) { return P.invd32; }
 
-// Per-warp shared memory: one staging buffer [vals cap][cols cap] and the
-// tile's in-flight y / z values [32R].  Sizes are rounded to 16 bytes.
-__host__ __device__ __forceinline__ int warp_bytes1(int cap, int R, int elem) {
-  return ((cap * elem + 15) & ~15) + ((cap * 4 + 15) & ~15) + ((kWarp * R * elem + 15) & ~15);
-}
+// ---------------------------------------------------------------------------
+// per-CTA shared memory of the substitution kernels (one CTA per group)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int r16(int bytes) { return (bytes + 15) & ~15; }
 
-template <typename VT>
-__device__ __forceinline__ void warp_bufs(unsigned char *base, int cap, int R, VT *&sv, int32_t *&sc, VT *&ysh) {
-  const int bytes_v = (cap * int(sizeof(VT)) + 15) & ~15;
-  const int bytes_c = (cap * 4 + 15) & ~15;
-  unsigned char *mine = base + (threadIdx.x >> 5) * warp_bytes1(cap, R, int(sizeof(VT)));
-  sv = reinterpret_cast<VT *>(mine);
-  sc = reinterpret_cast<int32_t *>(mine + bytes_v);
-  ysh = reinterpret_cast<VT *>(mine + bytes_v + bytes_c);
-}
-
-__device__ __forceinline__ TileDesc load_desc(const TileDesc *d) {
-  const int4 a = __ldg(reinterpret_cast<const int4 *>(d));
-  const int4 b = __ldg(reinterpret_cast<const int4 *>(d) + 1);
-  TileDesc t;
-  t.r0 = a.x; t.r1 = a.y; t.rounds = a.z; t.pad = a.w;
-  t.l0 = b.x; t.l1 = b.y; t.u0 = b.z; t.u1 = b.w;
-  return t;
-}
-
-__device__ __forceinline__ void load_task(const TaskDesc *t, TileDesc &first, int &tile0, int &ntiles) {
-  first = load_desc(&t->first);
-  const int4 c = __ldg(reinterpret_cast<const int4 *>(t) + 2);
-  tile0 = c.x;
-  ntiles = c.y;
-}
-
-// Everything of one tile step that no earlier kernel writes.
-template <typename PT, int R>
-struct Step {
-  int r0, r1, rounds;
-  Seg<PT> S;
-  int rb[R], re[R];
-  PT dv[R];
+struct GroupSmemPlan {
+  int o_sv, o_sc, o_rp, o_dv, o_sch, o_lp, o_w, o_spl, total;
 };
 
-template <typename PT, int R>
-__device__ __forceinline__ void step_load(const Params &P, const TileDesc &d, bool upper, PT *sv, int32_t *sc, int cap,
-                                          int lane, Step<PT, R> &st) {
-  st.r0 = d.r0;
-  st.r1 = d.r1;
-  st.rounds = upper ? (d.rounds >> 16) : (d.rounds & 0xffff);
-  st.S = upper ? stage_async<PT>(uvals<PT>(P), P.ucol, d.u0, d.u1, sv, sc, cap, lane)
-               : stage_async<PT>(lvals<PT>(P), P.lcol, d.l0, d.l1, sv, sc, cap, lane);
-  const int32_t *rp = upper ? P.urp : P.lrp;
-  const PT *idv = invds<PT>(P);
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const int i = d.r0 + lane + kWarp * k;
-    const bool ok = i < d.r1;
-    st.rb[k] = ok ? __ldg(rp + i) : 0;
-    st.re[k] = ok ? __ldg(rp + i + 1) : 0;
-    st.dv[k] = ok ? __ldg(idv + i) : PT(0);
-  }
+__host__ __device__ __forceinline__ GroupSmemPlan group_smem_plan(int cap, int rows, int levs, int elem) {
+  GroupSmemPlan p;
+  int o = 0;
+  p.o_sv = o; o += r16((cap + 8) * elem);
+  p.o_sc = o; o += r16((cap + 8) * 4);
+  p.o_rp = o; o += r16((rows + 9) * 4);
+  p.o_dv = o; o += r16((rows + 8) * elem);
+  p.o_sch = o; o += r16((rows + 8) * 4);
+  p.o_lp = o; o += r16((levs + 9) * 4);
+  p.o_w = o; o += r16(rows * elem);
+  p.o_spl = o; o += r16(rows * 4);
+  p.total = o;
+  return p;
 }
 
-// One tile of the forward (UPPER = false, L rows: out-of-tile entries are a
-// prefix of each row) or backward (UPPER = true, U rows: out-of-tile entries
-// are a suffix) substitution.  `src` is r (forward) or y (backward); `ext` is
-// the vector gathered for out-of-tile columns (y or z); the result goes to
-// `dst` (y or z).  UPDATE fuses x += alpha p, r -= alpha q, <r,r> in front.
-template <typename PT, int R, bool UPPER, bool UPDATE>
-__device__ __forceinline__ void tile_step(const Params &P, const Step<PT, R> &st, PT *ysh, int lane, double alpha,
-                                          const double *pn, double &rr_acc, double &rz_acc) {
-  const PT *ext = reinterpret_cast<const PT *>(UPPER ? P.z : P.y);
-  PT *dst = reinterpret_cast<PT *>(UPPER ? P.z : P.y);
-  const int r0 = st.r0, r1 = st.r1;
-  PT tv[R];
-  int ib[R], ie[R];   // in-tile entry range of each row
-  int lo[R][kCacheInt];
-  PT lv[R][kCacheInt];
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const int i = r0 + lane + kWarp * k;
-    tv[k] = PT(0);
-    ib[k] = ie[k] = 0;
-    if (i < r1) {
-      PT src;
-      if (UPPER) {
-        src = reinterpret_cast<const PT *>(P.y)[i];
-      } else {
-        double ri = P.r[i];
-        if (UPDATE) {
-          ri -= alpha * P.q[i];
-          P.r[i] = ri;
-          P.xh[i] += alpha * pn[i];
-          rr_acc += ri * ri;
-        }
-        src = PT(ri);
+template <typename PT>
+struct GroupSmem {
+  PT *sv;
+  int32_t *sc, *rp, *sch, *lp, *spl;
+  PT *dv, *w;
+};
+
+template <typename PT>
+__device__ __forceinline__ GroupSmem<PT> group_smem(unsigned char *base, const GroupSmemPlan &p) {
+  unsigned char *m = base;
+  GroupSmem<PT> s;
+  s.sv = reinterpret_cast<PT *>(m + p.o_sv);
+  s.sc = reinterpret_cast<int32_t *>(m + p.o_sc);
+  s.rp = reinterpret_cast<int32_t *>(m + p.o_rp);
+  s.dv = reinterpret_cast<PT *>(m + p.o_dv);
+  s.sch = reinterpret_cast<int32_t *>(m + p.o_sch);
+  s.lp = reinterpret_cast<int32_t *>(m + p.o_lp);
+  s.w = reinterpret_cast<PT *>(m + p.o_w);
+  s.spl = reinterpret_cast<int32_t *>(m + p.o_spl);
+  return s;
+}
+
+__device__ __forceinline__ GroupDesc load_group(const GroupDesc *g) {
+  const int4 *p = reinterpret_cast<const int4 *>(g);
+  const int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+  GroupDesc d;
+  d.r0 = a.x; d.r1 = a.y; d.l0 = a.z; d.l1 = a.w;
+  d.u0 = b.x; d.u1 = b.y; d.lf = b.z; d.lb = b.w;
+  d.nlf = c.x; d.nlb = c.y; d.fit = c.z;
+  return d;
+}
+
+// Where the static data of one sweep over a group lives (shared memory for a
+// fitting group, global memory otherwise).
+template <typename PT>
+struct Sweep {
+  Seg<PT> S;
+  bool fit;
+  int rpb, dvb, schb, lpb;       // index of the first staged element
+  const int32_t *grp, *gsch;     // global row pointers / schedule
+  const PT *gdv;
+  int lev0, nlev;                // level pointers at levp[lev0 ..]
+  __device__ __forceinline__ int rp(const GroupSmem<PT> &m, int i) const { return fit ? m.rp[i - rpb] : __ldg(grp + i); }
+  __device__ __forceinline__ PT dv(const GroupSmem<PT> &m, int i) const { return fit ? m.dv[i - dvb] : __ldg(gdv + i); }
+};
+
+// Stage (or describe) the static data of a forward (upper = false) or
+// backward (upper = true) sweep over group d.  Issues cp.async copies and
+// commits them; the caller waits.
+template <typename PT>
+__device__ __forceinline__ Sweep<PT> sweep_static(const Params &P, const GroupDesc &d, bool upper,
+                                                  const GroupSmem<PT> &m, int tid, int nthr) {
+  Sweep<PT> sw;
+  sw.fit = d.fit != 0;
+  sw.grp = upper ? P.urp : P.lrp;
+  sw.gsch = upper ? P.sched_b : P.sched_f;
+  sw.gdv = invds<PT>(P);
+  sw.lev0 = upper ? d.lb : d.lf;
+  sw.nlev = upper ? d.nlb : d.nlf;
+  sw.S.gv = upper ? uvals<PT>(P) : lvals<PT>(P);
+  sw.S.gc = upper ? P.ucol : P.lcol;
+  sw.S.sv = m.sv;
+  sw.S.sc = m.sc;
+  sw.S.staged = sw.fit;
+  sw.S.bv = sw.S.bc = 0;
+  sw.rpb = sw.dvb = sw.schb = sw.lpb = 0;
+  if (sw.fit) {
+    const int e0 = upper ? d.u0 : d.l0, e1 = upper ? d.u1 : d.l1;
+    sw.S.bv = stage_cover<PT>(sw.S.gv, e0, e1, m.sv, tid, nthr);
+    sw.S.bc = stage_cover<int32_t>(sw.S.gc, e0, e1, m.sc, tid, nthr);
+    sw.rpb = stage_cover<int32_t>(sw.grp, d.r0, d.r1 + 1, m.rp, tid, nthr);
+    sw.dvb = stage_cover<PT>(sw.gdv, d.r0, d.r1, m.dv, tid, nthr);
+    sw.schb = stage_cover<int32_t>(sw.gsch, d.r0, d.r1, m.sch, tid, nthr);
+    sw.lpb = stage_cover<int32_t>(P.levp, sw.lev0, sw.lev0 + sw.nlev + 1, m.lp, tid, nthr);
+  }
+  cp_commit();
+  return sw;
+}
+
+// One sweep over a group.  UPPER = false: forward, L rows (entries to earlier
+// colors are a prefix of each row, in-block entries the rest); the source is
+// r (with the x / r update when UPDATE) and the result y.  UPPER = true:
+// backward, U rows (in-block entries a prefix, later colors the rest); the
+// source is y (from `ysrc`: shared memory when the fused kernel keeps y of a
+// fitting group there) and the result z, with <r, z>.
+// Fitting groups keep t / y / z in m.w; other groups work in place in the
+// global result vector.
+template <typename PT, bool UPPER, bool UPDATE>
+__device__ __forceinline__ void group_sweep(const Params &P, const GroupDesc &d, const Sweep<PT> &sw,
+                                            const GroupSmem<PT> &m, int tid, int nthr, double alpha,
+                                            const double *pn, bool y_in_smem, bool store_result, double &rr_acc,
+                                            double &rz_acc) {
+  PT *yv = reinterpret_cast<PT *>(P.y);
+  PT *zv = reinterpret_cast<PT *>(P.z);
+  PT *res = UPPER ? zv : yv;        // global result vector
+  const PT *ext = UPPER ? zv : yv;  // gathered for out-of-group columns
+  const int r0 = d.r0, r1 = d.r1, nrows = r1 - r0;
+  const bool fit = sw.fit;
+  // phase A: out-of-group entries, all rows at once (one row per thread)
+  for (int l = tid; l < nrows; l += nthr) {
+    const int i = r0 + l;
+    const int rb = sw.rp(m, i), re = sw.rp(m, i + 1);
+    PT src;
+    if (UPPER) {
+      src = y_in_smem ? m.w[l] : yv[i];
+    } else {
+      double ri = P.r[i];
+      if (UPDATE) {
+        ri -= alpha * P.q[i];
+        P.r[i] = ri;
+        P.xh[i] += alpha * pn[i];
+        rr_acc += ri * ri;
       }
-      // L row: [rb, split) outside (c < r0), [split, re) inside
-      // U row: [rb, split) inside (c < r1), [split, re) outside
-      const int split = st.rb[k] + count_below(st.S, st.rb[k], st.re[k], UPPER ? r1 : r0);
-      const int xb = UPPER ? split : st.rb[k], xe = UPPER ? st.re[k] : split;
-      ib[k] = UPPER ? st.rb[k] : split;
-      ie[k] = UPPER ? split : st.re[k];
-      tv[k] = row_sub<PT, PT>(st.S, xb, xe, src, [&](int c) { return ext[c]; });
+      src = PT(ri);
     }
-#pragma unroll
-    for (int j = 0; j < kCacheInt; ++j) {
-      const int e = ib[k] + j;
-      const bool ok = e < ie[k];
-      lo[k][j] = ok ? st.S.c(e) - r0 : 0;
-      lv[k][j] = ok ? st.S.v(e) : PT(0);
-    }
-    if (i < r1) ysh[lane + kWarp * k] = tv[k] * st.dv[k];
-  }
-  // overflow of the register cache is rare (wide in-tile rows); warp-uniform
-  bool spill = false;
-#pragma unroll
-  for (int k = 0; k < R; ++k) spill |= (ie[k] - ib[k]) > kCacheInt;
-  spill = __any_sync(0xffffffffu, spill);
-  for (int rd = 1; rd < st.rounds; ++rd) {
-    __syncwarp();
-    PT yn[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      PT acc = tv[k];
-#pragma unroll
-      for (int j = 0; j < kCacheInt; ++j) acc -= lv[k][j] * ysh[lo[k][j]];
-      if (spill && ie[k] - ib[k] > kCacheInt)
-        acc = row_sub<PT, PT>(st.S, ib[k] + kCacheInt, ie[k], acc, [&](int c) { return ysh[c - r0]; });
-      yn[k] = acc * st.dv[k];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < R; ++k)
-      if (r0 + lane + kWarp * k < r1) ysh[lane + kWarp * k] = yn[k];
-  }
-  __syncwarp();
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const int i = r0 + lane + kWarp * k;
-    if (i < r1) {
-      const PT v = ysh[lane + kWarp * k];
-      dst[i] = v;
-      if (UPPER) rz_acc += P.r[i] * double(v);
+    const int split = rb + count_below(sw.S, rb, re, UPPER ? r1 : r0);
+    const int xb = UPPER ? split : rb, xe = UPPER ? re : split;
+    const PT t = row_sub<PT, PT>(sw.S, xb, xe, src, [&](int c) { return ext[c]; });
+    if (fit) {
+      m.w[l] = t;
+      m.spl[l] = split;
+    } else {
+      res[i] = t;
     }
   }
-  __syncwarp();
+  __syncthreads();
+  // phase B: in-block entries, level by level; a level's rows go to the
+  // first threads, so only as many warps as the level needs issue FP64 work
+  for (int lv = 0; lv < sw.nlev; ++lv) {
+    const int p0 = fit ? m.lp[sw.lev0 + lv - sw.lpb] : __ldg(P.levp + sw.lev0 + lv);
+    const int p1 = fit ? m.lp[sw.lev0 + lv + 1 - sw.lpb] : __ldg(P.levp + sw.lev0 + lv + 1);
+    for (int p = p0 + tid; p < p1; p += nthr) {
+      const int l = fit ? m.sch[r0 + p - sw.schb] : __ldg(sw.gsch + r0 + p);
+      const int i = r0 + l;
+      const int rb = sw.rp(m, i), re = sw.rp(m, i + 1);
+      int ib, ie;
+      PT acc;
+      if (fit) {
+        acc = m.w[l];
+        ib = UPPER ? rb : m.spl[l];
+        ie = UPPER ? m.spl[l] : re;
+        acc = row_sub<PT, PT>(sw.S, ib, ie, acc, [&](int c) { return m.w[c - r0]; });
+        m.w[l] = acc * sw.dv(m, i);
+      } else {
+        acc = res[i];
+        const int split = rb + count_below(sw.S, rb, re, UPPER ? r1 : r0);
+        ib = UPPER ? rb : split;
+        ie = UPPER ? split : re;
+        acc = row_sub<PT, PT>(sw.S, ib, ie, acc, [&](int c) { return res[c]; });
+        res[i] = acc * sw.dv(m, i);
+      }
+    }
+    __syncthreads();
+  }
+  // results: fitting groups store from shared memory (coalesced)
+  for (int l = tid; l < nrows; l += nthr) {
+    const int i = r0 + l;
+    const PT v = fit ? m.w[l] : res[i];
+    if (fit && store_result) res[i] = v;
+    if (UPPER) rz_acc += P.r[i] * double(v);
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -426,50 +458,43 @@ enum Fin { FIN_NONE = 0, FIN_ITER = 1, FIN_INIT = 2 };
 
 // ---------------------------------------------------------------------------
 // color kernel: MODE = forward sweep of one color, backward sweep of one
-// color, or both for the last color (fused)
+// color, or both for the last color (fused); one CTA per group
 // ---------------------------------------------------------------------------
-template <typename PT, int R, int MODE, bool UPDATE>
+template <typename PT, int MODE, bool UPDATE>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
-color_kernel(Params P, int task0, int task1, int cap, int fin) {
+color_kernel(Params P, int g0, int g1, GroupSmemPlan plan, int fin) {
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[kMaxWarpsPerCta];
   __shared__ int flag;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-  PT *sv; int32_t *sc; PT *ysh;
-  warp_bufs<PT>(smem, cap, R, sv, sc, ysh);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const GroupSmem<PT> m = group_smem<PT>(smem, plan);
   double rr_acc = 0.0, rz_acc = 0.0;
-  const int task = task0 + blockIdx.x * W + warp;
-  if (task < task1) {
-    TileDesc d;
-    int tile0, ntiles;
-    load_task(P.tasks + task, d, tile0, ntiles);
-    const int nsteps = MODE == M_FUSED ? 2 * ntiles : ntiles;
-    double alpha = 0.0;
-    const double *pn = nullptr;
-    for (int s = 0; s < nsteps; ++s) {
-      bool upper;
-      int tl;
-      if (MODE == M_FWD) { tl = tile0 + s; upper = false; }
-      else if (MODE == M_BWD) { tl = tile0 + ntiles - 1 - s; upper = true; }
-      else if (s < ntiles) { tl = tile0 + s; upper = false; }
-      else { tl = tile0 + 2 * ntiles - 1 - s; upper = true; }
-      if (s > 0 || MODE == M_BWD) {
-        if (!(s == 0 && ntiles == 1)) d = load_desc(P.tdesc + tl);
+  const int g = g0 + blockIdx.x;
+  if (g < g1) {
+    const GroupDesc d = load_group(P.groups + g);
+    const Sweep<PT> sw = sweep_static<PT>(P, d, MODE == M_BWD, m, tid, nthr);
+    cp_wait_all();
+    __syncthreads();
+    pdl_wait();
+    if (MODE == M_BWD) {
+      group_sweep<PT, true, false>(P, d, sw, m, tid, nthr, 0.0, nullptr, false, true, rr_acc, rz_acc);
+    } else {
+      double alpha = 0.0;
+      const double *pn = P.p0;
+      if (UPDATE) alpha = __ldcg(&P.sc->alpha);
+      group_sweep<PT, false, UPDATE>(P, d, sw, m, tid, nthr, alpha, pn, false, MODE == M_FWD || !sw.fit,
+                                     rr_acc, rz_acc);
+      if (MODE == M_FUSED) {
+        // the last color: y of a fitting group stays in shared memory; the
+        // backward sweep restages the U side (the schedule changes, 1/L_ii
+        // stays)
+        const bool keep = sw.fit;
+        const Sweep<PT> su = sweep_static<PT>(P, d, true, m, tid, nthr);
+        cp_wait_all();
+        __syncthreads();
+        group_sweep<PT, true, false>(P, d, su, m, tid, nthr, 0.0, nullptr, keep, true, rr_acc, rz_acc);
       }
-      Step<PT, R> st;
-      step_load<PT, R>(P, d, upper, sv, sc, cap, lane, st);
-      cp_wait_all();
-      __syncwarp();
-      if (s == 0) {
-        pdl_wait();
-        if (UPDATE) {
-          alpha = __ldcg(&P.sc->alpha);
-          pn = ((__ldcg(&P.sc->iter) + 1) & 1) ? P.p1 : P.p0;
-        }
-      }
-      if (upper) tile_step<PT, R, true, false>(P, st, ysh, lane, 0.0, nullptr, rr_acc, rz_acc);
-      else tile_step<PT, R, false, UPDATE>(P, st, ysh, lane, alpha, pn, rr_acc, rz_acc);
     }
   } else {
     pdl_wait();
@@ -481,14 +506,14 @@ color_kernel(Params P, int task0, int task1, int cap, int fin) {
   double ga, gb;
   if (group_reduce(P, cta_sum(a, red), two ? cta_sum(b, red) : 0.0, two, red, &flag, ga, gb)) {
     if (threadIdx.x == 0) {
-      // slot g was last written by an earlier launch on another SM: read it
+      // slot gg was last written by an earlier launch on another SM: read it
       // from L2, not from this SM's L1
-      const int g = blockIdx.x / kGroup;
-      if (MODE == M_FWD) P.acc_rr[g] = __ldcg(P.acc_rr + g) + ga;
-      else if (MODE == M_BWD || !UPDATE) P.acc_rz[g] = __ldcg(P.acc_rz + g) + ga;
+      const int gg = blockIdx.x / kGroup;
+      if (MODE == M_FWD) P.acc_rr[gg] = __ldcg(P.acc_rr + gg) + ga;
+      else if (MODE == M_BWD || !UPDATE) P.acc_rz[gg] = __ldcg(P.acc_rz + gg) + ga;
       else {
-        P.acc_rr[g] = __ldcg(P.acc_rr + g) + ga;
-        P.acc_rz[g] = __ldcg(P.acc_rz + g) + gb;
+        P.acc_rr[gg] = __ldcg(P.acc_rr + gg) + ga;
+        P.acc_rz[gg] = __ldcg(P.acc_rz + gg) + gb;
       }
     }
     if (fin != FIN_NONE && launch_last(P, &flag)) {
@@ -499,12 +524,25 @@ color_kernel(Params P, int task0, int task1, int cap, int fin) {
 }
 
 // ---------------------------------------------------------------------------
-// SpMV-shaped kernel over 32R-row tiles of A_hat, one warp per tile
+// p = z + beta p (start of an iteration; beta = 0 on the first)
 // ---------------------------------------------------------------------------
-// mode 0: q = A (z + beta p_old), p_new = z + beta p_old, <p_new, q>; last group: alpha
+template <typename ZT>
+__global__ void __launch_bounds__(kVecThreads) pupdate_kernel(Params P) {
+  pdl_trigger();
+  pdl_wait();
+  const double beta = __ldcg(&P.sc->beta);
+  const ZT *z = reinterpret_cast<const ZT *>(P.z);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x)
+    P.p0[i] = double(z[i]) + beta * P.p0[i];
+}
+
+// ---------------------------------------------------------------------------
+// SpMV over 32-row tiles of A_hat, one warp per tile, one row per lane
+// ---------------------------------------------------------------------------
+// mode 0: q = A p, <p, q>; last group: alpha = rz / pq
 // mode 1: r = b_hat - A x_hat, <r, r> group sums into gpq (solve start)
 // mode 2: q = A x_hat (plain SpMV)
-template <typename ZT, int R, int MODE>
+template <int MODE>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
 spmv_kernel(Params P, int cap) {
   pdl_trigger();
@@ -512,57 +550,41 @@ spmv_kernel(Params P, int cap) {
   __shared__ double red[kMaxWarpsPerCta];
   __shared__ int flag;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-  double *sv; int32_t *sc; double *unused;
-  warp_bufs<double>(smem, cap, 0, sv, sc, unused);
-  const int T = kWarp * R;
-  const int t0 = (blockIdx.x * W + warp) * T;
+  double *sv = reinterpret_cast<double *>(smem + warp * (r16((cap + 8) * 8) + r16((cap + 8) * 4)));
+  int32_t *sc = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(sv) + r16((cap + 8) * 8));
+  const int t0 = (blockIdx.x * W + warp) * kWarp;
   double acc = 0.0;
   if (t0 < P.n) {
-    const int t1 = min(P.n, t0 + T);
-    int rb[R], re[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int i = t0 + lane + kWarp * k;
-      rb[k] = i < t1 ? __ldg(P.arp + i) : 0;
-      re[k] = i < t1 ? __ldg(P.arp + i + 1) : 0;
-    }
-    const int e0 = __shfl_sync(0xffffffffu, rb[0], 0);
+    const int t1 = min(P.n, t0 + kWarp);
+    const int i = t0 + lane;
+    const int rb = i < t1 ? __ldg(P.arp + i) : 0;
+    const int re = i < t1 ? __ldg(P.arp + i + 1) : 0;
+    const int e0 = __shfl_sync(0xffffffffu, rb, 0);
     const int e1 = __ldg(P.arp + t1);
-    const Seg<double> S = stage_async<double>(P.aval, P.acol, e0, e1, sv, sc, cap, lane);
+    Seg<double> S;
+    S.gv = P.aval; S.gc = P.acol; S.sv = sv; S.sc = sc;
+    S.staged = e1 - e0 <= cap;
+    S.bv = S.bc = 0;
+    if (S.staged) {
+      S.bv = stage_cover<double>(P.aval, e0, e1, sv, lane, kWarp);
+      S.bc = stage_cover<int32_t>(P.acol, e0, e1, sc, lane, kWarp);
+    }
+    cp_commit();
     cp_wait_all();
     __syncwarp();
     pdl_wait();
-    const ZT *z = reinterpret_cast<const ZT *>(P.z);
-    double beta = 0.0;
-    const double *pold = P.p0;
-    double *pnew = P.p1;
-    if (MODE == 0) {
-      beta = __ldcg(&P.sc->beta);
-      const int it = __ldcg(&P.sc->iter);
-      pold = (it & 1) ? P.p1 : P.p0;
-      pnew = (it & 1) ? P.p0 : P.p1;
-    }
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int i = t0 + lane + kWarp * k;
-      if (i < t1) {
-        if (MODE == 0) {
-          const double s = -row_sub<double, double>(S, rb[k], re[k], 0.0,
-                                                    [&](int c) { return double(z[c]) + beta * pold[c]; });
-          const double pi = double(z[i]) + beta * pold[i];
-          pnew[i] = pi;
-          P.q[i] = s;
-          acc += pi * s;
-        } else {
-          const double s = -row_sub<double, double>(S, rb[k], re[k], 0.0, [&](int c) { return P.xh[c]; });
-          if (MODE == 1) {
-            const double ri = P.bh[i] - s;
-            P.r[i] = ri;
-            acc += ri * ri;
-          } else {
-            P.q[i] = s;
-          }
-        }
+    if (i < t1) {
+      const double *xin = MODE == 0 ? P.p0 : P.xh;
+      const double s = -row_sub<double, double>(S, rb, re, 0.0, [&](int c) { return xin[c]; });
+      if (MODE == 0) {
+        P.q[i] = s;
+        acc = xin[i] * s;
+      } else if (MODE == 1) {
+        const double ri = P.bh[i] - s;
+        P.r[i] = ri;
+        acc = ri * ri;
+      } else {
+        P.q[i] = s;
       }
     }
   } else {
@@ -617,7 +639,7 @@ __global__ void __launch_bounds__(kVecThreads) widen_kernel(const float *src, do
 }
 
 // ---------------------------------------------------------------------------
-// IC(0) (up-looking, one row per lane, rows of a tile level by level)
+// IC(0) (up-looking, rows of a group level by level, one row per lane)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void factor_row(const Params &P, int i) {
   const int rb = P.lrp[i], re = P.lrp[i + 1];
@@ -644,19 +666,14 @@ __device__ __forceinline__ void factor_row(const Params &P, int i) {
   P.ldiag[i] = sqrt(d);
 }
 
-__global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp) factor_color_kernel(Params P, int task0, int task1) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-  const int task = task0 + blockIdx.x * W + warp;
-  if (task >= task1) return;
-  const TaskDesc t = P.tasks[task];
-  for (int tl = t.tile0; tl < t.tile0 + t.ntiles; ++tl) {
-    const TileDesc d = P.tdesc[tl];
-    const int rounds = d.rounds & 0xffff;
-    for (int lv = 0; lv < rounds; ++lv) {
-      for (int i = d.r0 + lane; i < d.r1; i += kWarp)
-        if (P.lev[i] == lv) factor_row(P, i);
-      __syncwarp();
-    }
+__global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp) factor_color_kernel(Params P, int g0, int g1) {
+  const int g = g0 + blockIdx.x;
+  if (g >= g1) return;
+  const GroupDesc d = P.groups[g];
+  for (int lv = 0; lv < d.nlf; ++lv) {
+    const int p0 = P.levp[d.lf + lv], p1 = P.levp[d.lf + lv + 1];
+    for (int p = p0 + int(threadIdx.x); p < p1; p += blockDim.x) factor_row(P, d.r0 + P.sched_f[d.r0 + p]);
+    __syncthreads();
   }
 }
 
@@ -694,62 +711,59 @@ cudaError_t launch(void (*kernel)(KArgs...), int grid, int threads, int smem, co
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <typename PT, int R>
-cudaError_t launch_fwd(const Params &P, const Plan &L, int c, bool update, bool fused, int fin) {
-  const int threads = L.W * kWarp;
-  const int cap = fused ? max(P.cap_l, P.cap_u) : P.cap_l;
-  const int smem = fused ? L.smem_fused : L.smem_fwd;
-  const int g = L.grid_c[c], t0 = L.task0[c], t1 = L.task1[c];
-  if (update) {
-    if (fused) return launch(color_kernel<PT, R, M_FUSED, true>, g, threads, smem, L, P, t0, t1, cap, fin);
-    return launch(color_kernel<PT, R, M_FWD, true>, g, threads, smem, L, P, t0, t1, cap, fin);
-  }
-  if (fused) return launch(color_kernel<PT, R, M_FUSED, false>, g, threads, smem, L, P, t0, t1, cap, fin);
-  return launch(color_kernel<PT, R, M_FWD, false>, g, threads, smem, L, P, t0, t1, cap, fin);
+template <typename PT>
+GroupSmemPlan plan_of(const Params &P, bool fused, bool upper) {
+  const int cap = fused ? max(P.cap_l, P.cap_u) : (upper ? P.cap_u : P.cap_l);
+  return group_smem_plan(cap, P.cap_rows, P.cap_lev, int(sizeof(PT)));
 }
 
-template <typename PT, int R>
+template <typename PT>
+cudaError_t launch_fwd(const Params &P, const Plan &L, int c, bool update, bool fused, int fin) {
+  const int threads = L.W * kWarp;
+  const GroupSmemPlan pl = plan_of<PT>(P, fused, false);
+  const int smem = pl.total;
+  const int g = L.grid_c[c], t0 = L.task0[c], t1 = L.task1[c];
+  if (update) {
+    if (fused) return launch(color_kernel<PT, M_FUSED, true>, g, threads, smem, L, P, t0, t1, pl, fin);
+    return launch(color_kernel<PT, M_FWD, true>, g, threads, smem, L, P, t0, t1, pl, fin);
+  }
+  if (fused) return launch(color_kernel<PT, M_FUSED, false>, g, threads, smem, L, P, t0, t1, pl, fin);
+  return launch(color_kernel<PT, M_FWD, false>, g, threads, smem, L, P, t0, t1, pl, fin);
+}
+
+template <typename PT>
 cudaError_t launch_bwd(const Params &P, const Plan &L, int c, int fin) {
-  return launch(color_kernel<PT, R, M_BWD, false>, L.grid_c[c], L.W * kWarp, L.smem_bwd, L, P, L.task0[c],
-                L.task1[c], P.cap_u, fin);
+  const GroupSmemPlan pl = plan_of<PT>(P, false, true);
+  return launch(color_kernel<PT, M_BWD, false>, L.grid_c[c], L.W * kWarp, pl.total, L, P, L.task0[c],
+                L.task1[c], pl, fin);
 }
 
 // Forward sweep (with or without the x/r update), fused last color, backward
 // sweep.  fin_last: the epilogue run by the last launch.
-template <typename PT, int R>
+template <typename PT>
 cudaError_t sweep(const Params &P, const Plan &L, bool update, int fin_last, PhaseHook h, void *u) {
   cudaError_t e = cudaSuccess;
   const int nc = L.n_c;
   for (int c = 0; c < nc - 1 && e == cudaSuccess; ++c) {
     if (h) h(u, PH_FWD, 1);
-    e = launch_fwd<PT, R>(P, L, c, update, false, FIN_NONE);
+    e = launch_fwd<PT>(P, L, c, update, false, FIN_NONE);
     if (h) h(u, PH_FWD, 0);
   }
   if (e != cudaSuccess) return e;
   if (h) h(u, PH_FUSED, 1);
-  e = launch_fwd<PT, R>(P, L, nc - 1, update, true, nc == 1 ? fin_last : FIN_NONE);
+  e = launch_fwd<PT>(P, L, nc - 1, update, true, nc == 1 ? fin_last : FIN_NONE);
   if (h) h(u, PH_FUSED, 0);
   for (int c = nc - 2; c >= 0 && e == cudaSuccess; --c) {
     if (h) h(u, PH_BWD, 1);
-    e = launch_bwd<PT, R>(P, L, c, c == 0 ? fin_last : FIN_NONE);
+    e = launch_bwd<PT>(P, L, c, c == 0 ? fin_last : FIN_NONE);
     if (h) h(u, PH_BWD, 0);
   }
   return e;
 }
 
-template <typename ZT, int R, int MODE>
+template <int MODE>
 cudaError_t launch_spmv(const Params &P, const Plan &L) {
-  return launch(spmv_kernel<ZT, R, MODE>, L.grid_a, L.W * kWarp, L.smem_a, L, P, P.cap_a);
-}
-
-template <typename F>
-cudaError_t by_R(int R, F &&f) {
-  switch (R) {
-    case 1: return f(std::integral_constant<int, 1>());
-    case 2: return f(std::integral_constant<int, 2>());
-    case 4: return f(std::integral_constant<int, 4>());
-    default: return cudaErrorInvalidValue;
-  }
+  return launch(spmv_kernel<MODE>, L.grid_a, L.Wa * kWarp, L.smem_a, L, P, P.cap_a);
 }
 
 template <typename K>
@@ -760,32 +774,28 @@ cudaError_t allow_smem(K kernel) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
 }
 
-template <typename PT, int R>
-cudaError_t configure_pr() {
+template <typename PT>
+cudaError_t configure_pt() {
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = allow_smem(color_kernel<PT, R, M_FUSED, true>);
-  if (e == cudaSuccess) e = allow_smem(color_kernel<PT, R, M_FWD, true>);
-  if (e == cudaSuccess) e = allow_smem(color_kernel<PT, R, M_FUSED, false>);
-  if (e == cudaSuccess) e = allow_smem(color_kernel<PT, R, M_FWD, false>);
-  if (e == cudaSuccess) e = allow_smem(color_kernel<PT, R, M_BWD, false>);
-  if (e == cudaSuccess) e = allow_smem(spmv_kernel<PT, R, 0>);
-  if (e == cudaSuccess) e = allow_smem(spmv_kernel<PT, R, 1>);
-  if (e == cudaSuccess) e = allow_smem(spmv_kernel<PT, R, 2>);
+  if (e == cudaSuccess) e = allow_smem(color_kernel<PT, M_FUSED, true>);
+  if (e == cudaSuccess) e = allow_smem(color_kernel<PT, M_FWD, true>);
+  if (e == cudaSuccess) e = allow_smem(color_kernel<PT, M_FUSED, false>);
+  if (e == cudaSuccess) e = allow_smem(color_kernel<PT, M_FWD, false>);
+  if (e == cudaSuccess) e = allow_smem(color_kernel<PT, M_BWD, false>);
   return e;
 }
 
 }  // namespace
 
-int warp_smem_bytes(int cap, int R, int elem) { return warp_bytes1(cap, R, elem); }
+int group_smem_bytes(int cap, int rows, int levs, int elem) { return group_smem_plan(cap, rows, levs, elem).total; }
+int spmv_smem_bytes(int cap) { return r16((cap + 8) * 8) + r16((cap + 8) * 4); }
 
 cudaError_t configure_kernels() {
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = configure_pr<double, 1>();
-  if (e == cudaSuccess) e = configure_pr<double, 2>();
-  if (e == cudaSuccess) e = configure_pr<double, 4>();
-  if (e == cudaSuccess) e = configure_pr<float, 1>();
-  if (e == cudaSuccess) e = configure_pr<float, 2>();
-  if (e == cudaSuccess) e = configure_pr<float, 4>();
+  cudaError_t e = configure_pt<double>();
+  if (e == cudaSuccess) e = configure_pt<float>();
+  if (e == cudaSuccess) e = allow_smem(spmv_kernel<0>);
+  if (e == cudaSuccess) e = allow_smem(spmv_kernel<1>);
+  if (e == cudaSuccess) e = allow_smem(spmv_kernel<2>);
   return e;
 }
 
@@ -810,26 +820,23 @@ cudaError_t launch_solve_init(const Params &P, const Plan &L, bool fp32, PhaseHo
     perm_in_kernel<<<L.grid_v, kVecThreads, 0, L.stream>>>(P);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess)
-    e = by_R(L.R, [&](auto RC) { return launch_spmv<double, decltype(RC)::value, 1>(P, L); });
+  if (e == cudaSuccess) e = launch_spmv<1>(P, L);
   if (h) h(u, PH_INIT, 0);
   if (e != cudaSuccess) return e;
   if (h) h(u, PH_INIT, 1);
-  if (fp32) e = by_R(L.R, [&](auto RC) { return sweep<float, decltype(RC)::value>(P, L, false, FIN_INIT, nullptr, nullptr); });
-  else e = by_R(L.R, [&](auto RC) { return sweep<double, decltype(RC)::value>(P, L, false, FIN_INIT, nullptr, nullptr); });
+  e = fp32 ? sweep<float>(P, L, false, FIN_INIT, nullptr, nullptr) : sweep<double>(P, L, false, FIN_INIT, nullptr, nullptr);
   if (h) h(u, PH_INIT, 0);
   return e;
 }
 
 cudaError_t launch_solve_body(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u) {
-  cudaError_t e;
   if (h) h(u, PH_SPMV, 1);
-  if (fp32) e = by_R(L.R, [&](auto RC) { return launch_spmv<float, decltype(RC)::value, 0>(P, L); });
-  else e = by_R(L.R, [&](auto RC) { return launch_spmv<double, decltype(RC)::value, 0>(P, L); });
+  cudaError_t e = fp32 ? launch(pupdate_kernel<float>, L.grid_v, kVecThreads, 0, L, P)
+                       : launch(pupdate_kernel<double>, L.grid_v, kVecThreads, 0, L, P);
+  if (e == cudaSuccess) e = launch_spmv<0>(P, L);
   if (h) h(u, PH_SPMV, 0);
   if (e != cudaSuccess) return e;
-  if (fp32) return by_R(L.R, [&](auto RC) { return sweep<float, decltype(RC)::value>(P, L, true, FIN_ITER, h, u); });
-  return by_R(L.R, [&](auto RC) { return sweep<double, decltype(RC)::value>(P, L, true, FIN_ITER, h, u); });
+  return fp32 ? sweep<float>(P, L, true, FIN_ITER, h, u) : sweep<double>(P, L, true, FIN_ITER, h, u);
 }
 
 cudaError_t launch_solve_final(const Params &P, const Plan &L) {
@@ -838,13 +845,10 @@ cudaError_t launch_solve_final(const Params &P, const Plan &L) {
 }
 
 cudaError_t launch_precond(const Params &P, const Plan &L, bool fp32) {
-  if (fp32) return by_R(L.R, [&](auto RC) { return sweep<float, decltype(RC)::value>(P, L, false, FIN_NONE, nullptr, nullptr); });
-  return by_R(L.R, [&](auto RC) { return sweep<double, decltype(RC)::value>(P, L, false, FIN_NONE, nullptr, nullptr); });
+  return fp32 ? sweep<float>(P, L, false, FIN_NONE, nullptr, nullptr) : sweep<double>(P, L, false, FIN_NONE, nullptr, nullptr);
 }
 
-cudaError_t launch_spmv_plain(const Params &P, const Plan &L) {
-  return by_R(L.R, [&](auto RC) { return launch_spmv<double, decltype(RC)::value, 2>(P, L); });
-}
+cudaError_t launch_spmv_plain(const Params &P, const Plan &L) { return launch_spmv<2>(P, L); }
 
 cudaError_t launch_permute(const double *src, double *dst, const int32_t *perm, int32_t n, bool gather,
                            int32_t grid, cudaStream_t s) {

@@ -183,7 +183,7 @@ def iccg_profile_solve(ctx, b, x, tol=1e-8, maxit=10000):
     return st, it.value, dict(zip(PHASES, ms.tolist())), dict(zip(PHASES, ln.tolist()))
 
 
-INFO_KEYS = ("n", "nnz", "n_b", "n_c", "tiles", "tasks", "nL", "max_rounds", "max_task_rows")
+INFO_KEYS = ("n", "nnz", "n_b", "n_c", "groups", "global_groups", "nL", "max_levels", "max_group_rows")
 
 
 def iccg_info(ctx):
