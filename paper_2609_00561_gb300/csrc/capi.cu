@@ -242,10 +242,23 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     L.grid_c[c] = std::max(1, L.task1[c] - L.task0[c]);
     gbig = std::max(gbig, L.grid_c[c]);
   }
+  // slot regions: forward launches in color order (<r,r>), then the fused
+  // launch and the backward launches in launch order (<r,z>); the final
+  // launch (backward color 0, or the fused launch of a one-color ordering)
+  // sums everything written before its own region
+  L.off_rr.assign(n_c, 0);
+  L.off_rz.assign(n_c, 0);
+  int32_t nslot = 0;
+  for (int c = 0; c < n_c; ++c) { L.off_rr[c] = nslot; nslot += L.grid_c[c]; }
+  int32_t orz = 0;
+  if (n_c > 0) { L.off_rz[n_c - 1] = orz; orz += L.grid_c[n_c - 1]; }
+  for (int c = n_c - 2; c >= 0; --c) { L.off_rz[c] = orz; orz += L.grid_c[c]; }
+  L.last_rr = n_c > 1 ? nslot : 0;
+  L.last_rz = n_c > 1 ? L.off_rz[0] : 0;
   const int ntile_a = (n + 31) / 32;
-  L.grid_a = std::max(1, (ntile_a + Wa - 1) / Wa);
+  const int a_full = sms * spmv_resident_ctas(Wa, L.smem_a);
+  L.grid_a = std::max(1, std::min(a_full, (ntile_a + Wa - 1) / Wa));
   L.grid_v = std::max(1, std::min((n + 255) / 256, sms * 8));
-  gbig = std::max(gbig, L.grid_a);
 
   // device arrays
   Params &P = ctx->P;
@@ -303,14 +316,18 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   // reduction slots: one per CTA of the widest launch, doubled so the solve
   // start can keep <b,b> and <r0,r0> partials side by side; kept even for
   // 16-byte loads
+  P.nslot = std::max(nslot, 1);
   P.npart = gbig;
   P.ngroup = (gbig + kGroup - 1) / kGroup;
+  P.npart_a = L.grid_a;
   P.nbb = L.grid_v;
+  CK(dev_alloc(ctx, &P.slot_rr, size_t(P.nslot)), "alloc reductions");
+  CK(dev_alloc(ctx, &P.slot_rz, size_t(P.nslot)), "alloc reductions");
   CK(dev_alloc(ctx, &P.part0, size_t(P.npart)), "alloc reductions");
   CK(dev_alloc(ctx, &P.part1, size_t(P.npart)), "alloc reductions");
-  CK(dev_alloc(ctx, &P.acc_rr, size_t(P.ngroup)), "alloc reductions");
-  CK(dev_alloc(ctx, &P.acc_rz, size_t(P.ngroup)), "alloc reductions");
-  CK(dev_alloc(ctx, &P.gpq, size_t(P.ngroup)), "alloc reductions");
+  CK(dev_alloc(ctx, &P.gsum0, size_t(P.ngroup)), "alloc reductions");
+  CK(dev_alloc(ctx, &P.gsum1, size_t(P.ngroup)), "alloc reductions");
+  CK(dev_alloc(ctx, &P.part_a, size_t(P.npart_a)), "alloc reductions");
   CK(dev_alloc(ctx, &P.init_bb, size_t(P.nbb)), "alloc reductions");
   CK(dev_alloc(ctx, &P.gticket, size_t(P.ngroup)), "alloc reductions");
   CK(dev_alloc(ctx, &P.sc, 1), "alloc scalars");

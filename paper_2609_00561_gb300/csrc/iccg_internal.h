@@ -77,16 +77,20 @@ struct Params {
   const double *bin, *xin;      // original-order inputs
   double *xout;                 // original-order output
   const int32_t *perm;
-  // reductions, two levels: every CTA writes its partials to part0 / part1;
-  // the last CTA of each group of kGroup CTAs sums the group's partials in
-  // index order and adds them to the group's slot of acc_rr / acc_rz (carried
-  // across the launches of one iteration) or writes gpq; the last group of the
-  // launch runs the epilogue.  init_bb holds <b,b> partials of the solve start.
+  // reductions.  Every color launch stores one <r,r> and/or <r,z> partial
+  // per CTA into slot_rr / slot_rz (its own region, plain stores); the last
+  // launch of an iteration sums all slots: each of its CTAs sums a fixed chunk
+  // of the earlier launches' slots plus its own partial into part0 / part1,
+  // the last CTA of each group of kGroup CTAs sums its group into gsum0 /
+  // gsum1, and the last group runs the epilogue.  The SpMV stores one <p,q>
+  // partial per CTA in part_a; its last CTA sums them.  init_bb / part_a hold
+  // <b,b> and <r0,r0> partials at the solve start.
+  double *slot_rr, *slot_rz;    // [nslot]
   double *part0, *part1;        // [npart]
-  double *acc_rr, *acc_rz, *gpq;// [ngroup]
-  double *init_bb;              // [nbb]
+  double *gsum0, *gsum1;        // [ngroup]
+  double *part_a, *init_bb;     // [npart_a], [nbb]
   uint32_t *gticket;            // [ngroup] group arrival counters
-  int32_t npart, ngroup, nbb;
+  int32_t nslot, npart, ngroup, npart_a, nbb;
   Scalars *sc;
   double *hist;
   unsigned long long *err_row;  // IC(0) breakdown row (new numbering), ~0 = none
@@ -125,6 +129,8 @@ struct Plan {
   int32_t Wa = 4;                       // warps per CTA of the SpMV
   std::vector<int32_t> task0, task1;    // group range of each color
   std::vector<int32_t> grid_c;          // CTAs of the color-c kernels
+  std::vector<int32_t> off_rr, off_rz;  // slot regions of the color-c forward / backward launches
+  int32_t last_rr = 0, last_rz = 0;     // slots written before the final launch of an iteration
   int32_t grid_a = 0;                   // CTAs of the SpMV-shaped kernels
   int32_t grid_v = 0;                   // CTAs of the vector kernels
   int32_t smem_fwd = 0, smem_bwd = 0, smem_fused = 0, smem_a = 0;  // bytes per CTA
@@ -138,6 +144,7 @@ typedef void (*PhaseHook)(void *user, int phase, int begin);
 cudaError_t configure_kernels();
 int group_smem_bytes(int cap, int rows, int levs, int elem);  // per-warp plan of the color kernels
 int spmv_smem_bytes(int cap);                                // per-warp staging of the SpMV
+int spmv_resident_ctas(int Wa, int smem);                    // CTAs per SM of the SpMV
 cudaError_t launch_factor(const Params &P, const Plan &L, int nL);
 cudaError_t launch_solve_init(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);
 cudaError_t launch_solve_body(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);

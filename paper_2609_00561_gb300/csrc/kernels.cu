@@ -403,9 +403,8 @@ __device__ void set_condition(const Scalars *s, int keep_going) {
 }
 
 // After the backward sweep of iteration k: residual history, stop test, beta.
-__device__ void finish_iteration(const Params &P, double *red) {
-  const double rr = cta_sum_array(P.acc_rr, P.ngroup, red, true);
-  const double rz = cta_sum_array(P.acc_rz, P.ngroup, red, true);
+// rr, rz valid in thread 0.
+__device__ void finish_iteration(const Params &P, double rr, double rz) {
   if (threadIdx.x == 0) {
     Scalars *s = P.sc;
     const int k = s->iter;
@@ -424,12 +423,11 @@ __device__ void finish_iteration(const Params &P, double *red) {
 }
 
 // After r0 = b - A x0 and z0 = M^-1 r0: ||b||, history[0], stop test.
-// init_bb holds <b,b> partials, gpq the <r0,r0> group sums.
-__device__ void finish_init(const Params &P, double *red) {
-  const double bb = cta_sum_array(P.init_bb, P.nbb, red, true);
-  const double rr = cta_sum_array(P.gpq, P.ngroup, red, true);
-  const double rz = cta_sum_array(P.acc_rz, P.ngroup, red, true);
-  cta_sum_array(P.acc_rr, P.ngroup, red, true);
+// init_bb holds <b,b> partials, part_a the <r0,r0> partials; rz valid in
+// thread 0.
+__device__ void finish_init(const Params &P, double rz, double *red) {
+  const double bb = cta_sum_array(P.init_bb, P.nbb, red, false);
+  const double rr = cta_sum_array(P.part_a, P.npart_a, red, false);
   if (threadIdx.x == 0) {
     Scalars *s = P.sc;
     const double bn = sqrt(bb);
@@ -460,9 +458,14 @@ enum Fin { FIN_NONE = 0, FIN_ITER = 1, FIN_INIT = 2 };
 // color kernel: MODE = forward sweep of one color, backward sweep of one
 // color, or both for the last color (fused); one CTA per group
 // ---------------------------------------------------------------------------
+struct SlotArgs {
+  int off_rr, off_rz;     // this launch's slot regions
+  int last_rr, last_rz;   // slots of earlier launches (final launch only)
+};
+
 template <typename PT, int MODE, bool UPDATE>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
-color_kernel(Params P, int g0, int g1, GroupSmemPlan plan, int fin) {
+color_kernel(Params P, int g0, int g1, GroupSmemPlan plan, int fin, SlotArgs sa) {
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[kMaxWarpsPerCta];
@@ -499,26 +502,46 @@ color_kernel(Params P, int g0, int g1, GroupSmemPlan plan, int fin) {
   } else {
     pdl_wait();
   }
-  if (MODE == M_FWD && !UPDATE) return;
-  const bool two = MODE == M_FUSED && UPDATE;
-  const double a = MODE == M_BWD ? rz_acc : (MODE == M_FUSED && !UPDATE ? rz_acc : rr_acc);
-  const double b = rz_acc;
-  double ga, gb;
-  if (group_reduce(P, cta_sum(a, red), two ? cta_sum(b, red) : 0.0, two, red, &flag, ga, gb)) {
+  const bool has_rr = MODE != M_BWD && UPDATE, has_rz = MODE != M_FWD;
+  if (!has_rr && !has_rz) return;
+  const double rr_c = has_rr ? cta_sum(rr_acc, red) : 0.0;
+  const double rz_c = has_rz ? cta_sum(rz_acc, red) : 0.0;
+  if (fin == FIN_NONE) {
+    // one partial per CTA, plain stores: the iteration's last launch sums them
     if (threadIdx.x == 0) {
-      // slot gg was last written by an earlier launch on another SM: read it
-      // from L2, not from this SM's L1
-      const int gg = blockIdx.x / kGroup;
-      if (MODE == M_FWD) P.acc_rr[gg] = __ldcg(P.acc_rr + gg) + ga;
-      else if (MODE == M_BWD || !UPDATE) P.acc_rz[gg] = __ldcg(P.acc_rz + gg) + ga;
-      else {
-        P.acc_rr[gg] = __ldcg(P.acc_rr + gg) + ga;
-        P.acc_rz[gg] = __ldcg(P.acc_rz + gg) + gb;
-      }
+      if (has_rr) P.slot_rr[sa.off_rr + blockIdx.x] = rr_c;
+      if (has_rz) P.slot_rz[sa.off_rz + blockIdx.x] = rz_c;
     }
-    if (fin != FIN_NONE && launch_last(P, &flag)) {
-      if (fin == FIN_ITER) finish_iteration(P, red);
-      else finish_init(P, red);
+    return;
+  }
+  // The last launch of the iteration: every CTA sums a fixed chunk of the
+  // earlier launches' slots (complete: griddepcontrol.wait above) plus its own
+  // partial; then groups of CTAs, then the last group runs the epilogue.
+  const int nb = gridDim.x;
+  const int crr = (sa.last_rr + nb - 1) / nb, crz = (sa.last_rz + nb - 1) / nb;
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < crr; k += blockDim.x) {
+    const int idx = blockIdx.x * crr + k;
+    if (idx < sa.last_rr) a += __ldcg(P.slot_rr + idx);
+  }
+  for (int k = threadIdx.x; k < crz; k += blockDim.x) {
+    const int idx = blockIdx.x * crz + k;
+    if (idx < sa.last_rz) b += __ldcg(P.slot_rz + idx);
+  }
+  a = cta_sum(a, red);
+  b = cta_sum(b, red);
+  double ga, gb;
+  if (group_reduce(P, a + rr_c, b + rz_c, true, red, &flag, ga, gb)) {
+    if (threadIdx.x == 0) {
+      P.gsum0[blockIdx.x / kGroup] = ga;
+      P.gsum1[blockIdx.x / kGroup] = gb;
+    }
+    if (launch_last(P, &flag)) {
+      const int ng = (nb + kGroup - 1) / kGroup;
+      const double rr = cta_sum_array(P.gsum0, ng, red, false);
+      const double rz = cta_sum_array(P.gsum1, ng, red, false);
+      if (fin == FIN_ITER) finish_iteration(P, rr, rz);
+      else finish_init(P, rz, red);
     }
   }
 }
@@ -537,10 +560,12 @@ __global__ void __launch_bounds__(kVecThreads) pupdate_kernel(Params P) {
 }
 
 // ---------------------------------------------------------------------------
-// SpMV over 32-row tiles of A_hat, one warp per tile, one row per lane
+// SpMV over 32-row tiles of A_hat, one row per lane; a full-occupancy grid
+// walks the tiles grid-stride (each warp one tile at a time: the resident
+// warps keep enough loads in flight)
 // ---------------------------------------------------------------------------
-// mode 0: q = A p, <p, q>; last group: alpha = rz / pq
-// mode 1: r = b_hat - A x_hat, <r, r> group sums into gpq (solve start)
+// mode 0: q = A p, <p, q>; the last CTA sets alpha = rz / pq
+// mode 1: r = b_hat - A x_hat, <r, r> partials in part_a (solve start)
 // mode 2: q = A x_hat (plain SpMV)
 template <int MODE>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
@@ -552,10 +577,12 @@ spmv_kernel(Params P, int cap) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   double *sv = reinterpret_cast<double *>(smem + warp * (r16((cap + 8) * 8) + r16((cap + 8) * 4)));
   int32_t *sc = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(sv) + r16((cap + 8) * 8));
-  const int t0 = (blockIdx.x * W + warp) * kWarp;
+  const int ntile = (P.n + kWarp - 1) / kWarp;
+  const double *xin = MODE == 0 ? P.p0 : P.xh;
   double acc = 0.0;
-  if (t0 < P.n) {
-    const int t1 = min(P.n, t0 + kWarp);
+  bool waited = false;
+  for (int tile = blockIdx.x * W + warp; tile < ntile; tile += gridDim.x * W) {
+    const int t0 = tile * kWarp, t1 = min(P.n, t0 + kWarp);
     const int i = t0 + lane;
     const int rb = i < t1 ? __ldg(P.arp + i) : 0;
     const int re = i < t1 ? __ldg(P.arp + i + 1) : 0;
@@ -572,34 +599,34 @@ spmv_kernel(Params P, int cap) {
     cp_commit();
     cp_wait_all();
     __syncwarp();
-    pdl_wait();
+    if (!waited) {
+      pdl_wait();
+      waited = true;
+    }
     if (i < t1) {
-      const double *xin = MODE == 0 ? P.p0 : P.xh;
       const double s = -row_sub<double, double>(S, rb, re, 0.0, [&](int c) { return xin[c]; });
       if (MODE == 0) {
         P.q[i] = s;
-        acc = xin[i] * s;
+        acc += xin[i] * s;
       } else if (MODE == 1) {
         const double ri = P.bh[i] - s;
         P.r[i] = ri;
-        acc = ri * ri;
+        acc += ri * ri;
       } else {
         P.q[i] = s;
       }
     }
-  } else {
-    pdl_wait();
+    __syncwarp();
   }
+  if (!waited) pdl_wait();
   if (MODE == 2) return;
-  double ga, gb;
-  if (group_reduce(P, cta_sum(acc, red), 0.0, false, red, &flag, ga, gb)) {
-    if (threadIdx.x == 0) P.gpq[blockIdx.x / kGroup] = ga;
-    if (MODE == 0 && launch_last(P, &flag)) {
-      const double pq = cta_sum_array(P.gpq, P.ngroup, red, true);
-      if (threadIdx.x == 0) {
-        P.sc->pq = pq;
-        P.sc->alpha = P.sc->rz / pq;
-      }
+  const double tot = cta_sum(acc, red);
+  if (threadIdx.x == 0) P.part_a[blockIdx.x] = tot;
+  if (MODE == 0 && arrive_last(&P.sc->ticket, gridDim.x, &flag)) {
+    const double pq = cta_sum_array(P.part_a, gridDim.x, red, false);
+    if (threadIdx.x == 0) {
+      P.sc->pq = pq;
+      P.sc->alpha = __ldcg(&P.sc->rz) / pq;
     }
   }
 }
@@ -723,19 +750,24 @@ cudaError_t launch_fwd(const Params &P, const Plan &L, int c, bool update, bool 
   const GroupSmemPlan pl = plan_of<PT>(P, fused, false);
   const int smem = pl.total;
   const int g = L.grid_c[c], t0 = L.task0[c], t1 = L.task1[c];
+  // a final fused launch (one color) has no earlier slots
+  const SlotArgs sa{L.off_rr[c], L.off_rz[c], 0, 0};
   if (update) {
-    if (fused) return launch(color_kernel<PT, M_FUSED, true>, g, threads, smem, L, P, t0, t1, pl, fin);
-    return launch(color_kernel<PT, M_FWD, true>, g, threads, smem, L, P, t0, t1, pl, fin);
+    if (fused) return launch(color_kernel<PT, M_FUSED, true>, g, threads, smem, L, P, t0, t1, pl, fin, sa);
+    return launch(color_kernel<PT, M_FWD, true>, g, threads, smem, L, P, t0, t1, pl, fin, sa);
   }
-  if (fused) return launch(color_kernel<PT, M_FUSED, false>, g, threads, smem, L, P, t0, t1, pl, fin);
-  return launch(color_kernel<PT, M_FWD, false>, g, threads, smem, L, P, t0, t1, pl, fin);
+  if (fused) return launch(color_kernel<PT, M_FUSED, false>, g, threads, smem, L, P, t0, t1, pl, fin, sa);
+  return launch(color_kernel<PT, M_FWD, false>, g, threads, smem, L, P, t0, t1, pl, fin, sa);
 }
 
 template <typename PT>
 cudaError_t launch_bwd(const Params &P, const Plan &L, int c, int fin) {
   const GroupSmemPlan pl = plan_of<PT>(P, false, true);
+  // the final backward launch sums the <r,r> slots only in an iteration (the
+  // solve start has no x / r update)
+  const SlotArgs sa{0, L.off_rz[c], fin == FIN_ITER ? L.last_rr : 0, L.last_rz};
   return launch(color_kernel<PT, M_BWD, false>, L.grid_c[c], L.W * kWarp, pl.total, L, P, L.task0[c],
-                L.task1[c], pl, fin);
+                L.task1[c], pl, fin, sa);
 }
 
 // Forward sweep (with or without the x/r update), fused last color, backward
@@ -790,6 +822,15 @@ cudaError_t configure_pt() {
 int group_smem_bytes(int cap, int rows, int levs, int elem) { return group_smem_plan(cap, rows, levs, elem).total; }
 int spmv_smem_bytes(int cap) { return r16((cap + 8) * 8) + r16((cap + 8) * 4); }
 
+int spmv_resident_ctas(int Wa, int smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_kernel<0>, Wa * kWarp, size_t(smem)) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
 cudaError_t configure_kernels() {
   cudaError_t e = configure_pt<double>();
   if (e == cudaSuccess) e = configure_pt<float>();
@@ -811,10 +852,7 @@ cudaError_t launch_factor(const Params &P, const Plan &L, int nL) {
 
 cudaError_t launch_solve_init(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u) {
   if (h) h(u, PH_INIT, 1);
-  cudaError_t e = cudaMemsetAsync(P.acc_rr, 0, sizeof(double) * size_t(P.ngroup), L.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P.acc_rz, 0, sizeof(double) * size_t(P.ngroup), L.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P.gpq, 0, sizeof(double) * size_t(P.ngroup), L.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P.gticket, 0, sizeof(uint32_t) * size_t(P.ngroup), L.stream);
+  cudaError_t e = cudaMemsetAsync(P.gticket, 0, sizeof(uint32_t) * size_t(P.ngroup), L.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.p0, 0, sizeof(double) * size_t(P.n > 0 ? P.n : 1), L.stream);
   if (e == cudaSuccess) {
     perm_in_kernel<<<L.grid_v, kVecThreads, 0, L.stream>>>(P);
