@@ -52,16 +52,31 @@ typedef struct {
   int32_t precond_fp32;       /* 1: IC factors and substitutions stored and run in FP32
                                  with FP32 accumulation; IC(0) itself, the CG dots,
                                  alpha/beta and the x/r updates stay FP64 */
-  int32_t warps_per_cta;      /* warps per CTA of the per-color kernels; 0 = 4 */
-  int32_t rows_per_thread;    /* a warp's group holds up to 32 * rows_per_thread rows of
-                                 whole blocks; 1, 2, 4, 8, 16 or 32; 0 = 8 */
+  int32_t warps_per_cta;      /* warps per CTA of the substitution kernels; 1..16; 0 = 8 */
+  int32_t rows_per_thread;    /* a group (the work of one CTA) holds up to
+                                 32 * warps_per_cta * rows_per_thread rows of whole
+                                 blocks; 1, 2, 4, 8, 16 or 32; 0 = 1 */
   int32_t no_graph;           /* 1: drive the PCG loop from the host instead of a
                                  CUDA graph with a device-side WHILE condition */
   int32_t no_pdl;             /* 1: launch kernels without programmatic dependent
                                  launch (no overlap of a kernel's prologue with the
                                  tail of the previous one) */
-  int32_t reserved[3];        /* must be 0 */
+  int32_t solver;             /* ICCG_SOLVER_PHASED: one launch per phase (p update,
+                                 SpMV, each color), the PCG loop a CUDA graph;
+                                 ICCG_SOLVER_PERSISTENT: the whole solve in one
+                                 cooperative launch whose phases are separated by
+                                 grid barriers (groups only, no lane tiles);
+                                 ICCG_SOLVER_AUTO (0) = phased */
+  int32_t lane_block_max;     /* a color whose blocks all have at most this many rows
+                                 runs one block per lane of a warp (32 blocks per
+                                 warp, the block's rows in order); other colors run
+                                 one CTA per group of blocks, level by level; 1..32,
+                                 0 = 32, -1 = never (the persistent solver never
+                                 uses lanes) */
+  int32_t reserved[1];        /* must be 0 */
 } iccg_opts;
+
+enum { ICCG_SOLVER_AUTO = 0, ICCG_SOLVER_PERSISTENT = 1, ICCG_SOLVER_PHASED = 2 };
 
 /* ------------------------------------------------------------------------
  * iccg_setup -- Sec. 3: the block-multicolor ordering renumbers rows color
@@ -96,7 +111,7 @@ iccg_status iccg_setup(iccg_ctx **ctx, int32_t n, int64_t nnz,
  * (L L^T)_ij = a_hat_ij on it.  Runs on the device in FP64, color by color
  * like Alg. 1.  A pivot that is not positive (or not finite) returns
  * ICCG_ERR_BREAKDOWN; iccg_last_error gives the first such row in the
- * original numbering.  May be called again (e.g. after iccg_update_values).
+ * original numbering.  May be called again (recomputes the same factor).
  * ------------------------------------------------------------------------ */
 iccg_status iccg_factor(iccg_ctx *ctx);
 
@@ -115,7 +130,10 @@ iccg_status iccg_factor(iccg_ctx *ctx);
  *
  * b = 0 gives x = 0 and 0 iterations.  Returns ICCG_NOT_CONVERGED when maxit
  * is reached (x and history valid) and ICCG_ERR_NONFINITE on NaN/Inf.
- * Requires a successful iccg_factor.
+ * Requires a successful iccg_factor.  The persistent solver (the default
+ * where the device can hold all its CTAs at once) returns ICCG_ERR_TIMEOUT
+ * when a grid-barrier wait gave up (a phase longer than 4 s); the context
+ * stays usable and the phased solver (opts.solver) has no such limit.
  * ------------------------------------------------------------------------ */
 iccg_status iccg_solve(iccg_ctx *ctx, const double *b, double *x, double tol, int32_t maxit,
                        int32_t *iters, double *res_hist);
@@ -134,20 +152,23 @@ iccg_status iccg_spmv(iccg_ctx *ctx, const double *p, double *q);
  * lval = NULL to query it). */
 iccg_status iccg_get_factor(iccg_ctx *ctx, double *lval, int64_t *nnz_lower);
 
-/* Per-phase device time of one solve (CUDA events on the context's stream,
- * host-driven loop, one event pair around every kernel).  ms[6] receives the
- * summed milliseconds of: 0 init, 1 SpMV, 2 forward colors, 3 fused last
- * color, 4 backward colors, 5 everything (first to last event); launches[6]
- * the kernel launch counts.  Same arguments and results as iccg_solve. */
+/* Per-phase device time of one solve.  ms[6] receives the summed
+ * milliseconds of: 0 init, 1 p update + SpMV, 2 forward colors, 3 fused last
+ * color, 4 backward colors (with the closing reduction), 5 everything (CUDA
+ * events around the solve); launches[6] the number of kernel launches (phased
+ * solver: host-driven loop, one event pair around every kernel) or of grid
+ * barriers (persistent solver: the time each barrier is left, recorded on the
+ * device).  Same arguments and results as iccg_solve. */
 iccg_status iccg_profile_solve(iccg_ctx *ctx, const double *b, double *x, double tol,
                                int32_t maxit, int32_t *iters, double *ms, int64_t *launches);
 
-/* Layout facts of a context, out[9]: n, nnz, n_b, n_c, number of groups (a
- * group = consecutive whole blocks of one color, at most 32 * rows_per_thread
- * rows, or one larger block; one warp each), number of groups too large for
- * the shared-memory plan, strictly-lower entries nL, deepest in-block level
- * count, largest group (rows). */
-iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[9]);
+/* Layout facts of a context, out[11]: n, nnz, n_b, n_c, number of groups (a
+ * group = consecutive whole blocks of one color, at most 32 * warps_per_cta *
+ * rows_per_thread rows, or one larger block; one CTA each), number of groups
+ * too large for the shared-memory plan, strictly-lower entries nL, deepest
+ * in-group level count, largest group (rows), number of lane tiles (32
+ * blocks, one warp each), number of colors run as lane tiles. */
+iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[11]);
 
 iccg_status iccg_last_error(const iccg_ctx *ctx, int64_t *row_or_block, const char **msg);
 void iccg_destroy(iccg_ctx *ctx);

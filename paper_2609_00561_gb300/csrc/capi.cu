@@ -17,6 +17,7 @@ struct iccg_ctx {
   cudaStream_t stream = nullptr;
   iccg_opts opts{};
   bool fp32 = false;
+  bool persistent = false;         // the whole solve as one cooperative launch
   HostLayout H;
   Plan plan;
   Params P{};
@@ -152,8 +153,9 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   if (!rowptr || (n > 0 && (!colind || !val || !perm || !block_ptr || !color_ptr))) return ICCG_ERR_ARG;
   iccg_opts o{};
   if (opts) o = *opts;
-  for (int k = 0; k < 3; ++k)
-    if (o.reserved[k] != 0) return ICCG_ERR_ARG;
+  if (o.reserved[0] != 0) return ICCG_ERR_ARG;
+  if (o.lane_block_max > 32 || o.lane_block_max < -1) return ICCG_ERR_ARG;
+  if (o.solver < ICCG_SOLVER_AUTO || o.solver > ICCG_SOLVER_PHASED) return ICCG_ERR_ARG;
   if (o.warps_per_cta == 0) o.warps_per_cta = 8;
   if (o.rows_per_thread == 0) o.rows_per_thread = 1;
   if (o.warps_per_cta < 1 || o.warps_per_cta > kMaxWarpsPerCta) return ICCG_ERR_ARG;
@@ -183,8 +185,11 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   if (n == 0) { hbp.assign(1, 0); hcp.assign(1, 0); }
   const int R = o.rows_per_thread, W = o.warps_per_cta;
   const int G = 32 * W * R;   // rows of a group (one CTA of W warps)
+  // lane tiles for colors of small blocks; the persistent kernel runs groups only
+  const int lane_max = o.solver == ICCG_SOLVER_PERSISTENT || o.lane_block_max < 0 ? 0
+                       : (o.lane_block_max == 0 ? 32 : o.lane_block_max);
   iccg_status st = build_layout(n, nnz, hrp.data(), hci.data(), hval.data(), hperm.data(), hbp.data(),
-                                hcp.data(), n_b, n_c, G, ctx->H, ctx->err_index, ctx->err_msg);
+                                hcp.data(), n_b, n_c, G, lane_max, ctx->H, ctx->err_index, ctx->err_msg);
   if (st != ICCG_OK) return st;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaGetDevice");
   {
@@ -232,14 +237,24 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   L.smem_fused = group_smem_bytes(std::max(cap_l, cap_u), cap_rows, cap_lev, elem);
   L.smem_a = Wa * spmv_smem_bytes(cap_a);
   // one CTA per group (color kernels), one warp per 32-row tile (SpMV)
+  // (a lane-tile color: Wt tiles per CTA)
   L.grid_c.assign(n_c, 0);
   L.task0.assign(n_c, 0);
   L.task1.assign(n_c, 0);
+  L.tile0.assign(n_c, 0);
+  L.tile1.assign(n_c, 0);
+  // lane tiles: one CTA of up to 8 warps per tile (steps shared out in phases
+  // A and C)
+  L.Wt = std::max(1, std::min(8, H.lane_max));
+  L.smem_tile = tile_smem_bytes(std::max(H.lane_max, 1), H.wi_max, elem);
   int32_t gbig = 1;
   for (int c = 0; c < n_c; ++c) {
     L.task0[c] = H.color_group[c];
     L.task1[c] = H.color_group[c + 1];
-    L.grid_c[c] = std::max(1, L.task1[c] - L.task0[c]);
+    L.tile0[c] = H.color_tile[c];
+    L.tile1[c] = H.color_tile[c + 1];
+    const int nt = L.tile1[c] - L.tile0[c];
+    L.grid_c[c] = nt > 0 ? nt : std::max(1, L.task1[c] - L.task0[c]);
     gbig = std::max(gbig, L.grid_c[c]);
   }
   // slot regions: forward launches in color order (<r,r>), then the fused
@@ -265,6 +280,21 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   P.n = n; P.R = R; P.W = Wc; P.n_c = n_c;
   P.cap_l = cap_l; P.cap_u = cap_u; P.cap_a = cap_a;
   P.cap_rows = cap_rows; P.cap_lev = cap_lev;
+  // persistent kernel: as many CTAs as fit on the device at once (cooperative
+  // launch), but no more than the widest phase can use
+  {
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+    L.smem_p = persistent_smem_bytes(P, ctx->fp32, Wc, kCtaSmemBudget, &L.cap_p);
+    const int per_sm = coop ? persistent_resident_ctas(ctx->fp32, Wc, L.smem_p) : 0;
+    const int widest = std::max(gbig, (ntile_a + Wc - 1) / Wc);
+    L.grid_p = per_sm > 0 ? std::max(1, std::min(sms * per_sm, widest)) : 0;
+    if (o.solver == ICCG_SOLVER_PERSISTENT && L.grid_p == 0) {
+      ctx->err_msg = "the persistent solve kernel cannot be made resident on this device";
+      return ICCG_ERR_ARG;
+    }
+    ctx->persistent = o.solver == ICCG_SOLVER_PERSISTENT;
+  }
   int32_t *d_arp, *d_acol, *d_lrp, *d_lcol, *d_urp, *d_ucol, *d_umap, *d_perm, *d_sf, *d_sb, *d_levp;
   GroupDesc *d_groups;
   double *d_aval, *d_ainit, *d_adiag;
@@ -283,6 +313,42 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   CK(dev_upload(ctx, &d_sb, H.sched_b), "alloc groups");
   CK(dev_upload(ctx, &d_levp, H.levp), "alloc groups");
   CK(dev_upload(ctx, &d_perm, H.perm), "alloc perm");
+  int32_t *d_cg;
+  CK(dev_upload(ctx, &d_cg, H.color_group), "alloc groups");
+  P.color_group = d_cg;
+  {
+    TileDesc *d_tiles;
+    StepDesc *d_steps;
+    int32_t *d_slc, *d_suc, *d_slm, *d_sum, *d_sic, *d_uic, *d_sim, *d_uim;
+    CK(dev_upload(ctx, &d_tiles, H.tiles), "alloc tiles");
+    CK(dev_upload(ctx, &d_steps, H.steps), "alloc tiles");
+    CK(dev_upload(ctx, &d_slc, H.sl_col), "alloc tiles");
+    CK(dev_upload(ctx, &d_suc, H.su_col), "alloc tiles");
+    CK(dev_upload(ctx, &d_slm, H.sl_map), "alloc tiles");
+    CK(dev_upload(ctx, &d_sum, H.su_map), "alloc tiles");
+    CK(dev_upload(ctx, &d_sic, H.si_col), "alloc tiles");
+    CK(dev_upload(ctx, &d_uic, H.ui_col), "alloc tiles");
+    CK(dev_upload(ctx, &d_sim, H.si_map), "alloc tiles");
+    CK(dev_upload(ctx, &d_uim, H.ui_map), "alloc tiles");
+    P.tiles = d_tiles; P.steps = d_steps;
+    P.sl_col = d_slc; P.su_col = d_suc; P.sl_map = d_slm; P.su_map = d_sum;
+    P.si_col = d_sic; P.ui_col = d_uic; P.si_map = d_sim; P.ui_map = d_uim;
+    P.nsl = int32_t(H.sl_col.size());
+    P.nsu = int32_t(H.su_col.size());
+    P.nsi = int32_t(H.si_col.size());
+    P.nui = int32_t(H.ui_col.size());
+    P.lane_max = std::max(H.lane_max, 1);
+    P.wi_max = H.wi_max;
+    CK(dev_alloc(ctx, &P.sl_val, H.sl_col.size()), "alloc tiles");
+    CK(dev_alloc(ctx, &P.su_val, H.su_col.size()), "alloc tiles");
+    CK(dev_alloc(ctx, &P.si_val, H.si_col.size()), "alloc tiles");
+    CK(dev_alloc(ctx, &P.ui_val, H.ui_col.size()), "alloc tiles");
+    CK(dev_alloc(ctx, &P.sl_val32, H.sl_col.size()), "alloc tiles");
+    CK(dev_alloc(ctx, &P.su_val32, H.su_col.size()), "alloc tiles");
+    CK(dev_alloc(ctx, &P.si_val32, H.si_col.size()), "alloc tiles");
+    CK(dev_alloc(ctx, &P.ui_val32, H.ui_col.size()), "alloc tiles");
+  }
+  CK(dev_alloc(ctx, &P.bar, 1), "alloc barrier");
   P.arp = d_arp; P.acol = d_acol; P.aval = d_aval;
   P.lrp = d_lrp; P.lcol = d_lcol; P.urp = d_urp; P.ucol = d_ucol; P.umap = d_umap;
   P.ainit = d_ainit; P.adiag = d_adiag;
@@ -317,10 +383,10 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   // start can keep <b,b> and <r0,r0> partials side by side; kept even for
   // 16-byte loads
   P.nslot = std::max(nslot, 1);
-  P.npart = gbig;
+  P.npart = std::max(gbig, L.grid_p);
   P.ngroup = (gbig + kGroup - 1) / kGroup;
   P.npart_a = L.grid_a;
-  P.nbb = L.grid_v;
+  P.nbb = std::max(L.grid_v, L.grid_p);
   CK(dev_alloc(ctx, &P.slot_rr, size_t(P.nslot)), "alloc reductions");
   CK(dev_alloc(ctx, &P.slot_rz, size_t(P.nslot)), "alloc reductions");
   CK(dev_alloc(ctx, &P.part0, size_t(P.npart)), "alloc reductions");
@@ -467,7 +533,8 @@ static iccg_status solve_impl(iccg_ctx *ctx, const double *b, double *x, double 
   iccg_status st = ensure_hist(ctx, maxit);
   if (st != ICCG_OK) return st;
   cudaStream_t s = ctx->stream;
-  const bool use_graph = ctx->opts.no_graph == 0 && prof == nullptr;
+  const bool persistent = ctx->persistent && prof == nullptr;
+  const bool use_graph = !persistent && ctx->opts.no_graph == 0 && prof == nullptr;
   if (use_graph && !ctx->gexec) {
     st = build_graph(ctx);
     if (st != ICCG_OK) { destroy_graph(ctx); return st; }
@@ -482,7 +549,9 @@ static iccg_status solve_impl(iccg_ctx *ctx, const double *b, double *x, double 
   sh->cond_handle = ctx->cond_handle;
   sh->status = ICCG_NOT_CONVERGED;
   CK(cudaMemcpyAsync(ctx->P.sc, sh, sizeof(Scalars), cudaMemcpyHostToDevice, s), "scalars");
-  if (use_graph) {
+  if (persistent) {
+    CK(launch_solve_persistent(ctx->P, ctx->plan, ctx->fp32), "persistent launch");
+  } else if (use_graph) {
     CK(cudaGraphLaunch(ctx->gexec, s), "graph launch");
   } else {
     CK(launch_solve_init(ctx->P, ctx->plan, ctx->fp32, prof ? ProfileState::hook : nullptr, prof), "init");
@@ -499,6 +568,10 @@ static iccg_status solve_impl(iccg_ctx *ctx, const double *b, double *x, double 
   CK(cudaStreamSynchronize(s), "solve sync");
   const int32_t it = sh->iter;
   if (iters) *iters = it;
+  if (sh->status == ICCG_ERR_TIMEOUT) {
+    ctx->err_index = -1;
+    ctx->err_msg = "a grid-barrier wait of the persistent solve gave up";
+  }
   if (res_hist) {
     CK(cudaMemcpyAsync(ctx->hist_host, ctx->hist, sizeof(double) * size_t(it + 1), cudaMemcpyDeviceToHost, s), "history");
     CK(cudaStreamSynchronize(s), "history sync");
@@ -512,10 +585,71 @@ iccg_status iccg_solve(iccg_ctx *ctx, const double *b, double *x, double tol, in
   return solve_impl(ctx, b, x, tol, maxit, iters, res_hist, nullptr);
 }
 
+// Persistent solver: CTA 0 stamps the time it leaves every grid barrier with
+// the phase that barrier ends; a phase's time is the gap to the previous
+// stamp (the first phase counts from the kernel's start event).
+static iccg_status profile_persistent(iccg_ctx *ctx, const double *b, double *x, double tol, int32_t maxit,
+                                      int32_t *iters, double *ms, int64_t *launches) {
+  const int64_t cap64 = (int64_t(maxit) + 3) * (2 * int64_t(ctx->H.n_c) + 4) + 16;
+  if (cap64 > (int64_t(1) << 28)) return ICCG_ERR_ARG;
+  const int32_t cap = int32_t(cap64);
+  unsigned long long *tr = nullptr;
+  int32_t *tlen = nullptr;
+  CK(cudaMalloc(&tr, sizeof(unsigned long long) * size_t(cap)), "alloc trace");
+  if (cudaMalloc(&tlen, sizeof(int32_t)) != cudaSuccess) {
+    cudaFree(tr);
+    return cuda_fail(ctx, cudaGetLastError(), "alloc trace");
+  }
+  struct Free {
+    void *a, *b;
+    ~Free() { cudaFree(a); cudaFree(b); }
+  } fr{tr, tlen};
+  cudaEvent_t a0, a1;
+  CK(cudaEventCreate(&a0), "event");
+  CK(cudaEventCreate(&a1), "event");
+  struct FreeEv {
+    cudaEvent_t a, b;
+    ~FreeEv() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } fe{a0, a1};
+  ctx->P.trace = tr;
+  ctx->P.trace_len = tlen;
+  ctx->P.trace_cap = cap;
+  CK(cudaEventRecord(a0, ctx->stream), "event");
+  iccg_status st = solve_impl(ctx, b, x, tol, maxit, iters, nullptr, nullptr);
+  cudaEventRecord(a1, ctx->stream);
+  ctx->P.trace = nullptr;
+  ctx->P.trace_len = nullptr;
+  ctx->P.trace_cap = 0;
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  int32_t len = 0;
+  CK(cudaMemcpy(&len, tlen, sizeof(len), cudaMemcpyDeviceToHost), "trace");
+  len = std::max(0, std::min(len, cap));
+  std::vector<unsigned long long> h(size_t(len) + 1);
+  if (len) CK(cudaMemcpy(h.data(), tr, sizeof(unsigned long long) * size_t(len), cudaMemcpyDeviceToHost), "trace");
+  float tall = 0.f;
+  cudaEventElapsedTime(&tall, a0, a1);
+  double pms[PH_COUNT] = {0};
+  int64_t pn[PH_COUNT] = {0};
+  for (int32_t k = 1; k < len; ++k) {
+    const int tag = int(h[size_t(k)] & 15u);
+    const double dt = double((h[size_t(k)] >> 4) - (h[size_t(k) - 1] >> 4)) * 1e-6;
+    const int ph = tag == PH_ALL ? PH_BWD : tag;   // the tail after the last barrier
+    if (ph >= 0 && ph < PH_ALL) { pms[ph] += dt; pn[ph] += tag == PH_ALL ? 0 : 1; }
+  }
+  pms[PH_ALL] = tall;
+  for (int k = 0; k < PH_ALL; ++k) pn[PH_ALL] += pn[k];
+  for (int k = 0; k < PH_COUNT; ++k) {
+    if (ms) ms[k] = pms[k];
+    if (launches) launches[k] = pn[k];
+  }
+  return st;
+}
+
 iccg_status iccg_profile_solve(iccg_ctx *ctx, const double *b, double *x, double tol, int32_t maxit,
                                int32_t *iters, double *ms, int64_t *launches) {
   if (!ctx) return ICCG_ERR_ARG;
   DeviceGuard guard(ctx->device);
+  if (ctx->persistent && ctx->H.n > 0) return profile_persistent(ctx, b, x, tol, maxit, iters, ms, launches);
   ProfileState ps;
   ps.s = ctx->stream;
   ps.ev.resize(4096);
@@ -596,15 +730,25 @@ iccg_status iccg_get_factor(iccg_ctx *ctx, double *lval, int64_t *nnz_lower) {
   if (H.nL) CK(cudaMemcpyAsync(lv.data(), ctx->P.lval, sizeof(double) * lv.size(), cudaMemcpyDeviceToHost, ctx->stream), "copy L");
   if (H.n) CK(cudaMemcpyAsync(dg.data(), ctx->P.ldiag, sizeof(double) * dg.size(), cudaMemcpyDeviceToHost, ctx->stream), "copy D");
   CK(cudaStreamSynchronize(ctx->stream), "sync");
+  // rows and columns back in the caller's block-multicolor order (lane tiles
+  // store a color's rows step-major)
+  std::vector<int32_t> iord(size_t(H.n));
+  for (int32_t i = 0; i < H.n; ++i) iord[size_t(H.ord[size_t(i)])] = i;
+  std::vector<std::pair<int32_t, double>> row;
   int64_t k = 0;
-  for (int32_t i = 0; i < H.n; ++i) {
-    for (int32_t p = H.lrp[i]; p < H.lrp[i + 1]; ++p) lval[k++] = lv[p];
-    lval[k++] = dg[i];
+  for (int32_t u = 0; u < H.n; ++u) {
+    const int32_t i = iord[size_t(u)];
+    row.clear();
+    for (int32_t p = H.lrp[i]; p < H.lrp[i + 1]; ++p) row.emplace_back(H.ord[size_t(H.lcol[p])], lv[size_t(p)]);
+    std::sort(row.begin(), row.end(),
+              [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) { return a.first < b.first; });
+    for (const auto &pr : row) lval[k++] = pr.second;
+    lval[k++] = dg[size_t(i)];
   }
   return ICCG_OK;
 }
 
-iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[9]) {
+iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[11]) {
   if (!ctx || !out) return ICCG_ERR_ARG;
   const HostLayout &H = ctx->H;
   out[0] = H.n;
@@ -617,6 +761,8 @@ iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[9]) {
   out[6] = H.nL;
   out[7] = H.max_levels;
   out[8] = H.max_group_rows;
+  out[9] = int64_t(H.tiles.size());
+  out[10] = H.tile_colors;
   return ICCG_OK;
 }
 

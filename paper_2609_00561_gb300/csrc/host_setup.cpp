@@ -3,7 +3,8 @@
 // Sec. 6.6).  Validates the CSR matrix, the permutation, the block and color
 // pointers and the coloring invariant of Sec. 3 (blocks of one color share no
 // edge), then builds the permuted matrix, the strictly lower / upper parts of
-// the IC(0) pattern and the per-color warp tiles.
+// the IC(0) pattern, the lane tiles of small-block colors and the groups of
+// the other colors.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -25,7 +26,7 @@ iccg_status fail(iccg_status st, int64_t idx, const char *what, int64_t &bad, st
 iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
                          const double *val, const int32_t *perm, const int32_t *block_ptr,
                          const int32_t *color_ptr, int32_t n_b, int32_t n_c, int32_t group_rows,
-                         HostLayout &H, int64_t &bad, std::string &msg) {
+                         int32_t lane_max, HostLayout &H, int64_t &bad, std::string &msg) {
   bad = -1;
   if (n < 0 || nnz < 0 || nnz >= (int64_t(1) << 31)) return fail(ICCG_ERR_ARG, -1, "n or nnz out of range", bad, msg);
   if (n > 0 && (n_b < 1 || n_c < 1 || n_b > n || n_c > n_b)) return fail(ICCG_ERR_ARG, -1, "n_b / n_c out of range", bad, msg);
@@ -120,6 +121,94 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
   if (sym_bad >= 0) return fail(ICCG_ERR_ARG, sym_bad, "pattern of A is not symmetric", bad, msg);
   if (col_bad >= 0) return fail(ICCG_ERR_COLORING, col_bad, "two blocks of one color share an edge", bad, msg);
 
+  // lane tiles: a color whose blocks all have at most lane_max rows is cut
+  // into tiles of 32 blocks (sorted by size, largest first, so the lanes still
+  // active at a step are a prefix), its rows stored step-major per tile
+  lane_max = std::max(0, std::min(lane_max, 32));
+  std::vector<char> tcol(n_c > 0 ? n_c : 1, 0);
+  H.ord.resize(n);
+  for (int32_t i = 0; i < n; ++i) H.ord[i] = i;
+  H.lane_max = 0;
+  H.tile_colors = 0;
+  struct TileRows { int32_t row0, nsteps, nlanes; std::vector<int32_t> cnt; };
+  std::vector<std::vector<TileRows>> ctiles(n_c > 0 ? n_c : 1);
+  for (int32_t c = 0; c < n_c && lane_max > 0; ++c) {
+    int32_t mb = 0, wb = 0;
+    for (int32_t j = color_ptr[c]; j < color_ptr[c + 1]; ++j) mb = std::max(mb, block_ptr[j + 1] - block_ptr[j]);
+    if (mb > lane_max) continue;
+    // widest in-block row (lower or upper part): the tile's shared-memory
+    // staging must fit the budget
+    for (int32_t i = block_ptr[color_ptr[c]]; i < block_ptr[color_ptr[c + 1]]; ++i) {
+      int32_t lo = 0, up = 0;
+      for (int32_t e = H.arp[i]; e < H.arp[i + 1]; ++e) {
+        const int32_t j = H.acol[e];
+        if (j != i && blk[j] == blk[i]) (j < i ? lo : up)++;
+      }
+      wb = std::max(wb, std::max(lo, up));
+    }
+    if (tile_smem_bytes(mb, wb, 8) > kTileSmemBudget) continue;
+    tcol[c] = 1;
+    H.tile_colors++;
+    H.lane_max = std::max(H.lane_max, mb);
+    std::vector<int32_t> bl;
+    for (int32_t j = color_ptr[c]; j < color_ptr[c + 1]; ++j) bl.push_back(j);
+    std::stable_sort(bl.begin(), bl.end(), [&](int32_t a, int32_t b) {
+      return block_ptr[a + 1] - block_ptr[a] > block_ptr[b + 1] - block_ptr[b];
+    });
+    int32_t row = block_ptr[color_ptr[c]];
+    for (size_t t0 = 0; t0 < bl.size(); t0 += kWarp) {
+      const int32_t nl = int32_t(std::min<size_t>(kWarp, bl.size() - t0));
+      TileRows tr;
+      tr.row0 = row;
+      tr.nlanes = nl;
+      tr.nsteps = block_ptr[bl[t0] + 1] - block_ptr[bl[t0]];
+      for (int32_t k = 0; k < tr.nsteps; ++k) {
+        int32_t cnt = 0;
+        while (cnt < nl && block_ptr[bl[t0 + cnt] + 1] - block_ptr[bl[t0 + cnt]] > k) ++cnt;
+        for (int32_t l = 0; l < cnt; ++l) H.ord[row++] = block_ptr[bl[t0 + l]] + k;
+        tr.cnt.push_back(cnt);
+      }
+      ctiles[c].push_back(std::move(tr));
+    }
+  }
+  if (H.tile_colors > 0) {
+    // renumber: internal row i is row ord[i] of the caller's order
+    std::vector<int32_t> iord(n);
+    for (int32_t i = 0; i < n; ++i) iord[H.ord[i]] = i;
+    std::vector<int32_t> arp(n + 1, 0), acol(nnz);
+    std::vector<double> aval(nnz);
+    for (int32_t i = 0; i < n; ++i) arp[i + 1] = arp[i] + (H.arp[H.ord[i] + 1] - H.arp[H.ord[i]]);
+#pragma omp parallel
+    {
+      std::vector<std::pair<int32_t, double>> tmp;
+#pragma omp for schedule(dynamic, 1024)
+      for (int32_t i = 0; i < n; ++i) {
+        const int32_t u = H.ord[i];
+        tmp.clear();
+        for (int32_t e = H.arp[u]; e < H.arp[u + 1]; ++e) tmp.emplace_back(iord[H.acol[e]], H.aval[e]);
+        std::sort(tmp.begin(), tmp.end(),
+                  [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) { return a.first < b.first; });
+        for (size_t k = 0; k < tmp.size(); ++k) {
+          acol[arp[i] + k] = tmp[k].first;
+          aval[arp[i] + k] = tmp[k].second;
+        }
+      }
+    }
+    H.arp.swap(arp);
+    H.acol.swap(acol);
+    H.aval.swap(aval);
+    for (int32_t i = 0; i < n; ++i) {
+      H.perm[i] = perm[H.ord[i]];
+      H.iperm[H.perm[i]] = i;
+    }
+  }
+  // block of every internal row and the row's position (step) in its block
+  std::vector<int32_t> iblk(n), istep(n);
+  for (int32_t i = 0; i < n; ++i) {
+    iblk[i] = blk[H.ord[i]];
+    istep[i] = H.ord[i] - block_ptr[iblk[i]];
+  }
+
   // strictly lower (L) and strictly upper (U = L^T) parts
   H.lrp.assign(n + 1, 0);
   H.urp.assign(n + 1, 0);
@@ -158,31 +247,105 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
     }
   }
 
-  // groups: consecutive whole blocks of one color, at most G rows (a larger
-  // block is a group of its own); one CTA per group
+  // lane tiles: descriptors and the sliced-ELL L / U entries of every step,
+  // split into entries to other colors and in-block entries
+  H.color_tile.assign(n_c + 1, 0);
+  H.tiles.clear();
+  H.steps.clear();
+  H.sl_col.clear(); H.su_col.clear(); H.sl_map.clear(); H.su_map.clear();
+  H.si_col.clear(); H.ui_col.clear(); H.si_map.clear(); H.ui_map.clear();
+  H.wi_max = 0;
+  // appends, sliced-ELL, the entries of rows row .. row+cnt-1 that are
+  // in-block (inb) or not; emap maps a CSR entry to its L entry (null:
+  // itself); returns the width
+  std::vector<std::vector<int32_t>> sel;
+  auto sell = [&](int32_t row, int32_t cnt, const std::vector<int32_t> &rp, const std::vector<int32_t> &cols,
+                  const int32_t *emap, bool inb, std::vector<int32_t> &ocol, std::vector<int32_t> &omap) {
+    int32_t width = 0;
+    sel.assign(size_t(cnt), std::vector<int32_t>());
+    for (int32_t l = 0; l < cnt; ++l) {
+      const int32_t i = row + l;
+      for (int32_t e = rp[i]; e < rp[i + 1]; ++e)
+        if ((iblk[cols[e]] == iblk[i]) == inb) sel[size_t(l)].push_back(e);
+      width = std::max(width, int32_t(sel[size_t(l)].size()));
+    }
+    for (int32_t j = 0; j < width; ++j)
+      for (int32_t l = 0; l < cnt; ++l) {
+        if (j < int32_t(sel[size_t(l)].size())) {
+          const int32_t e = sel[size_t(l)][size_t(j)];
+          ocol.push_back(inb ? istep[cols[e]] : cols[e]);
+          omap.push_back(emap ? emap[e] : e);
+        } else {
+          ocol.push_back(inb ? 0 : kPadCol);
+          omap.push_back(-1);
+        }
+      }
+    return width;
+  };
+  for (int32_t c = 0; c < n_c; ++c) {
+    H.color_tile[c] = int32_t(H.tiles.size());
+    for (const TileRows &tr : ctiles[c]) {
+      TileDesc td{};
+      td.row0 = tr.row0;
+      td.nsteps = tr.nsteps;
+      td.step0 = int32_t(H.steps.size());
+      td.nlanes = tr.nlanes;
+      int32_t row = tr.row0;
+      for (int32_t k = 0; k < tr.nsteps; ++k) {
+        const int32_t cnt = tr.cnt[k];
+        StepDesc sd{};
+        sd.row = row;
+        sd.cnt = cnt;
+        sd.lo = int32_t(H.sl_col.size());
+        sd.lw = sell(row, cnt, H.lrp, H.lcol, nullptr, false, H.sl_col, H.sl_map);
+        sd.li = int32_t(H.si_col.size());
+        sd.liw = sell(row, cnt, H.lrp, H.lcol, nullptr, true, H.si_col, H.si_map);
+        sd.uo = int32_t(H.su_col.size());
+        sd.uw = sell(row, cnt, H.urp, H.ucol, H.umap.data(), false, H.su_col, H.su_map);
+        sd.ui = int32_t(H.ui_col.size());
+        sd.uiw = sell(row, cnt, H.urp, H.ucol, H.umap.data(), true, H.ui_col, H.ui_map);
+        td.wl = std::max(td.wl, sd.liw);
+        td.wu = std::max(td.wu, sd.uiw);
+        H.steps.push_back(sd);
+        row += cnt;
+      }
+      H.wi_max = std::max(H.wi_max, std::max(td.wl, td.wu));
+      H.tiles.push_back(td);
+    }
+  }
+  H.color_tile[n_c] = int32_t(H.tiles.size());
+  const size_t lim = size_t(1) << 31;
+  if (H.sl_col.size() >= lim || H.su_col.size() >= lim || H.si_col.size() >= lim || H.ui_col.size() >= lim)
+    return fail(ICCG_ERR_ARG, -1, "lane-tile layout exceeds 2^31 entries", bad, msg);
+
+  // groups (the other colors): consecutive whole blocks of one color, at most
+  // G rows (a larger block is a group of its own); one CTA per group
   const int32_t G = std::max(group_rows, 1);
-  std::vector<int32_t> grow(1, 0);
+  std::vector<int32_t> gr0, gr1;   // rows [gr0[g], gr1[g]) of group g
   H.color_group.assign(n_c + 1, 0);
   for (int32_t c = 0; c < n_c; ++c) {
-    H.color_group[c] = int32_t(grow.size()) - 1;
+    H.color_group[c] = int32_t(gr0.size());
+    if (tcol[c]) continue;
     int32_t j = color_ptr[c];
     while (j < color_ptr[c + 1]) {
       int32_t end = j + 1;
       while (end < color_ptr[c + 1] && block_ptr[end + 1] - block_ptr[j] <= G) ++end;
-      grow.push_back(block_ptr[end]);
+      gr0.push_back(block_ptr[j]);
+      gr1.push_back(block_ptr[end]);
       j = end;
     }
   }
-  H.color_group[n_c] = int32_t(grow.size()) - 1;
-  const int32_t ngroups = int32_t(grow.size()) - 1;
+  H.color_group[n_c] = int32_t(gr0.size());
+  const int32_t ngroups = int32_t(gr0.size());
 
   // in-group levels: forward over L (rows ascending), backward over U (rows
   // descending); the schedule of a group lists its rows level by level
   // (ascending row inside a level) and is stored at the group's row offset
   std::vector<int32_t> levf(n, 0), levb(n, 0), nlf(ngroups), nlb(ngroups);
+  // (group colors keep the caller's order: internal row = caller's row)
 #pragma omp parallel for schedule(dynamic, 64)
   for (int32_t g = 0; g < ngroups; ++g) {
-    const int32_t r0 = grow[g], r1 = grow[g + 1];
+    const int32_t r0 = gr0[g], r1 = gr1[g];
     int32_t df = 0, db = 0;
     for (int32_t i = r0; i < r1; ++i) {
       int32_t lv = 0;
@@ -205,7 +368,7 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
   int32_t off = 0;
   for (int32_t g = 0; g < ngroups; ++g) {
     GroupDesc &d = H.groups[g];
-    d.r0 = grow[g]; d.r1 = grow[g + 1];
+    d.r0 = gr0[g]; d.r1 = gr1[g];
     d.l0 = H.lrp[d.r0]; d.l1 = H.lrp[d.r1];
     d.u0 = H.urp[d.r0]; d.u1 = H.urp[d.r1];
     d.nlf = nlf[g]; d.nlb = nlb[g];

@@ -6,15 +6,22 @@
 //           diagonal separately (ldiag, invd = 1/L_ii).
 //   U = L^T strictly upper part in CSR (urp/ucol/uval); umap[k] is the L
 //           entry that U entry k mirrors.
-//   Tiles   a tile is <= 32*R consecutive rows that one warp owns (lane l
-//           holds rows r0 + l + 32k).  A tile holds whole blocks of one color
-//           (several small blocks may share a tile), or one 32*R-row slice of
-//           a larger block.  A task is the tile sequence one warp walks in
-//           order (a large block = one task of several tiles); tasks of one
-//           color are contiguous.
-//   Within a tile the in-tile dependencies form a DAG; the substitution
-//   resolves it with `rounds` sweeps over the tile (after sweep k every row of
-//   level <= k is final), so a tile needs (depth + 1) sweeps.
+//   A color is processed in one of two layouts:
+//   Lane tiles (colors whose blocks all have at most lane_max rows): 32
+//           blocks of the color form a tile, one block per lane of a warp;
+//           the lane walks its block's rows in order (step k = k-th row).  The
+//           tile's rows are stored step-major (the rows of step k of all its
+//           lanes are consecutive), so every step reads and writes 32
+//           consecutive rows.  Blocks of one color share no edge, so this
+//           renumbering keeps every row's order relative to all rows it is
+//           connected to: the IC(0) factor and the substitutions are the same
+//           as in the user's block-multicolor order.  L and U rows of a step
+//           are stored sliced-ELL (entry j of lane l at off + j*cnt + l), with
+//           a reference to an earlier (later) row of the same block coded as
+//           -(step + 1): that value sits in the warp's shared memory.
+//   Groups  (other colors): consecutive whole blocks of one color up to
+//           group_rows rows, or one larger block; one CTA each, rows resolved
+//           level by level of the in-group dependency DAG.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -44,6 +51,35 @@ struct __align__(16) GroupDesc {
 };
 
 constexpr int kGroup = 32;   // CTAs per first-level reduction group
+
+// A lane tile: its step descriptors are steps[step0 .. step0 + nsteps);
+// wl / wu: the widest in-block L / U step of the tile.
+struct __align__(16) TileDesc {
+  int32_t row0, nsteps, step0, nlanes, wl, wu, pad0, pad1;
+};
+// One step of a tile: rows [row, row + cnt) (lanes 0 .. cnt-1; blocks are
+// sorted by size, so the active lanes are a prefix).  Sliced-ELL entry j of
+// lane l sits at off + j*cnt + l: L entries to other colors at (lo, lw),
+// in-block L entries at (li, liw), U likewise (uo, uw), (ui, uiw).
+struct __align__(16) StepDesc {
+  int32_t row, cnt, lo, lw, li, liw, uo, uw, ui, uiw, pad0, pad1;
+};
+constexpr int32_t kPadCol = 0x7fffffff;   // padding entry of a sliced-ELL step
+constexpr int kTileSmemBudget = 96 * 1024;  // shared memory of one tile's CTA, bytes
+
+// Shared memory of a lane tile's CTA: per step and lane the row's value (w)
+// and 1/L_ii, the staged in-block entries (column: step, value), and per step
+// (row, cnt, in-block width).
+__host__ __device__ inline int tile_smem_bytes(int steps, int width, int elem) {
+  return steps * kWarp * 2 * elem + steps * width * kWarp * (4 + elem) + steps * 3 * 4;
+}
+
+// Grid barrier of the persistent solve kernel: arrival count, generation
+// (bumped by the last arrival) and a sticky error word set by a CTA whose
+// bounded wait gave up.  count and err start at zero for every launch.
+struct GridBar {
+  uint32_t count, gen, err, pad;
+};
 
 // Device-resident scalars of one solve.
 struct Scalars {
@@ -92,6 +128,26 @@ struct Params {
   uint32_t *gticket;            // [ngroup] group arrival counters
   int32_t nslot, npart, ngroup, npart_a, nbb;
   Scalars *sc;
+  // lane tiles: sliced-ELL entries to other colors (sl_ / su_: column, or
+  // kPadCol for padding) and in-block entries (si_ / ui_: the step of the
+  // same block's row); values are filled from the factor through the maps
+  // (the L entry an entry takes, -1: padding)
+  const TileDesc *tiles;
+  const StepDesc *steps;
+  const int32_t *sl_col, *su_col, *sl_map, *su_map;
+  const int32_t *si_col, *ui_col, *si_map, *ui_map;
+  double *sl_val, *su_val, *si_val, *ui_val;
+  float *sl_val32, *su_val32, *si_val32, *ui_val32;
+  int32_t nsl, nsu, nsi, nui;
+  int32_t lane_max, wi_max;     // largest tile block (steps) and in-block width
+  // persistent solve: first group of each color [n_c + 1], grid barrier
+  const int32_t *color_group;
+  GridBar *bar;
+  // optional phase trace of the persistent solve: (ns << 4 | phase) per
+  // barrier, written by CTA 0 (null: off); trace_len receives the count
+  unsigned long long *trace;
+  int32_t *trace_len;
+  int32_t trace_cap;
   double *hist;
   unsigned long long *err_row;  // IC(0) breakdown row (new numbering), ~0 = none
 };
@@ -107,7 +163,16 @@ struct HostLayout {
   std::vector<double> ainit, adiag;
   std::vector<GroupDesc> groups;
   std::vector<int32_t> sched_f, sched_b, levp;
-  std::vector<int32_t> color_group;   // n_c + 1
+  std::vector<int32_t> color_group;   // n_c + 1 (no groups for a tile color)
+  std::vector<int32_t> color_tile;    // n_c + 1 (no tiles for a group color)
+  std::vector<TileDesc> tiles;
+  std::vector<StepDesc> steps;
+  std::vector<int32_t> sl_col, su_col, sl_map, su_map;
+  std::vector<int32_t> si_col, ui_col, si_map, ui_map;
+  int32_t wi_max = 0;                 // widest in-block step of any tile
+  std::vector<int32_t> ord;           // internal row -> row of the caller's block-multicolor order
+  int32_t lane_max = 0;               // largest block of a tile color
+  int32_t tile_colors = 0;
   std::vector<int32_t> block_ptr, color_ptr;
   int32_t max_group_rows = 0, max_levels = 0;   // over all groups
   int32_t fit_rows = 0, fit_levels = 0;         // over groups of at most 32R rows
@@ -116,10 +181,12 @@ struct HostLayout {
 
 // Validates inputs and builds the layout (groups of at most group_rows rows);
 // returns ICCG_OK or an error with (bad_index, message) filled in.
+// Colors whose blocks all have at most lane_max rows (<= 32; 0 = none) use
+// lane tiles.
 iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
                          const double *val, const int32_t *perm, const int32_t *block_ptr,
                          const int32_t *color_ptr, int32_t n_b, int32_t n_c, int32_t group_rows,
-                         HostLayout &out, int64_t &bad_index, std::string &msg);
+                         int32_t lane_max, HostLayout &out, int64_t &bad_index, std::string &msg);
 
 // ---- launch plan (host side) ---------------------------------------------
 struct Plan {
@@ -129,11 +196,16 @@ struct Plan {
   int32_t Wa = 4;                       // warps per CTA of the SpMV
   std::vector<int32_t> task0, task1;    // group range of each color
   std::vector<int32_t> grid_c;          // CTAs of the color-c kernels
+  std::vector<int32_t> tile0, tile1;    // tile range of each color (empty: groups)
+  int32_t Wt = 2;                       // warps (tiles) per CTA of the lane-tile kernels
+  int32_t smem_tile = 0;                // bytes per CTA of the lane-tile kernels
   std::vector<int32_t> off_rr, off_rz;  // slot regions of the color-c forward / backward launches
   int32_t last_rr = 0, last_rz = 0;     // slots written before the final launch of an iteration
   int32_t grid_a = 0;                   // CTAs of the SpMV-shaped kernels
   int32_t grid_v = 0;                   // CTAs of the vector kernels
   int32_t smem_fwd = 0, smem_bwd = 0, smem_fused = 0, smem_a = 0;  // bytes per CTA
+  int32_t grid_p = 0, smem_p = 0;       // persistent kernel: CTAs (all co-resident), bytes per CTA
+  int32_t cap_p = 0;                    // persistent kernel: staged SpMV entries per warp
 };
 
 // phase ids for the profiling hook
@@ -149,6 +221,11 @@ cudaError_t launch_factor(const Params &P, const Plan &L, int nL);
 cudaError_t launch_solve_init(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);
 cudaError_t launch_solve_body(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);
 cudaError_t launch_solve_final(const Params &P, const Plan &L);
+// bytes per CTA of the persistent kernel within max(group plan, budget);
+// *cap_spmv = staged SpMV entries per warp
+int persistent_smem_bytes(const Params &P, bool fp32, int W, int budget, int *cap_spmv);
+int persistent_resident_ctas(bool fp32, int W, int smem);        // CTAs per SM
+cudaError_t launch_solve_persistent(const Params &P, const Plan &L, bool fp32);  // whole solve, one launch
 cudaError_t launch_precond(const Params &P, const Plan &L, bool fp32);  // z(perm) from r(perm)
 cudaError_t launch_spmv_plain(const Params &P, const Plan &L);          // q = A_hat xh
 cudaError_t launch_permute(const double *src, double *dst, const int32_t *perm, int32_t n,

@@ -38,9 +38,13 @@
 // this static traffic overlaps the previous launch.  A group too large for the
 // shared-memory plan reads the same data from global memory.
 //
+// Vectors that other CTAs write during a solve (r, q, x, p, y, z) are read
+// with L2 loads (ld.global.cg), so no SM ever sees a stale L1 line of them.
+//
 // Reductions are deterministic and two-level: every CTA writes its partial;
 // the last CTA of each group of kGroup CTAs (arrival ticket) sums the group's
 // partials in index order; the last group of the launch runs the epilogue.
+#include <algorithm>
 #include <cstdio>
 #include <type_traits>
 
@@ -277,12 +281,15 @@ struct Sweep {
   __device__ __forceinline__ PT dv(const GroupSmem<PT> &m, int i) const { return fit ? m.dv[i - dvb] : __ldg(gdv + i); }
 };
 
-// Stage (or describe) the static data of a forward (upper = false) or
-// backward (upper = true) sweep over group d.  Issues cp.async copies and
-// commits them; the caller waits.
+// index of the first element of the 16-byte-aligned cover that stage_cover copies
+template <typename T>
+__device__ __forceinline__ int cover_base(int a) { return a & ~(int(16 / sizeof(T)) - 1); }
+
+// Describe where the static data of a forward (upper = false) or backward
+// (upper = true) sweep over group d lives once sweep_issue's copies landed.
 template <typename PT>
-__device__ __forceinline__ Sweep<PT> sweep_static(const Params &P, const GroupDesc &d, bool upper,
-                                                  const GroupSmem<PT> &m, int tid, int nthr) {
+__device__ __forceinline__ Sweep<PT> sweep_desc(const Params &P, const GroupDesc &d, bool upper,
+                                                const GroupSmem<PT> &m) {
   Sweep<PT> sw;
   sw.fit = d.fit != 0;
   sw.grp = upper ? P.urp : P.lrp;
@@ -298,16 +305,41 @@ __device__ __forceinline__ Sweep<PT> sweep_static(const Params &P, const GroupDe
   sw.S.bv = sw.S.bc = 0;
   sw.rpb = sw.dvb = sw.schb = sw.lpb = 0;
   if (sw.fit) {
-    const int e0 = upper ? d.u0 : d.l0, e1 = upper ? d.u1 : d.l1;
-    sw.S.bv = stage_cover<PT>(sw.S.gv, e0, e1, m.sv, tid, nthr);
-    sw.S.bc = stage_cover<int32_t>(sw.S.gc, e0, e1, m.sc, tid, nthr);
-    sw.rpb = stage_cover<int32_t>(sw.grp, d.r0, d.r1 + 1, m.rp, tid, nthr);
-    sw.dvb = stage_cover<PT>(sw.gdv, d.r0, d.r1, m.dv, tid, nthr);
-    sw.schb = stage_cover<int32_t>(sw.gsch, d.r0, d.r1, m.sch, tid, nthr);
-    sw.lpb = stage_cover<int32_t>(P.levp, sw.lev0, sw.lev0 + sw.nlev + 1, m.lp, tid, nthr);
+    const int e0 = upper ? d.u0 : d.l0;
+    sw.S.bv = cover_base<PT>(e0);
+    sw.S.bc = cover_base<int32_t>(e0);
+    sw.rpb = cover_base<int32_t>(d.r0);
+    sw.dvb = cover_base<PT>(d.r0);
+    sw.schb = cover_base<int32_t>(d.r0);
+    sw.lpb = cover_base<int32_t>(sw.lev0);
   }
-  cp_commit();
   return sw;
+}
+
+// Issue (without committing) the cp.async copies of a fitting group's static
+// sweep data into m; nothing for a group that reads global memory.
+template <typename PT>
+__device__ __forceinline__ void sweep_issue(const Params &P, const GroupDesc &d, bool upper, const GroupSmem<PT> &m,
+                                            int tid, int nthr) {
+  if (!d.fit) return;
+  const int e0 = upper ? d.u0 : d.l0, e1 = upper ? d.u1 : d.l1;
+  const int lev0 = upper ? d.lb : d.lf, nlev = upper ? d.nlb : d.nlf;
+  stage_cover<PT>(upper ? uvals<PT>(P) : lvals<PT>(P), e0, e1, m.sv, tid, nthr);
+  stage_cover<int32_t>(upper ? P.ucol : P.lcol, e0, e1, m.sc, tid, nthr);
+  stage_cover<int32_t>(upper ? P.urp : P.lrp, d.r0, d.r1 + 1, m.rp, tid, nthr);
+  stage_cover<PT>(invds<PT>(P), d.r0, d.r1, m.dv, tid, nthr);
+  stage_cover<int32_t>(upper ? P.sched_b : P.sched_f, d.r0, d.r1, m.sch, tid, nthr);
+  stage_cover<int32_t>(P.levp, lev0, lev0 + nlev + 1, m.lp, tid, nthr);
+}
+
+// Stage and describe the static data of one sweep; commits the copies, the
+// caller waits.
+template <typename PT>
+__device__ __forceinline__ Sweep<PT> sweep_static(const Params &P, const GroupDesc &d, bool upper,
+                                                  const GroupSmem<PT> &m, int tid, int nthr) {
+  sweep_issue<PT>(P, d, upper, m, tid, nthr);
+  cp_commit();
+  return sweep_desc<PT>(P, d, upper, m);
 }
 
 // One sweep over a group.  UPPER = false: forward, L rows (entries to earlier
@@ -335,20 +367,20 @@ __device__ __forceinline__ void group_sweep(const Params &P, const GroupDesc &d,
     const int rb = sw.rp(m, i), re = sw.rp(m, i + 1);
     PT src;
     if (UPPER) {
-      src = y_in_smem ? m.w[l] : yv[i];
+      src = y_in_smem ? m.w[l] : __ldcg(yv + i);
     } else {
-      double ri = P.r[i];
+      double ri = __ldcg(P.r + i);
       if (UPDATE) {
-        ri -= alpha * P.q[i];
+        ri -= alpha * __ldcg(P.q + i);
         P.r[i] = ri;
-        P.xh[i] += alpha * pn[i];
+        P.xh[i] = __ldcg(P.xh + i) + alpha * __ldcg(pn + i);
         rr_acc += ri * ri;
       }
       src = PT(ri);
     }
     const int split = rb + count_below(sw.S, rb, re, UPPER ? r1 : r0);
     const int xb = UPPER ? split : rb, xe = UPPER ? re : split;
-    const PT t = row_sub<PT, PT>(sw.S, xb, xe, src, [&](int c) { return ext[c]; });
+    const PT t = row_sub<PT, PT>(sw.S, xb, xe, src, [&](int c) { return __ldcg(ext + c); });
     if (fit) {
       m.w[l] = t;
       m.spl[l] = split;
@@ -375,11 +407,11 @@ __device__ __forceinline__ void group_sweep(const Params &P, const GroupDesc &d,
         acc = row_sub<PT, PT>(sw.S, ib, ie, acc, [&](int c) { return m.w[c - r0]; });
         m.w[l] = acc * sw.dv(m, i);
       } else {
-        acc = res[i];
+        acc = __ldcg(res + i);
         const int split = rb + count_below(sw.S, rb, re, UPPER ? r1 : r0);
         ib = UPPER ? rb : split;
         ie = UPPER ? split : re;
-        acc = row_sub<PT, PT>(sw.S, ib, ie, acc, [&](int c) { return res[c]; });
+        acc = row_sub<PT, PT>(sw.S, ib, ie, acc, [&](int c) { return __ldcg(res + c); });
         res[i] = acc * sw.dv(m, i);
       }
     }
@@ -388,9 +420,9 @@ __device__ __forceinline__ void group_sweep(const Params &P, const GroupDesc &d,
   // results: fitting groups store from shared memory (coalesced)
   for (int l = tid; l < nrows; l += nthr) {
     const int i = r0 + l;
-    const PT v = fit ? m.w[l] : res[i];
+    const PT v = fit ? m.w[l] : __ldcg(res + i);
     if (fit && store_result) res[i] = v;
-    if (UPPER) rz_acc += P.r[i] * double(v);
+    if (UPPER) rz_acc += __ldcg(P.r + i) * double(v);
   }
   __syncthreads();
 }
@@ -463,6 +495,53 @@ struct SlotArgs {
   int last_rr, last_rz;   // slots of earlier launches (final launch only)
 };
 
+// End of a color launch: this CTA's <r,r> / <r,z> partials.  A non-final
+// launch stores one partial per CTA in its slot region (plain stores: the
+// iteration's last launch sums them).  The last launch of the iteration:
+// every CTA sums a fixed chunk of the earlier launches' slots (complete:
+// griddepcontrol.wait before) plus its own partial; then groups of CTAs, then
+// the last group runs the epilogue.
+__device__ __forceinline__ void launch_epilogue(const Params &P, int fin, const SlotArgs &sa, bool has_rr,
+                                                bool has_rz, double rr_acc, double rz_acc, double *red, int *flag) {
+  if (!has_rr && !has_rz) return;
+  const double rr_c = has_rr ? cta_sum(rr_acc, red) : 0.0;
+  const double rz_c = has_rz ? cta_sum(rz_acc, red) : 0.0;
+  if (fin == FIN_NONE) {
+    if (threadIdx.x == 0) {
+      if (has_rr) P.slot_rr[sa.off_rr + blockIdx.x] = rr_c;
+      if (has_rz) P.slot_rz[sa.off_rz + blockIdx.x] = rz_c;
+    }
+    return;
+  }
+  const int nb = gridDim.x;
+  const int crr = (sa.last_rr + nb - 1) / nb, crz = (sa.last_rz + nb - 1) / nb;
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < crr; k += blockDim.x) {
+    const int idx = blockIdx.x * crr + k;
+    if (idx < sa.last_rr) a += __ldcg(P.slot_rr + idx);
+  }
+  for (int k = threadIdx.x; k < crz; k += blockDim.x) {
+    const int idx = blockIdx.x * crz + k;
+    if (idx < sa.last_rz) b += __ldcg(P.slot_rz + idx);
+  }
+  a = cta_sum(a, red);
+  b = cta_sum(b, red);
+  double ga, gb;
+  if (group_reduce(P, a + rr_c, b + rz_c, true, red, flag, ga, gb)) {
+    if (threadIdx.x == 0) {
+      P.gsum0[blockIdx.x / kGroup] = ga;
+      P.gsum1[blockIdx.x / kGroup] = gb;
+    }
+    if (launch_last(P, flag)) {
+      const int ng = (nb + kGroup - 1) / kGroup;
+      const double rr = cta_sum_array(P.gsum0, ng, red, false);
+      const double rz = cta_sum_array(P.gsum1, ng, red, false);
+      if (fin == FIN_ITER) finish_iteration(P, rr, rz);
+      else finish_init(P, rz, red);
+    }
+  }
+}
+
 template <typename PT, int MODE, bool UPDATE>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
 color_kernel(Params P, int g0, int g1, GroupSmemPlan plan, int fin, SlotArgs sa) {
@@ -502,48 +581,218 @@ color_kernel(Params P, int g0, int g1, GroupSmemPlan plan, int fin, SlotArgs sa)
   } else {
     pdl_wait();
   }
-  const bool has_rr = MODE != M_BWD && UPDATE, has_rz = MODE != M_FWD;
-  if (!has_rr && !has_rz) return;
-  const double rr_c = has_rr ? cta_sum(rr_acc, red) : 0.0;
-  const double rz_c = has_rz ? cta_sum(rz_acc, red) : 0.0;
-  if (fin == FIN_NONE) {
-    // one partial per CTA, plain stores: the iteration's last launch sums them
-    if (threadIdx.x == 0) {
-      if (has_rr) P.slot_rr[sa.off_rr + blockIdx.x] = rr_c;
-      if (has_rz) P.slot_rz[sa.off_rz + blockIdx.x] = rz_c;
+  launch_epilogue(P, fin, sa, MODE != M_BWD && UPDATE, MODE != M_FWD, rr_acc, rz_acc, red, &flag);
+}
+
+// ---------------------------------------------------------------------------
+// lane-tile kernels: one CTA per tile of up to 32 blocks of one color, one
+// block per lane (Alg. 1: blocks of a color in parallel, rows of a block in
+// sequence).  Step k of the tile is the k-th row of every block; its 32 rows
+// are consecutive.
+//   A  all warps, steps in parallel: the x / r update, the entries to other
+//      colors (gathers of y or z), 1/L_ii and the step's in-block entries
+//      into shared memory;
+//   B  one warp: the in-block recurrence, step after step, every lane on its
+//      own block, shared memory only (no barrier inside);
+//   C  all warps: results to global memory, <r,z>.
+// ---------------------------------------------------------------------------
+template <typename PT> __device__ __forceinline__ const PT *slv(const Params &P);
+template <> __device__ __forceinline__ const double *slv<double>(const Params &P) { return P.sl_val; }
+template <> __device__ __forceinline__ const float *slv<float>(const Params &P) { return P.sl_val32; }
+template <typename PT> __device__ __forceinline__ const PT *suv(const Params &P);
+template <> __device__ __forceinline__ const double *suv<double>(const Params &P) { return P.su_val; }
+template <> __device__ __forceinline__ const float *suv<float>(const Params &P) { return P.su_val32; }
+template <typename PT> __device__ __forceinline__ const PT *siv(const Params &P);
+template <> __device__ __forceinline__ const double *siv<double>(const Params &P) { return P.si_val; }
+template <> __device__ __forceinline__ const float *siv<float>(const Params &P) { return P.si_val32; }
+template <typename PT> __device__ __forceinline__ const PT *uiv(const Params &P);
+template <> __device__ __forceinline__ const double *uiv<double>(const Params &P) { return P.ui_val; }
+template <> __device__ __forceinline__ const float *uiv<float>(const Params &P) { return P.ui_val32; }
+
+__device__ __forceinline__ TileDesc load_tile(const TileDesc *t) {
+  const int4 *p = reinterpret_cast<const int4 *>(t);
+  const int4 a = __ldg(p), b = __ldg(p + 1);
+  TileDesc d;
+  d.row0 = a.x; d.nsteps = a.y; d.step0 = a.z; d.nlanes = a.w;
+  d.wl = b.x; d.wu = b.y; d.pad0 = d.pad1 = 0;
+  return d;
+}
+
+__device__ __forceinline__ StepDesc load_step(const StepDesc *s) {
+  const int4 *p = reinterpret_cast<const int4 *>(s);
+  const int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+  StepDesc d;
+  d.row = a.x; d.cnt = a.y; d.lo = a.z; d.lw = a.w;
+  d.li = b.x; d.liw = b.y; d.uo = b.z; d.uw = b.w;
+  d.ui = c.x; d.uiw = c.y; d.pad0 = d.pad1 = 0;
+  return d;
+}
+
+template <typename PT>
+struct TileSmem {
+  PT *w, *dv, *sv;          // [step][lane], [step][lane], [step][j][lane]
+  int32_t *sc;              // [step][j][lane]
+  int32_t *mrow, *mcnt, *mw;  // [step]
+};
+
+template <typename PT>
+__device__ __forceinline__ TileSmem<PT> tile_smem(unsigned char *base, int S, int WI) {
+  TileSmem<PT> m;
+  m.w = reinterpret_cast<PT *>(base);
+  m.dv = m.w + S * kWarp;
+  m.sv = m.dv + S * kWarp;
+  m.sc = reinterpret_cast<int32_t *>(m.sv + S * WI * kWarp);
+  m.mrow = m.sc + S * WI * kWarp;
+  m.mcnt = m.mrow + S;
+  m.mw = m.mcnt + S;
+  return m;
+}
+
+// acc -= sum over a step's sliced-ELL entries to other colors of v * g[col],
+// storage order; loads in predicated batches of kChunk
+template <typename PT>
+__device__ __forceinline__ PT sell_sub(const int32_t *col, const PT *val, int e, int stride, int width, PT acc,
+                                       const PT *g) {
+  for (int j0 = 0; j0 < width; j0 += kChunk) {
+    int cc[kChunk];
+    PT vv[kChunk];
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) {
+      const bool ok = j0 + j < width;
+      cc[j] = ok ? __ldg(col + e + (j0 + j) * stride) : kPadCol;
+      vv[j] = ok ? __ldg(val + e + (j0 + j) * stride) : PT(0);
     }
-    return;
+    PT xx[kChunk];
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) xx[j] = cc[j] == kPadCol ? PT(0) : __ldcg(g + cc[j]);
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j)
+      if (cc[j] != kPadCol) acc -= vv[j] * xx[j];
   }
-  // The last launch of the iteration: every CTA sums a fixed chunk of the
-  // earlier launches' slots (complete: griddepcontrol.wait above) plus its own
-  // partial; then groups of CTAs, then the last group runs the epilogue.
-  const int nb = gridDim.x;
-  const int crr = (sa.last_rr + nb - 1) / nb, crz = (sa.last_rz + nb - 1) / nb;
-  double a = 0.0, b = 0.0;
-  for (int k = threadIdx.x; k < crr; k += blockDim.x) {
-    const int idx = blockIdx.x * crr + k;
-    if (idx < sa.last_rr) a += __ldcg(P.slot_rr + idx);
-  }
-  for (int k = threadIdx.x; k < crz; k += blockDim.x) {
-    const int idx = blockIdx.x * crz + k;
-    if (idx < sa.last_rz) b += __ldcg(P.slot_rz + idx);
-  }
-  a = cta_sum(a, red);
-  b = cta_sum(b, red);
-  double ga, gb;
-  if (group_reduce(P, a + rr_c, b + rz_c, true, red, &flag, ga, gb)) {
-    if (threadIdx.x == 0) {
-      P.gsum0[blockIdx.x / kGroup] = ga;
-      P.gsum1[blockIdx.x / kGroup] = gb;
+  return acc;
+}
+
+// Phase A of a forward (UPPER = false: source r with the x / r update when
+// UPDATE, gathers of y) or backward (source y from shared memory or global
+// memory, gathers of z) sweep over a tile.
+template <typename PT, bool UPPER, bool UPDATE>
+__device__ __forceinline__ void tile_phase_a(const Params &P, const TileDesc &t, const TileSmem<PT> &m, int WI,
+                                             double alpha, const double *pn, bool y_in_smem, double &rr_acc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  PT *yv = reinterpret_cast<PT *>(P.y);
+  const PT *zv = reinterpret_cast<const PT *>(P.z);
+  const PT *dinv = invds<PT>(P);
+  for (int k = warp; k < t.nsteps; k += W) {
+    const StepDesc s = load_step(P.steps + t.step0 + k);
+    const int wi = UPPER ? s.uiw : s.liw;
+    if (lane == 0) {
+      m.mrow[k] = s.row;
+      m.mcnt[k] = s.cnt;
+      m.mw[k] = wi;
     }
-    if (launch_last(P, &flag)) {
-      const int ng = (nb + kGroup - 1) / kGroup;
-      const double rr = cta_sum_array(P.gsum0, ng, red, false);
-      const double rz = cta_sum_array(P.gsum1, ng, red, false);
-      if (fin == FIN_ITER) finish_iteration(P, rr, rz);
-      else finish_init(P, rz, red);
+    if (lane < s.cnt) {
+      const int i = s.row + lane;
+      PT acc;
+      if (UPPER) {
+        const PT src = y_in_smem ? m.w[k * kWarp + lane] : __ldcg(yv + i);
+        acc = sell_sub<PT>(P.su_col, suv<PT>(P), s.uo + lane, s.cnt, s.uw, src, zv);
+      } else {
+        double ri = __ldcg(P.r + i);
+        if (UPDATE) {
+          ri -= alpha * __ldcg(P.q + i);
+          P.r[i] = ri;
+          P.xh[i] = __ldcg(P.xh + i) + alpha * __ldcg(pn + i);
+          rr_acc += ri * ri;
+        }
+        acc = sell_sub<PT>(P.sl_col, slv<PT>(P), s.lo + lane, s.cnt, s.lw, PT(ri), yv);
+      }
+      m.w[k * kWarp + lane] = acc;
+      m.dv[k * kWarp + lane] = __ldg(dinv + i);
+      const int32_t *ic = UPPER ? P.ui_col : P.si_col;
+      const PT *iv = UPPER ? uiv<PT>(P) : siv<PT>(P);
+      const int eo = (UPPER ? s.ui : s.li) + lane;
+      for (int j = 0; j < wi; ++j) {
+        m.sc[(k * WI + j) * kWarp + lane] = __ldg(ic + eo + j * s.cnt);
+        m.sv[(k * WI + j) * kWarp + lane] = __ldg(iv + eo + j * s.cnt);
+      }
     }
   }
+}
+
+// Phase B: warp 0 resolves the in-block recurrence, steps ascending (forward)
+// or descending (backward); a lane reads only its own block's values.
+// In-block padding entries have value 0 and step 0 (a finite value).
+template <typename PT, bool UPPER>
+__device__ __forceinline__ void tile_phase_b(const TileDesc &t, const TileSmem<PT> &m, int WI) {
+  if (threadIdx.x >= kWarp) return;
+  const int lane = threadIdx.x;
+  for (int kk = 0; kk < t.nsteps; ++kk) {
+    const int k = UPPER ? t.nsteps - 1 - kk : kk;
+    const int cnt = m.mcnt[k], wi = m.mw[k];
+    if (lane < cnt) {
+      PT acc = m.w[k * kWarp + lane];
+      for (int j = 0; j < wi; ++j) {
+        const int c = m.sc[(k * WI + j) * kWarp + lane];
+        acc -= m.sv[(k * WI + j) * kWarp + lane] * m.w[c * kWarp + lane];
+      }
+      m.w[k * kWarp + lane] = acc * m.dv[k * kWarp + lane];
+    }
+  }
+}
+
+// Phase C: the tile's results to global memory (y or z), <r,z> (backward)
+template <typename PT, bool UPPER>
+__device__ __forceinline__ void tile_phase_c(const Params &P, const TileDesc &t, const TileSmem<PT> &m, bool store,
+                                             double &rz_acc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  PT *res = reinterpret_cast<PT *>(UPPER ? P.z : P.y);
+  for (int k = warp; k < t.nsteps; k += W) {
+    const int cnt = m.mcnt[k], row = m.mrow[k];
+    if (lane < cnt) {
+      const int i = row + lane;
+      const PT v = m.w[k * kWarp + lane];
+      if (store) res[i] = v;
+      if (UPPER) rz_acc += __ldcg(P.r + i) * double(v);
+    }
+  }
+}
+
+template <typename PT, int MODE, bool UPDATE>
+__global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
+tile_kernel(Params P, int t0, int fin, SlotArgs sa) {
+  pdl_trigger();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[kMaxWarpsPerCta];
+  __shared__ int flag;
+  const int S = P.lane_max, WI = P.wi_max;
+  const TileSmem<PT> m = tile_smem<PT>(smem, S, WI);
+  double rr_acc = 0.0, rz_acc = 0.0;
+  const TileDesc td = load_tile(P.tiles + t0 + blockIdx.x);
+  pdl_wait();
+  if (MODE == M_BWD) {
+    tile_phase_a<PT, true, false>(P, td, m, WI, 0.0, nullptr, false, rr_acc);
+    __syncthreads();
+    tile_phase_b<PT, true>(td, m, WI);
+    __syncthreads();
+    tile_phase_c<PT, true>(P, td, m, true, rz_acc);
+  } else {
+    const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
+    tile_phase_a<PT, false, UPDATE>(P, td, m, WI, alpha, P.p0, false, rr_acc);
+    __syncthreads();
+    tile_phase_b<PT, false>(td, m, WI);
+    __syncthreads();
+    if (MODE == M_FWD) {
+      tile_phase_c<PT, false>(P, td, m, true, rz_acc);
+    } else {
+      // the last color: y stays in shared memory for the backward sweep
+      tile_phase_a<PT, true, false>(P, td, m, WI, 0.0, nullptr, true, rr_acc);
+      __syncthreads();
+      tile_phase_b<PT, true>(td, m, WI);
+      __syncthreads();
+      tile_phase_c<PT, true>(P, td, m, true, rz_acc);
+    }
+  }
+  launch_epilogue(P, fin, sa, MODE != M_BWD && UPDATE, MODE != M_FWD, rr_acc, rz_acc, red, &flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -556,7 +805,7 @@ __global__ void __launch_bounds__(kVecThreads) pupdate_kernel(Params P) {
   const double beta = __ldcg(&P.sc->beta);
   const ZT *z = reinterpret_cast<const ZT *>(P.z);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x)
-    P.p0[i] = double(z[i]) + beta * P.p0[i];
+    P.p0[i] = double(__ldcg(z + i)) + beta * __ldcg(P.p0 + i);
 }
 
 // ---------------------------------------------------------------------------
@@ -604,12 +853,12 @@ spmv_kernel(Params P, int cap) {
       waited = true;
     }
     if (i < t1) {
-      const double s = -row_sub<double, double>(S, rb, re, 0.0, [&](int c) { return xin[c]; });
+      const double s = -row_sub<double, double>(S, rb, re, 0.0, [&](int c) { return __ldcg(xin + c); });
       if (MODE == 0) {
         P.q[i] = s;
-        acc += xin[i] * s;
+        acc += __ldcg(xin + i) * s;
       } else if (MODE == 1) {
-        const double ri = P.bh[i] - s;
+        const double ri = __ldcg(P.bh + i) - s;
         P.r[i] = ri;
         acc += ri * ri;
       } else {
@@ -704,7 +953,19 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp) factor_color_kernel(P
   }
 }
 
-// invd = 1/L_ii, U values mirrored from L, FP32 copies
+// lane tiles: a thread factors its block's rows in order
+__global__ void __launch_bounds__(kVecThreads) factor_tile_kernel(Params P, int t0, int t1) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = t0 + gt / kWarp, lane = gt % kWarp;
+  if (t >= t1) return;
+  const TileDesc td = P.tiles[t];
+  for (int k = 0; k < td.nsteps; ++k) {
+    const StepDesc s = P.steps[td.step0 + k];
+    if (lane < s.cnt) factor_row(P, s.row + lane);
+  }
+}
+
+// invd = 1/L_ii, U values mirrored from L, FP32 copies, sliced-ELL values
 __global__ void __launch_bounds__(kVecThreads) factor_finish_kernel(Params P, int nL) {
   const int stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
@@ -718,11 +979,411 @@ __global__ void __launch_bounds__(kVecThreads) factor_finish_kernel(Params P, in
     P.uval32[u] = float(lv);
     P.lval32[u] = float(P.lval[u]);
   }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.nsl; e += stride) {
+    const int m = P.sl_map[e];
+    const double v = m >= 0 ? P.lval[m] : 0.0;
+    P.sl_val[e] = v;
+    P.sl_val32[e] = float(v);
+  }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.nsu; e += stride) {
+    const int m = P.su_map[e];
+    const double v = m >= 0 ? P.lval[m] : 0.0;
+    P.su_val[e] = v;
+    P.su_val32[e] = float(v);
+  }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.nsi; e += stride) {
+    const int m = P.si_map[e];
+    const double v = m >= 0 ? P.lval[m] : 0.0;
+    P.si_val[e] = v;
+    P.si_val32[e] = float(v);
+  }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.nui; e += stride) {
+    const int m = P.ui_map[e];
+    const double v = m >= 0 ? P.lval[m] : 0.0;
+    P.ui_val[e] = v;
+    P.ui_val32[e] = float(v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent solve: the whole PCG solve in one cooperative launch.  The
+// phases of an iteration are
+//   SpMV     p = z + beta p (into the other p buffer) and q = A p in one pass:
+//            a row's q gathers (z_j + beta p_j), the value the owner of row j
+//            stores as its new p_j, so no barrier separates the two; <p,q>
+//   fwd c    colors 0 .. n_c-2 (x / r update, <r,r>, L y = r)
+//   fused    the last color, forward then backward
+//   bwd c    colors n_c-2 .. 0 (L^T z = y, <r,z>)
+// with one grid barrier after each (2 n_c per iteration).  Every CTA reduces
+// the per-CTA partials itself, in index order, right after the barrier that
+// completes them, so all CTAs take identical decisions with no broadcast.
+// A CTA walks the groups g0_c + blockIdx.x + k * gridDim.x of each color; the
+// static data of its next group (next color, next pass) is copied into the
+// other of two shared-memory buffers while it computes the current one, and
+// across the barriers in between.
+// ---------------------------------------------------------------------------
+
+// A barrier wait gives up after kWaitNs of wall time (or kSpinLimit polls,
+// whichever comes first): long enough for any phase of a solve the shared
+// memory plan admits, short enough that a missing CTA cannot hang the device.
+constexpr unsigned long long kWaitNs = 4000000000ull;
+constexpr long long kSpinLimit = 1ll << 27;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Sense-reversing grid barrier with a bounded wait.  Returns false (for the
+// whole CTA) when this CTA or another one gave up; the error word stays set.
+__device__ __forceinline__ bool grid_sync(GridBar *bar, unsigned &gen, int *flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&bar->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicExch(&bar->gen, gen + 1);
+    } else {
+      const unsigned long long t0 = global_ns();
+      for (long long k = 1; ld_acquire_u32(&bar->gen) == gen; ++k) {
+        if ((k & 63) == 0 &&
+            (k > kSpinLimit || global_ns() - t0 > kWaitNs || ld_acquire_u32(&bar->err) != 0u)) {
+          atomicExch(&bar->err, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    gen = gen + 1;
+    *flag = ok && ld_acquire_u32(&bar->err) == 0u;
+  }
+  __syncthreads();
+  return *flag != 0;
+}
+
+// Barrier state of one CTA plus the optional phase trace (CTA 0 records the
+// time it leaves each barrier, tagged with the phase that barrier ends).
+struct GridSync {
+  GridBar *bar;
+  unsigned gen;
+  int *flag;
+  unsigned long long *trace;
+  int tk, cap;
+};
+
+__device__ __forceinline__ bool phase_end(GridSync &s, int tag) {
+  const bool ok = grid_sync(s.bar, s.gen, s.flag);
+  if (s.trace && blockIdx.x == 0 && threadIdx.x == 0 && s.tk < s.cap)
+    s.trace[s.tk++] = (global_ns() << 4) | unsigned(tag);
+  return ok;
+}
+
+// sum of arr[0 .. count) (fixed order), broadcast to every thread
+__device__ __forceinline__ double cta_sum_bcast(const double *arr, int count, double *red, double *bc) {
+  const double s = cta_sum_array(const_cast<double *>(arr), count, red, false);
+  if (threadIdx.x == 0) *bc = s;
+  __syncthreads();
+  const double v = *bc;
+  __syncthreads();
+  return v;
+}
+
+// One pass over all 32-row tiles of A_hat, one row per lane, entries staged
+// per warp.  INIT: r = b_hat - A x_hat, returns this thread's share of <r,r>.
+// Otherwise: p_new = z + beta p_old, q = A p_new, share of <p_new, q>.
+template <bool INIT, typename ZT>
+__device__ __forceinline__ double spmv_pass(const Params &P, unsigned char *smem, int cap, double beta,
+                                            const double *pold, double *pnew) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  double *sv = reinterpret_cast<double *>(smem + warp * (r16((cap + 8) * 8) + r16((cap + 8) * 4)));
+  int32_t *sc = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(sv) + r16((cap + 8) * 8));
+  const int ntile = (P.n + kWarp - 1) / kWarp;
+  const ZT *z = reinterpret_cast<const ZT *>(P.z);
+  double acc = 0.0;
+  for (int tile = blockIdx.x * W + warp; tile < ntile; tile += gridDim.x * W) {
+    const int t0 = tile * kWarp, t1 = min(P.n, t0 + kWarp);
+    const int i = t0 + lane;
+    const int rb = i < t1 ? __ldg(P.arp + i) : 0;
+    const int re = i < t1 ? __ldg(P.arp + i + 1) : 0;
+    const int e0 = __shfl_sync(0xffffffffu, rb, 0);
+    const int e1 = __ldg(P.arp + t1);
+    Seg<double> S;
+    S.gv = P.aval; S.gc = P.acol; S.sv = sv; S.sc = sc;
+    S.staged = e1 - e0 <= cap;
+    S.bv = S.bc = 0;
+    if (S.staged) {
+      S.bv = stage_cover<double>(P.aval, e0, e1, sv, lane, kWarp);
+      S.bc = stage_cover<int32_t>(P.acol, e0, e1, sc, lane, kWarp);
+    }
+    cp_commit();
+    cp_wait_all();
+    __syncwarp();
+    if (i < t1) {
+      if (INIT) {
+        const double s = -row_sub<double, double>(S, rb, re, 0.0, [&](int c) { return __ldcg(P.xh + c); });
+        const double ri = __ldcg(P.bh + i) - s;
+        P.r[i] = ri;
+        acc += ri * ri;
+      } else {
+        const double s = -row_sub<double, double>(
+            S, rb, re, 0.0, [&](int c) { return double(__ldcg(z + c)) + beta * __ldcg(pold + c); });
+        const double pi = double(__ldcg(z + i)) + beta * __ldcg(pold + i);
+        pnew[i] = pi;
+        P.q[i] = s;
+        acc += pi * s;
+      }
+    }
+    __syncwarp();
+  }
+  return acc;
+}
+
+// ---- the work items of one preconditioner pass ----------------------------
+// Phase ph in [0, 2 n_c - 1): ph < n_c is the forward sweep of color ph (the
+// last of them fused with its backward sweep), ph >= n_c the backward sweep
+// of color 2 n_c - 2 - ph.  An item is one sweep over one group; the fused
+// phase has two per group (sub 0 forward, sub 1 backward).
+struct Item {
+  int ph, g, sub;
+  bool ok, wrap;   // wrap: the item belongs to the next pass
+};
+
+__device__ __forceinline__ int ph_color(int ph, int nc) { return ph < nc ? ph : 2 * nc - 2 - ph; }
+
+// first item of this CTA at phase >= ph (group g of phase ph, or its first)
+__device__ __forceinline__ Item seek_item(const Params &P, int ph, int g) {
+  const int nc = P.n_c;
+  for (; ph < 2 * nc - 1; ++ph, g = -1) {
+    const int c = ph_color(ph, nc);
+    if (g < 0) g = __ldg(P.color_group + c) + int(blockIdx.x);
+    if (g < __ldg(P.color_group + c + 1)) return Item{ph, g, 0, true, false};
+  }
+  return Item{0, 0, 0, false, false};
+}
+
+__device__ __forceinline__ Item next_item(const Params &P, const Item &it) {
+  if (it.ph == P.n_c - 1 && it.sub == 0) return Item{it.ph, it.g, 1, true, false};
+  Item n = seek_item(P, it.ph, it.g + int(gridDim.x));
+  if (!n.ok) {
+    n = seek_item(P, 0, -1);
+    n.wrap = true;
+  }
+  return n;
+}
+
+__device__ __forceinline__ bool item_upper(const Item &it, int nc) { return it.ph >= nc || it.sub == 1; }
+
+// Double-buffered group plan: static data of buffer k at k * o_w, the
+// row-work arrays (w, spl) shared by both buffers after them.
+template <typename PT>
+__device__ __forceinline__ GroupSmem<PT> group_smem_buf(unsigned char *base, const GroupSmemPlan &p, int k) {
+  GroupSmem<PT> s = group_smem<PT>(base + k * p.o_w, p);
+  s.w = reinterpret_cast<PT *>(base + 2 * p.o_w);
+  s.spl = reinterpret_cast<int32_t *>(base + p.o_w + p.o_spl);
+  return s;
+}
+
+// copies of item it's static data into buffer k, committed as one group
+// (an empty group when there is no item)
+template <typename PT>
+__device__ __forceinline__ void stage_item(const Params &P, const Item &it, unsigned char *smem,
+                                           const GroupSmemPlan &plan, int k) {
+  if (it.ok) {
+    const GroupDesc d = load_group(P.groups + it.g);
+    sweep_issue<PT>(P, d, item_upper(it, P.n_c), group_smem_buf<PT>(smem, plan, k), threadIdx.x, blockDim.x);
+  }
+  cp_commit();
+}
+
+// One preconditioner pass (forward colors, fused color, backward colors)
+// with a barrier after every phase but the last; `cur` (staged in buffer
+// `buf`) is this CTA's first item and becomes the first item of the next
+// pass.  Accumulates this thread's <r,r> (UPDATE) and <r,z> shares.
+template <typename PT, bool UPDATE>
+__device__ __forceinline__ bool precond_pass(const Params &P, const GroupSmemPlan &plan, unsigned char *smem,
+                                             Item &cur, int &buf, double alpha, const double *pn, double &rr_acc,
+                                             double &rz_acc, GridSync &gs) {
+  const int nc = P.n_c, nph = 2 * nc - 1;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  cur.wrap = false;
+  for (int ph = 0; ph < nph; ++ph) {
+    while (cur.ok && !cur.wrap && cur.ph == ph) {
+      const Item nx = next_item(P, cur);
+      stage_item<PT>(P, nx, smem, plan, buf ^ 1);
+      cp_wait_prev();
+      __syncthreads();
+      const GroupSmem<PT> m = group_smem_buf<PT>(smem, plan, buf);
+      const GroupDesc d = load_group(P.groups + cur.g);
+      const bool fused = ph == nc - 1;
+      if (!item_upper(cur, nc)) {
+        const Sweep<PT> sw = sweep_desc<PT>(P, d, false, m);
+        group_sweep<PT, false, UPDATE>(P, d, sw, m, tid, nthr, alpha, pn, false, !fused || !sw.fit, rr_acc,
+                                       rz_acc);
+      } else {
+        const Sweep<PT> sw = sweep_desc<PT>(P, d, true, m);
+        group_sweep<PT, true, false>(P, d, sw, m, tid, nthr, 0.0, nullptr, fused && sw.fit, true, rr_acc, rz_acc);
+      }
+      buf ^= 1;
+      cur = nx;
+    }
+    if (ph < nph - 1 && !phase_end(gs, ph < nc - 1 ? PH_FWD : (ph == nc - 1 ? PH_FUSED : PH_BWD))) return false;
+  }
+  return true;
+}
+
+// 64 registers a thread: up to 2 CTAs of 16 warps (or 8 of 4) per SM
+#ifndef ICCG_PERSIST_MIN_CTAS
+#define ICCG_PERSIST_MIN_CTAS 2
+#endif
+
+template <typename PT>
+__global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp, ICCG_PERSIST_MIN_CTAS)
+persistent_kernel(Params P, GroupSmemPlan plan, int cap_a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[kMaxWarpsPerCta];
+  __shared__ double bc;
+  __shared__ int flag;
+  const int tid = threadIdx.x, nthr = blockDim.x, nb = gridDim.x, b = blockIdx.x;
+  const int gstride = nb * nthr, gi = b * nthr + tid;
+  unsigned char *smem_a = smem + plan.o_w + plan.total;   // SpMV staging
+  GridSync gs{P.bar, 0u, &flag, P.trace, 0, P.trace_cap};
+  Scalars *S = P.sc;
+  const double tol = __ldcg(&S->tol);
+  const int maxit = __ldcg(&S->maxit);
+  double *pp_a = P.part0, *pp_b = P.part1;   // per-CTA partials [gridDim.x]
+  int status = ICCG_ERR_TIMEOUT, it = 0;
+  bool ok = true;
+
+  // this CTA's first preconditioner item, staged while the solve starts
+  int buf = 0;
+  Item cur = seek_item(P, 0, -1);
+  stage_item<PT>(P, cur, smem, plan, 0);
+
+  // solve start: b_hat, x_hat, p = 0, <b,b>
+  double acc = 0.0;
+  for (int i = gi; i < P.n; i += gstride) {
+    const int o = __ldg(P.perm + i);
+    const double bi = __ldcg(P.bin + o);
+    P.bh[i] = bi;
+    P.xh[i] = __ldcg(P.xin + o);
+    P.p0[i] = 0.0;
+    acc += bi * bi;
+  }
+  acc = cta_sum(acc, red);
+  if (tid == 0) P.init_bb[b] = acc;
+  ok = phase_end(gs, PH_INIT);
+  // r0 = b_hat - A x_hat, <r0, r0>
+  if (ok) {
+    acc = cta_sum(spmv_pass<true, PT>(P, smem_a, cap_a, 0.0, nullptr, nullptr), red);
+    if (tid == 0) pp_a[b] = acc;
+    ok = phase_end(gs, PH_INIT);
+  }
+  // z0 = M^-1 r0, <r0, z0>
+  double rr_acc = 0.0, rz_acc = 0.0;
+  if (ok) ok = precond_pass<PT, false>(P, plan, smem, cur, buf, 0.0, nullptr, rr_acc, rz_acc, gs);
+  if (ok) {
+    acc = cta_sum(rz_acc, red);
+    if (tid == 0) pp_b[b] = acc;
+    ok = phase_end(gs, PH_INIT);
+  }
+  double bnorm = 0.0, rz = 0.0;
+  bool done = false;
+  if (ok) {
+    const double bb = cta_sum_bcast(P.init_bb, nb, red, &bc);
+    const double rr0 = cta_sum_bcast(pp_a, nb, red, &bc);
+    rz = cta_sum_bcast(pp_b, nb, red, &bc);
+    bnorm = sqrt(bb);
+    if (bnorm == 0.0) {
+      done = true;
+      status = ICCG_OK;
+      if (b == 0 && tid == 0) P.hist[0] = 0.0;
+    } else {
+      const double rn = sqrt(rr0) / bnorm;
+      if (b == 0 && tid == 0) P.hist[0] = rn;
+      if (!isfinite(rn) || !isfinite(rz)) { done = true; status = ICCG_ERR_NONFINITE; }
+      else if (rn <= tol) { done = true; status = ICCG_OK; }
+      else if (maxit <= 0) { done = true; status = ICCG_NOT_CONVERGED; }
+    }
+    // pp_a is next written by the SpMV, read after its barrier; pp_b after at
+    // least one color barrier: every CTA has read both by then
+  }
+  double beta = 0.0;
+  while (ok && !done) {
+    // p_new = z + beta p_old, q = A p_new, <p_new, q>, alpha
+    const double *pold = (it & 1) ? P.p1 : P.p0;
+    double *pnew = (it & 1) ? P.p0 : P.p1;
+    acc = cta_sum(spmv_pass<false, PT>(P, smem_a, cap_a, beta, pold, pnew), red);
+    if (tid == 0) pp_a[b] = acc;
+    if (!(ok = phase_end(gs, PH_SPMV))) break;
+    const double pq = cta_sum_bcast(pp_a, nb, red, &bc);
+    const double alpha = rz / pq;
+    // x / r update, forward and backward substitution
+    rr_acc = 0.0;
+    rz_acc = 0.0;
+    if (!(ok = precond_pass<PT, true>(P, plan, smem, cur, buf, alpha, pnew, rr_acc, rz_acc, gs))) break;
+    const double rrc = cta_sum(rr_acc, red);
+    const double rzc = cta_sum(rz_acc, red);
+    if (tid == 0) { pp_a[b] = rrc; pp_b[b] = rzc; }
+    if (!(ok = phase_end(gs, PH_BWD))) break;
+    const double rr = cta_sum_bcast(pp_a, nb, red, &bc);
+    const double rz_new = cta_sum_bcast(pp_b, nb, red, &bc);
+    ++it;
+    const double rn = sqrt(rr) / bnorm;
+    if (b == 0 && tid == 0) P.hist[it] = rn;
+    if (!isfinite(rn) || !isfinite(rz_new)) { done = true; status = ICCG_ERR_NONFINITE; }
+    else if (rn <= tol) { done = true; status = ICCG_OK; }
+    else if (it >= maxit) { done = true; status = ICCG_NOT_CONVERGED; }
+    else {
+      beta = rz_new / rz;
+      rz = rz_new;
+    }
+  }
+  cp_wait_all();
+  if (ok) {
+    for (int i = gi; i < P.n; i += gstride) P.xout[__ldg(P.perm + i)] = bnorm == 0.0 ? 0.0 : __ldcg(P.xh + i);
+  }
+  if (b == 0 && tid == 0) {
+    S->iter = it;
+    S->status = ok ? status : ICCG_ERR_TIMEOUT;
+    S->bnorm = bnorm;
+    S->done = 1;
+    if (P.trace && gs.tk < P.trace_cap) P.trace[gs.tk++] = (global_ns() << 4) | unsigned(PH_ALL);
+    if (P.trace_len) *P.trace_len = gs.tk;
+  }
 }
 
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
+template <typename... KArgs, typename... Args>
+cudaError_t launch_coop(void (*kernel)(KArgs...), int grid, int threads, int smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(unsigned(threads));
+  cfg.dynamicSmemBytes = size_t(smem);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch(void (*kernel)(KArgs...), int grid, int threads, int smem, const Plan &L, Args... args) {
   cudaLaunchConfig_t cfg = {};
@@ -745,7 +1406,21 @@ GroupSmemPlan plan_of(const Params &P, bool fused, bool upper) {
 }
 
 template <typename PT>
+cudaError_t launch_tile(const Params &P, const Plan &L, int c, int mode, bool update, int fin, const SlotArgs &sa) {
+  const int g = L.grid_c[c], t0 = L.tile0[c], th = L.Wt * kWarp, sm = L.smem_tile;
+  if (mode == M_BWD) return launch(tile_kernel<PT, M_BWD, false>, g, th, sm, L, P, t0, fin, sa);
+  if (update) {
+    if (mode == M_FUSED) return launch(tile_kernel<PT, M_FUSED, true>, g, th, sm, L, P, t0, fin, sa);
+    return launch(tile_kernel<PT, M_FWD, true>, g, th, sm, L, P, t0, fin, sa);
+  }
+  if (mode == M_FUSED) return launch(tile_kernel<PT, M_FUSED, false>, g, th, sm, L, P, t0, fin, sa);
+  return launch(tile_kernel<PT, M_FWD, false>, g, th, sm, L, P, t0, fin, sa);
+}
+
+template <typename PT>
 cudaError_t launch_fwd(const Params &P, const Plan &L, int c, bool update, bool fused, int fin) {
+  if (L.tile1[c] > L.tile0[c])
+    return launch_tile<PT>(P, L, c, fused ? M_FUSED : M_FWD, update, fin, SlotArgs{L.off_rr[c], L.off_rz[c], 0, 0});
   const int threads = L.W * kWarp;
   const GroupSmemPlan pl = plan_of<PT>(P, fused, false);
   const int smem = pl.total;
@@ -766,6 +1441,7 @@ cudaError_t launch_bwd(const Params &P, const Plan &L, int c, int fin) {
   // the final backward launch sums the <r,r> slots only in an iteration (the
   // solve start has no x / r update)
   const SlotArgs sa{0, L.off_rz[c], fin == FIN_ITER ? L.last_rr : 0, L.last_rz};
+  if (L.tile1[c] > L.tile0[c]) return launch_tile<PT>(P, L, c, M_BWD, false, fin, sa);
   return launch(color_kernel<PT, M_BWD, false>, L.grid_c[c], L.W * kWarp, pl.total, L, P, L.task0[c],
                 L.task1[c], pl, fin, sa);
 }
@@ -814,6 +1490,12 @@ cudaError_t configure_pt() {
   if (e == cudaSuccess) e = allow_smem(color_kernel<PT, M_FUSED, false>);
   if (e == cudaSuccess) e = allow_smem(color_kernel<PT, M_FWD, false>);
   if (e == cudaSuccess) e = allow_smem(color_kernel<PT, M_BWD, false>);
+  if (e == cudaSuccess) e = allow_smem(persistent_kernel<PT>);
+  if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_FUSED, true>);
+  if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_FWD, true>);
+  if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_FUSED, false>);
+  if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_FWD, false>);
+  if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_BWD, false>);
   return e;
 }
 
@@ -831,6 +1513,41 @@ int spmv_resident_ctas(int Wa, int smem) {
   return nb > 0 ? nb : 1;
 }
 
+int persistent_smem_bytes(const Params &P, bool fp32, int W, int budget, int *cap_spmv) {
+  const GroupSmemPlan pl = fp32 ? plan_of<float>(P, true, false) : plan_of<double>(P, true, false);
+  // two buffers of static group data, the shared row-work arrays, then the
+  // SpMV staging; a tile larger than the staging capacity that fits the
+  // budget reads global memory instead
+  const int groups = pl.o_w + pl.total;
+  int cap = P.cap_a;
+  while (cap > 4 && W * spmv_smem_bytes(cap) > budget) cap = std::max(4, (cap / 2) & ~3);
+  *cap_spmv = cap;
+  return groups + W * spmv_smem_bytes(cap);
+}
+
+int persistent_resident_ctas(bool fp32, int W, int smem) {
+  int nb = 0;
+  const cudaError_t e =
+      fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel<float>, W * kWarp, size_t(smem))
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel<double>, W * kWarp, size_t(smem));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+cudaError_t launch_solve_persistent(const Params &P, const Plan &L, bool fp32) {
+  cudaError_t e = cudaMemsetAsync(P.bar, 0, sizeof(GridBar), L.stream);
+  if (e != cudaSuccess) return e;
+  const int threads = L.W * kWarp;
+  if (fp32)
+    return launch_coop(persistent_kernel<float>, L.grid_p, threads, L.smem_p, L.stream, P,
+                       plan_of<float>(P, true, false), L.cap_p);
+  return launch_coop(persistent_kernel<double>, L.grid_p, threads, L.smem_p, L.stream, P,
+                     plan_of<double>(P, true, false), L.cap_p);
+}
+
 cudaError_t configure_kernels() {
   cudaError_t e = configure_pt<double>();
   if (e == cudaSuccess) e = configure_pt<float>();
@@ -842,7 +1559,13 @@ cudaError_t configure_kernels() {
 
 cudaError_t launch_factor(const Params &P, const Plan &L, int nL) {
   for (int c = 0; c < L.n_c; ++c) {
-    factor_color_kernel<<<L.grid_c[c], L.W * kWarp, 0, L.stream>>>(P, L.task0[c], L.task1[c]);
+    if (L.tile1[c] > L.tile0[c]) {
+      const int nt = L.tile1[c] - L.tile0[c];
+      factor_tile_kernel<<<(nt * kWarp + kVecThreads - 1) / kVecThreads, kVecThreads, 0, L.stream>>>(P, L.tile0[c],
+                                                                                                    L.tile1[c]);
+    } else {
+      factor_color_kernel<<<L.grid_c[c], L.W * kWarp, 0, L.stream>>>(P, L.task0[c], L.task1[c]);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

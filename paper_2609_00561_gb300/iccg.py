@@ -32,7 +32,11 @@ class IccgError(RuntimeError):
 class iccg_opts(ctypes.Structure):
     _fields_ = [("precond_fp32", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("rows_per_thread", ctypes.c_int32), ("no_graph", ctypes.c_int32),
-                ("no_pdl", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("no_pdl", ctypes.c_int32), ("solver", ctypes.c_int32), ("lane_block_max", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
+
+
+SOLVERS = {"auto": 0, "persistent": 1, "phased": 2}
 
 
 _lib = None
@@ -108,10 +112,13 @@ def _as(a, dt):
     return np.ascontiguousarray(a, dtype=dt)
 
 
-def make_opts(precond_fp32=0, warps_per_cta=0, rows_per_thread=0, no_graph=0, no_pdl=0):
+def make_opts(precond_fp32=0, warps_per_cta=0, rows_per_thread=0, no_graph=0, no_pdl=0, solver="auto",
+              lane_block_max=0):
     o = iccg_opts()
     o.precond_fp32, o.warps_per_cta, o.rows_per_thread, o.no_graph, o.no_pdl = (
         int(precond_fp32), int(warps_per_cta), int(rows_per_thread), int(no_graph), int(no_pdl))
+    o.solver = SOLVERS[solver] if isinstance(solver, str) else int(solver)
+    o.lane_block_max = int(lane_block_max)
     return o
 
 
@@ -183,11 +190,12 @@ def iccg_profile_solve(ctx, b, x, tol=1e-8, maxit=10000):
     return st, it.value, dict(zip(PHASES, ms.tolist())), dict(zip(PHASES, ln.tolist()))
 
 
-INFO_KEYS = ("n", "nnz", "n_b", "n_c", "groups", "global_groups", "nL", "max_levels", "max_group_rows")
+INFO_KEYS = ("n", "nnz", "n_b", "n_c", "groups", "global_groups", "nL", "max_levels", "max_group_rows", "tiles",
+             "tile_colors")
 
 
 def iccg_info(ctx):
-    out = np.zeros(9, dtype=np.int64)
+    out = np.zeros(len(INFO_KEYS), dtype=np.int64)
     _check(load().iccg_info(ctx, _ptr(out)), "iccg_info", ctx)
     return dict(zip(INFO_KEYS, out.tolist()))
 
@@ -288,11 +296,13 @@ class Solver:
     """Owns one iccg context: setup + factor at construction."""
 
     def __init__(self, a, bl, precond_fp32=False, warps_per_cta=0, rows_per_thread=0, no_graph=False,
-                 no_pdl=False, stream=None, factor=True):
+                 no_pdl=False, stream=None, factor=True, solver="auto", lane_block_max=0):
         self.n = a.n
         self.ctx = iccg_setup(a.n, a.nnz, a.rowptr, a.colind, a.val, bl["perm"], bl["block_ptr"],
                               bl["color_ptr"], bl["n_b"], bl["n_c"],
-                              make_opts(precond_fp32, warps_per_cta, rows_per_thread, no_graph, no_pdl), stream)
+                              make_opts(precond_fp32, warps_per_cta, rows_per_thread, no_graph, no_pdl, solver,
+                                        lane_block_max),
+                              stream)
         if factor:
             iccg_factor(self.ctx)
 

@@ -74,6 +74,17 @@ def test_setup_rejects_bad_inputs_before_gpu():
     # non-finite value
     a5 = gen.CSR(a.n, a.rowptr.copy(), a.colind.copy(), a.val.copy()); a5.val[7] = np.nan
     assert _setup_err(a5, perm, bp, cp, nb, nc).status == 1
+    # invalid options: solver id, warps per CTA, rows per thread, reserved words
+    for kw in (dict(solver=3), dict(solver=-1), dict(warps_per_cta=17), dict(rows_per_thread=3),
+               dict(lane_block_max=33), dict(lane_block_max=-2)):
+        with pytest.raises(iccg.IccgError) as ei:
+            iccg.iccg_setup(a.n, a.nnz, a.rowptr, a.colind, a.val, perm, bp, cp, nb, nc, iccg.make_opts(**kw))
+        assert ei.value.status == 1, kw
+    o = iccg.make_opts()
+    o.reserved[0] = 1
+    with pytest.raises(iccg.IccgError) as ei:
+        iccg.iccg_setup(a.n, a.nnz, a.rowptr, a.colind, a.val, perm, bp, cp, nb, nc, o)
+    assert ei.value.status == 1
 
 
 CASES = {

@@ -8,8 +8,10 @@ Bars (element by element on the same seeded inputs):
   * blockings / permutations are inputs and bit-exact by construction.
 Cases span several tiles, ragged tails, multi-tile blocks (ABMC s > 32R,
 Leiden modularity blocks of hundreds of rows), one-color and one-row systems,
-and every launch shape (rows per thread, warps per CTA, graph or host loop,
-with or without programmatic dependent launch).
+and every launch shape: lane tiles (one block per lane) and CTA groups
+(level by level) under several rows-per-thread / warps-per-CTA choices, the
+phased solve as a CUDA graph or a host loop, with or without programmatic
+dependent launch, and the persistent single-launch solve.
 """
 import numpy as np
 import pytest
@@ -64,14 +66,20 @@ def _rel(x, y):
     return float(np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300))
 
 
-SHAPES = [dict(), dict(rows_per_thread=2), dict(rows_per_thread=4, warps_per_cta=8),
-          dict(warps_per_cta=1), dict(warps_per_cta=16), dict(no_graph=1), dict(no_pdl=1)]
+SHAPES = [dict(), dict(lane_block_max=8), dict(lane_block_max=-1),
+          dict(lane_block_max=-1, rows_per_thread=2, warps_per_cta=4), dict(lane_block_max=-1, warps_per_cta=1),
+          dict(lane_block_max=-1, warps_per_cta=16), dict(no_graph=1), dict(no_pdl=1),
+          dict(solver="persistent"), dict(solver="persistent", rows_per_thread=4, warps_per_cta=4),
+          dict(solver="persistent", warps_per_cta=16)]
+LAYOUTS = {"lanes": dict(), "groups": dict(lane_block_max=-1)}
+SOLVERS = {"lanes": dict(), "groups": dict(lane_block_max=-1), "persistent": dict(solver="persistent")}
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_factor_spmv_precond_match_oracle(name):
+@pytest.mark.parametrize("layout", sorted(LAYOUTS))
+def test_factor_spmv_precond_match_oracle(name, layout):
     a, b, bl, ref = _case(name)
-    S = iccg.Solver(a, bl)
+    S = iccg.Solver(a, bl, **LAYOUTS[layout])
     ah = oracle.permute(a, bl["perm"])
     lptr, lcol, aval = oracle.tril_csr(ah)
     lref, brow = oracle.ic0(lptr, lcol, aval)
@@ -114,11 +122,12 @@ def test_solve_fp64_matches_oracle(name, shape):
 
 
 @pytest.mark.parametrize("name", ["c1_abmc16", "grid3d_abmc100", "grid2d_leiden_md", "diff27", "elast27"])
-def test_solve_fp32_preconditioner(name):
+@pytest.mark.parametrize("solver", sorted(SOLVERS))
+def test_solve_fp32_preconditioner(name, solver):
     """Extension 1: FP32 factors/substitutions, FP64 CG; reaches the same
     recursive residual; its error against the FP64 oracle is reported."""
     a, b, bl, ref = _case(name)
-    S = iccg.Solver(a, bl, precond_fp32=True)
+    S = iccg.Solver(a, bl, precond_fp32=True, **SOLVERS[solver])
     x = np.zeros(a.n)
     st, it, hist = iccg.iccg_solve(S.ctx, b, x, 1e-8, 20000)
     assert st == iccg.ICCG_OK and hist[-1] <= 1e-8
@@ -133,9 +142,10 @@ def test_solve_fp32_preconditioner(name):
     S.close()
 
 
-def test_device_and_host_pointers_agree_and_are_deterministic():
+@pytest.mark.parametrize("solver", sorted(SOLVERS))
+def test_device_and_host_pointers_agree_and_are_deterministic(solver):
     a, b, bl, ref = _case("grid3d_abmc32")
-    S = iccg.Solver(a, bl)
+    S = iccg.Solver(a, bl, **SOLVERS[solver])
     xh = np.zeros(a.n)
     iccg.iccg_solve(S.ctx, b, xh)
     bd = torch.tensor(b, device="cuda")
@@ -148,9 +158,10 @@ def test_device_and_host_pointers_agree_and_are_deterministic():
     S.close()
 
 
-def test_edge_cases():
+@pytest.mark.parametrize("solver", sorted(SOLVERS))
+def test_edge_cases(solver):
     a, b, bl, ref = _case("c1_abmc16")
-    S = iccg.Solver(a, bl)
+    S = iccg.Solver(a, bl, **SOLVERS[solver])
     # b = 0 -> x = 0, 0 iterations
     x = np.full(a.n, 3.0)
     st, it, hist = iccg.iccg_solve(S.ctx, np.zeros(a.n), x)
@@ -185,11 +196,12 @@ def _factor_of(a, bl):
     return lptr, lcol, lval
 
 
-def test_single_block_tridiagonal_converges_in_one_iteration():
+@pytest.mark.parametrize("solver", sorted(SOLVERS))
+def test_single_block_tridiagonal_converges_in_one_iteration(solver):
     a = _tri(300)
     bl = {"perm": np.arange(300, dtype=np.int32), "block_ptr": np.array([0, 300], dtype=np.int32),
           "color_ptr": np.array([0, 1], dtype=np.int32), "n_b": 1, "n_c": 1}
-    S = iccg.Solver(a, bl)
+    S = iccg.Solver(a, bl, **SOLVERS[solver])
     b = gen.rhs_uniform(300, 2)
     x = np.zeros(300)
     st, it, hist = iccg.iccg_solve(S.ctx, b, x, 1e-12)
@@ -198,11 +210,12 @@ def test_single_block_tridiagonal_converges_in_one_iteration():
     S.close()
 
 
-def test_one_row_system():
+@pytest.mark.parametrize("solver", sorted(SOLVERS))
+def test_one_row_system(solver):
     a = gen.from_scipy(sp.csr_matrix(np.array([[4.0]])))
     bl = {"perm": np.array([0], dtype=np.int32), "block_ptr": np.array([0, 1], dtype=np.int32),
           "color_ptr": np.array([0, 1], dtype=np.int32), "n_b": 1, "n_c": 1}
-    S = iccg.Solver(a, bl)
+    S = iccg.Solver(a, bl, **SOLVERS[solver])
     x = np.zeros(1)
     st, it, hist = iccg.iccg_solve(S.ctx, np.array([2.0]), x)
     assert st == iccg.ICCG_OK and it == 1 and abs(x[0] - 0.5) < 1e-15
@@ -236,4 +249,24 @@ def test_production_blocking_drives_the_same_solve():
     st, it, hist = iccg.iccg_solve(S.ctx, b, x)
     ref = oracle.iccg(a, b, bo["perm"])
     assert abs(it - ref["iterations"]) <= 1 and _rel(x, ref["x"]) <= 1e-10
+    S.close()
+
+
+def test_layout_choice_follows_block_sizes():
+    """Colors of blocks up to lane_block_max rows run as lane tiles (32 blocks
+    per tile); larger blocks run as CTA groups."""
+    a, b, bl, ref = _case("grid3d_abmc8")
+    cp = np.asarray(bl["color_ptr"])
+    S = iccg.Solver(a, bl)
+    info = iccg.iccg_info(S.ctx)
+    assert info["tile_colors"] == bl["n_c"]
+    assert info["tiles"] == sum((int(cp[c + 1] - cp[c]) + 31) // 32 for c in range(bl["n_c"]))
+    assert info["groups"] == 0
+    S.close()
+    S = iccg.Solver(a, bl, lane_block_max=-1)
+    assert iccg.iccg_info(S.ctx)["tile_colors"] == 0
+    S.close()
+    a, b, bl, ref = _case("grid3d_abmc100")
+    S = iccg.Solver(a, bl)
+    assert iccg.iccg_info(S.ctx)["tile_colors"] == 0
     S.close()
