@@ -246,7 +246,15 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   // lane tiles: one CTA of up to 8 warps per tile (steps shared out in phases
   // A and C)
   L.Wt = std::max(1, std::min(8, H.lane_max));
-  L.smem_tile = tile_smem_bytes(std::max(H.lane_max, 1), H.wi_max, elem);
+  {
+    const TilePlan tp = tile_plan(std::max(H.lane_max, 1), H.tcap_r, H.tcap_i, elem);
+    L.smem_tile = tile_launch_bytes(tp, false);
+    L.smem_tile2 = tile_launch_bytes(tp, true);
+  }
+  // a lane-tile launch: at most the CTAs the device holds at once, each
+  // walking tiles grid-stride
+  const int tile_full =
+      H.tile_colors > 0 ? sms * tile_resident_ctas(ctx->fp32, L.Wt * kWarp, L.smem_tile) : 1;
   int32_t gbig = 1;
   for (int c = 0; c < n_c; ++c) {
     L.task0[c] = H.color_group[c];
@@ -254,7 +262,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     L.tile0[c] = H.color_tile[c];
     L.tile1[c] = H.color_tile[c + 1];
     const int nt = L.tile1[c] - L.tile0[c];
-    L.grid_c[c] = nt > 0 ? nt : std::max(1, L.task1[c] - L.task0[c]);
+    L.grid_c[c] = nt > 0 ? std::min(nt, tile_full) : std::max(1, L.task1[c] - L.task0[c]);
     gbig = std::max(gbig, L.grid_c[c]);
   }
   // slot regions: forward launches in color order (<r,r>), then the fused
@@ -339,6 +347,8 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     P.nui = int32_t(H.ui_col.size());
     P.lane_max = std::max(H.lane_max, 1);
     P.wi_max = H.wi_max;
+    P.tcap_r = H.tcap_r;
+    P.tcap_i = H.tcap_i;
     CK(dev_alloc(ctx, &P.sl_val, H.sl_col.size()), "alloc tiles");
     CK(dev_alloc(ctx, &P.su_val, H.su_col.size()), "alloc tiles");
     CK(dev_alloc(ctx, &P.si_val, H.si_col.size()), "alloc tiles");

@@ -136,8 +136,9 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
     int32_t mb = 0, wb = 0;
     for (int32_t j = color_ptr[c]; j < color_ptr[c + 1]; ++j) mb = std::max(mb, block_ptr[j + 1] - block_ptr[j]);
     if (mb > lane_max) continue;
-    // widest in-block row (lower or upper part): the tile's shared-memory
-    // staging must fit the budget
+    // widest in-block row (lower or upper part): a tile's shared-memory
+    // staging (both entry sets, sliced-ELL padding to the widest row) must
+    // fit the budget
     for (int32_t i = block_ptr[color_ptr[c]]; i < block_ptr[color_ptr[c + 1]]; ++i) {
       int32_t lo = 0, up = 0;
       for (int32_t e = H.arp[i]; e < H.arp[i + 1]; ++e) {
@@ -146,7 +147,7 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
       }
       wb = std::max(wb, std::max(lo, up));
     }
-    if (tile_smem_bytes(mb, wb, 8) > kTileSmemBudget) continue;
+    if (tile_launch_bytes(tile_plan(mb, kWarp * mb, kWarp * mb * wb, 8), true) > kTileSmemBudget) continue;
     tcol[c] = 1;
     H.tile_colors++;
     H.lane_max = std::max(H.lane_max, mb);
@@ -255,6 +256,7 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
   H.sl_col.clear(); H.su_col.clear(); H.sl_map.clear(); H.su_map.clear();
   H.si_col.clear(); H.ui_col.clear(); H.si_map.clear(); H.ui_map.clear();
   H.wi_max = 0;
+  H.tcap_r = H.tcap_i = 0;
   // appends, sliced-ELL, the entries of rows row .. row+cnt-1 that are
   // in-block (inb) or not; emap maps a CSR entry to its L entry (null:
   // itself); returns the width
@@ -289,7 +291,10 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
       td.row0 = tr.row0;
       td.nsteps = tr.nsteps;
       td.step0 = int32_t(H.steps.size());
-      td.nlanes = tr.nlanes;
+      td.lo0 = int32_t(H.sl_col.size());
+      td.li0 = int32_t(H.si_col.size());
+      td.uo0 = int32_t(H.su_col.size());
+      td.ui0 = int32_t(H.ui_col.size());
       int32_t row = tr.row0;
       for (int32_t k = 0; k < tr.nsteps; ++k) {
         const int32_t cnt = tr.cnt[k];
@@ -309,7 +314,14 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
         H.steps.push_back(sd);
         row += cnt;
       }
+      td.nrows = row - tr.row0;
+      td.lo1 = int32_t(H.sl_col.size());
+      td.li1 = int32_t(H.si_col.size());
+      td.uo1 = int32_t(H.su_col.size());
+      td.ui1 = int32_t(H.ui_col.size());
       H.wi_max = std::max(H.wi_max, std::max(td.wl, td.wu));
+      H.tcap_r = std::max(H.tcap_r, td.nrows);
+      H.tcap_i = std::max(H.tcap_i, std::max(td.li1 - td.li0, td.ui1 - td.ui0));
       H.tiles.push_back(td);
     }
   }

@@ -52,10 +52,12 @@ struct __align__(16) GroupDesc {
 
 constexpr int kGroup = 32;   // CTAs per first-level reduction group
 
-// A lane tile: its step descriptors are steps[step0 .. step0 + nsteps);
-// wl / wu: the widest in-block L / U step of the tile.
+// A lane tile: rows [row0, row0 + nrows), step descriptors steps[step0 ..
+// step0 + nsteps); its sliced-ELL entries are the contiguous ranges
+// [lo0, lo1) (L, other colors), [li0, li1) (L, in-block), [uo0, uo1),
+// [ui0, ui1) (U); wl / wu: its widest in-block L / U step.
 struct __align__(16) TileDesc {
-  int32_t row0, nsteps, step0, nlanes, wl, wu, pad0, pad1;
+  int32_t row0, nrows, nsteps, step0, lo0, lo1, li0, li1, uo0, uo1, ui0, ui1, wl, wu, pad0, pad1;
 };
 // One step of a tile: rows [row, row + cnt) (lanes 0 .. cnt-1; blocks are
 // sorted by size, so the active lanes are a prefix).  Sliced-ELL entry j of
@@ -67,11 +69,41 @@ struct __align__(16) StepDesc {
 constexpr int32_t kPadCol = 0x7fffffff;   // padding entry of a sliced-ELL step
 constexpr int kTileSmemBudget = 96 * 1024;  // shared memory of one tile's CTA, bytes
 
-// Shared memory of a lane tile's CTA: per step and lane the row's value (w)
-// and 1/L_ii, the staged in-block entries (column: step, value), and per step
-// (row, cnt, in-block width).
-__host__ __device__ inline int tile_smem_bytes(int steps, int width, int elem) {
-  return steps * kWarp * 2 * elem + steps * width * kWarp * (4 + elem) + steps * 3 * 4;
+// Shared memory of a lane tile's CTA (offsets in bytes, 16-byte aligned).
+// Two buffers, each: the step descriptors, 1/L_ii of the tile's rows and
+// the in-block sliced-ELL entries (steps, values) of L and/or U, copied as the
+// 16-byte-aligned cover of the tile's range (capacity: the largest tile + 16
+// bytes on either side); the CTA computes one tile from one buffer while the
+// next tile is copied into the other.  Then the row values w[step][lane].
+struct TilePlan {
+  int cap_s, cap_r, cap_i;          // steps, rows, in-block entries per tile
+  int o_steps, o_dv, o_ic, o_iv;    // within a buffer
+  int o_ic2, o_iv2;                 // second entry set (U of a fused launch)
+  int buf1, buf2;                   // buffer bytes with one / two entry sets
+  int w_bytes;
+};
+
+__host__ __device__ inline int r16b(int bytes) { return (bytes + 15) & ~15; }
+
+__host__ __device__ inline TilePlan tile_plan(int cap_s, int cap_r, int cap_i, int elem) {
+  TilePlan p;
+  p.cap_s = cap_s; p.cap_r = cap_r; p.cap_i = cap_i;
+  int o = 0;
+  p.o_steps = o; o += r16b(cap_s * 48);
+  p.o_dv = o; o += r16b((cap_r + 8) * elem);
+  p.o_ic = o; o += r16b((cap_i + 8) * 4);
+  p.o_iv = o; o += r16b((cap_i + 8) * elem);
+  p.buf1 = o;
+  p.o_ic2 = o; o += r16b((cap_i + 8) * 4);
+  p.o_iv2 = o; o += r16b((cap_i + 8) * elem);
+  p.buf2 = o;
+  p.w_bytes = r16b(cap_s * kWarp * elem);
+  return p;
+}
+
+// bytes of a lane-tile launch: two buffers and w
+__host__ __device__ inline int tile_launch_bytes(const TilePlan &p, bool two_sets) {
+  return 2 * (two_sets ? p.buf2 : p.buf1) + p.w_bytes;
 }
 
 // Grid barrier of the persistent solve kernel: arrival count, generation
@@ -140,6 +172,7 @@ struct Params {
   float *sl_val32, *su_val32, *si_val32, *ui_val32;
   int32_t nsl, nsu, nsi, nui;
   int32_t lane_max, wi_max;     // largest tile block (steps) and in-block width
+  int32_t tcap_r, tcap_i;       // largest tile: rows, in-block entries (L or U)
   // persistent solve: first group of each color [n_c + 1], grid barrier
   const int32_t *color_group;
   GridBar *bar;
@@ -170,6 +203,7 @@ struct HostLayout {
   std::vector<int32_t> sl_col, su_col, sl_map, su_map;
   std::vector<int32_t> si_col, ui_col, si_map, ui_map;
   int32_t wi_max = 0;                 // widest in-block step of any tile
+  int32_t tcap_r = 0, tcap_i = 0;     // largest tile: rows, in-block entries
   std::vector<int32_t> ord;           // internal row -> row of the caller's block-multicolor order
   int32_t lane_max = 0;               // largest block of a tile color
   int32_t tile_colors = 0;
@@ -197,8 +231,8 @@ struct Plan {
   std::vector<int32_t> task0, task1;    // group range of each color
   std::vector<int32_t> grid_c;          // CTAs of the color-c kernels
   std::vector<int32_t> tile0, tile1;    // tile range of each color (empty: groups)
-  int32_t Wt = 2;                       // warps (tiles) per CTA of the lane-tile kernels
-  int32_t smem_tile = 0;                // bytes per CTA of the lane-tile kernels
+  int32_t Wt = 8;                       // warps per CTA of the lane-tile kernels (one tile at a time)
+  int32_t smem_tile = 0, smem_tile2 = 0;  // bytes per CTA of the lane-tile kernels (one / two entry sets)
   std::vector<int32_t> off_rr, off_rz;  // slot regions of the color-c forward / backward launches
   int32_t last_rr = 0, last_rz = 0;     // slots written before the final launch of an iteration
   int32_t grid_a = 0;                   // CTAs of the SpMV-shaped kernels
@@ -217,6 +251,7 @@ cudaError_t configure_kernels();
 int group_smem_bytes(int cap, int rows, int levs, int elem);  // per-warp plan of the color kernels
 int spmv_smem_bytes(int cap);                                // per-warp staging of the SpMV
 int spmv_resident_ctas(int Wa, int smem);                    // CTAs per SM of the SpMV
+int tile_resident_ctas(bool fp32, int threads, int smem);    // CTAs per SM of the lane-tile kernels
 cudaError_t launch_factor(const Params &P, const Plan &L, int nL);
 cudaError_t launch_solve_init(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);
 cudaError_t launch_solve_body(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);

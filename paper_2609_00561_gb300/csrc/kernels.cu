@@ -67,6 +67,8 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// all but the most recently committed group
+__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -611,91 +613,99 @@ template <> __device__ __forceinline__ const float *uiv<float>(const Params &P) 
 
 __device__ __forceinline__ TileDesc load_tile(const TileDesc *t) {
   const int4 *p = reinterpret_cast<const int4 *>(t);
-  const int4 a = __ldg(p), b = __ldg(p + 1);
-  TileDesc d;
-  d.row0 = a.x; d.nsteps = a.y; d.step0 = a.z; d.nlanes = a.w;
-  d.wl = b.x; d.wu = b.y; d.pad0 = d.pad1 = 0;
-  return d;
+  const int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+  TileDesc r;
+  r.row0 = a.x; r.nrows = a.y; r.nsteps = a.z; r.step0 = a.w;
+  r.lo0 = b.x; r.lo1 = b.y; r.li0 = b.z; r.li1 = b.w;
+  r.uo0 = c.x; r.uo1 = c.y; r.ui0 = c.z; r.ui1 = c.w;
+  r.wl = d.x; r.wu = d.y; r.pad0 = r.pad1 = 0;
+  return r;
 }
 
-__device__ __forceinline__ StepDesc load_step(const StepDesc *s) {
-  const int4 *p = reinterpret_cast<const int4 *>(s);
-  const int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
-  StepDesc d;
-  d.row = a.x; d.cnt = a.y; d.lo = a.z; d.lw = a.w;
-  d.li = b.x; d.liw = b.y; d.uo = b.z; d.uw = b.w;
-  d.ui = c.x; d.uiw = c.y; d.pad0 = d.pad1 = 0;
-  return d;
-}
-
+// One staged buffer of a tile: step descriptors, 1/L_ii (index row - bdv),
+// in-block entries of the first and second set (index entry - base).
 template <typename PT>
-struct TileSmem {
-  PT *w, *dv, *sv;          // [step][lane], [step][lane], [step][j][lane]
-  int32_t *sc;              // [step][j][lane]
-  int32_t *mrow, *mcnt, *mw;  // [step]
+struct TileBuf {
+  const StepDesc *st;
+  const PT *dv;
+  const int32_t *ic, *ic2;
+  const PT *iv, *iv2;
 };
 
 template <typename PT>
-__device__ __forceinline__ TileSmem<PT> tile_smem(unsigned char *base, int S, int WI) {
-  TileSmem<PT> m;
-  m.w = reinterpret_cast<PT *>(base);
-  m.dv = m.w + S * kWarp;
-  m.sv = m.dv + S * kWarp;
-  m.sc = reinterpret_cast<int32_t *>(m.sv + S * WI * kWarp);
-  m.mrow = m.sc + S * WI * kWarp;
-  m.mcnt = m.mrow + S;
-  m.mw = m.mcnt + S;
-  return m;
+__device__ __forceinline__ TileBuf<PT> tile_buf(unsigned char *smem, const TilePlan &pl, int size, int k) {
+  unsigned char *b = smem + k * size;
+  TileBuf<PT> t;
+  t.st = reinterpret_cast<const StepDesc *>(b + pl.o_steps);
+  t.dv = reinterpret_cast<const PT *>(b + pl.o_dv);
+  t.ic = reinterpret_cast<const int32_t *>(b + pl.o_ic);
+  t.iv = reinterpret_cast<const PT *>(b + pl.o_iv);
+  t.ic2 = reinterpret_cast<const int32_t *>(b + pl.o_ic2);
+  t.iv2 = reinterpret_cast<const PT *>(b + pl.o_iv2);
+  return t;
 }
 
-// acc -= sum over a step's sliced-ELL entries to other colors of v * g[col],
-// storage order; loads in predicated batches of kChunk
+// Issue (no commit) the copies of tile t's static data into buffer tb:
+// steps, 1/L_ii, in-block entries of L (FIRST_UPPER = false) or U, and of U
+// as the second set when TWO.
+template <typename PT, bool FIRST_UPPER, bool TWO>
+__device__ __forceinline__ void tile_stage(const Params &P, const TileDesc &t, const TileBuf<PT> &tb) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  int4 *st = reinterpret_cast<int4 *>(const_cast<StepDesc *>(tb.st));
+  const int4 *gs = reinterpret_cast<const int4 *>(P.steps + t.step0);
+  for (int k = tid; k < t.nsteps * 3; k += nthr) cp_async16(st + k, gs + k);
+  stage_cover<PT>(invds<PT>(P), t.row0, t.row0 + t.nrows, const_cast<PT *>(tb.dv), tid, nthr);
+  const int i0 = FIRST_UPPER ? t.ui0 : t.li0, i1 = FIRST_UPPER ? t.ui1 : t.li1;
+  stage_cover<int32_t>(FIRST_UPPER ? P.ui_col : P.si_col, i0, i1, const_cast<int32_t *>(tb.ic), tid, nthr);
+  stage_cover<PT>(FIRST_UPPER ? uiv<PT>(P) : siv<PT>(P), i0, i1, const_cast<PT *>(tb.iv), tid, nthr);
+  if (TWO) {
+    stage_cover<int32_t>(P.ui_col, t.ui0, t.ui1, const_cast<int32_t *>(tb.ic2), tid, nthr);
+    stage_cover<PT>(uiv<PT>(P), t.ui0, t.ui1, const_cast<PT *>(tb.iv2), tid, nthr);
+  }
+}
+
+// acc -= sum over a step's sliced-ELL entries to other colors of v * g[col]
+// (coalesced loads of the entries, then the gathers; FMAs only for the
+// step's real width, a warp-uniform count; padding entries are (kPadCol, 0))
 template <typename PT>
-__device__ __forceinline__ PT sell_sub(const int32_t *col, const PT *val, int e, int stride, int width, PT acc,
-                                       const PT *g) {
+__device__ __forceinline__ PT ext_sub(const int32_t *col, const PT *val, int e, int stride, int width, PT acc,
+                                      const PT *g) {
   for (int j0 = 0; j0 < width; j0 += kChunk) {
+    const int nj = min(kChunk, width - j0);
     int cc[kChunk];
-    PT vv[kChunk];
+    PT vv[kChunk], xx[kChunk];
 #pragma unroll
     for (int j = 0; j < kChunk; ++j) {
-      const bool ok = j0 + j < width;
-      cc[j] = ok ? __ldg(col + e + (j0 + j) * stride) : kPadCol;
-      vv[j] = ok ? __ldg(val + e + (j0 + j) * stride) : PT(0);
+      cc[j] = j < nj ? __ldg(col + e + (j0 + j) * stride) : kPadCol;
+      vv[j] = j < nj ? __ldg(val + e + (j0 + j) * stride) : PT(0);
     }
-    PT xx[kChunk];
 #pragma unroll
     for (int j = 0; j < kChunk; ++j) xx[j] = cc[j] == kPadCol ? PT(0) : __ldcg(g + cc[j]);
 #pragma unroll
     for (int j = 0; j < kChunk; ++j)
-      if (cc[j] != kPadCol) acc -= vv[j] * xx[j];
+      if (j < nj) acc -= vv[j] * xx[j];
   }
   return acc;
 }
 
-// Phase A of a forward (UPPER = false: source r with the x / r update when
-// UPDATE, gathers of y) or backward (source y from shared memory or global
-// memory, gathers of z) sweep over a tile.
+// Phase A: forward (UPPER = false; source r with the x / r update when
+// UPDATE, gathers of y) or backward (source y from w or global memory,
+// gathers of z); the partial row value goes to w[step][lane].
 template <typename PT, bool UPPER, bool UPDATE>
-__device__ __forceinline__ void tile_phase_a(const Params &P, const TileDesc &t, const TileSmem<PT> &m, int WI,
+__device__ __forceinline__ void tile_phase_a(const Params &P, const TileDesc &t, const TileBuf<PT> &tb, PT *w,
                                              double alpha, const double *pn, bool y_in_smem, double &rr_acc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   PT *yv = reinterpret_cast<PT *>(P.y);
   const PT *zv = reinterpret_cast<const PT *>(P.z);
-  const PT *dinv = invds<PT>(P);
   for (int k = warp; k < t.nsteps; k += W) {
-    const StepDesc s = load_step(P.steps + t.step0 + k);
-    const int wi = UPPER ? s.uiw : s.liw;
-    if (lane == 0) {
-      m.mrow[k] = s.row;
-      m.mcnt[k] = s.cnt;
-      m.mw[k] = wi;
-    }
-    if (lane < s.cnt) {
+    const StepDesc &s = tb.st[k];
+    const int cnt = s.cnt;
+    if (lane < cnt) {
       const int i = s.row + lane;
       PT acc;
       if (UPPER) {
-        const PT src = y_in_smem ? m.w[k * kWarp + lane] : __ldcg(yv + i);
-        acc = sell_sub<PT>(P.su_col, suv<PT>(P), s.uo + lane, s.cnt, s.uw, src, zv);
+        const PT src = y_in_smem ? w[k * kWarp + lane] : __ldcg(yv + i);
+        acc = ext_sub<PT>(P.su_col, suv<PT>(P), s.uo + lane, cnt, s.uw, src, zv);
       } else {
         double ri = __ldcg(P.r + i);
         if (UPDATE) {
@@ -704,108 +714,141 @@ __device__ __forceinline__ void tile_phase_a(const Params &P, const TileDesc &t,
           P.xh[i] = __ldcg(P.xh + i) + alpha * __ldcg(pn + i);
           rr_acc += ri * ri;
         }
-        acc = sell_sub<PT>(P.sl_col, slv<PT>(P), s.lo + lane, s.cnt, s.lw, PT(ri), yv);
+        acc = ext_sub<PT>(P.sl_col, slv<PT>(P), s.lo + lane, cnt, s.lw, PT(ri), yv);
       }
-      m.w[k * kWarp + lane] = acc;
-      m.dv[k * kWarp + lane] = __ldg(dinv + i);
-      const int32_t *ic = UPPER ? P.ui_col : P.si_col;
-      const PT *iv = UPPER ? uiv<PT>(P) : siv<PT>(P);
-      const int eo = (UPPER ? s.ui : s.li) + lane;
-      for (int j = 0; j < wi; ++j) {
-        m.sc[(k * WI + j) * kWarp + lane] = __ldg(ic + eo + j * s.cnt);
-        m.sv[(k * WI + j) * kWarp + lane] = __ldg(iv + eo + j * s.cnt);
-      }
+      w[k * kWarp + lane] = acc;
     }
   }
 }
 
 // Phase B: warp 0 resolves the in-block recurrence, steps ascending (forward)
-// or descending (backward); a lane reads only its own block's values.
-// In-block padding entries have value 0 and step 0 (a finite value).
+// or descending (backward), from shared memory only; a lane reads only its
+// own block's values.  In-block padding entries are (step 0, value 0).
 template <typename PT, bool UPPER>
-__device__ __forceinline__ void tile_phase_b(const TileDesc &t, const TileSmem<PT> &m, int WI) {
+__device__ __forceinline__ void tile_phase_b(const TileDesc &t, const StepDesc *st, const PT *dv,
+                                             const int32_t *ic, const PT *iv, PT *w) {
   if (threadIdx.x >= kWarp) return;
   const int lane = threadIdx.x;
   for (int kk = 0; kk < t.nsteps; ++kk) {
     const int k = UPPER ? t.nsteps - 1 - kk : kk;
-    const int cnt = m.mcnt[k], wi = m.mw[k];
+    const StepDesc &s = st[k];
+    const int cnt = s.cnt, wi = UPPER ? s.uiw : s.liw, e = (UPPER ? s.ui : s.li) + lane;
     if (lane < cnt) {
-      PT acc = m.w[k * kWarp + lane];
-      for (int j = 0; j < wi; ++j) {
-        const int c = m.sc[(k * WI + j) * kWarp + lane];
-        acc -= m.sv[(k * WI + j) * kWarp + lane] * m.w[c * kWarp + lane];
-      }
-      m.w[k * kWarp + lane] = acc * m.dv[k * kWarp + lane];
+      PT acc = w[k * kWarp + lane];
+      for (int j = 0; j < wi; ++j) acc -= iv[e + j * cnt] * w[ic[e + j * cnt] * kWarp + lane];
+      w[k * kWarp + lane] = acc * dv[s.row + lane];
     }
   }
 }
 
 // Phase C: the tile's results to global memory (y or z), <r,z> (backward)
 template <typename PT, bool UPPER>
-__device__ __forceinline__ void tile_phase_c(const Params &P, const TileDesc &t, const TileSmem<PT> &m, bool store,
-                                             double &rz_acc) {
+__device__ __forceinline__ void tile_phase_c(const Params &P, const TileDesc &t, const StepDesc *st, const PT *w,
+                                             bool store, double &rz_acc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   PT *res = reinterpret_cast<PT *>(UPPER ? P.z : P.y);
   for (int k = warp; k < t.nsteps; k += W) {
-    const int cnt = m.mcnt[k], row = m.mrow[k];
-    if (lane < cnt) {
-      const int i = row + lane;
-      const PT v = m.w[k * kWarp + lane];
+    const StepDesc &s = st[k];
+    if (lane < s.cnt) {
+      const int i = s.row + lane;
+      const PT v = w[k * kWarp + lane];
       if (store) res[i] = v;
       if (UPPER) rz_acc += __ldcg(P.r + i) * double(v);
     }
   }
 }
 
+// A lane-tile launch: CTAs walk the color's tiles grid-stride; the static
+// data of the next tile is copied into the other buffer while the current one
+// is computed (the first tile's before griddepcontrol.wait); one <r,r> /
+// <r,z> reduction per CTA at the end.
 template <typename PT, int MODE, bool UPDATE>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
-tile_kernel(Params P, int t0, int fin, SlotArgs sa) {
+tile_kernel(Params P, int t0, int t1, TilePlan pl, int fin, SlotArgs sa) {
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[kMaxWarpsPerCta];
   __shared__ int flag;
-  const int S = P.lane_max, WI = P.wi_max;
-  const TileSmem<PT> m = tile_smem<PT>(smem, S, WI);
+  constexpr bool FU = MODE == M_BWD, TWO = MODE == M_FUSED;
+  const int bsize = TWO ? pl.buf2 : pl.buf1;
+  PT *w = reinterpret_cast<PT *>(smem + 2 * bsize);
   double rr_acc = 0.0, rz_acc = 0.0;
-  const TileDesc td = load_tile(P.tiles + t0 + blockIdx.x);
+  int t = t0 + int(blockIdx.x), buf = 0;
+  TileDesc td = load_tile(P.tiles + min(t, t1 - 1));
+  if (t < t1) tile_stage<PT, FU, TWO>(P, td, tile_buf<PT>(smem, pl, bsize, 0));
+  cp_commit();
   pdl_wait();
-  if (MODE == M_BWD) {
-    tile_phase_a<PT, true, false>(P, td, m, WI, 0.0, nullptr, false, rr_acc);
-    __syncthreads();
-    tile_phase_b<PT, true>(td, m, WI);
-    __syncthreads();
-    tile_phase_c<PT, true>(P, td, m, true, rz_acc);
-  } else {
-    const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
-    tile_phase_a<PT, false, UPDATE>(P, td, m, WI, alpha, P.p0, false, rr_acc);
-    __syncthreads();
-    tile_phase_b<PT, false>(td, m, WI);
-    __syncthreads();
-    if (MODE == M_FWD) {
-      tile_phase_c<PT, false>(P, td, m, true, rz_acc);
-    } else {
-      // the last color: y stays in shared memory for the backward sweep
-      tile_phase_a<PT, true, false>(P, td, m, WI, 0.0, nullptr, true, rr_acc);
-      __syncthreads();
-      tile_phase_b<PT, true>(td, m, WI);
-      __syncthreads();
-      tile_phase_c<PT, true>(P, td, m, true, rz_acc);
+  const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
+  for (; t < t1; t += gridDim.x) {
+    const int tn = t + int(gridDim.x);
+    TileDesc tdn = td;
+    if (tn < t1) {
+      tdn = load_tile(P.tiles + tn);
+      tile_stage<PT, FU, TWO>(P, tdn, tile_buf<PT>(smem, pl, bsize, buf ^ 1));
     }
+    cp_commit();
+    cp_wait_prev();
+    __syncthreads();
+    const TileBuf<PT> tb = tile_buf<PT>(smem, pl, bsize, buf);
+    const PT *dv = tb.dv - cover_base<PT>(td.row0);
+    if (MODE == M_BWD) {
+      tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, false, rr_acc);
+      __syncthreads();
+      tile_phase_b<PT, true>(td, tb.st, dv, tb.ic - cover_base<int32_t>(td.ui0), tb.iv - cover_base<PT>(td.ui0), w);
+      __syncthreads();
+      tile_phase_c<PT, true>(P, td, tb.st, w, true, rz_acc);
+    } else {
+      tile_phase_a<PT, false, UPDATE>(P, td, tb, w, alpha, P.p0, false, rr_acc);
+      __syncthreads();
+      tile_phase_b<PT, false>(td, tb.st, dv, tb.ic - cover_base<int32_t>(td.li0), tb.iv - cover_base<PT>(td.li0), w);
+      __syncthreads();
+      if (MODE == M_FWD) {
+        tile_phase_c<PT, false>(P, td, tb.st, w, true, rz_acc);
+      } else {
+        // the last color: y stays in shared memory for the backward sweep
+        tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, true, rr_acc);
+        __syncthreads();
+        tile_phase_b<PT, true>(td, tb.st, dv, tb.ic2 - cover_base<int32_t>(td.ui0),
+                               tb.iv2 - cover_base<PT>(td.ui0), w);
+        __syncthreads();
+        tile_phase_c<PT, true>(P, td, tb.st, w, true, rz_acc);
+      }
+    }
+    __syncthreads();   // buffer buf and w are reused by the next tile
+    buf ^= 1;
+    td = tdn;
   }
+  cp_wait_all();
   launch_epilogue(P, fin, sa, MODE != M_BWD && UPDATE, MODE != M_FWD, rr_acc, rz_acc, red, &flag);
 }
 
 // ---------------------------------------------------------------------------
 // p = z + beta p (start of an iteration; beta = 0 on the first)
 // ---------------------------------------------------------------------------
+// (two rows per thread per pass: 16-byte loads of p and, for FP64 z, of z)
 template <typename ZT>
 __global__ void __launch_bounds__(kVecThreads) pupdate_kernel(Params P) {
   pdl_trigger();
   pdl_wait();
   const double beta = __ldcg(&P.sc->beta);
   const ZT *z = reinterpret_cast<const ZT *>(P.z);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x)
-    P.p0[i] = double(__ldcg(z + i)) + beta * __ldcg(P.p0 + i);
+  const int n2 = P.n / 2;
+  const int stride = gridDim.x * blockDim.x;
+  double2 *p2 = reinterpret_cast<double2 *>(P.p0);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n2; k += stride) {
+    const double2 pv = __ldcg(p2 + k);
+    double z0, z1;
+    if (sizeof(ZT) == 8) {
+      const double2 zv = __ldcg(reinterpret_cast<const double2 *>(z) + k);
+      z0 = zv.x; z1 = zv.y;
+    } else {
+      const float2 zv = __ldcg(reinterpret_cast<const float2 *>(z) + k);
+      z0 = double(zv.x); z1 = double(zv.y);
+    }
+    p2[k] = make_double2(z0 + beta * pv.x, z1 + beta * pv.y);
+  }
+  if ((P.n & 1) && blockIdx.x == 0 && threadIdx.x == 0)
+    P.p0[P.n - 1] = double(__ldcg(z + P.n - 1)) + beta * __ldcg(P.p0 + P.n - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -852,8 +895,27 @@ spmv_kernel(Params P, int cap) {
       pdl_wait();
       waited = true;
     }
+    // the tile's widest row sets a warp-uniform FMA count; shorter rows add
+    // exact zeros
+    const int width = __reduce_max_sync(0xffffffffu, unsigned(re - rb));
     if (i < t1) {
-      const double s = -row_sub<double, double>(S, rb, re, 0.0, [&](int c) { return __ldcg(xin + c); });
+      double s = 0.0;
+      for (int j0 = 0; j0 < width; j0 += kChunk) {
+        const int nj = min(kChunk, width - j0);
+        int cc[kChunk];
+        double vv[kChunk], xx[kChunk];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+          const bool ok = rb + j0 + j < re;
+          cc[j] = ok ? S.c(rb + j0 + j) : -1;
+          vv[j] = ok ? S.v(rb + j0 + j) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) xx[j] = cc[j] >= 0 ? __ldcg(xin + cc[j]) : 0.0;
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j)
+          if (j < nj) s += vv[j] * xx[j];
+      }
       if (MODE == 0) {
         P.q[i] = s;
         acc += __ldcg(xin + i) * s;
@@ -1040,8 +1102,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-
-__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // Sense-reversing grid barrier with a bounded wait.  Returns false (for the
 // whole CTA) when this CTA or another one gave up; the error word stays set.
@@ -1406,15 +1466,22 @@ GroupSmemPlan plan_of(const Params &P, bool fused, bool upper) {
 }
 
 template <typename PT>
+TilePlan tile_plan_of(const Params &P) {
+  return tile_plan(P.lane_max, P.tcap_r, P.tcap_i, int(sizeof(PT)));
+}
+
+template <typename PT>
 cudaError_t launch_tile(const Params &P, const Plan &L, int c, int mode, bool update, int fin, const SlotArgs &sa) {
-  const int g = L.grid_c[c], t0 = L.tile0[c], th = L.Wt * kWarp, sm = L.smem_tile;
-  if (mode == M_BWD) return launch(tile_kernel<PT, M_BWD, false>, g, th, sm, L, P, t0, fin, sa);
+  const TilePlan pl = tile_plan_of<PT>(P);
+  const int g = L.grid_c[c], t0 = L.tile0[c], t1 = L.tile1[c], th = L.Wt * kWarp;
+  const int sm = tile_launch_bytes(pl, mode == M_FUSED);
+  if (mode == M_BWD) return launch(tile_kernel<PT, M_BWD, false>, g, th, sm, L, P, t0, t1, pl, fin, sa);
   if (update) {
-    if (mode == M_FUSED) return launch(tile_kernel<PT, M_FUSED, true>, g, th, sm, L, P, t0, fin, sa);
-    return launch(tile_kernel<PT, M_FWD, true>, g, th, sm, L, P, t0, fin, sa);
+    if (mode == M_FUSED) return launch(tile_kernel<PT, M_FUSED, true>, g, th, sm, L, P, t0, t1, pl, fin, sa);
+    return launch(tile_kernel<PT, M_FWD, true>, g, th, sm, L, P, t0, t1, pl, fin, sa);
   }
-  if (mode == M_FUSED) return launch(tile_kernel<PT, M_FUSED, false>, g, th, sm, L, P, t0, fin, sa);
-  return launch(tile_kernel<PT, M_FWD, false>, g, th, sm, L, P, t0, fin, sa);
+  if (mode == M_FUSED) return launch(tile_kernel<PT, M_FUSED, false>, g, th, sm, L, P, t0, t1, pl, fin, sa);
+  return launch(tile_kernel<PT, M_FWD, false>, g, th, sm, L, P, t0, t1, pl, fin, sa);
 }
 
 template <typename PT>
@@ -1503,6 +1570,18 @@ cudaError_t configure_pt() {
 
 int group_smem_bytes(int cap, int rows, int levs, int elem) { return group_smem_plan(cap, rows, levs, elem).total; }
 int spmv_smem_bytes(int cap) { return r16((cap + 8) * 8) + r16((cap + 8) * 4); }
+
+int tile_resident_ctas(bool fp32, int threads, int smem) {
+  int nb = 0;
+  const cudaError_t e =
+      fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tile_kernel<float, M_FUSED, true>, threads, size_t(smem))
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tile_kernel<double, M_FUSED, true>, threads, size_t(smem));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
 
 int spmv_resident_ctas(int Wa, int smem) {
   int nb = 0;
