@@ -1,6 +1,8 @@
 """Benchmark: ICCG time to 1e-8 relative residual on the 3D 7-point Poisson
 problem (128^3, n = 2,097,152, 14.58M nonzeros, b ~ U[-1,1] from seed 0) with
-ABMC blocking and greedy block coloring.
+ABMC blocking (block size 8 by default) and greedy block coloring.
+`--workload diffusion96 --fp32` runs the 27-point variable-coefficient
+diffusion problem (96^3, ABMC 32) with the FP32 preconditioner (extension 1).
 
 A step is one pass of the device hot path on inputs resident in HBM:
 iccg_factor (IC(0), FP64) followed by iccg_solve (PCG with block-multicolor
@@ -93,21 +95,36 @@ def dist_env():
     return rank, world, local
 
 
+WORKLOADS = {
+    "poisson128": "3D 7-point Poisson {nx}^3",
+    "diffusion96": "3D 27-point variable-coefficient diffusion {nx}^3 (contrast 1e3, shift 1e-6 max diag)",
+}
+
+
 def workload(args):
+    if args.workload == "diffusion96":
+        a = gen.diffusion3d_27pt(args.nx, seed=args.seed)
+        return a, gen.rhs_uniform(a.n, args.seed)
     a, b, _ = gen.config2(nx=args.nx, seed=args.seed)
     return a, b
 
 
 def bytes_model(n, nnz, nL, fp32):
     """Algorithmic bytes per PCG iteration (each array counted once, gathered
-    vector reads assumed cached), by kernel family of this implementation."""
+    vector reads assumed to hit cache), by kernel family:
+      SpMV + <p,q>   values and columns 12 nnz, row pointers 4n, p in 8n, q out 8n
+      p update       z, p in, p out: 24n (FP32 z: 20n)
+      forward sweep  L entries (value + column) per strictly-lower entry, row
+                     pointers 4n, 1/L_ii, the fused x/r update (r, q, x, p in,
+                     r, x out: 48n), y out
+      backward sweep U entries, row pointers 4n, 1/L_ii, y in, z out, r in (dot)
+    The substitution roofline uses forward + backward."""
     pe = 4 if fp32 else 8
-    spmv = 12 * nnz + 4 * n + 4 * 8 * n            # A, rowptr, z + p_old in, p_new + q out
-    fwd = (8 + 4) * nL if not fp32 else (4 + 4) * nL
-    fwd += 4 * n + pe * n + 8 * 6 * n + pe * n     # rowptr, 1/L_ii, r(rw) q x(rw) p, y out
-    bwd = (8 + 4) * nL if not fp32 else (4 + 4) * nL
-    bwd += 4 * n + pe * n + pe * n + 8 * n + pe * n  # rowptr, 1/L_ii, y in, r in, z out
-    return {"spmv": spmv, "subst": fwd + bwd, "total": spmv + fwd + bwd}
+    spmv = 12 * nnz + 4 * n + 16 * n
+    pupd = (16 + pe) * n + 8 * n
+    fwd = (pe + 4) * nL + 4 * n + pe * n + 48 * n + pe * n
+    bwd = (pe + 4) * nL + 4 * n + pe * n + pe * n + pe * n + 8 * n
+    return {"spmv": spmv, "pupdate": pupd, "subst": fwd + bwd, "total": spmv + pupd + fwd + bwd}
 
 
 def run_gpu(args):
@@ -209,7 +226,10 @@ def run_gpu(args):
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
 
     n_c = info["n_c"]
-    launches_per_step = (n_c + 1) + (2 + 2 * n_c - 1) + iters * (2 * n_c) + 1
+    # iccg_factor: one launch per color + finish; iccg_solve: perm_in, the
+    # residual SpMV, the 2 n_c - 1 color launches of z0, then per iteration
+    # p update + SpMV + 2 n_c - 1 color launches, and perm_out
+    launches_per_step = (n_c + 1) + (2 + 2 * n_c - 1) + iters * (2 + 2 * n_c - 1) + 1
     result = {
         "metric": "ICCG time to 1e-8 rel. residual",
         "value": round(ms, 4),
@@ -223,13 +243,15 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32+f64" if args.fp32 else "f64",
         "data": "synthetic",
-        "config": {"workload": f"3D 7-point Poisson {args.nx}^3 (n={a.n}, nnz={a.nnz}), b~U[-1,1] seed {args.seed}, "
+        "config": {"workload": WORKLOADS[args.workload].format(nx=args.nx) +
+                               f" (n={a.n}, nnz={a.nnz}), b~U[-1,1] seed {args.seed}, "
                                f"ABMC s={args.block_size} + greedy coloring (n_b={bl['n_b']}, n_c={n_c}), "
-                               f"IC(0) + PCG to {args.tol:g}",
+                               f"IC(0) + PCG to {args.tol:g}" + (", FP32 preconditioner" if args.fp32 else ""),
                    "step": "iccg_factor + iccg_solve, inputs resident",
-                   "l2": "inputs larger than L2 (A 175 MB + factors 180 MB > 129 MB)",
+                   "l2": "inputs larger than L2 (matrix + factors > 129 MB)",
                    "parallelism": "replicas only" if world > 1 else "1 GPU",
-                   "warps_per_cta": args.warps or 4, "rows_per_thread": args.rows or 1},
+                   "layout": f"{info['tile_colors']} of {n_c} colors as lane tiles ({info['tiles']} tiles), "
+                             f"{info['groups']} CTA groups"},
         "iterations": iters,
         "status": iccg.STATUS.get(st, st),
         "true_relres": true_rel,
@@ -239,7 +261,8 @@ def run_gpu(args):
         "setup": {"gen_s": round(t_gen, 3), "blocking_s": round(t_block, 3), "setup_s": round(t_setup, 3)},
         "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()},
         "phase_launches": phase_ln,
-        "roofline": {"bound": "hbm", "kernel": "block-multicolor substitution sweep (fwd + fused + bwd color kernels)",
+        "roofline": {"bound": "hbm", "kernel": "block-multicolor substitution sweep (forward, fused and backward "
+                                               "color launches of one PCG iteration)",
                      "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4), "peak_source": peak_src,
                      "bytes_per_iteration": bm["subst"], "launches_per_iteration": sub_launch / max(it_p, 1),
@@ -305,8 +328,9 @@ def run_reference(args):
               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
               "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
               "data": "synthetic",
-              "config": {"workload": f"3D 7-point Poisson {args.nx}^3, ABMC s={args.block_size} + greedy coloring, "
-                                     f"IC(0) + PCG to {args.tol:g} (CPU oracle)"},
+              "config": {"workload": WORKLOADS[args.workload].format(nx=args.nx) +
+                                     f", ABMC s={args.block_size} + greedy coloring, IC(0) + PCG to {args.tol:g} "
+                                     f"(CPU oracle)"},
               "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
                                "sample": f"each step: IC(0) + {args.cpu_sample_iters} PCG iterations, scaled to "
                                          f"{iters_full} iterations"},
@@ -320,19 +344,24 @@ def main():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--nx", type=int, default=128)
+    p.add_argument("--workload", default="poisson128", choices=sorted(WORKLOADS))
+    p.add_argument("--nx", type=int, default=None, help="grid side (default 128, or 96 for diffusion96)")
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--block-size", type=int, default=16)
+    p.add_argument("--block-size", type=int, default=None, help="ABMC block size (default 8, or 32 for diffusion96)")
     p.add_argument("--tol", type=float, default=1e-8)
     p.add_argument("--maxit", type=int, default=5000)
     p.add_argument("--fp32", action="store_true", help="FP32 preconditioner (extension 1)")
     p.add_argument("--warps", type=int, default=0)
     p.add_argument("--rows", type=int, default=0)
     p.add_argument("--cpu-sample-iters", type=int, default=20)
-    p.add_argument("--ref-iters", type=int, default=173,
+    p.add_argument("--ref-iters", type=int, default=176,
                    help="iterations the full solve takes (scales the reference sample)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args()
+    if args.nx is None:
+        args.nx = 96 if args.workload == "diffusion96" else 128
+    if args.block_size is None:
+        args.block_size = 32 if args.workload == "diffusion96" else 8
     if args.steps < 1 or args.warmup < 0:
         raise SystemExit("steps >= 1, warmup >= 0")
     if args.impl == "reference":

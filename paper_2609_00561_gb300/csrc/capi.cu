@@ -247,8 +247,28 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   // A and C)
   L.Wt = std::max(1, std::min(8, H.lane_max));
   {
-    const TilePlan tp = tile_plan(std::max(H.lane_max, 1), H.tcap_r, H.tcap_i, elem);
+    // every tile's in-block entries staged: two buffers within
+    // kTileSmemBudget, else one buffer within kTileSmemBudget1 (the fused
+    // launch's second set may then read global memory); else the capacity
+    // shrinks and larger tiles read their in-block entries from global memory
+    const int S = std::max(H.lane_max, 1);
+    int cap_i = H.tcap_i, nbuf = 2;
+    TilePlan tp = tile_plan(S, H.tcap_r, cap_i, elem);
+    if (tile_launch_bytes(tp, false) > kTileSmemBudget) {
+      nbuf = 1;
+      tp.nbuf = 1;
+      while (cap_i > 0 && tile_launch_bytes(tp, false) > kTileSmemBudget1) {
+        cap_i /= 2;
+        tp = tile_plan(S, H.tcap_r, cap_i, elem);
+        tp.nbuf = 1;
+      }
+    }
+    L.cap_ti = cap_i;
+    L.nbuf_t = nbuf;
     L.smem_tile = tile_launch_bytes(tp, false);
+    // the fused launch stages its second set only where both fit
+    L.cap_ti2 = tile_launch_bytes(tp, true) <= (nbuf == 2 ? kTileSmemBudget : kTileSmemBudget1) ? cap_i : 0;
+    tp.cap_i2 = L.cap_ti2;
     L.smem_tile2 = tile_launch_bytes(tp, true);
   }
   // a lane-tile launch: at most the CTAs the device holds at once, each
@@ -348,7 +368,9 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     P.lane_max = std::max(H.lane_max, 1);
     P.wi_max = H.wi_max;
     P.tcap_r = H.tcap_r;
-    P.tcap_i = H.tcap_i;
+    P.tcap_i = L.cap_ti;
+    P.tnbuf = L.nbuf_t;
+    P.tcap_i2 = L.cap_ti2;
     CK(dev_alloc(ctx, &P.sl_val, H.sl_col.size()), "alloc tiles");
     CK(dev_alloc(ctx, &P.su_val, H.su_col.size()), "alloc tiles");
     CK(dev_alloc(ctx, &P.si_val, H.si_col.size()), "alloc tiles");

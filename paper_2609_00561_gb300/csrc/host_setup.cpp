@@ -133,21 +133,12 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
   struct TileRows { int32_t row0, nsteps, nlanes; std::vector<int32_t> cnt; };
   std::vector<std::vector<TileRows>> ctiles(n_c > 0 ? n_c : 1);
   for (int32_t c = 0; c < n_c && lane_max > 0; ++c) {
-    int32_t mb = 0, wb = 0;
+    int32_t mb = 0;
     for (int32_t j = color_ptr[c]; j < color_ptr[c + 1]; ++j) mb = std::max(mb, block_ptr[j + 1] - block_ptr[j]);
     if (mb > lane_max) continue;
-    // widest in-block row (lower or upper part): a tile's shared-memory
-    // staging (both entry sets, sliced-ELL padding to the widest row) must
-    // fit the budget
-    for (int32_t i = block_ptr[color_ptr[c]]; i < block_ptr[color_ptr[c + 1]]; ++i) {
-      int32_t lo = 0, up = 0;
-      for (int32_t e = H.arp[i]; e < H.arp[i + 1]; ++e) {
-        const int32_t j = H.acol[e];
-        if (j != i && blk[j] == blk[i]) (j < i ? lo : up)++;
-      }
-      wb = std::max(wb, std::max(lo, up));
-    }
-    if (tile_launch_bytes(tile_plan(mb, kWarp * mb, kWarp * mb * wb, 8), true) > kTileSmemBudget) continue;
+    // a tile's step descriptors, 1/L_ii and row values must fit the CTA's
+    // shared memory (its in-block entries are staged only when they fit too)
+    if (tile_launch_bytes(tile_plan(mb, kWarp * mb, 0, 8), true) > kTileSmemBudget) continue;
     tcol[c] = 1;
     H.tile_colors++;
     H.lane_max = std::max(H.lane_max, mb);

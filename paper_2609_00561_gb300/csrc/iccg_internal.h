@@ -67,20 +67,24 @@ struct __align__(16) StepDesc {
   int32_t row, cnt, lo, lw, li, liw, uo, uw, ui, uiw, pad0, pad1;
 };
 constexpr int32_t kPadCol = 0x7fffffff;   // padding entry of a sliced-ELL step
-constexpr int kTileSmemBudget = 96 * 1024;  // shared memory of one tile's CTA, bytes
+constexpr int kTileSmemBudget = 96 * 1024;      // lane-tile CTA with two buffers, bytes
+constexpr int kTileSmemBudget1 = 200 * 1024;    // lane-tile CTA with one buffer, bytes
 
 // Shared memory of a lane tile's CTA (offsets in bytes, 16-byte aligned).
 // Two buffers, each: the step descriptors, 1/L_ii of the tile's rows and
 // the in-block sliced-ELL entries (steps, values) of L and/or U, copied as the
-// 16-byte-aligned cover of the tile's range (capacity: the largest tile + 16
-// bytes on either side); the CTA computes one tile from one buffer while the
-// next tile is copied into the other.  Then the row values w[step][lane].
+// 16-byte-aligned cover of the tile's range (capacity cap_i entries + 16 bytes
+// on either side; a tile with more in-block entries reads them from global
+// memory); the CTA computes one tile from one buffer while the next tile is
+// copied into the other.  Then the row values w[step][lane].
 struct TilePlan {
   int cap_s, cap_r, cap_i;          // steps, rows, in-block entries per tile
   int o_steps, o_dv, o_ic, o_iv;    // within a buffer
   int o_ic2, o_iv2;                 // second entry set (U of a fused launch)
   int buf1, buf2;                   // buffer bytes with one / two entry sets
   int w_bytes;
+  int nbuf;                         // 2: the next tile is copied while one is computed; 1: in turn
+  int cap_i2;                       // second-set capacity of a fused launch (0: read from global memory)
 };
 
 __host__ __device__ inline int r16b(int bytes) { return (bytes + 15) & ~15; }
@@ -98,12 +102,14 @@ __host__ __device__ inline TilePlan tile_plan(int cap_s, int cap_r, int cap_i, i
   p.o_iv2 = o; o += r16b((cap_i + 8) * elem);
   p.buf2 = o;
   p.w_bytes = r16b(cap_s * kWarp * elem);
+  p.nbuf = 2;
+  p.cap_i2 = cap_i;
   return p;
 }
 
-// bytes of a lane-tile launch: two buffers and w
+// bytes of a lane-tile launch: nbuf buffers and w
 __host__ __device__ inline int tile_launch_bytes(const TilePlan &p, bool two_sets) {
-  return 2 * (two_sets ? p.buf2 : p.buf1) + p.w_bytes;
+  return p.nbuf * (two_sets && p.cap_i2 > 0 ? p.buf2 : p.buf1) + p.w_bytes;
 }
 
 // Grid barrier of the persistent solve kernel: arrival count, generation
@@ -172,7 +178,9 @@ struct Params {
   float *sl_val32, *su_val32, *si_val32, *ui_val32;
   int32_t nsl, nsu, nsi, nui;
   int32_t lane_max, wi_max;     // largest tile block (steps) and in-block width
-  int32_t tcap_r, tcap_i;       // largest tile: rows, in-block entries (L or U)
+  int32_t tcap_r, tcap_i;       // largest tile rows; in-block entries staged per tile (L or U)
+  int32_t tnbuf;                // lane-tile staging buffers per CTA (1 or 2)
+  int32_t tcap_i2;              // fused launch: second-set staging capacity (0: global)
   // persistent solve: first group of each color [n_c + 1], grid barrier
   const int32_t *color_group;
   GridBar *bar;
@@ -233,6 +241,9 @@ struct Plan {
   std::vector<int32_t> tile0, tile1;    // tile range of each color (empty: groups)
   int32_t Wt = 8;                       // warps per CTA of the lane-tile kernels (one tile at a time)
   int32_t smem_tile = 0, smem_tile2 = 0;  // bytes per CTA of the lane-tile kernels (one / two entry sets)
+  int32_t cap_ti = 0;                   // in-block entries of a tile staged in shared memory
+  int32_t nbuf_t = 2;                   // lane-tile staging buffers per CTA
+  int32_t cap_ti2 = 0;                  // second-set (fused launch) staging capacity
   std::vector<int32_t> off_rr, off_rz;  // slot regions of the color-c forward / backward launches
   int32_t last_rr = 0, last_rz = 0;     // slots written before the final launch of an iteration
   int32_t grid_a = 0;                   // CTAs of the SpMV-shaped kernels

@@ -647,21 +647,40 @@ __device__ __forceinline__ TileBuf<PT> tile_buf(unsigned char *smem, const TileP
 
 // Issue (no commit) the copies of tile t's static data into buffer tb:
 // steps, 1/L_ii, in-block entries of L (FIRST_UPPER = false) or U, and of U
-// as the second set when TWO.
+// as the second set when TWO; an in-block range larger than the capacity
+// stays in global memory.
 template <typename PT, bool FIRST_UPPER, bool TWO>
-__device__ __forceinline__ void tile_stage(const Params &P, const TileDesc &t, const TileBuf<PT> &tb) {
+__device__ __forceinline__ void tile_stage(const Params &P, const TileDesc &t, const TileBuf<PT> &tb, int cap_i,
+                                           int cap_i2) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   int4 *st = reinterpret_cast<int4 *>(const_cast<StepDesc *>(tb.st));
   const int4 *gs = reinterpret_cast<const int4 *>(P.steps + t.step0);
   for (int k = tid; k < t.nsteps * 3; k += nthr) cp_async16(st + k, gs + k);
   stage_cover<PT>(invds<PT>(P), t.row0, t.row0 + t.nrows, const_cast<PT *>(tb.dv), tid, nthr);
   const int i0 = FIRST_UPPER ? t.ui0 : t.li0, i1 = FIRST_UPPER ? t.ui1 : t.li1;
-  stage_cover<int32_t>(FIRST_UPPER ? P.ui_col : P.si_col, i0, i1, const_cast<int32_t *>(tb.ic), tid, nthr);
-  stage_cover<PT>(FIRST_UPPER ? uiv<PT>(P) : siv<PT>(P), i0, i1, const_cast<PT *>(tb.iv), tid, nthr);
-  if (TWO) {
+  if (i1 - i0 <= cap_i) {
+    stage_cover<int32_t>(FIRST_UPPER ? P.ui_col : P.si_col, i0, i1, const_cast<int32_t *>(tb.ic), tid, nthr);
+    stage_cover<PT>(FIRST_UPPER ? uiv<PT>(P) : siv<PT>(P), i0, i1, const_cast<PT *>(tb.iv), tid, nthr);
+  }
+  if (TWO && t.ui1 - t.ui0 <= cap_i2) {
     stage_cover<int32_t>(P.ui_col, t.ui0, t.ui1, const_cast<int32_t *>(tb.ic2), tid, nthr);
     stage_cover<PT>(uiv<PT>(P), t.ui0, t.ui1, const_cast<PT *>(tb.iv2), tid, nthr);
   }
+}
+
+// The in-block entries a tile's chain reads: staged (index entry - base) or
+// the global arrays.
+template <typename PT>
+struct InBlock {
+  const int32_t *ic;
+  const PT *iv;
+};
+
+template <typename PT>
+__device__ __forceinline__ InBlock<PT> in_block(const int32_t *sc, const PT *sv, const int32_t *gc, const PT *gv,
+                                               int i0, int i1, int cap_i) {
+  if (i1 - i0 <= cap_i) return InBlock<PT>{sc - cover_base<int32_t>(i0), sv - cover_base<PT>(i0)};
+  return InBlock<PT>{gc, gv};
 }
 
 // acc -= sum over a step's sliced-ELL entries to other colors of v * g[col]
@@ -770,52 +789,60 @@ tile_kernel(Params P, int t0, int t1, TilePlan pl, int fin, SlotArgs sa) {
   __shared__ double red[kMaxWarpsPerCta];
   __shared__ int flag;
   constexpr bool FU = MODE == M_BWD, TWO = MODE == M_FUSED;
-  const int bsize = TWO ? pl.buf2 : pl.buf1;
-  PT *w = reinterpret_cast<PT *>(smem + 2 * bsize);
+  const int bsize = TWO && pl.cap_i2 > 0 ? pl.buf2 : pl.buf1;
+  const int nbuf = pl.nbuf;
+  PT *w = reinterpret_cast<PT *>(smem + nbuf * bsize);
   double rr_acc = 0.0, rz_acc = 0.0;
   int t = t0 + int(blockIdx.x), buf = 0;
   TileDesc td = load_tile(P.tiles + min(t, t1 - 1));
-  if (t < t1) tile_stage<PT, FU, TWO>(P, td, tile_buf<PT>(smem, pl, bsize, 0));
+  if (t < t1) tile_stage<PT, FU, TWO>(P, td, tile_buf<PT>(smem, pl, bsize, 0), pl.cap_i, pl.cap_i2);
   cp_commit();
   pdl_wait();
   const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
   for (; t < t1; t += gridDim.x) {
     const int tn = t + int(gridDim.x);
     TileDesc tdn = td;
-    if (tn < t1) {
-      tdn = load_tile(P.tiles + tn);
-      tile_stage<PT, FU, TWO>(P, tdn, tile_buf<PT>(smem, pl, bsize, buf ^ 1));
-    }
+    if (tn < t1) tdn = load_tile(P.tiles + tn);
+    if (tn < t1 && nbuf == 2) tile_stage<PT, FU, TWO>(P, tdn, tile_buf<PT>(smem, pl, bsize, buf ^ 1), pl.cap_i, pl.cap_i2);
     cp_commit();
     cp_wait_prev();
     __syncthreads();
     const TileBuf<PT> tb = tile_buf<PT>(smem, pl, bsize, buf);
     const PT *dv = tb.dv - cover_base<PT>(td.row0);
+    const InBlock<PT> ul = in_block<PT>(tb.ic, tb.iv, P.ui_col, uiv<PT>(P), td.ui0, td.ui1, pl.cap_i);
+    const InBlock<PT> ll = in_block<PT>(tb.ic, tb.iv, P.si_col, siv<PT>(P), td.li0, td.li1, pl.cap_i);
     if (MODE == M_BWD) {
       tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, false, rr_acc);
       __syncthreads();
-      tile_phase_b<PT, true>(td, tb.st, dv, tb.ic - cover_base<int32_t>(td.ui0), tb.iv - cover_base<PT>(td.ui0), w);
+      tile_phase_b<PT, true>(td, tb.st, dv, ul.ic, ul.iv, w);
       __syncthreads();
       tile_phase_c<PT, true>(P, td, tb.st, w, true, rz_acc);
     } else {
       tile_phase_a<PT, false, UPDATE>(P, td, tb, w, alpha, P.p0, false, rr_acc);
       __syncthreads();
-      tile_phase_b<PT, false>(td, tb.st, dv, tb.ic - cover_base<int32_t>(td.li0), tb.iv - cover_base<PT>(td.li0), w);
+      tile_phase_b<PT, false>(td, tb.st, dv, ll.ic, ll.iv, w);
       __syncthreads();
       if (MODE == M_FWD) {
         tile_phase_c<PT, false>(P, td, tb.st, w, true, rz_acc);
       } else {
         // the last color: y stays in shared memory for the backward sweep
+        const InBlock<PT> u2 = in_block<PT>(tb.ic2, tb.iv2, P.ui_col, uiv<PT>(P), td.ui0, td.ui1, pl.cap_i2);
         tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, true, rr_acc);
         __syncthreads();
-        tile_phase_b<PT, true>(td, tb.st, dv, tb.ic2 - cover_base<int32_t>(td.ui0),
-                               tb.iv2 - cover_base<PT>(td.ui0), w);
+        tile_phase_b<PT, true>(td, tb.st, dv, u2.ic, u2.iv, w);
         __syncthreads();
         tile_phase_c<PT, true>(P, td, tb.st, w, true, rz_acc);
       }
     }
     __syncthreads();   // buffer buf and w are reused by the next tile
-    buf ^= 1;
+    if (nbuf == 1) {
+      // one buffer: the next tile's copies start now (waited on by the next
+      // pass's cp_wait_prev, which leaves only its own empty group pending)
+      if (tn < t1) tile_stage<PT, FU, TWO>(P, tdn, tile_buf<PT>(smem, pl, bsize, 0), pl.cap_i, pl.cap_i2);
+      cp_commit();
+    } else {
+      buf ^= 1;
+    }
     td = tdn;
   }
   cp_wait_all();
@@ -1467,7 +1494,10 @@ GroupSmemPlan plan_of(const Params &P, bool fused, bool upper) {
 
 template <typename PT>
 TilePlan tile_plan_of(const Params &P) {
-  return tile_plan(P.lane_max, P.tcap_r, P.tcap_i, int(sizeof(PT)));
+  TilePlan p = tile_plan(P.lane_max, P.tcap_r, P.tcap_i, int(sizeof(PT)));
+  p.nbuf = P.tnbuf;
+  p.cap_i2 = P.tcap_i2;
+  return p;
 }
 
 template <typename PT>
