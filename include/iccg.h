@@ -174,6 +174,57 @@ iccg_status iccg_last_error(const iccg_ctx *ctx, int64_t *row_or_block, const ch
 void iccg_destroy(iccg_ctx *ctx);
 
 /* ------------------------------------------------------------------------
+ * Batched solve (extension: many systems, several right-hand sides each, in
+ * one launch).  Each system is the ICCG of iccg_solve (Alg. 1 substitutions
+ * inside standard PCG) run for all its right-hand sides at once; the systems
+ * are independent.  The whole solve is one cooperative kernel launch (the
+ * PCG loop runs inside it) replayed as a CUDA graph.
+ *
+ *   iccg_batch_create  ctxs[nsys]: factored contexts on one device, all with
+ *                      the same precond_fp32, set up with lane_block_max = -1
+ *                      (CTA-group layout, blocks of at most 64 rows); the
+ *                      batch borrows them (destroy the batch first) and runs
+ *                      on ctxs[0]'s stream.  nrhs in 1..32.  opts may be NULL
+ *                      (warps_per_cta 0 = 8, ctas_per_sm 0 = as many as fit,
+ *                      autotune 1 = time every candidate shape on a short
+ *                      solve and keep the fastest, reserved must be 0).
+ *                      Errors: ICCG_ERR_ARG (arguments, layouts), ICCG_ERR_STATE
+ *                      (a context not factored), ICCG_ERR_CUDA.
+ *   iccg_batch_solve   B[s], X[s]: double[nrhs * n_s], right-hand side j of
+ *                      system s at B[s][j * n_s ..] in the original numbering
+ *                      (host or device); X[s] holds x0 on entry and x on
+ *                      return.  Stops each right-hand side at ||r||/||b|| <=
+ *                      tol or maxit iterations.  iters / status (may be NULL):
+ *                      int32[nsys * nrhs]; res_hist (may be NULL, or entries
+ *                      NULL): res_hist[s] = host double[(maxit + 1) * nrhs],
+ *                      entry (k, j) = ||r_k||/||b|| of right-hand side j (0
+ *                      past its last iteration).  Returns ICCG_OK when every
+ *                      right-hand side converged, else the worst status.
+ *   iccg_batch_tune    re-runs the shape search; *best_ms (may be NULL) gets
+ *                      the chosen shape's time for a 5-iteration solve.
+ *   iccg_batch_info    out[5]: warps per CTA, CTAs per SM, grid, padded nrhs,
+ *                      largest block.
+ * The paper has no batched solver; this serves many independent systems
+ * (e.g. the learned-blocking sweep) and multiple right-hand sides.
+ * ------------------------------------------------------------------------ */
+typedef struct iccg_batch iccg_batch;
+typedef struct {
+  int32_t warps_per_cta;
+  int32_t ctas_per_sm;
+  int32_t autotune;
+  int32_t reserved[5];
+} iccg_batch_opts;
+
+iccg_status iccg_batch_create(iccg_batch **batch, iccg_ctx *const *ctxs, int32_t nsys, int32_t nrhs,
+                              const iccg_batch_opts *opts);
+iccg_status iccg_batch_solve(iccg_batch *batch, const double *const *B, double *const *X, double tol,
+                             int32_t maxit, int32_t *iters, int32_t *status, double *const *res_hist);
+iccg_status iccg_batch_tune(iccg_batch *batch, double *best_ms);
+iccg_status iccg_batch_info(const iccg_batch *batch, int32_t out[5]);
+iccg_status iccg_batch_last_error(const iccg_batch *batch, const char **msg);
+void iccg_batch_destroy(iccg_batch *batch);
+
+/* ------------------------------------------------------------------------
  * iccg_spmv_dot_noalloc -- q = A p and *pq = <p, q> with no device
  * allocation at all.  The paper has no counterpart: this entry point exists
  * for callers that cannot allocate device memory where they need the

@@ -12,32 +12,6 @@
 using namespace iccg;
 
 
-struct iccg_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  iccg_opts opts{};
-  bool fp32 = false;
-  bool persistent = false;         // the whole solve as one cooperative launch
-  HostLayout H;
-  Plan plan;
-  Params P{};
-  bool factored = false;
-  std::vector<void *> allocs;
-  // solve state
-  double *hist = nullptr;
-  int32_t hist_cap = 0;
-  double *bin = nullptr, *xin = nullptr, *xout = nullptr;
-  Scalars *sc_host = nullptr;      // pinned
-  double *hist_host = nullptr;     // pinned
-  int32_t hist_host_cap = 0;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  unsigned long long cond_handle = 0;
-  // error record
-  int64_t err_index = -1;
-  std::string err_msg;
-};
-
 namespace {
 
 struct DeviceGuard {

@@ -279,3 +279,31 @@ cudaError_t launch_permute(const double *src, double *dst, const int32_t *perm, 
 cudaError_t launch_widen(const float *src, double *dst, int32_t n, int32_t grid, cudaStream_t s);
 
 }  // namespace iccg
+
+// A context (C ABI handle): the layout, the launch plan, device arrays and
+// solve state of one system.
+struct iccg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  iccg_opts opts{};
+  bool fp32 = false;
+  bool persistent = false;         // the whole solve as one cooperative launch
+  iccg::HostLayout H;
+  iccg::Plan plan;
+  iccg::Params P{};
+  bool factored = false;
+  std::vector<void *> allocs;
+  // solve state
+  double *hist = nullptr;
+  int32_t hist_cap = 0;
+  double *bin = nullptr, *xin = nullptr, *xout = nullptr;
+  iccg::Scalars *sc_host = nullptr;      // pinned
+  double *hist_host = nullptr;     // pinned
+  int32_t hist_host_cap = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  unsigned long long cond_handle = 0;
+  // error record
+  int64_t err_index = -1;
+  std::string err_msg;
+};

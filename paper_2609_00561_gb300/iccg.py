@@ -39,6 +39,11 @@ class iccg_opts(ctypes.Structure):
 SOLVERS = {"auto": 0, "persistent": 1, "phased": 2}
 
 
+class iccg_batch_opts(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
 _lib = None
 
 
@@ -68,6 +73,11 @@ def load():
         "iccg_sort_blocks_desc": [i32, i32, vp],
         "iccg_color_order": [i32, vp, vp, i32, vp, vp, P(i32), vp, vp, vp],
         "iccg_spmv_dot_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp],
+        "iccg_batch_create": [P(vp), vp, i32, i32, P(iccg_batch_opts)],
+        "iccg_batch_solve": [vp, vp, vp, d, i32, vp, vp, vp],
+        "iccg_batch_tune": [vp, P(d)],
+        "iccg_batch_info": [vp, vp],
+        "iccg_batch_last_error": [vp, P(ctypes.c_char_p)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -75,6 +85,8 @@ def load():
         f.restype = ctypes.c_int
     L.iccg_destroy.argtypes = [vp]
     L.iccg_destroy.restype = None
+    L.iccg_batch_destroy.argtypes = [vp]
+    L.iccg_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -325,3 +337,81 @@ class Solver:
                 self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# batched solve (many systems, several right-hand sides each, one launch)
+# ---------------------------------------------------------------------------
+def _batch_check(st, where, h):
+    if st in (ICCG_OK, ICCG_NOT_CONVERGED):
+        return st
+    m = ctypes.c_char_p()
+    if h:
+        load().iccg_batch_last_error(h, ctypes.byref(m))
+    raise IccgError(st, where, -1, (m.value or b"").decode())
+
+
+class BatchSolver:
+    """iccg_batch over factored Solvers (set up with lane_block_max=-1)."""
+
+    def __init__(self, solvers, nrhs, warps_per_cta=0, ctas_per_sm=0, autotune=False):
+        self.solvers = list(solvers)
+        self.nrhs = int(nrhs)
+        self.ns = [s.n for s in self.solvers]
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s.ctx for s in self.solvers])
+        o = iccg_batch_opts()
+        o.warps_per_cta, o.ctas_per_sm, o.autotune = int(warps_per_cta), int(ctas_per_sm), int(bool(autotune))
+        h = ctypes.c_void_p()
+        st = load().iccg_batch_create(ctypes.byref(h), arr, len(self.solvers), self.nrhs, ctypes.byref(o))
+        self.h = h
+        if st != ICCG_OK:
+            err = None
+            try:
+                _batch_check(st, "iccg_batch_create", h)
+            except IccgError as e:
+                err = e
+            if h.value:
+                load().iccg_batch_destroy(h)
+                self.h = None
+            raise err
+
+    def info(self):
+        out = np.zeros(5, dtype=np.int32)
+        _batch_check(load().iccg_batch_info(self.h, _ptr(out)), "iccg_batch_info", self.h)
+        return dict(zip(("warps_per_cta", "ctas_per_sm", "grid", "kp", "smax"), out.tolist()))
+
+    def tune(self):
+        ms = ctypes.c_double(0.0)
+        _batch_check(load().iccg_batch_tune(self.h, ctypes.byref(ms)), "iccg_batch_tune", self.h)
+        return ms.value
+
+    def solve(self, B, X, tol=1e-8, maxit=10000, want_hist=False):
+        """B[s], X[s]: (nrhs, n_s) C-contiguous float64 (numpy or torch, host or
+        device); X holds x0 and receives x.  Returns (status, iters, per-RHS
+        status, histories)."""
+        ns = len(self.solvers)
+        bp = (ctypes.c_void_p * ns)(*[_ptr(b) for b in B])
+        xp = (ctypes.c_void_p * ns)(*[_ptr(x) for x in X])
+        it = np.zeros(ns * self.nrhs, dtype=np.int32)
+        stv = np.zeros(ns * self.nrhs, dtype=np.int32)
+        hists = None
+        hp = None
+        if want_hist:
+            hists = [np.zeros((maxit + 1, self.nrhs)) for _ in range(ns)]
+            hp = (ctypes.c_void_p * ns)(*[h.ctypes.data for h in hists])
+        st = load().iccg_batch_solve(self.h, bp, xp, float(tol), int(maxit), _ptr(it), _ptr(stv), hp)
+        if st not in (ICCG_OK, ICCG_NOT_CONVERGED, 7):
+            _batch_check(st, "iccg_batch_solve", self.h)
+        return st, it.reshape(ns, self.nrhs), stv.reshape(ns, self.nrhs), hists
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().iccg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -80,6 +80,12 @@ def test_setup_rejects_bad_inputs_before_gpu():
         with pytest.raises(iccg.IccgError) as ei:
             iccg.iccg_setup(a.n, a.nnz, a.rowptr, a.colind, a.val, perm, bp, cp, nb, nc, iccg.make_opts(**kw))
         assert ei.value.status == 1, kw
+    # batched: null contexts, bad right-hand-side counts
+    import ctypes
+    L = iccg.load()
+    h = ctypes.c_void_p()
+    for nsys, nrhs in ((0, 4), (1, 0), (1, 33)):
+        assert L.iccg_batch_create(ctypes.byref(h), None, nsys, nrhs, None) == 1
     o = iccg.make_opts()
     o.reserved[0] = 1
     with pytest.raises(iccg.IccgError) as ei:
