@@ -3,6 +3,9 @@ problem (128^3, n = 2,097,152, 14.58M nonzeros, b ~ U[-1,1] from seed 0) with
 ABMC blocking (block size 8 by default) and greedy block coloring.
 `--workload diffusion96 --fp32` runs the 27-point variable-coefficient
 diffusion problem (96^3, ABMC 32) with the FP32 preconditioner (extension 1).
+`--workload batch64` runs the batched extension: 64 shifted 7-point systems
+(sides U{16..64}), 16 right-hand sides each, ABMC 32, FP32 preconditioner,
+all in one launch; a step is the whole batch solved to 1e-8.
 
 A step is one pass of the device hot path on inputs resident in HBM:
 iccg_factor (IC(0), FP64) followed by iccg_solve (PCG with block-multicolor
@@ -98,6 +101,7 @@ def dist_env():
 WORKLOADS = {
     "poisson128": "3D 7-point Poisson {nx}^3",
     "diffusion96": "3D 27-point variable-coefficient diffusion {nx}^3 (contrast 1e3, shift 1e-6 max diag)",
+    "batch64": "batch of 64 shifted 3D 7-point systems (sides U{{16..64}}, shift U[1e-4,1e-1]) x 16 right-hand sides",
 }
 
 
@@ -282,6 +286,133 @@ def run_gpu(args):
         print(json.dumps(result))
 
 
+def run_batch(args):
+    """Extension 2: the whole batch (every system, every right-hand side) to
+    tol in one launch per step; inputs resident.  The plain FP64 GPU solver
+    is timed on the first right-hand side of every system (scaled by the
+    right-hand-side count) for the comparison."""
+    import torch
+    from paper_2609_00561_gb300 import build as libbuild
+    from paper_2609_00561_gb300 import iccg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    libbuild.build()
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    systems, opt = gen.config4(seed=args.seed, nsys=args.nsys, nrhs=args.nrhs)
+    t_gen = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    blocks = [iccg.blocking(a, "abmc", args.block_size) for a, _ in systems]
+    t_block = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    solvers = [iccg.Solver(a, bl, precond_fp32=not args.fp64_batch, lane_block_max=-1, stream=stream.cuda_stream)
+               for (a, _), bl in zip(systems, blocks)]
+    bs = iccg.BatchSolver(solvers, args.nrhs)
+    B = [torch.tensor(b, device=dev) for _, b in systems]
+    tune_ms = bs.tune(B, args.tol, args.maxit)     # shape search on this batch (setup, untimed)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    shape = bs.info()
+    X = [torch.zeros_like(b) for b in B]
+
+    def step():
+        for x in X:
+            x.zero_()
+        return bs.solve(B, X, args.tol, args.maxit)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st, its, stv, _ = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # accuracy: true residual of every right-hand side; FP64 oracle on a sample
+    worst_res = 0.0
+    for (a, b), x in zip(systems, X):
+        m = a.to_scipy()
+        xh = x.cpu().numpy()
+        for j in range(b.shape[0]):
+            worst_res = max(worst_res, float(np.linalg.norm(b[j] - m @ xh[j]) / np.linalg.norm(b[j])))
+    # bytes per right-hand-side iteration (matrix + factors shared, vectors per RHS)
+    pe = 8 if args.fp64_batch else 4
+    tot_bytes = 0.0
+    for (a, b), S, it_s in zip(systems, solvers, its):
+        info = S.info()
+        mat = 12 * info["nnz"] + (pe + 4) * 2 * info["nL"] + (4 * 3 + pe) * info["n"]
+        vec = (8 * 12 + pe * 6) * info["n"]      # x, r, p, q, y, z traffic of one iteration per RHS
+        tot_bytes += float(int(it_s.max())) * mat + float(it_s.sum()) * vec
+    achieved = tot_bytes / (ms * 1e-3) / 1e9
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    # plain FP64 single-system GPU solve of the first right-hand side of each system
+    single_ms = 0.0
+    for (a, b), bl in zip(systems, blocks):
+        S1 = iccg.Solver(a, bl, stream=stream.cuda_stream)
+        bd = torch.tensor(b[0], device=dev)
+        xd = torch.zeros_like(bd)
+        iccg.iccg_solve(S1.ctx, bd, xd, args.tol, args.maxit, want_hist=False)
+        xd.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        iccg.iccg_solve(S1.ctx, bd, xd, args.tol, args.maxit, want_hist=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        single_ms += e0.elapsed_time(e1)
+        S1.close()
+    single_ms *= args.nrhs
+    # e2e: host (pinned) right-hand sides and solutions through the C ABI
+    Bh = [torch.tensor(b).pin_memory().numpy() for _, b in systems]
+    Xh = [torch.zeros(b.shape, dtype=torch.float64).pin_memory().numpy() for _, b in systems]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for x in Xh:
+            x[:] = 0.0
+        bs.solve(Bh, Xh, args.tol, args.maxit)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    nrhs_total = args.nsys * args.nrhs
+    ntot = sum(a.n for a, _ in systems)
+    result = {
+        "metric": "ICCG time to 1e-8 rel. residual", "value": round(ms, 4), "unit": "ms",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.fp64_batch else "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["batch64"].format(nx=0) + f": n total {ntot}, ABMC s={args.block_size}, "
+                               f"{'FP64' if args.fp64_batch else 'FP32'} preconditioner, FP64 CG, tol {args.tol:g}",
+                   "step": "iccg_batch_solve of the whole batch, inputs resident",
+                   "l2": "inputs larger than L2", "parallelism": "1 GPU", "shape": shape,
+                   "autotune": "warps/CTA x CTAs/SM, each candidate timed on this batch's full solve"},
+        "rhs_solves_per_s": round(nrhs_total / (ms * 1e-3), 1),
+        "iterations": {"min": int(its.min()), "max": int(its.max()), "mean": round(float(its.mean()), 1)},
+        "status": iccg.STATUS.get(st, st), "worst_true_relres": worst_res,
+        "plain_fp64_single_solves_ms": round(single_ms, 2),
+        "speedup_vs_plain_fp64": round(single_ms / ms, 2),
+        "setup": {"gen_s": round(t_gen, 3), "blocking_s": round(t_block, 3), "setup_s": round(t_setup, 3)},
+        "roofline": {"bound": "hbm", "kernel": "batched persistent ICCG (whole solve)", "achieved": round(achieved, 1),
+                     "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "traffic": None},
+        "e2e": {"value": round(e2e_ms, 4), "unit": "ms",
+                "h2d_bytes_per_step": 2 * 8 * ntot * args.nrhs, "d2h_bytes_per_step": 8 * ntot * args.nrhs},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    bs.close()
+    for S in solvers:
+        S.close()
+    if rank == 0:
+        print(json.dumps(result))
+
+
 def oracle_sample(a, b, perm, sample_iters):
     """IC(0) + `sample_iters` PCG iterations of the oracle; returns seconds."""
     import oracle
@@ -357,15 +488,20 @@ def main():
     p.add_argument("--ref-iters", type=int, default=176,
                    help="iterations the full solve takes (scales the reference sample)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--nsys", type=int, default=64, help="batch64: systems")
+    p.add_argument("--nrhs", type=int, default=16, help="batch64: right-hand sides per system")
+    p.add_argument("--fp64-batch", action="store_true", help="batch64: FP64 preconditioner")
     args = p.parse_args()
     if args.nx is None:
         args.nx = 96 if args.workload == "diffusion96" else 128
     if args.block_size is None:
-        args.block_size = 32 if args.workload == "diffusion96" else 8
+        args.block_size = 32 if args.workload in ("diffusion96", "batch64") else 8
     if args.steps < 1 or args.warmup < 0:
         raise SystemExit("steps >= 1, warmup >= 0")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_gpu(args)
 

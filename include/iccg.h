@@ -200,10 +200,16 @@ void iccg_destroy(iccg_ctx *ctx);
  *                      entry (k, j) = ||r_k||/||b|| of right-hand side j (0
  *                      past its last iteration).  Returns ICCG_OK when every
  *                      right-hand side converged, else the worst status.
- *   iccg_batch_tune    re-runs the shape search; *best_ms (may be NULL) gets
- *                      the chosen shape's time for a 5-iteration solve.
- *   iccg_batch_info    out[5]: warps per CTA, CTAs per SM, grid, padded nrhs,
- *                      largest block.
+ *   iccg_batch_tune    re-runs the shape search: every candidate (warps per
+ *                      CTA x CTAs per SM x CTA-split exponent) solves B (as in iccg_batch_solve,
+ *                      from x0 = 0, to tol / maxit; host or device), or, with
+ *                      B = NULL, random right-hand sides for 20 iterations;
+ *                      the fastest is kept and *best_ms (may be NULL) gets
+ *                      its time.
+ *   iccg_batch_info    out[6]: warps per CTA, CTAs per SM, grid, padded nrhs,
+ *                      largest block, 3 x the exponent e of the CTA split
+ *                      (CTAs per system proportional to n^e; e = 1 or 4/3,
+ *                      chosen by the tuner with the shape).
  * The paper has no batched solver; this serves many independent systems
  * (e.g. the learned-blocking sweep) and multiple right-hand sides.
  * ------------------------------------------------------------------------ */
@@ -219,8 +225,9 @@ iccg_status iccg_batch_create(iccg_batch **batch, iccg_ctx *const *ctxs, int32_t
                               const iccg_batch_opts *opts);
 iccg_status iccg_batch_solve(iccg_batch *batch, const double *const *B, double *const *X, double tol,
                              int32_t maxit, int32_t *iters, int32_t *status, double *const *res_hist);
-iccg_status iccg_batch_tune(iccg_batch *batch, double *best_ms);
-iccg_status iccg_batch_info(const iccg_batch *batch, int32_t out[5]);
+iccg_status iccg_batch_tune(iccg_batch *batch, const double *const *B, double tol, int32_t maxit,
+                            double *best_ms);
+iccg_status iccg_batch_info(const iccg_batch *batch, int32_t out[6]);
 iccg_status iccg_batch_last_error(const iccg_batch *batch, const char **msg);
 void iccg_batch_destroy(iccg_batch *batch);
 

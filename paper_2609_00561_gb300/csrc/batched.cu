@@ -423,6 +423,7 @@ struct iccg_batch {
   int hist_cap = 0;
   // launch shape
   int W = 8, cps = 1, grid = 0, smem = 0, max_part_ctas = 0;
+  double wexp = 1.0;     // CTAs per system proportional to n^wexp
   std::vector<int32_t> cta0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -466,17 +467,24 @@ void destroy_batch_graph(iccg_batch *b) {
   b->graph = nullptr;
 }
 
-// CTA ranges per system (proportional to rows, >= 1 each) for a grid of G
-// CTAs; returns false when G < nsys.
+// CTA ranges per system (>= 1 each) for a grid of G CTAs, proportional to
+// n^wexp: wexp = 1 spreads rows evenly, wexp = 4/3 weights rows by an
+// iteration count that grows with the grid side (CG on a discretised
+// elliptic operator needs O(sqrt kappa) = O(side) iterations); returns false
+// when G < nsys.
 bool assign_ctas(iccg_batch *b, int G) {
   if (G < b->nsys) return false;
   double tot = 0.0;
-  for (int s = 0; s < b->nsys; ++s) tot += double(b->n[s]);
+  std::vector<double> wt(b->nsys);
+  for (int s = 0; s < b->nsys; ++s) {
+    wt[s] = std::pow(double(b->n[s]), b->wexp);
+    tot += wt[s];
+  }
   std::vector<int32_t> c(b->nsys, 1);
   int used = b->nsys;
   // largest remainder over the CTAs beyond one per system
   std::vector<double> want(b->nsys);
-  for (int s = 0; s < b->nsys; ++s) want[s] = double(G) * double(b->n[s]) / tot;
+  for (int s = 0; s < b->nsys; ++s) want[s] = double(G) * wt[s] / tot;
   for (int s = 0; s < b->nsys; ++s) {
     const int extra = std::max(0, int(want[s]) - 1);
     c[s] += extra;
@@ -748,7 +756,7 @@ iccg_status iccg_batch_create(iccg_batch **out, iccg_ctx *const *ctxs, int32_t n
   iccg_status st = set_shape(b, o.warps_per_cta > 0 ? o.warps_per_cta : 8, o.ctas_per_sm, sms);
   if (st != ICCG_OK) return st;
   if (o.autotune) {
-    st = iccg_batch_tune(b, nullptr);
+    st = iccg_batch_tune(b, nullptr, 0.0, 0, nullptr);
     if (st != ICCG_OK) return st;
   }
   return ICCG_OK;
@@ -815,52 +823,68 @@ iccg_status iccg_batch_solve(iccg_batch *b, const double *const *B, double *cons
   return worst;
 }
 
-iccg_status iccg_batch_tune(iccg_batch *b, double *best_ms) {
-  if (!b) return ICCG_ERR_ARG;
+iccg_status iccg_batch_tune(iccg_batch *b, const double *const *B, double tol, int32_t maxit, double *best_ms) {
+  if (!b || (B && (tol < 0 || !(tol == tol) || maxit < 0))) return ICCG_ERR_ARG;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  // a fixed 5-iteration solve (tol 0) of random right-hand sides per shape
+  // every candidate shape solves the given right-hand sides from x0 = 0 to
+  // (tol, maxit), or, without B, random right-hand sides for a fixed 20
+  // iterations (tol 0); the fastest shape is kept
   std::vector<std::vector<double>> hb(b->nsys), hx(b->nsys);
-  std::vector<const double *> B(b->nsys);
+  std::vector<const double *> Bp(b->nsys);
   std::vector<double *> X(b->nsys);
   uint64_t st = 0x9e3779b97f4a7c15ull;
   for (int s = 0; s < b->nsys; ++s) {
-    hb[s].resize(size_t(b->n[s]) * b->k);
     hx[s].assign(size_t(b->n[s]) * b->k, 0.0);
+    X[s] = hx[s].data();
+    if (B) {
+      Bp[s] = B[s];
+      if (!B[s]) return ICCG_ERR_ARG;
+      continue;
+    }
+    hb[s].resize(size_t(b->n[s]) * b->k);
     for (double &v : hb[s]) {
       st ^= st << 13; st ^= st >> 7; st ^= st << 17;
       v = double(st >> 11) * (1.0 / 9007199254740992.0) - 0.5;
     }
-    B[s] = hb[s].data();
-    X[s] = hx[s].data();
+    Bp[s] = hb[s].data();
   }
+  const double ttol = B ? tol : 0.0;
+  const int tmax = B ? maxit : 20;
   const int Ws[3] = {4, 8, 16};
-  double best = 1e300;
+  const double Es[2] = {1.0, 4.0 / 3.0};
+  double best = 1e300, bE = b->wexp;
   int bW = b->W, bC = b->cps;
+  for (double E : Es)
   for (int W : Ws) {
     const int occ = batch_occupancy(b, W, batch_smem(b, W));
-    for (int cps = 1; cps <= std::min(occ, 4); ++cps) {
+    for (int cps = 1; cps <= std::min(occ, 4); cps *= 2) {
+      b->wexp = E;
       if (set_shape(b, W, cps, sms) != ICCG_OK) continue;
-      // first call captures the graph; the second is timed
-      if (iccg_batch_solve(b, B.data(), X.data(), 0.0, 5, nullptr, nullptr, nullptr) == ICCG_ERR_CUDA) continue;
+      for (auto &x : hx) std::fill(x.begin(), x.end(), 0.0);
+      // the first call captures the graph; the second is timed
+      if (iccg_batch_solve(b, Bp.data(), X.data(), ttol, tmax, nullptr, nullptr, nullptr) == ICCG_ERR_CUDA) continue;
+      for (auto &x : hx) std::fill(x.begin(), x.end(), 0.0);
       const auto t0 = std::chrono::steady_clock::now();
-      const iccg_status r = iccg_batch_solve(b, B.data(), X.data(), 0.0, 5, nullptr, nullptr, nullptr);
+      const iccg_status r = iccg_batch_solve(b, Bp.data(), X.data(), ttol, tmax, nullptr, nullptr, nullptr);
       const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
       if (r == ICCG_ERR_CUDA || r == ICCG_ERR_TIMEOUT) continue;
-      if (ms < best) { best = ms; bW = W; bC = cps; }
+      if (ms < best) { best = ms; bW = W; bC = cps; bE = E; }
     }
   }
   if (best_ms) *best_ms = best;
+  b->wexp = bE;
   return set_shape(b, bW, bC, sms);
 }
 
-iccg_status iccg_batch_info(const iccg_batch *b, int32_t out[5]) {
+iccg_status iccg_batch_info(const iccg_batch *b, int32_t out[6]) {
   if (!b || !out) return ICCG_ERR_ARG;
   out[0] = b->W;
   out[1] = b->cps;
   out[2] = b->grid;
   out[3] = b->kp;
   out[4] = b->smax;
+  out[5] = int32_t(b->wexp * 3.0 + 0.5);   // 3 x the CTA-split exponent (3: rows, 4: rows^(4/3))
   return ICCG_OK;
 }
 

@@ -75,7 +75,7 @@ def load():
         "iccg_spmv_dot_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp],
         "iccg_batch_create": [P(vp), vp, i32, i32, P(iccg_batch_opts)],
         "iccg_batch_solve": [vp, vp, vp, d, i32, vp, vp, vp],
-        "iccg_batch_tune": [vp, P(d)],
+        "iccg_batch_tune": [vp, vp, d, i32, P(d)],
         "iccg_batch_info": [vp, vp],
         "iccg_batch_last_error": [vp, P(ctypes.c_char_p)],
     }
@@ -376,13 +376,16 @@ class BatchSolver:
             raise err
 
     def info(self):
-        out = np.zeros(5, dtype=np.int32)
+        out = np.zeros(6, dtype=np.int32)
         _batch_check(load().iccg_batch_info(self.h, _ptr(out)), "iccg_batch_info", self.h)
-        return dict(zip(("warps_per_cta", "ctas_per_sm", "grid", "kp", "smax"), out.tolist()))
+        return dict(zip(("warps_per_cta", "ctas_per_sm", "grid", "kp", "smax", "split_exp_x3"), out.tolist()))
 
-    def tune(self):
+    def tune(self, B=None, tol=1e-8, maxit=10000):
+        """Shape search on B (x0 = 0, to tol) or, without B, a random probe."""
         ms = ctypes.c_double(0.0)
-        _batch_check(load().iccg_batch_tune(self.h, ctypes.byref(ms)), "iccg_batch_tune", self.h)
+        bp = None if B is None else (ctypes.c_void_p * len(B))(*[_ptr(b) for b in B])
+        _batch_check(load().iccg_batch_tune(self.h, bp, float(tol), int(maxit), ctypes.byref(ms)),
+                     "iccg_batch_tune", self.h)
         return ms.value
 
     def solve(self, B, X, tol=1e-8, maxit=10000, want_hist=False):
