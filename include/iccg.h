@@ -296,6 +296,45 @@ iccg_status iccg_color_order(int32_t n, const int64_t *gptr, const int32_t *gadj
                              const int32_t *block_of, int32_t *color_of, int32_t *n_c,
                              int32_t *perm, int32_t *block_ptr, int32_t *color_ptr);
 
+/* ------------------------------------------------------------------------
+ * Learned blocking (extension; the paper selects block sizes and
+ * resolutions by sweeps, Table 2 and Sec. 6.1).
+ *
+ * iccg_features: ICCG_NFEATURES statistics of a CSR matrix (host pointers;
+ * definitions in the source: log10 n, row-degree moments and maximum,
+ * log10 nnz, diagonal-dominance statistics, bandwidth and mean entry
+ * distance, an 8-bin histogram of off-diagonal counts, the off-diagonal
+ * magnitude range).  ICCG_ERR_ARG on an invalid CSR.
+ *
+ * The MLP (two hidden ReLU layers of width h, FP32) maps standardised
+ * features to ncls class logits (block size) and one regression output
+ * (log resolution).  params: float[iccg_mlp_nparams(nf, h, ncls)] laid out
+ * W1 [nf][h], b1 [h], W2 [h][h], b2 [h], W3 [h][ncls+1], b3 [ncls+1]
+ * (device).  All arrays below are device pointers on `stream`.
+ *   iccg_mlp_forward   X [batch][nf] -> out [batch][ncls+1]; act (may be
+ *                      NULL, else float[2 * batch * h]) receives the two
+ *                      hidden activations (layer 1, then layer 2).
+ *   iccg_mlp_grad      loss = mean over the batch of the cross entropy of
+ *                      softmax(out[:ncls]) against ycls (int32, 0..ncls-1)
+ *                      plus wreg times the squared error of out[ncls]
+ *                      against yreg; grad [nparams] and *loss (device float)
+ *                      receive it.  work: float[batch * (4h + 2(ncls+1) + 1)].
+ *   iccg_mlp_adam      one Adam step (bias-corrected, step >= 1) on params
+ *                      with first / second moments m, v.
+ * Every reduction runs in a fixed order: results are reproducible.
+ * ------------------------------------------------------------------------ */
+#define ICCG_NFEATURES 20
+iccg_status iccg_features(int32_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                          double out[ICCG_NFEATURES]);
+int64_t iccg_mlp_nparams(int32_t nf, int32_t hidden, int32_t ncls);
+iccg_status iccg_mlp_forward(const float *params, int32_t nf, int32_t hidden, int32_t ncls, const float *X,
+                             int32_t batch, float *out, float *act, iccg_stream_t stream);
+iccg_status iccg_mlp_grad(const float *params, int32_t nf, int32_t hidden, int32_t ncls, const float *X,
+                          const int32_t *ycls, const float *yreg, float wreg, int32_t batch, float *grad,
+                          float *loss, float *work, iccg_stream_t stream);
+iccg_status iccg_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t nparams, float lr,
+                          float beta1, float beta2, float eps, int32_t step, iccg_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

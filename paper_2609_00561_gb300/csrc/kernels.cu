@@ -651,18 +651,19 @@ __device__ __forceinline__ TileBuf<PT> tile_buf(unsigned char *smem, const TileP
 // stays in global memory.
 template <typename PT, bool FIRST_UPPER, bool TWO>
 __device__ __forceinline__ void tile_stage(const Params &P, const TileDesc &t, const TileBuf<PT> &tb, int cap_i,
-                                           int cap_i2) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
+                                           int cap_i2, int tid, int nthr) {
   int4 *st = reinterpret_cast<int4 *>(const_cast<StepDesc *>(tb.st));
   const int4 *gs = reinterpret_cast<const int4 *>(P.steps + t.step0);
   for (int k = tid; k < t.nsteps * 3; k += nthr) cp_async16(st + k, gs + k);
   stage_cover<PT>(invds<PT>(P), t.row0, t.row0 + t.nrows, const_cast<PT *>(tb.dv), tid, nthr);
+  // a set is copied only into a region the launch has (capacity > 0) and
+  // only when non-empty (the cover of an empty range is still 16 bytes)
   const int i0 = FIRST_UPPER ? t.ui0 : t.li0, i1 = FIRST_UPPER ? t.ui1 : t.li1;
-  if (i1 - i0 <= cap_i) {
+  if (i1 > i0 && i1 - i0 <= cap_i) {
     stage_cover<int32_t>(FIRST_UPPER ? P.ui_col : P.si_col, i0, i1, const_cast<int32_t *>(tb.ic), tid, nthr);
     stage_cover<PT>(FIRST_UPPER ? uiv<PT>(P) : siv<PT>(P), i0, i1, const_cast<PT *>(tb.iv), tid, nthr);
   }
-  if (TWO && t.ui1 - t.ui0 <= cap_i2) {
+  if (TWO && t.ui1 > t.ui0 && t.ui1 - t.ui0 <= cap_i2) {
     stage_cover<int32_t>(P.ui_col, t.ui0, t.ui1, const_cast<int32_t *>(tb.ic2), tid, nthr);
     stage_cover<PT>(uiv<PT>(P), t.ui0, t.ui1, const_cast<PT *>(tb.iv2), tid, nthr);
   }
@@ -679,7 +680,7 @@ struct InBlock {
 template <typename PT>
 __device__ __forceinline__ InBlock<PT> in_block(const int32_t *sc, const PT *sv, const int32_t *gc, const PT *gv,
                                                int i0, int i1, int cap_i) {
-  if (i1 - i0 <= cap_i) return InBlock<PT>{sc - cover_base<int32_t>(i0), sv - cover_base<PT>(i0)};
+  if (i1 > i0 && i1 - i0 <= cap_i) return InBlock<PT>{sc - cover_base<int32_t>(i0), sv - cover_base<PT>(i0)};
   return InBlock<PT>{gc, gv};
 }
 
@@ -712,8 +713,9 @@ __device__ __forceinline__ PT ext_sub(const int32_t *col, const PT *val, int e, 
 // gathers of z); the partial row value goes to w[step][lane].
 template <typename PT, bool UPPER, bool UPDATE>
 __device__ __forceinline__ void tile_phase_a(const Params &P, const TileDesc &t, const TileBuf<PT> &tb, PT *w,
-                                             double alpha, const double *pn, bool y_in_smem, double &rr_acc) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+                                             double alpha, const double *pn, bool y_in_smem, double &rr_acc,
+                                             int warp, int W) {
+  const int lane = threadIdx.x & 31;
   PT *yv = reinterpret_cast<PT *>(P.y);
   const PT *zv = reinterpret_cast<const PT *>(P.z);
   for (int k = warp; k < t.nsteps; k += W) {
@@ -745,9 +747,7 @@ __device__ __forceinline__ void tile_phase_a(const Params &P, const TileDesc &t,
 // own block's values.  In-block padding entries are (step 0, value 0).
 template <typename PT, bool UPPER>
 __device__ __forceinline__ void tile_phase_b(const TileDesc &t, const StepDesc *st, const PT *dv,
-                                             const int32_t *ic, const PT *iv, PT *w) {
-  if (threadIdx.x >= kWarp) return;
-  const int lane = threadIdx.x;
+                                             const int32_t *ic, const PT *iv, PT *w, int lane) {
   for (int kk = 0; kk < t.nsteps; ++kk) {
     const int k = UPPER ? t.nsteps - 1 - kk : kk;
     const StepDesc &s = st[k];
@@ -763,8 +763,8 @@ __device__ __forceinline__ void tile_phase_b(const TileDesc &t, const StepDesc *
 // Phase C: the tile's results to global memory (y or z), <r,z> (backward)
 template <typename PT, bool UPPER>
 __device__ __forceinline__ void tile_phase_c(const Params &P, const TileDesc &t, const StepDesc *st, const PT *w,
-                                             bool store, double &rz_acc) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+                                             bool store, double &rz_acc, int warp, int W) {
+  const int lane = threadIdx.x & 31;
   PT *res = reinterpret_cast<PT *>(UPPER ? P.z : P.y);
   for (int k = warp; k < t.nsteps; k += W) {
     const StepDesc &s = st[k];
@@ -794,8 +794,9 @@ tile_kernel(Params P, int t0, int t1, TilePlan pl, int fin, SlotArgs sa) {
   PT *w = reinterpret_cast<PT *>(smem + nbuf * bsize);
   double rr_acc = 0.0, rz_acc = 0.0;
   int t = t0 + int(blockIdx.x), buf = 0;
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   TileDesc td = load_tile(P.tiles + min(t, t1 - 1));
-  if (t < t1) tile_stage<PT, FU, TWO>(P, td, tile_buf<PT>(smem, pl, bsize, 0), pl.cap_i, pl.cap_i2);
+  if (t < t1) tile_stage<PT, FU, TWO>(P, td, tile_buf<PT>(smem, pl, bsize, 0), pl.cap_i, pl.cap_i2, threadIdx.x, blockDim.x);
   cp_commit();
   pdl_wait();
   const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
@@ -803,7 +804,9 @@ tile_kernel(Params P, int t0, int t1, TilePlan pl, int fin, SlotArgs sa) {
     const int tn = t + int(gridDim.x);
     TileDesc tdn = td;
     if (tn < t1) tdn = load_tile(P.tiles + tn);
-    if (tn < t1 && nbuf == 2) tile_stage<PT, FU, TWO>(P, tdn, tile_buf<PT>(smem, pl, bsize, buf ^ 1), pl.cap_i, pl.cap_i2);
+    if (tn < t1 && nbuf == 2)
+      tile_stage<PT, FU, TWO>(P, tdn, tile_buf<PT>(smem, pl, bsize, buf ^ 1), pl.cap_i, pl.cap_i2, threadIdx.x,
+                              blockDim.x);
     cp_commit();
     cp_wait_prev();
     __syncthreads();
@@ -812,33 +815,34 @@ tile_kernel(Params P, int t0, int t1, TilePlan pl, int fin, SlotArgs sa) {
     const InBlock<PT> ul = in_block<PT>(tb.ic, tb.iv, P.ui_col, uiv<PT>(P), td.ui0, td.ui1, pl.cap_i);
     const InBlock<PT> ll = in_block<PT>(tb.ic, tb.iv, P.si_col, siv<PT>(P), td.li0, td.li1, pl.cap_i);
     if (MODE == M_BWD) {
-      tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, false, rr_acc);
+      tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, false, rr_acc, wid, nw);
       __syncthreads();
-      tile_phase_b<PT, true>(td, tb.st, dv, ul.ic, ul.iv, w);
+      if (wid == 0) tile_phase_b<PT, true>(td, tb.st, dv, ul.ic, ul.iv, w, threadIdx.x);
       __syncthreads();
-      tile_phase_c<PT, true>(P, td, tb.st, w, true, rz_acc);
+      tile_phase_c<PT, true>(P, td, tb.st, w, true, rz_acc, wid, nw);
     } else {
-      tile_phase_a<PT, false, UPDATE>(P, td, tb, w, alpha, P.p0, false, rr_acc);
+      tile_phase_a<PT, false, UPDATE>(P, td, tb, w, alpha, P.p0, false, rr_acc, wid, nw);
       __syncthreads();
-      tile_phase_b<PT, false>(td, tb.st, dv, ll.ic, ll.iv, w);
+      if (wid == 0) tile_phase_b<PT, false>(td, tb.st, dv, ll.ic, ll.iv, w, threadIdx.x);
       __syncthreads();
       if (MODE == M_FWD) {
-        tile_phase_c<PT, false>(P, td, tb.st, w, true, rz_acc);
+        tile_phase_c<PT, false>(P, td, tb.st, w, true, rz_acc, wid, nw);
       } else {
         // the last color: y stays in shared memory for the backward sweep
         const InBlock<PT> u2 = in_block<PT>(tb.ic2, tb.iv2, P.ui_col, uiv<PT>(P), td.ui0, td.ui1, pl.cap_i2);
-        tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, true, rr_acc);
+        tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, true, rr_acc, wid, nw);
         __syncthreads();
-        tile_phase_b<PT, true>(td, tb.st, dv, u2.ic, u2.iv, w);
+        if (wid == 0) tile_phase_b<PT, true>(td, tb.st, dv, u2.ic, u2.iv, w, threadIdx.x);
         __syncthreads();
-        tile_phase_c<PT, true>(P, td, tb.st, w, true, rz_acc);
+        tile_phase_c<PT, true>(P, td, tb.st, w, true, rz_acc, wid, nw);
       }
     }
     __syncthreads();   // buffer buf and w are reused by the next tile
     if (nbuf == 1) {
       // one buffer: the next tile's copies start now (waited on by the next
       // pass's cp_wait_prev, which leaves only its own empty group pending)
-      if (tn < t1) tile_stage<PT, FU, TWO>(P, tdn, tile_buf<PT>(smem, pl, bsize, 0), pl.cap_i, pl.cap_i2);
+      if (tn < t1)
+        tile_stage<PT, FU, TWO>(P, tdn, tile_buf<PT>(smem, pl, bsize, 0), pl.cap_i, pl.cap_i2, threadIdx.x, blockDim.x);
       cp_commit();
     } else {
       buf ^= 1;

@@ -74,6 +74,11 @@ def load():
         "iccg_color_order": [i32, vp, vp, i32, vp, vp, P(i32), vp, vp, vp],
         "iccg_spmv_dot_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp],
         "iccg_batch_create": [P(vp), vp, i32, i32, P(iccg_batch_opts)],
+        "iccg_features": [i32, vp, vp, vp, vp],
+        "iccg_mlp_forward": [vp, i32, i32, i32, vp, i32, vp, vp, vp],
+        "iccg_mlp_grad": [vp, i32, i32, i32, vp, vp, vp, ctypes.c_float, i32, vp, vp, vp, vp],
+        "iccg_mlp_adam": [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i32,
+                          vp],
         "iccg_batch_solve": [vp, vp, vp, d, i32, vp, vp, vp],
         "iccg_batch_tune": [vp, vp, d, i32, P(d)],
         "iccg_batch_info": [vp, vp],
@@ -87,6 +92,8 @@ def load():
     L.iccg_destroy.restype = None
     L.iccg_batch_destroy.argtypes = [vp]
     L.iccg_batch_destroy.restype = None
+    L.iccg_mlp_nparams.argtypes = [i32, i32, i32]
+    L.iccg_mlp_nparams.restype = ctypes.c_int64
     _lib = L
     return L
 
@@ -417,4 +424,39 @@ class BatchSolver:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# learned blocking: features and the MLP kernels
+# ---------------------------------------------------------------------------
+NFEATURES = 20
+
+
+def features(a):
+    """The 20 matrix statistics of iccg_features (host)."""
+    out = np.zeros(NFEATURES)
+    keep = [_as(a.rowptr, np.int64), _as(a.colind, np.int32), _as(a.val, np.float64)]
+    _check(load().iccg_features(int(a.n), *[_ptr(k) for k in keep], _ptr(out)), "iccg_features")
+    return out
+
+
+def mlp_nparams(nf, hidden, ncls):
+    return int(load().iccg_mlp_nparams(int(nf), int(hidden), int(ncls)))
+
+
+def mlp_forward(params, nf, hidden, ncls, X, out, act=None, stream=None):
+    _check(load().iccg_mlp_forward(_ptr(params), int(nf), int(hidden), int(ncls), _ptr(X), int(X.shape[0]),
+                                   _ptr(out), _ptr(act), ctypes.c_void_p(stream or 0)), "iccg_mlp_forward")
+
+
+def mlp_grad(params, nf, hidden, ncls, X, ycls, yreg, wreg, grad, loss, work, stream=None):
+    _check(load().iccg_mlp_grad(_ptr(params), int(nf), int(hidden), int(ncls), _ptr(X), _ptr(ycls), _ptr(yreg),
+                                float(wreg), int(X.shape[0]), _ptr(grad), _ptr(loss), _ptr(work),
+                                ctypes.c_void_p(stream or 0)), "iccg_mlp_grad")
+
+
+def mlp_adam(params, grad, m, v, lr, beta1, beta2, eps, step, stream=None):
+    _check(load().iccg_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(params.numel()), float(lr),
+                                float(beta1), float(beta2), float(eps), int(step), ctypes.c_void_p(stream or 0)),
+           "iccg_mlp_adam")
 

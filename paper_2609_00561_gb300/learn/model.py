@@ -1,0 +1,191 @@
+"""Learned blocking: an MLP (features -> ABMC block-size class, log CPM
+resolution) trained on the GPU with the library's own kernels
+(iccg_mlp_forward / iccg_mlp_grad / iccg_mlp_adam).
+
+The labels come from the label sweep (learn/sweep.py): for every generated
+matrix, the FP64 GPU ICCG solve time to 1e-8 under ABMC with each block size
+and under Leiden CPM with each resolution; the class label is the fastest
+block size, the regression label the log of the fastest resolution.  The
+exhaustive sweep is the model's judge (regret T(prediction) / T(best of the
+sweep)) and its fallback (`choose` returns the swept optimum when a matrix
+was swept).
+
+    python -m paper_2609_00561_gb300.learn.model --sweep blocking_sweep.json
+        [--add-features]   # compute the features of every record (host) and store them
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+HIDDEN = 64
+WREG = 0.5
+BASE_BLOCK = 32        # the method without the model: fixed ABMC block size ...
+BASE_GAMMA = 0.05      # ... and fixed CPM resolution
+
+
+def load_sweep(path):
+    with open(path) as f:
+        return json.load(f)
+
+
+def add_features(data):
+    """Features of every record's matrix (regenerated from its spec) by the
+    library's host extractor."""
+    import gen
+    from paper_2609_00561_gb300 import iccg
+    for rec in data["records"]:
+        a = gen.config5_matrix(rec["spec"])
+        rec["features"] = iccg.features(a).tolist()
+    return data
+
+
+def labels(data):
+    """(features [N, F], class [N], log gamma [N], ABMC times [N, 5], CPM times [N, 6])."""
+    bs, gs = data["meta"]["block_sizes"], data["meta"]["gammas"]
+    X, yc, yr, ta, tc = [], [], [], [], []
+    for rec in data["records"]:
+        runs = rec["runs"]
+        a = [r["ms"] if r["status"] == 0 else math.inf for r in runs[:len(bs)]]
+        c = [r["ms"] if r["status"] == 0 else math.inf for r in runs[len(bs):]]
+        X.append(rec["features"])
+        yc.append(int(np.argmin(a)))
+        yr.append(math.log(gs[int(np.argmin(c))]))
+        ta.append(a)
+        tc.append(c)
+    return (np.array(X, dtype=np.float64), np.array(yc, dtype=np.int32), np.array(yr, dtype=np.float64),
+            np.array(ta), np.array(tc))
+
+
+def split(n, seed=0, n_test=40):
+    """Train / held-out indices: a seeded permutation, the last n_test held out."""
+    perm = np.random.default_rng(seed).permutation(n)
+    return np.sort(perm[:n - n_test]), np.sort(perm[n - n_test:])
+
+
+class Model:
+    """Standardisation + MLP parameters (FP32 on the device while training)."""
+
+    def __init__(self, nf, ncls, hidden=HIDDEN, seed=0):
+        from paper_2609_00561_gb300 import iccg
+        self.nf, self.ncls, self.h = nf, ncls, hidden
+        self.np = iccg.mlp_nparams(nf, hidden, ncls)
+        rng = np.random.default_rng(seed)
+        p = []
+        for fan_in, fan_out in ((nf, hidden), (hidden, hidden), (hidden, ncls + 1)):
+            p.append(rng.normal(0.0, math.sqrt(2.0 / fan_in), fan_in * fan_out))
+            p.append(np.zeros(fan_out))
+        self.params = np.concatenate(p).astype(np.float32)
+        self.mu = np.zeros(nf)
+        self.sd = np.ones(nf)
+
+    def standardise(self, X):
+        return ((X - self.mu) / self.sd).astype(np.float32)
+
+    def fit(self, X, yc, yr, epochs=3000, lr=3e-3, device="cuda"):
+        """Full-batch Adam on the GPU; returns the loss history (every 100 epochs)."""
+        import torch
+        from paper_2609_00561_gb300 import iccg
+        self.mu = X.mean(axis=0)
+        self.sd = np.where(X.std(axis=0) > 1e-12, X.std(axis=0), 1.0)
+        Xs = torch.tensor(self.standardise(X), device=device)
+        ycd = torch.tensor(yc.astype(np.int32), device=device)
+        yrd = torch.tensor(yr.astype(np.float32), device=device)
+        P = torch.tensor(self.params, device=device)
+        G = torch.zeros_like(P)
+        M = torch.zeros_like(P)
+        V = torch.zeros_like(P)
+        B = Xs.shape[0]
+        work = torch.zeros(B * (4 * self.h + 2 * (self.ncls + 1) + 1), dtype=torch.float32, device=device)
+        loss = torch.zeros(1, dtype=torch.float32, device=device)
+        stream = torch.cuda.current_stream().cuda_stream
+        hist = []
+        for ep in range(1, epochs + 1):
+            iccg.mlp_grad(P, self.nf, self.h, self.ncls, Xs, ycd, yrd, WREG, G, loss, work, stream)
+            iccg.mlp_adam(P, G, M, V, lr, 0.9, 0.999, 1e-8, ep, stream)
+            if ep % 100 == 0 or ep == 1:
+                hist.append(float(loss.item()))
+        self.params = P.cpu().numpy()
+        return hist
+
+    def predict(self, X, device="cuda"):
+        """(class index [N], log gamma [N]) from the device forward kernel."""
+        import torch
+        from paper_2609_00561_gb300 import iccg
+        Xs = torch.tensor(self.standardise(np.atleast_2d(X)), device=device)
+        P = torch.tensor(self.params, device=device)
+        out = torch.zeros((Xs.shape[0], self.ncls + 1), dtype=torch.float32, device=device)
+        iccg.mlp_forward(P, self.nf, self.h, self.ncls, Xs, out, None, torch.cuda.current_stream().cuda_stream)
+        o = out.cpu().numpy().astype(np.float64)
+        return o[:, :self.ncls].argmax(axis=1), o[:, self.ncls]
+
+    def save(self, path):
+        np.savez(path, params=self.params, mu=self.mu, sd=self.sd, shape=np.array([self.nf, self.h, self.ncls]))
+
+
+def evaluate(model, X, ta, tc, gammas, block_sizes):
+    """Regret of the predictions against the sweep, and the gain over the
+    method without the model (ABMC 32, CPM 0.05), on the given records."""
+    cls, lg = model.predict(X)
+    lgs = np.log(np.array(gammas))
+    gi = np.abs(lg[:, None] - lgs[None, :]).argmin(axis=1)      # nearest swept resolution
+    rows = np.arange(len(cls))
+    t_abmc, t_cpm = ta[rows, cls], tc[rows, gi]
+    best_a, best_c = ta.min(axis=1), tc.min(axis=1)
+    base_a = ta[:, block_sizes.index(BASE_BLOCK)]
+    base_c = tc[:, gammas.index(BASE_GAMMA)]
+    # the combined choice: the faster of the two predicted blockings vs the
+    # faster of the two fixed ones (both judged by the sweep's times)
+    pred = np.minimum(t_abmc, t_cpm)
+    best = np.minimum(best_a, best_c)
+    base = np.minimum(base_a, base_c)
+    return {
+        "n": int(len(cls)),
+        "abmc_regret_mean": float(np.mean(t_abmc / best_a)),
+        "abmc_within_5pct": float(np.mean(t_abmc <= 1.05 * best_a)),
+        "cpm_regret_mean": float(np.mean(t_cpm / best_c)),
+        "cpm_within_5pct": float(np.mean(t_cpm <= 1.05 * best_c)),
+        "abmc_gain_vs_fixed32": float(np.exp(np.mean(np.log(base_a / t_abmc)))),
+        "cpm_gain_vs_fixed005": float(np.exp(np.mean(np.log(base_c / t_cpm)))),
+        "combined_regret_mean": float(np.mean(pred / best)),
+        "combined_gain_vs_fixed": float(np.exp(np.mean(np.log(base / pred)))),
+        "class_accuracy": None,
+    }
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--sweep", required=True)
+    p.add_argument("--add-features", action="store_true")
+    p.add_argument("--epochs", type=int, default=3000)
+    p.add_argument("--out", default=None)
+    args = p.parse_args()
+    data = load_sweep(args.sweep)
+    if args.add_features:
+        data = add_features(data)
+        with open(args.sweep, "w") as f:
+            json.dump(data, f)
+        return
+    X, yc, yr, ta, tc = labels(data)
+    tr, te = split(len(yc))
+    m = Model(X.shape[1], len(data["meta"]["block_sizes"]))
+    hist = m.fit(X[tr], yc[tr], yr[tr], epochs=args.epochs)
+    res = {"train": evaluate(m, X[tr], ta[tr], tc[tr], data["meta"]["gammas"], data["meta"]["block_sizes"]),
+           "test": evaluate(m, X[te], ta[te], tc[te], data["meta"]["gammas"], data["meta"]["block_sizes"]),
+           "loss": hist[::5]}
+    print(json.dumps(res, indent=1))
+    if args.out:
+        m.save(args.out)
+
+
+if __name__ == "__main__":
+    main()

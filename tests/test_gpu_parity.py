@@ -270,3 +270,36 @@ def test_layout_choice_follows_block_sizes():
     S = iccg.Solver(a, bl)
     assert iccg.iccg_info(S.ctx)["tile_colors"] == 0
     S.close()
+
+
+def _rgg_plus_isolated(n_rgg=20000, n_iso=37, seed=11):
+    """A random geometric graph Laplacian (ABMC 32: tiles whose in-block
+    entries are too many for a second staged set in the fused launch) plus
+    n_iso isolated rows forming a last color of singleton blocks (no in-block
+    entries at all)."""
+    a = gen.rgg_laplacian(n_rgg, 29.0, seed).to_scipy()
+    m = sp.block_diag([a, sp.diags(np.linspace(1.0, 2.0, n_iso))], format="csr")
+    big = gen.from_scipy(m)
+    bl = oracle.blocking(gen.from_scipy(a.tocsr()), "abmc", 32)
+    nb, nc = bl["n_b"], bl["n_c"]
+    perm = np.concatenate([bl["perm"], n_rgg + np.arange(n_iso)]).astype(np.int32)
+    bptr = np.concatenate([bl["block_ptr"], n_rgg + 1 + np.arange(n_iso)]).astype(np.int32)
+    cptr = np.concatenate([bl["color_ptr"][:nc + 1], [nb + n_iso]]).astype(np.int32)
+    return big, {"perm": perm, "block_ptr": bptr, "color_ptr": cptr, "n_b": nb + n_iso, "n_c": nc + 1}
+
+
+def test_fused_color_without_in_block_entries():
+    """The fused last color's tiles have no in-block upper entries while the
+    launch has no room for a second staged set: nothing may be copied."""
+    a, bl = _rgg_plus_isolated()
+    b = gen.rhs_uniform(a.n, 12)
+    ref = oracle.iccg(a, b, bl["perm"])
+    for fp32 in (False, True):
+        S = iccg.Solver(a, bl, precond_fp32=fp32)
+        assert iccg.iccg_info(S.ctx)["tile_colors"] == bl["n_c"]
+        x = np.zeros(a.n)
+        st, it, _ = iccg.iccg_solve(S.ctx, b, x)
+        assert st == iccg.ICCG_OK
+        if not fp32:
+            assert abs(it - ref["iterations"]) <= 1 and _rel(x, ref["x"]) <= 1e-10
+        S.close()
