@@ -6,6 +6,10 @@ diffusion problem (96^3, ABMC 32) with the FP32 preconditioner (extension 1).
 `--workload batch64` runs the batched extension: 64 shifted 7-point systems
 (sides U{16..64}), 16 right-hand sides each, ABMC 32, FP32 preconditioner,
 all in one launch; a step is the whole batch solved to 1e-8.
+`--workload learned` trains the learned-blocking MLP on the GPU (library
+kernels) from the committed label sweep and solves the held-out matrices
+with the predicted ABMC block size and with the fixed block size 32; a step
+is the held-out set solved once with the predicted settings.
 
 A step is one pass of the device hot path on inputs resident in HBM:
 iccg_factor (IC(0), FP64) followed by iccg_solve (PCG with block-multicolor
@@ -102,6 +106,8 @@ WORKLOADS = {
     "poisson128": "3D 7-point Poisson {nx}^3",
     "diffusion96": "3D 27-point variable-coefficient diffusion {nx}^3 (contrast 1e3, shift 1e-6 max diag)",
     "batch64": "batch of 64 shifted 3D 7-point systems (sides U{{16..64}}, shift U[1e-4,1e-1]) x 16 right-hand sides",
+    "learned": "40 held-out generated SPD matrices (5/7/27-point anisotropic stencils, random geometric graph "
+               "Laplacians, 3-dof spring networks; n 2e4-2e5), ABMC block size predicted by the learned-blocking MLP",
 }
 
 
@@ -413,6 +419,83 @@ def run_batch(args):
         print(json.dumps(result))
 
 
+def run_learned(args):
+    import torch
+    from paper_2609_00561_gb300 import build as libbuild
+    from paper_2609_00561_gb300 import iccg
+    from paper_2609_00561_gb300.learn import model as lm
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    libbuild.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    data = lm.load_sweep(os.path.join(ROOT, "paper_2609_00561_gb300", "learn", "blocking_sweep.json"))
+    X, yc, yr, ta, tc = lm.labels(data)
+    tr, te = lm.split(len(yc))
+    bs_list, gammas = data["meta"]["block_sizes"], data["meta"]["gammas"]
+    m = lm.Model(X.shape[1], len(bs_list), seed=args.seed)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hist = m.fit(X[tr], yc[tr], yr[tr], epochs=3000)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    ev_sweep = lm.evaluate(m, X[te], ta[te], tc[te], gammas, bs_list)
+    cls, _ = m.predict(X[te])
+    # live: each held-out matrix solved with the predicted and with the fixed block size
+    import gen
+    solvers = []
+    for k, idx in enumerate(te):
+        spec = data["records"][idx]["spec"]
+        a = gen.config5_matrix(spec)
+        b = np.random.default_rng(spec["seed"] + 7).uniform(-1.0, 1.0, a.n)
+        pair = []
+        for s_blk in (bs_list[int(cls[k])], lm.BASE_BLOCK):
+            S = iccg.Solver(a, iccg.blocking(a, "abmc", s_blk), stream=stream.cuda_stream)
+            pair.append(S)
+        solvers.append((pair, torch.tensor(b, device=dev)))
+
+    def step(which):
+        tot = 0.0
+        for pair, bd in solvers:
+            xd = torch.zeros_like(bd)
+            e0.record(stream)
+            iccg.iccg_solve(pair[which].ctx, bd, xd, args.tol, args.maxit, want_hist=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot
+
+    for _ in range(args.warmup):
+        step(0)
+        step(1)
+    with ClockSampler(local) as clk:
+        pred_ms = statistics.mean(step(0) for _ in range(args.steps))
+    fixed_ms = statistics.mean(step(1) for _ in range(args.steps))
+    for pair, _ in solvers:
+        for S in pair:
+            S.close()
+    result = {
+        "metric": "ICCG time to 1e-8 rel. residual", "value": round(pred_ms, 3), "unit": "ms",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(pred_ms, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["learned"], "step": "the 40 held-out systems solved once each, "
+                   "inputs resident, blocking and setup excluded", "l2": "mixed (systems 0.5-30 MB)",
+                   "parallelism": "1 GPU"},
+        "fixed_block32_ms": round(fixed_ms, 3),
+        "gain_vs_fixed_block32": round(fixed_ms / pred_ms, 3),
+        "train_ms": round(train_ms, 1), "train_loss": [round(v, 4) for v in hist[::6]],
+        "held_out_vs_sweep": ev_sweep,
+        "roofline": None,
+        "e2e": None,
+        "gpu_launches": None,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(result))
+
+
 def oracle_sample(a, b, perm, sample_iters):
     """IC(0) + `sample_iters` PCG iterations of the oracle; returns seconds."""
     import oracle
@@ -502,6 +585,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_gpu(args)
 

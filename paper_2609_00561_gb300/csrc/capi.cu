@@ -219,7 +219,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   L.tile1.assign(n_c, 0);
   // lane tiles: one CTA of up to 8 warps per tile (steps shared out in phases
   // A and C)
-  L.Wt = std::max(1, std::min(8, H.lane_max));
+  L.Wt = std::max(1, std::min(W, H.lane_max));   // warps per lane-tile CTA (one tile at a time)
   {
     // every tile's in-block entries staged: two buffers within
     // kTileSmemBudget, else one buffer within kTileSmemBudget1 (the fused

@@ -158,8 +158,33 @@ def evaluate(model, X, ta, tc, gammas, block_sizes):
         "cpm_gain_vs_fixed005": float(np.exp(np.mean(np.log(base_c / t_cpm)))),
         "combined_regret_mean": float(np.mean(pred / best)),
         "combined_gain_vs_fixed": float(np.exp(np.mean(np.log(base / pred)))),
-        "class_accuracy": None,
     }
+
+
+def choose(model, a, block_sizes, gammas, swept=None):
+    """(ABMC block size, CPM resolution) for matrix a: the sweep's optimum when
+    `swept` (a record of the label sweep for this matrix) is given, else the
+    model's prediction from the library's features (the resolution snapped to
+    the nearest swept value)."""
+    if swept is not None:
+        runs = swept["runs"]
+        ta = [r["ms"] if r["status"] == 0 else math.inf for r in runs[:len(block_sizes)]]
+        tc = [r["ms"] if r["status"] == 0 else math.inf for r in runs[len(block_sizes):]]
+        return block_sizes[int(np.argmin(ta))], gammas[int(np.argmin(tc))]
+    from paper_2609_00561_gb300 import iccg
+    cls, lg = model.predict(iccg.features(a)[None, :])
+    gi = int(np.abs(lg[0] - np.log(np.array(gammas))).argmin())
+    return block_sizes[int(cls[0])], gammas[gi]
+
+
+def evaluate_fixed(ta, tc, gammas, block_sizes):
+    """Regret of the method without the model (ABMC 32, CPM 0.05)."""
+    base_a = ta[:, block_sizes.index(BASE_BLOCK)]
+    base_c = tc[:, gammas.index(BASE_GAMMA)]
+    best_a, best_c = ta.min(axis=1), tc.min(axis=1)
+    return {"abmc_regret_mean": float(np.mean(base_a / best_a)),
+            "cpm_regret_mean": float(np.mean(base_c / best_c)),
+            "combined_regret_mean": float(np.mean(np.minimum(base_a, base_c) / np.minimum(best_a, best_c)))}
 
 
 def main():
@@ -179,9 +204,9 @@ def main():
     tr, te = split(len(yc))
     m = Model(X.shape[1], len(data["meta"]["block_sizes"]))
     hist = m.fit(X[tr], yc[tr], yr[tr], epochs=args.epochs)
-    res = {"train": evaluate(m, X[tr], ta[tr], tc[tr], data["meta"]["gammas"], data["meta"]["block_sizes"]),
-           "test": evaluate(m, X[te], ta[te], tc[te], data["meta"]["gammas"], data["meta"]["block_sizes"]),
-           "loss": hist[::5]}
+    g, b = data["meta"]["gammas"], data["meta"]["block_sizes"]
+    res = {"train": evaluate(m, X[tr], ta[tr], tc[tr], g, b), "test": evaluate(m, X[te], ta[te], tc[te], g, b),
+           "test_fixed": evaluate_fixed(ta[te], tc[te], g, b), "loss": hist[::5]}
     print(json.dumps(res, indent=1))
     if args.out:
         m.save(args.out)

@@ -20,8 +20,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-BLOCK_SIZES = [8, 16, 32, 64, 128]
-GAMMAS = [0.01, 0.02, 0.05, 0.1, 0.2, 0.5]
+# the paper's ranges (block sizes 8..128, resolutions 0.01..0.5) extended on
+# both sides: on GB300 the fastest settings lie at or beyond their small-block
+# ends (block size 8 and resolution 0.5 won on every matrix of a first sweep)
+BLOCK_SIZES = [2, 4, 8, 16, 32, 64, 128]
+GAMMAS = [0.01, 0.02, 0.05, 0.1, 0.2, 0.5, 1.0, 2.0]
 
 
 def _blockings(spec):
