@@ -297,6 +297,18 @@ iccg_status iccg_color_order(int32_t n, const int64_t *gptr, const int32_t *gadj
                              const int32_t *block_of, int32_t *color_of, int32_t *n_c,
                              int32_t *perm, int32_t *block_ptr, int32_t *color_ptr);
 
+/* Diagnostics (host only, no device): builds the layout iccg_setup would
+ * build for these inputs (groups of at most group_rows rows, lane tiles for
+ * colors of blocks of at most lane_max rows, 0 = none) and checks the index
+ * ranges the kernels rely on.  report[4]: lane tiles, groups, failed checks,
+ * the tile / group / color of the first failure (-1 none); *what (may be
+ * NULL) names the first failed check.  ICCG_OK, ICCG_ERR_STATE when a check
+ * failed, or the validation error of iccg_setup. */
+iccg_status iccg_check_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
+                              const double *val, const int32_t *perm, const int32_t *block_ptr,
+                              const int32_t *color_ptr, int32_t n_b, int32_t n_c, int32_t group_rows,
+                              int32_t lane_max, int64_t report[4], const char **what);
+
 /* ------------------------------------------------------------------------
  * Learned blocking (extension; the paper selects block sizes and
  * resolutions by sweeps, Table 2 and Sec. 6.1).

@@ -423,3 +423,117 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
 }
 
 }  // namespace iccg
+
+// ---------------------------------------------------------------------------
+// Diagnostics: build the layout as iccg_setup does (host only) and check the
+// index ranges the kernels rely on.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Checker {
+  int64_t failed = 0, first = -1;
+  const char *what = nullptr;
+  void operator()(bool ok, int64_t where, const char *msg) {
+    if (ok) return;
+    if (failed++ == 0) {
+      first = where;
+      what = msg;
+    }
+  }
+};
+
+}  // namespace
+
+extern "C" iccg_status iccg_check_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
+                                         const double *val, const int32_t *perm, const int32_t *block_ptr,
+                                         const int32_t *color_ptr, int32_t n_b, int32_t n_c, int32_t group_rows,
+                                         int32_t lane_max, int64_t report[4], const char **what) {
+  using namespace iccg;
+  if (!report || !rowptr) return ICCG_ERR_ARG;
+  HostLayout H;
+  int64_t bad = -1;
+  std::string msg;
+  const iccg_status st = build_layout(n, nnz, rowptr, colind, val, perm, block_ptr, color_ptr, n_b, n_c,
+                                      std::max(group_rows, 1), lane_max, H, bad, msg);
+  report[0] = report[1] = report[2] = report[3] = 0;
+  if (st != ICCG_OK) {
+    report[3] = bad;
+    return st;
+  }
+  Checker ck;
+  // tiles: step rows consecutive, active lanes a prefix, entries inside their
+  // step's range, in-block references to existing earlier (L) or later (U)
+  // steps of the same lane, other-color columns in range
+  for (size_t t = 0; t < H.tiles.size(); ++t) {
+    const TileDesc &td = H.tiles[t];
+    ck(td.nsteps >= 1 && td.nsteps <= H.lane_max, int64_t(t), "tile steps");
+    ck(td.nrows <= H.tcap_r, int64_t(t), "tile rows");
+    int32_t row = td.row0;
+    for (int s = 0; s < td.nsteps; ++s) {
+      const StepDesc &sd = H.steps[size_t(td.step0 + s)];
+      ck(sd.row == row, int64_t(t), "step rows");
+      ck(sd.cnt >= 1 && sd.cnt <= kWarp, int64_t(t), "step lanes");
+      if (s) ck(sd.cnt <= H.steps[size_t(td.step0 + s - 1)].cnt, int64_t(t), "active lanes a prefix");
+      ck(sd.lo >= td.lo0 && sd.lo + sd.lw * sd.cnt <= td.lo1, int64_t(t), "L other-color range");
+      ck(sd.li >= td.li0 && sd.li + sd.liw * sd.cnt <= td.li1, int64_t(t), "L in-block range");
+      ck(sd.uo >= td.uo0 && sd.uo + sd.uw * sd.cnt <= td.uo1, int64_t(t), "U other-color range");
+      ck(sd.ui >= td.ui0 && sd.ui + sd.uiw * sd.cnt <= td.ui1, int64_t(t), "U in-block range");
+      for (int j = 0; j < sd.liw; ++j)
+        for (int l = 0; l < sd.cnt; ++l) {
+          const size_t e = size_t(sd.li + j * sd.cnt + l);
+          const int c = H.si_col[e];
+          ck(c >= 0 && c < td.nsteps, int64_t(t), "in-block L step");
+          if (H.si_map[e] >= 0) ck(c < s && l < H.steps[size_t(td.step0 + c)].cnt, int64_t(t), "in-block L order");
+        }
+      for (int j = 0; j < sd.uiw; ++j)
+        for (int l = 0; l < sd.cnt; ++l) {
+          const size_t e = size_t(sd.ui + j * sd.cnt + l);
+          const int c = H.ui_col[e];
+          ck(c >= 0 && c < td.nsteps, int64_t(t), "in-block U step");
+          if (H.ui_map[e] >= 0) ck(c > s && l < H.steps[size_t(td.step0 + c)].cnt, int64_t(t), "in-block U order");
+        }
+      for (int j = 0; j < sd.lw; ++j)
+        for (int l = 0; l < sd.cnt; ++l) {
+          const int c = H.sl_col[size_t(sd.lo + j * sd.cnt + l)];
+          ck(c == kPadCol || (c >= 0 && c < n), int64_t(t), "L other-color column");
+        }
+      for (int j = 0; j < sd.uw; ++j)
+        for (int l = 0; l < sd.cnt; ++l) {
+          const int c = H.su_col[size_t(sd.uo + j * sd.cnt + l)];
+          ck(c == kPadCol || (c >= 0 && c < n), int64_t(t), "U other-color column");
+        }
+      row += sd.cnt;
+    }
+    ck(row == td.row0 + td.nrows, int64_t(t), "tile row count");
+  }
+  // groups: level pointers monotone and complete, schedules a permutation
+  for (size_t g = 0; g < H.groups.size(); ++g) {
+    const GroupDesc &gd = H.groups[g];
+    const int rows = gd.r1 - gd.r0;
+    ck(rows >= 1, int64_t(g), "group rows");
+    for (int pass = 0; pass < 2; ++pass) {
+      const int lp0 = pass ? gd.lb : gd.lf, nl = pass ? gd.nlb : gd.nlf;
+      ck(H.levp[size_t(lp0)] == 0 && H.levp[size_t(lp0 + nl)] == rows, int64_t(g), "level pointers");
+      for (int lv = 0; lv < nl; ++lv) ck(H.levp[size_t(lp0 + lv)] <= H.levp[size_t(lp0 + lv + 1)], int64_t(g), "levels");
+      std::vector<char> seen(size_t(rows), 0);
+      const std::vector<int32_t> &sch = pass ? H.sched_b : H.sched_f;
+      for (int i = gd.r0; i < gd.r1; ++i) {
+        const int l = sch[size_t(i)];
+        ck(l >= 0 && l < rows && !seen[size_t(std::max(0, std::min(l, rows - 1)))], int64_t(g), "schedule");
+        if (l >= 0 && l < rows) seen[size_t(l)] = 1;
+      }
+    }
+  }
+  // every color either tiles or groups, covering its rows
+  for (int c = 0; c < n_c; ++c) {
+    const bool tile = H.color_tile[size_t(c) + 1] > H.color_tile[size_t(c)];
+    const bool grp = H.color_group[size_t(c) + 1] > H.color_group[size_t(c)];
+    ck(tile != grp, c, "color layout");
+  }
+  report[0] = int64_t(H.tiles.size());
+  report[1] = int64_t(H.groups.size());
+  report[2] = ck.failed;
+  report[3] = ck.first;
+  if (what) *what = ck.what;
+  return ck.failed ? ICCG_ERR_STATE : ICCG_OK;
+}
