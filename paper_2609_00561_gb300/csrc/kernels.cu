@@ -760,51 +760,6 @@ __device__ __forceinline__ void tile_phase_b(const TileDesc &t, const StepDesc *
   }
 }
 
-// Phase B for blocks of at most S rows (S = 8 or 16): the lane's block lives
-// in registers (y[k] = row k of the block); an in-block operand is picked by
-// a select tree over its step index, so the recurrence waits only on its
-// FMAs.  Same arithmetic and order as tile_phase_b.
-template <int S, typename PT>
-__device__ __forceinline__ PT pick(const PT (&y)[S], int c) {
-  PT r = y[0];
-#pragma unroll
-  for (int q = 1; q < S; ++q) r = c == q ? y[q] : r;
-  return r;
-}
-
-template <int S, typename PT, bool UPPER>
-__device__ __forceinline__ void tile_phase_b_reg(const TileDesc &t, const StepDesc *st, const PT *dv,
-                                                 const int32_t *ic, const PT *iv, PT *w, int lane) {
-  PT y[S];
-#pragma unroll
-  for (int k = 0; k < S; ++k) y[k] = (k < t.nsteps && lane < st[k].cnt) ? w[k * kWarp + lane] : PT(0);
-#pragma unroll
-  for (int kk = 0; kk < S; ++kk) {
-    const int k = UPPER ? S - 1 - kk : kk;
-    if (k < t.nsteps) {
-      const StepDesc &s = st[k];
-      const int cnt = s.cnt, wi = UPPER ? s.uiw : s.liw, e = (UPPER ? s.ui : s.li) + lane;
-      if (lane < cnt) {
-        PT acc = y[k];
-        for (int j = 0; j < wi; ++j) acc -= iv[e + j * cnt] * pick<S, PT>(y, ic[e + j * cnt]);
-        y[k] = acc * dv[s.row + lane];
-      }
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < S; ++k)
-    if (k < t.nsteps && lane < st[k].cnt) w[k * kWarp + lane] = y[k];
-}
-
-// Phase B dispatch on the plan's largest block
-template <typename PT, bool UPPER>
-__device__ __forceinline__ void tile_chain(const TilePlan &pl, const TileDesc &t, const StepDesc *st, const PT *dv,
-                                           const int32_t *ic, const PT *iv, PT *w, int lane) {
-  if (pl.cap_s <= 8) tile_phase_b_reg<8, PT, UPPER>(t, st, dv, ic, iv, w, lane);
-  else if (pl.cap_s <= 16) tile_phase_b_reg<16, PT, UPPER>(t, st, dv, ic, iv, w, lane);
-  else tile_phase_b<PT, UPPER>(t, st, dv, ic, iv, w, lane);
-}
-
 // Phase C: the tile's results to global memory (y or z), <r,z> (backward)
 template <typename PT, bool UPPER>
 __device__ __forceinline__ void tile_phase_c(const Params &P, const TileDesc &t, const StepDesc *st, const PT *w,
@@ -862,13 +817,13 @@ tile_kernel(Params P, int t0, int t1, TilePlan pl, int fin, SlotArgs sa) {
     if (MODE == M_BWD) {
       tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, false, rr_acc, wid, nw);
       __syncthreads();
-      if (wid == 0) tile_chain<PT, true>(pl, td, tb.st, dv, ul.ic, ul.iv, w, threadIdx.x);
+      if (wid == 0) tile_phase_b<PT, true>(td, tb.st, dv, ul.ic, ul.iv, w, threadIdx.x);
       __syncthreads();
       tile_phase_c<PT, true>(P, td, tb.st, w, true, rz_acc, wid, nw);
     } else {
       tile_phase_a<PT, false, UPDATE>(P, td, tb, w, alpha, P.p0, false, rr_acc, wid, nw);
       __syncthreads();
-      if (wid == 0) tile_chain<PT, false>(pl, td, tb.st, dv, ll.ic, ll.iv, w, threadIdx.x);
+      if (wid == 0) tile_phase_b<PT, false>(td, tb.st, dv, ll.ic, ll.iv, w, threadIdx.x);
       __syncthreads();
       if (MODE == M_FWD) {
         tile_phase_c<PT, false>(P, td, tb.st, w, true, rz_acc, wid, nw);
@@ -877,7 +832,7 @@ tile_kernel(Params P, int t0, int t1, TilePlan pl, int fin, SlotArgs sa) {
         const InBlock<PT> u2 = in_block<PT>(tb.ic2, tb.iv2, P.ui_col, uiv<PT>(P), td.ui0, td.ui1, pl.cap_i2);
         tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, true, rr_acc, wid, nw);
         __syncthreads();
-        if (wid == 0) tile_chain<PT, true>(pl, td, tb.st, dv, u2.ic, u2.iv, w, threadIdx.x);
+        if (wid == 0) tile_phase_b<PT, true>(td, tb.st, dv, u2.ic, u2.iv, w, threadIdx.x);
         __syncthreads();
         tile_phase_c<PT, true>(P, td, tb.st, w, true, rz_acc, wid, nw);
       }
