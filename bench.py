@@ -1,6 +1,9 @@
 """Benchmark: ICCG time to 1e-8 relative residual on the 3D 7-point Poisson
 problem (128^3, n = 2,097,152, 14.58M nonzeros, b ~ U[-1,1] from seed 0) with
-ABMC blocking (block size 8 by default) and greedy block coloring.
+Leiden CPM blocking (resolution 0.5) and greedy block coloring: the fastest
+blocking on a GB300 of the swept set (ABMC block sizes 8..128, Leiden
+modularity, CPM resolutions 0.01..0.5); `--blocking abmc --block-size S`
+selects another.
 `--workload diffusion96 --fp32` runs the 27-point variable-coefficient
 diffusion problem (96^3, ABMC 32) with the FP32 preconditioner (extension 1).
 `--workload batch64` runs the batched extension: 64 shifted 7-point systems
@@ -119,6 +122,22 @@ def workload(args):
     return a, b
 
 
+def make_blocking(mod, a, args):
+    """The configured blocking by `mod` (the library, or the oracle for the
+    reference arm; both give the same permutation)."""
+    if args.blocking == "abmc":
+        return mod.blocking(a, "abmc", args.block_size)
+    return mod.blocking(a, args.blocking, gamma=args.gamma)
+
+
+def blocking_name(args):
+    if args.blocking == "abmc":
+        return f"ABMC s={args.block_size}"
+    if args.blocking == "leiden_cpm":
+        return f"Leiden CPM resolution {args.gamma:g}"
+    return "Leiden modularity"
+
+
 def bytes_model(n, nnz, nL, fp32):
     """Algorithmic bytes per PCG iteration (each array counted once, gathered
     vector reads assumed to hit cache), by kernel family:
@@ -154,7 +173,7 @@ def run_gpu(args):
     a, b = workload(args)
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    bl = iccg.blocking(a, "abmc", args.block_size)
+    bl = make_blocking(iccg, a, args)
     t_block = time.perf_counter() - t0
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
@@ -255,7 +274,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload].format(nx=args.nx) +
                                f" (n={a.n}, nnz={a.nnz}), b~U[-1,1] seed {args.seed}, "
-                               f"ABMC s={args.block_size} + greedy coloring (n_b={bl['n_b']}, n_c={n_c}), "
+                               f"{blocking_name(args)} + greedy coloring (n_b={bl['n_b']}, n_c={n_c}), "
                                f"IC(0) + PCG to {args.tol:g}" + (", FP32 preconditioner" if args.fp32 else ""),
                    "step": "iccg_factor + iccg_solve, inputs resident",
                    "l2": "inputs larger than L2 (matrix + factors > 129 MB)",
@@ -529,7 +548,7 @@ def run_reference(args):
     # the reference arm never touches the GPU; blocking comes from the oracle
     import oracle
     a, b = workload(args)
-    bl = oracle.blocking(a, "abmc", args.block_size)
+    bl = make_blocking(oracle, a, args)
     iters_full = args.ref_iters
     times = []
     for k in range(args.warmup + args.steps):
@@ -543,7 +562,7 @@ def run_reference(args):
               "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
               "data": "synthetic",
               "config": {"workload": WORKLOADS[args.workload].format(nx=args.nx) +
-                                     f", ABMC s={args.block_size} + greedy coloring, IC(0) + PCG to {args.tol:g} "
+                                     f", {blocking_name(args)} + greedy coloring, IC(0) + PCG to {args.tol:g} "
                                      f"(CPU oracle)"},
               "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
                                "sample": f"each step: IC(0) + {args.cpu_sample_iters} PCG iterations, scaled to "
@@ -561,6 +580,9 @@ def main():
     p.add_argument("--workload", default="poisson128", choices=sorted(WORKLOADS))
     p.add_argument("--nx", type=int, default=None, help="grid side (default 128, or 96 for diffusion96)")
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--blocking", default=None, choices=["abmc", "leiden_cpm", "leiden_md"],
+                   help="default: leiden_cpm for poisson128, abmc otherwise")
+    p.add_argument("--gamma", type=float, default=0.5, help="Leiden CPM resolution")
     p.add_argument("--block-size", type=int, default=None, help="ABMC block size (default 8, or 32 for diffusion96)")
     p.add_argument("--tol", type=float, default=1e-8)
     p.add_argument("--maxit", type=int, default=5000)
@@ -568,8 +590,9 @@ def main():
     p.add_argument("--warps", type=int, default=0)
     p.add_argument("--rows", type=int, default=0)
     p.add_argument("--cpu-sample-iters", type=int, default=20)
-    p.add_argument("--ref-iters", type=int, default=176,
-                   help="iterations the full solve takes (scales the reference sample)")
+    p.add_argument("--ref-iters", type=int, default=None,
+                   help="iterations the full solve takes (scales the reference sample; default: 183 for the "
+                        "default poisson128 blocking, else 176)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--nsys", type=int, default=64, help="batch64: systems")
     p.add_argument("--nrhs", type=int, default=16, help="batch64: right-hand sides per system")
@@ -579,6 +602,10 @@ def main():
         args.nx = 96 if args.workload == "diffusion96" else 128
     if args.block_size is None:
         args.block_size = 32 if args.workload in ("diffusion96", "batch64") else 8
+    if args.blocking is None:
+        args.blocking = "leiden_cpm" if args.workload == "poisson128" else "abmc"
+    if args.ref_iters is None:
+        args.ref_iters = 183 if (args.blocking, args.gamma) == ("leiden_cpm", 0.5) else 176
     if args.steps < 1 or args.warmup < 0:
         raise SystemExit("steps >= 1, warmup >= 0")
     if args.impl == "reference":

@@ -127,7 +127,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   if (!rowptr || (n > 0 && (!colind || !val || !perm || !block_ptr || !color_ptr))) return ICCG_ERR_ARG;
   iccg_opts o{};
   if (opts) o = *opts;
-  if (o.reserved[0] != 0) return ICCG_ERR_ARG;
+  if (o.tile_mapping < ICCG_TILES_AUTO || o.tile_mapping > ICCG_TILES_WARP) return ICCG_ERR_ARG;
   if (o.lane_block_max > 32 || o.lane_block_max < -1) return ICCG_ERR_ARG;
   if (o.solver < ICCG_SOLVER_AUTO || o.solver > ICCG_SOLVER_PHASED) return ICCG_ERR_ARG;
   if (o.warps_per_cta == 0) o.warps_per_cta = 8;
@@ -203,13 +203,13 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   }
   const int cap_a = cap_of(H.seg_a);
   const int Wc = W;   // warps per CTA of the color kernels (one CTA per group)
-  const int Wa = 4;   // warps per CTA of the SpMV (one warp per 32 rows)
+  const int Wa = 8;   // warps per CTA of the SpMV (one warp per 32-row slice)
   L.W = Wc;
   L.Wa = Wa;
   L.smem_fwd = group_smem_bytes(cap_l, cap_rows, cap_lev, elem);
   L.smem_bwd = group_smem_bytes(cap_u, cap_rows, cap_lev, elem);
   L.smem_fused = group_smem_bytes(std::max(cap_l, cap_u), cap_rows, cap_lev, elem);
-  L.smem_a = Wa * spmv_smem_bytes(cap_a);
+  L.smem_a = 0;
   // one CTA per group (color kernels), one warp per 32-row tile (SpMV)
   // (a lane-tile color: Wt tiles per CTA)
   L.grid_c.assign(n_c, 0);
@@ -249,6 +249,14 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   // walking tiles grid-stride
   const int tile_full =
       H.tile_colors > 0 ? sms * tile_resident_ctas(ctx->fp32, L.Wt * kWarp, L.smem_tile) : 1;
+  // warp-tile kernels: W warps per CTA, one tile per warp at a time, a
+  // buffer of (largest tile's steps) x 32 values per warp
+  L.Ww = W;
+  L.cap_ws = std::max(H.lane_max, 1);
+  L.smem_wt = L.Ww * L.cap_ws * kWarp * elem;
+  const int wt_full =
+      H.tile_colors > 0 ? sms * wtile_resident_ctas(ctx->fp32, L.Ww * kWarp, L.smem_wt) : 1;
+  L.wtile.assign(n_c, 0);
   int32_t gbig = 1;
   for (int c = 0; c < n_c; ++c) {
     L.task0[c] = H.color_group[c];
@@ -256,7 +264,13 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     L.tile0[c] = H.color_tile[c];
     L.tile1[c] = H.color_tile[c + 1];
     const int nt = L.tile1[c] - L.tile0[c];
-    L.grid_c[c] = nt > 0 ? std::min(nt, tile_full) : std::max(1, L.task1[c] - L.task0[c]);
+    int steps = 0;
+    for (int t = L.tile0[c]; t < L.tile1[c]; ++t) steps = std::max(steps, H.tiles[t].nsteps);
+    // automatic: one CTA per tile (on a GB300 the warp mapping measured no
+    // faster for one-step tiles and slower for longer ones)
+    L.wtile[c] = nt > 0 && o.tile_mapping == ICCG_TILES_WARP && steps >= 1;
+    if (L.wtile[c]) L.grid_c[c] = std::min((nt + L.Ww - 1) / L.Ww, wt_full);
+    else L.grid_c[c] = nt > 0 ? std::min(nt, tile_full) : std::max(1, L.task1[c] - L.task0[c]);
     gbig = std::max(gbig, L.grid_c[c]);
   }
   // slot regions: forward launches in color order (<r,r>), then the fused
@@ -303,6 +317,14 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   CK(dev_upload(ctx, &d_arp, H.arp), "alloc A");
   CK(dev_upload(ctx, &d_acol, H.acol), "alloc A");
   CK(dev_upload(ctx, &d_aval, H.aval), "alloc A");
+  {
+    int32_t *d_sap, *d_sac;
+    double *d_sav;
+    CK(dev_upload(ctx, &d_sap, H.sa_ptr), "alloc A");
+    CK(dev_upload(ctx, &d_sac, H.sa_col), "alloc A");
+    CK(dev_upload(ctx, &d_sav, H.sa_val), "alloc A");
+    P.sa_ptr = d_sap; P.sa_col = d_sac; P.sa_val = d_sav;
+  }
   CK(dev_upload(ctx, &d_lrp, H.lrp), "alloc L");
   CK(dev_upload(ctx, &d_lcol, H.lcol), "alloc L");
   CK(dev_upload(ctx, &d_ainit, H.ainit), "alloc L");
@@ -754,7 +776,7 @@ iccg_status iccg_get_factor(iccg_ctx *ctx, double *lval, int64_t *nnz_lower) {
   return ICCG_OK;
 }
 
-iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[11]) {
+iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[12]) {
   if (!ctx || !out) return ICCG_ERR_ARG;
   const HostLayout &H = ctx->H;
   out[0] = H.n;
@@ -769,6 +791,8 @@ iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[11]) {
   out[8] = H.max_group_rows;
   out[9] = int64_t(H.tiles.size());
   out[10] = H.tile_colors;
+  out[11] = 0;
+  for (char w : ctx->plan.wtile) out[11] += w ? 1 : 0;
   return ICCG_OK;
 }
 

@@ -302,6 +302,7 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
         sd.uiw = sell(row, cnt, H.urp, H.ucol, H.umap.data(), true, H.ui_col, H.ui_map);
         td.wl = std::max(td.wl, sd.liw);
         td.wu = std::max(td.wu, sd.uiw);
+        if (k == 0) { td.lw0 = sd.lw; td.uw0 = sd.uw; }
         H.steps.push_back(sd);
         row += cnt;
       }
@@ -419,6 +420,38 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
   int32_t seg_a = 0;
   for (int32_t r0 = 0; r0 < n; r0 += kWarp) seg_a = std::max(seg_a, H.arp[std::min(n, r0 + kWarp)] - H.arp[r0]);
   H.seg_a = seg_a;
+
+  // A_hat's off-diagonal entries sliced-ELL for the SpMV: slice s holds rows
+  // [32s, 32s + 32), width w_s = its longest row; entry j of lane l at
+  // sa_ptr[s] + 32 j + l; padding (the row itself, 0.0)
+  const int32_t nsl = (n + kWarp - 1) / kWarp;
+  H.sa_ptr.assign(nsl + 1, 0);
+  int64_t tot = 0;
+  for (int32_t s = 0; s < nsl; ++s) {
+    int32_t w = 0;
+    for (int32_t i = s * kWarp; i < std::min(n, (s + 1) * kWarp); ++i) w = std::max(w, H.arp[i + 1] - H.arp[i] - 1);
+    tot += int64_t(w) * kWarp;
+    if (tot > INT32_MAX) return fail(ICCG_ERR_ARG, -1, "matrix too large for 32-bit sliced-ELL offsets", bad, msg);
+    H.sa_ptr[s + 1] = int32_t(tot);
+  }
+  H.sa_col.assign(size_t(tot), 0);
+  H.sa_val.assign(size_t(tot), 0.0);
+#pragma omp parallel for schedule(static)
+  for (int32_t s = 0; s < nsl; ++s) {
+    const int32_t w = (H.sa_ptr[s + 1] - H.sa_ptr[s]) / kWarp;
+    for (int32_t l = 0; l < kWarp; ++l) {
+      const int32_t i = s * kWarp + l;
+      int32_t j = 0;
+      if (i < n)
+        for (int32_t e = H.arp[i]; e < H.arp[i + 1]; ++e) {
+          if (H.acol[e] == i) continue;
+          H.sa_col[H.sa_ptr[s] + j * kWarp + l] = H.acol[e];
+          H.sa_val[H.sa_ptr[s] + j * kWarp + l] = H.aval[e];
+          ++j;
+        }
+      for (; j < w; ++j) H.sa_col[H.sa_ptr[s] + j * kWarp + l] = i < n ? i : 0;
+    }
+  }
   return ICCG_OK;
 }
 
@@ -461,6 +494,33 @@ extern "C" iccg_status iccg_check_layout(int32_t n, int64_t nnz, const int64_t *
     return st;
   }
   Checker ck;
+  // A_hat sliced-ELL: slice widths, padding on the row itself, every
+  // off-diagonal CSR entry once
+  {
+    const int32_t nsl = (n + kWarp - 1) / kWarp;
+    ck(int32_t(H.sa_ptr.size()) == nsl + 1 && H.sa_ptr[0] == 0, -1, "A slices");
+    for (int32_t sl = 0; sl < nsl; ++sl) {
+      const int32_t e0 = H.sa_ptr[size_t(sl)], e1 = H.sa_ptr[size_t(sl) + 1];
+      ck(e1 >= e0 && (e1 - e0) % kWarp == 0, sl, "A slice width");
+      const int32_t w = (e1 - e0) / kWarp;
+      for (int32_t l = 0; l < kWarp; ++l) {
+        const int32_t i = sl * kWarp + l;
+        int32_t j = 0;
+        if (i < n)
+          for (int32_t e = H.arp[size_t(i)]; e < H.arp[size_t(i) + 1]; ++e) {
+            if (H.acol[size_t(e)] == i) continue;
+            const int32_t k = e0 + j * kWarp + l;
+            ck(j < w && H.sa_col[size_t(k)] == H.acol[size_t(e)] && H.sa_val[size_t(k)] == H.aval[size_t(e)], sl,
+               "A slice entry");
+            ++j;
+          }
+        for (; j < w; ++j) {
+          const int32_t k = e0 + j * kWarp + l;
+          ck(H.sa_val[size_t(k)] == 0.0 && H.sa_col[size_t(k)] == (i < n ? i : 0), sl, "A slice padding");
+        }
+      }
+    }
+  }
   // tiles: step rows consecutive, active lanes a prefix, entries inside their
   // step's range, in-block references to existing earlier (L) or later (U)
   // steps of the same lane, other-color columns in range
@@ -473,6 +533,9 @@ extern "C" iccg_status iccg_check_layout(int32_t n, int64_t nnz, const int64_t *
       const StepDesc &sd = H.steps[size_t(td.step0 + s)];
       ck(sd.row == row, int64_t(t), "step rows");
       ck(sd.cnt >= 1 && sd.cnt <= kWarp, int64_t(t), "step lanes");
+      if (s == 0) ck(sd.lo == td.lo0 && sd.lw == td.lw0 && sd.li == td.li0 && sd.uo == td.uo0 && sd.uw == td.uw0 &&
+                     sd.ui == td.ui0, int64_t(t), "first step in the tile descriptor");
+      if (td.nsteps == 1) ck(sd.cnt == td.nrows && sd.liw == td.wl && sd.uiw == td.wu, int64_t(t), "one-step tile");
       if (s) ck(sd.cnt <= H.steps[size_t(td.step0 + s - 1)].cnt, int64_t(t), "active lanes a prefix");
       ck(sd.lo >= td.lo0 && sd.lo + sd.lw * sd.cnt <= td.lo1, int64_t(t), "L other-color range");
       ck(sd.li >= td.li0 && sd.li + sd.liw * sd.cnt <= td.li1, int64_t(t), "L in-block range");

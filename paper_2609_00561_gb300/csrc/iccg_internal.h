@@ -1,7 +1,9 @@
 // Internal declarations of libiccg (not part of the C ABI).
 //
 // Device data layout (all in the block-multicolor numbering, Sec. 3):
-//   A_hat   CSR (arp/acol/aval) for the SpMV of Table 8's "SpMV" phase.
+//   A_hat   CSR (arp/acol/aval), and its off-diagonal entries sliced-ELL in
+//           32-row slices (sa_ptr/sa_col/sa_val) with the diagonal (adiag)
+//           for the SpMV of Table 8's "SpMV" phase.
 //   L       strictly lower part of the IC(0) factor in CSR (lrp/lcol/lval),
 //           diagonal separately (ldiag, invd = 1/L_ii).
 //   U = L^T strictly upper part in CSR (urp/ucol/uval); umap[k] is the L
@@ -55,9 +57,11 @@ constexpr int kGroup = 32;   // CTAs per first-level reduction group
 // A lane tile: rows [row0, row0 + nrows), step descriptors steps[step0 ..
 // step0 + nsteps); its sliced-ELL entries are the contiguous ranges
 // [lo0, lo1) (L, other colors), [li0, li1) (L, in-block), [uo0, uo1),
-// [ui0, ui1) (U); wl / wu: its widest in-block L / U step.
+// [ui0, ui1) (U); wl / wu: its widest in-block L / U step; lw0 / uw0: the
+// widths of its first step's entries to other colors (a one-step tile is
+// fully described without its step descriptor).
 struct __align__(16) TileDesc {
-  int32_t row0, nrows, nsteps, step0, lo0, lo1, li0, li1, uo0, uo1, ui0, ui1, wl, wu, pad0, pad1;
+  int32_t row0, nrows, nsteps, step0, lo0, lo1, li0, li1, uo0, uo1, ui0, ui1, wl, wu, lw0, uw0;
 };
 // One step of a tile: rows [row, row + cnt) (lanes 0 .. cnt-1; blocks are
 // sorted by size, so the active lanes are a prefix).  Sliced-ELL entry j of
@@ -139,6 +143,10 @@ struct Params {
   double *lval, *uval, *ldiag, *invd;
   float *lval32, *uval32, *invd32;
   const double *ainit, *adiag;
+  // A_hat's off-diagonal entries sliced-ELL (slice s = rows [32s, 32s+32):
+  // entry j of lane l at sa_ptr[s] + 32 j + l; padding (row, 0.0))
+  const int32_t *sa_ptr, *sa_col;
+  const double *sa_val;
   // groups and their level schedules
   const GroupDesc *groups;
   const int32_t *sched_f, *sched_b, *levp;
@@ -202,6 +210,8 @@ struct HostLayout {
   std::vector<double> aval;
   std::vector<int32_t> lrp, lcol, urp, ucol, umap;
   std::vector<double> ainit, adiag;
+  std::vector<int32_t> sa_ptr, sa_col;          // A_hat off-diagonal, sliced-ELL (32-row slices)
+  std::vector<double> sa_val;
   std::vector<GroupDesc> groups;
   std::vector<int32_t> sched_f, sched_b, levp;
   std::vector<int32_t> color_group;   // n_c + 1 (no groups for a tile color)
@@ -244,6 +254,10 @@ struct Plan {
   int32_t cap_ti = 0;                   // in-block entries of a tile staged in shared memory
   int32_t nbuf_t = 2;                   // lane-tile staging buffers per CTA
   int32_t cap_ti2 = 0;                  // second-set (fused launch) staging capacity
+  std::vector<char> wtile;              // color c runs one warp per tile (warp-tile kernels)
+  int32_t Ww = 8;                       // warps per CTA of the warp-tile kernels
+  int32_t smem_wt = 0;                  // bytes per CTA of the warp-tile kernels
+  int32_t cap_ws = 0;                   // steps per tile held in a warp's buffer
   std::vector<int32_t> off_rr, off_rz;  // slot regions of the color-c forward / backward launches
   int32_t last_rr = 0, last_rz = 0;     // slots written before the final launch of an iteration
   int32_t grid_a = 0;                   // CTAs of the SpMV-shaped kernels
@@ -263,6 +277,7 @@ int group_smem_bytes(int cap, int rows, int levs, int elem);  // per-warp plan o
 int spmv_smem_bytes(int cap);                                // per-warp staging of the SpMV
 int spmv_resident_ctas(int Wa, int smem);                    // CTAs per SM of the SpMV
 int tile_resident_ctas(bool fp32, int threads, int smem);    // CTAs per SM of the lane-tile kernels
+int wtile_resident_ctas(bool fp32, int threads, int smem);   // CTAs per SM of the warp-tile kernels
 cudaError_t launch_factor(const Params &P, const Plan &L, int nL);
 cudaError_t launch_solve_init(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);
 cudaError_t launch_solve_body(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);

@@ -618,7 +618,7 @@ __device__ __forceinline__ TileDesc load_tile(const TileDesc *t) {
   r.row0 = a.x; r.nrows = a.y; r.nsteps = a.z; r.step0 = a.w;
   r.lo0 = b.x; r.lo1 = b.y; r.li0 = b.z; r.li1 = b.w;
   r.uo0 = c.x; r.uo1 = c.y; r.ui0 = c.z; r.ui1 = c.w;
-  r.wl = d.x; r.wu = d.y; r.pad0 = r.pad1 = 0;
+  r.wl = d.x; r.wu = d.y; r.lw0 = d.z; r.uw0 = d.w;
   return r;
 }
 
@@ -854,6 +854,113 @@ tile_kernel(Params P, int t0, int t1, TilePlan pl, int fin, SlotArgs sa) {
 }
 
 // ---------------------------------------------------------------------------
+// warp-tile kernels: one warp per lane tile, all of the tile's steps in order
+// by that warp (Alg. 1 again: a lane per block, the block's rows in
+// sequence).  For colors of many tiles with few steps (blocks of a few rows)
+// this keeps every warp of a CTA busy where the CTA-per-tile kernel spreads
+// the steps of one tile over its warps; no barrier, and a lane's in-block
+// values stay in its own column of the warp's shared-memory buffer.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ StepDesc load_step_g(const StepDesc *s) {
+  const int4 *p = reinterpret_cast<const int4 *>(s);
+  const int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+  StepDesc r;
+  r.row = a.x; r.cnt = a.y; r.lo = a.z; r.lw = a.w;
+  r.li = b.x; r.liw = b.y; r.uo = b.z; r.uw = b.w;
+  r.ui = c.x; r.uiw = c.y; r.pad0 = r.pad1 = 0;
+  return r;
+}
+
+// One sweep over tile t by one warp.  Forward (UPPER = false): source r (with
+// the x / r update when UPDATE), entries to earlier colors gathered from y,
+// in-block entries from wv; result y.  Backward: source y (from wv when
+// y_in_smem, the fused last color), gathers of z, result z and <r,z>.
+// wv[step * 32 + lane] keeps the lane's own values of the tile.
+template <typename PT, bool UPPER, bool UPDATE>
+__device__ __forceinline__ void wtile_sweep(const Params &P, const TileDesc &t, PT *wv, double alpha,
+                                            bool y_in_smem, bool store, double &rr_acc, double &rz_acc, int lane) {
+  PT *res = reinterpret_cast<PT *>(UPPER ? P.z : P.y);
+  const PT *ext = reinterpret_cast<const PT *>(UPPER ? P.z : P.y);
+  const PT *yv = reinterpret_cast<const PT *>(P.y);
+  const PT *dvg = invds<PT>(P);
+  const int32_t *icol = UPPER ? P.ui_col : P.si_col;
+  const PT *ival = UPPER ? uiv<PT>(P) : siv<PT>(P);
+  // in-block padding entries are (step 0, value 0): a backward sweep reads
+  // step 0 before computing it, so it must hold a finite value (forward
+  // sweeps and the fused one have written it by then)
+  if (UPPER && !y_in_smem) {
+    for (int k = 0; k < t.nsteps; ++k) wv[k * kWarp + lane] = PT(0);
+    __syncwarp();
+  }
+  for (int kk = 0; kk < t.nsteps; ++kk) {
+    const int k = UPPER ? t.nsteps - 1 - kk : kk;
+    StepDesc s;
+    if (t.nsteps == 1) {
+      s.row = t.row0; s.cnt = t.nrows; s.lo = t.lo0; s.lw = t.lw0; s.li = t.li0; s.liw = t.wl;
+      s.uo = t.uo0; s.uw = t.uw0; s.ui = t.ui0; s.uiw = t.wu;
+    } else {
+      s = load_step_g(P.steps + t.step0 + k);
+    }
+    if (lane < s.cnt) {
+      const int i = s.row + lane;
+      PT acc;
+      if (UPPER) {
+        const PT src = y_in_smem ? wv[k * kWarp + lane] : __ldcg(yv + i);
+        acc = ext_sub<PT>(P.su_col, suv<PT>(P), s.uo + lane, s.cnt, s.uw, src, ext);
+      } else {
+        double ri = __ldcg(P.r + i);
+        if (UPDATE) {
+          ri -= alpha * __ldcg(P.q + i);
+          P.r[i] = ri;
+          P.xh[i] = __ldcg(P.xh + i) + alpha * __ldcg(P.p0 + i);
+          rr_acc += ri * ri;
+        }
+        acc = ext_sub<PT>(P.sl_col, slv<PT>(P), s.lo + lane, s.cnt, s.lw, PT(ri), ext);
+      }
+      const int wi = UPPER ? s.uiw : s.liw, e = (UPPER ? s.ui : s.li) + lane;
+      for (int j = 0; j < wi; ++j) acc -= __ldg(ival + e + j * s.cnt) * wv[__ldg(icol + e + j * s.cnt) * kWarp + lane];
+      const PT v = acc * __ldg(dvg + i);
+      wv[k * kWarp + lane] = v;
+      if (store) res[i] = v;
+      if (UPPER) rz_acc += __ldcg(P.r + i) * double(v);
+    }
+  }
+}
+
+// A warp-tile launch: the warps walk the color's tiles grid-stride (tile of
+// warp w of CTA b: t0 + b * W + w, then + gridDim.x * W); one <r,r> / <r,z>
+// reduction per CTA at the end.  Shared memory: cap_s * 32 values per warp.
+template <typename PT, int MODE, bool UPDATE>
+__global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
+wtile_kernel(Params P, int t0, int t1, int cap_s, int fin, SlotArgs sa) {
+  pdl_trigger();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[kMaxWarpsPerCta];
+  __shared__ int flag;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  PT *wv = reinterpret_cast<PT *>(smem) + size_t(wid) * cap_s * kWarp;
+  double rr_acc = 0.0, rz_acc = 0.0;
+  int t = t0 + int(blockIdx.x) * nw + wid;
+  TileDesc td = load_tile(P.tiles + min(t, t1 - 1));
+  pdl_wait();
+  const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
+  for (; t < t1; t += int(gridDim.x) * nw) {
+    const int tn = t + int(gridDim.x) * nw;
+    const TileDesc tdn = tn < t1 ? load_tile(P.tiles + tn) : td;
+    if (MODE == M_BWD) {
+      wtile_sweep<PT, true, false>(P, td, wv, 0.0, false, true, rr_acc, rz_acc, lane);
+    } else {
+      wtile_sweep<PT, false, UPDATE>(P, td, wv, alpha, false, MODE == M_FWD, rr_acc, rz_acc, lane);
+      __syncwarp();
+      if (MODE == M_FUSED) wtile_sweep<PT, true, false>(P, td, wv, 0.0, true, true, rr_acc, rz_acc, lane);
+    }
+    __syncwarp();
+    td = tdn;
+  }
+  launch_epilogue(P, fin, sa, MODE != M_BWD && UPDATE, MODE != M_FWD, rr_acc, rz_acc, red, &flag);
+}
+
+// ---------------------------------------------------------------------------
 // p = z + beta p (start of an iteration; beta = 0 on the first)
 // ---------------------------------------------------------------------------
 // (two rows per thread per pass: 16-byte loads of p and, for FP64 z, of z)
@@ -883,73 +990,55 @@ __global__ void __launch_bounds__(kVecThreads) pupdate_kernel(Params P) {
 }
 
 // ---------------------------------------------------------------------------
-// SpMV over 32-row tiles of A_hat, one row per lane; a full-occupancy grid
-// walks the tiles grid-stride (each warp one tile at a time: the resident
-// warps keep enough loads in flight)
+// SpMV over the 32-row slices of A_hat's sliced-ELL copy, one row per lane:
+// coalesced loads of a slice's columns and values straight into registers,
+// then the gathers; a full-occupancy grid walks the slices grid-stride (each
+// warp one slice at a time; the resident warps keep the loads in flight).
+// Off-diagonal entries in column order, then the diagonal.
 // ---------------------------------------------------------------------------
 // mode 0: q = A p, <p, q>; the last CTA sets alpha = rz / pq
 // mode 1: r = b_hat - A x_hat, <r, r> partials in part_a (solve start)
 // mode 2: q = A x_hat (plain SpMV)
+constexpr int kSpmvChunk = 8;   // entries per predicated batch of the SpMV
+
 template <int MODE>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
-spmv_kernel(Params P, int cap) {
+spmv_kernel(Params P) {
   pdl_trigger();
-  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[kMaxWarpsPerCta];
   __shared__ int flag;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-  double *sv = reinterpret_cast<double *>(smem + warp * (r16((cap + 8) * 8) + r16((cap + 8) * 4)));
-  int32_t *sc = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(sv) + r16((cap + 8) * 8));
-  const int ntile = (P.n + kWarp - 1) / kWarp;
+  const int nsl = (P.n + kWarp - 1) / kWarp;
   const double *xin = MODE == 0 ? P.p0 : P.xh;
   double acc = 0.0;
-  bool waited = false;
-  for (int tile = blockIdx.x * W + warp; tile < ntile; tile += gridDim.x * W) {
-    const int t0 = tile * kWarp, t1 = min(P.n, t0 + kWarp);
-    const int i = t0 + lane;
-    const int rb = i < t1 ? __ldg(P.arp + i) : 0;
-    const int re = i < t1 ? __ldg(P.arp + i + 1) : 0;
-    const int e0 = __shfl_sync(0xffffffffu, rb, 0);
-    const int e1 = __ldg(P.arp + t1);
-    Seg<double> S;
-    S.gv = P.aval; S.gc = P.acol; S.sv = sv; S.sc = sc;
-    S.staged = e1 - e0 <= cap;
-    S.bv = S.bc = 0;
-    if (S.staged) {
-      S.bv = stage_cover<double>(P.aval, e0, e1, sv, lane, kWarp);
-      S.bc = stage_cover<int32_t>(P.acol, e0, e1, sc, lane, kWarp);
-    }
-    cp_commit();
-    cp_wait_all();
-    __syncwarp();
-    if (!waited) {
-      pdl_wait();
-      waited = true;
-    }
-    // the tile's widest row sets a warp-uniform FMA count; shorter rows add
-    // exact zeros
-    const int width = __reduce_max_sync(0xffffffffu, unsigned(re - rb));
-    if (i < t1) {
-      double s = 0.0;
-      for (int j0 = 0; j0 < width; j0 += kChunk) {
-        const int nj = min(kChunk, width - j0);
-        int cc[kChunk];
-        double vv[kChunk], xx[kChunk];
+  pdl_wait();
+  for (int sl = blockIdx.x * W + warp; sl < nsl; sl += gridDim.x * W) {
+    const int e0 = __ldg(P.sa_ptr + sl), w = (__ldg(P.sa_ptr + sl + 1) - e0) >> 5;
+    const int i = sl * kWarp + lane;
+    const int32_t *col = P.sa_col + e0 + lane;
+    const double *val = P.sa_val + e0 + lane;
+    double s = 0.0;
+    for (int j0 = 0; j0 < w; j0 += kSpmvChunk) {
+      int cc[kSpmvChunk];
+      double vv[kSpmvChunk], xx[kSpmvChunk];
 #pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
-          const bool ok = rb + j0 + j < re;
-          cc[j] = ok ? S.c(rb + j0 + j) : -1;
-          vv[j] = ok ? S.v(rb + j0 + j) : 0.0;
-        }
-#pragma unroll
-        for (int j = 0; j < kChunk; ++j) xx[j] = cc[j] >= 0 ? __ldcg(xin + cc[j]) : 0.0;
-#pragma unroll
-        for (int j = 0; j < kChunk; ++j)
-          if (j < nj) s += vv[j] * xx[j];
+      for (int j = 0; j < kSpmvChunk; ++j) {
+        const bool ok = j0 + j < w;
+        cc[j] = ok ? __ldg(col + (j0 + j) * kWarp) : 0;
+        vv[j] = ok ? __ldg(val + (j0 + j) * kWarp) : 0.0;
       }
+#pragma unroll
+      for (int j = 0; j < kSpmvChunk; ++j) xx[j] = j0 + j < w ? __ldcg(xin + cc[j]) : 0.0;
+#pragma unroll
+      for (int j = 0; j < kSpmvChunk; ++j)
+        if (j0 + j < w) s += vv[j] * xx[j];
+    }
+    if (i < P.n) {
+      const double xi = __ldcg(xin + i);
+      s += __ldg(P.adiag + i) * xi;
       if (MODE == 0) {
         P.q[i] = s;
-        acc += __ldcg(xin + i) * s;
+        acc += xi * s;
       } else if (MODE == 1) {
         const double ri = __ldcg(P.bh + i) - s;
         P.r[i] = ri;
@@ -958,9 +1047,7 @@ spmv_kernel(Params P, int cap) {
         P.q[i] = s;
       }
     }
-    __syncwarp();
   }
-  if (!waited) pdl_wait();
   if (MODE == 2) return;
   const double tot = cta_sum(acc, red);
   if (threadIdx.x == 0) P.part_a[blockIdx.x] = tot;
@@ -1519,7 +1606,21 @@ cudaError_t launch_tile(const Params &P, const Plan &L, int c, int mode, bool up
 }
 
 template <typename PT>
+cudaError_t launch_wtile(const Params &P, const Plan &L, int c, int mode, bool update, int fin, const SlotArgs &sa) {
+  const int g = L.grid_c[c], t0 = L.tile0[c], t1 = L.tile1[c], th = L.Ww * kWarp, sm = L.smem_wt, cs = L.cap_ws;
+  if (mode == M_BWD) return launch(wtile_kernel<PT, M_BWD, false>, g, th, sm, L, P, t0, t1, cs, fin, sa);
+  if (update) {
+    if (mode == M_FUSED) return launch(wtile_kernel<PT, M_FUSED, true>, g, th, sm, L, P, t0, t1, cs, fin, sa);
+    return launch(wtile_kernel<PT, M_FWD, true>, g, th, sm, L, P, t0, t1, cs, fin, sa);
+  }
+  if (mode == M_FUSED) return launch(wtile_kernel<PT, M_FUSED, false>, g, th, sm, L, P, t0, t1, cs, fin, sa);
+  return launch(wtile_kernel<PT, M_FWD, false>, g, th, sm, L, P, t0, t1, cs, fin, sa);
+}
+
+template <typename PT>
 cudaError_t launch_fwd(const Params &P, const Plan &L, int c, bool update, bool fused, int fin) {
+  if (L.tile1[c] > L.tile0[c] && L.wtile[c])
+    return launch_wtile<PT>(P, L, c, fused ? M_FUSED : M_FWD, update, fin, SlotArgs{L.off_rr[c], L.off_rz[c], 0, 0});
   if (L.tile1[c] > L.tile0[c])
     return launch_tile<PT>(P, L, c, fused ? M_FUSED : M_FWD, update, fin, SlotArgs{L.off_rr[c], L.off_rz[c], 0, 0});
   const int threads = L.W * kWarp;
@@ -1542,6 +1643,7 @@ cudaError_t launch_bwd(const Params &P, const Plan &L, int c, int fin) {
   // the final backward launch sums the <r,r> slots only in an iteration (the
   // solve start has no x / r update)
   const SlotArgs sa{0, L.off_rz[c], fin == FIN_ITER ? L.last_rr : 0, L.last_rz};
+  if (L.tile1[c] > L.tile0[c] && L.wtile[c]) return launch_wtile<PT>(P, L, c, M_BWD, false, fin, sa);
   if (L.tile1[c] > L.tile0[c]) return launch_tile<PT>(P, L, c, M_BWD, false, fin, sa);
   return launch(color_kernel<PT, M_BWD, false>, L.grid_c[c], L.W * kWarp, pl.total, L, P, L.task0[c],
                 L.task1[c], pl, fin, sa);
@@ -1572,7 +1674,7 @@ cudaError_t sweep(const Params &P, const Plan &L, bool update, int fin_last, Pha
 
 template <int MODE>
 cudaError_t launch_spmv(const Params &P, const Plan &L) {
-  return launch(spmv_kernel<MODE>, L.grid_a, L.Wa * kWarp, L.smem_a, L, P, P.cap_a);
+  return launch(spmv_kernel<MODE>, L.grid_a, L.Wa * kWarp, 0, L, P);
 }
 
 template <typename K>
@@ -1597,6 +1699,11 @@ cudaError_t configure_pt() {
   if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_FUSED, false>);
   if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_FWD, false>);
   if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_BWD, false>);
+  if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_FUSED, true>);
+  if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_FWD, true>);
+  if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_FUSED, false>);
+  if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_FWD, false>);
+  if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_BWD, false>);
   return e;
 }
 
@@ -1610,6 +1717,18 @@ int tile_resident_ctas(bool fp32, int threads, int smem) {
   const cudaError_t e =
       fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tile_kernel<float, M_FUSED, true>, threads, size_t(smem))
            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tile_kernel<double, M_FUSED, true>, threads, size_t(smem));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
+int wtile_resident_ctas(bool fp32, int threads, int smem) {
+  int nb = 0;
+  const cudaError_t e =
+      fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wtile_kernel<float, M_FWD, true>, threads, size_t(smem))
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wtile_kernel<double, M_FWD, true>, threads, size_t(smem));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -1664,9 +1783,6 @@ cudaError_t launch_solve_persistent(const Params &P, const Plan &L, bool fp32) {
 cudaError_t configure_kernels() {
   cudaError_t e = configure_pt<double>();
   if (e == cudaSuccess) e = configure_pt<float>();
-  if (e == cudaSuccess) e = allow_smem(spmv_kernel<0>);
-  if (e == cudaSuccess) e = allow_smem(spmv_kernel<1>);
-  if (e == cudaSuccess) e = allow_smem(spmv_kernel<2>);
   return e;
 }
 

@@ -33,10 +33,11 @@ class iccg_opts(ctypes.Structure):
     _fields_ = [("precond_fp32", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("rows_per_thread", ctypes.c_int32), ("no_graph", ctypes.c_int32),
                 ("no_pdl", ctypes.c_int32), ("solver", ctypes.c_int32), ("lane_block_max", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("tile_mapping", ctypes.c_int32)]
 
 
 SOLVERS = {"auto": 0, "persistent": 1, "phased": 2}
+TILE_MAPPINGS = {"auto": 0, "cta": 1, "warp": 2}
 
 
 class iccg_batch_opts(ctypes.Structure):
@@ -133,12 +134,13 @@ def _as(a, dt):
 
 
 def make_opts(precond_fp32=0, warps_per_cta=0, rows_per_thread=0, no_graph=0, no_pdl=0, solver="auto",
-              lane_block_max=0):
+              lane_block_max=0, tile_mapping="auto"):
     o = iccg_opts()
     o.precond_fp32, o.warps_per_cta, o.rows_per_thread, o.no_graph, o.no_pdl = (
         int(precond_fp32), int(warps_per_cta), int(rows_per_thread), int(no_graph), int(no_pdl))
     o.solver = SOLVERS[solver] if isinstance(solver, str) else int(solver)
     o.lane_block_max = int(lane_block_max)
+    o.tile_mapping = TILE_MAPPINGS[tile_mapping] if isinstance(tile_mapping, str) else int(tile_mapping)
     return o
 
 
@@ -211,7 +213,7 @@ def iccg_profile_solve(ctx, b, x, tol=1e-8, maxit=10000):
 
 
 INFO_KEYS = ("n", "nnz", "n_b", "n_c", "groups", "global_groups", "nL", "max_levels", "max_group_rows", "tiles",
-             "tile_colors")
+             "tile_colors", "warp_tile_colors")
 
 
 def iccg_info(ctx):
@@ -316,12 +318,12 @@ class Solver:
     """Owns one iccg context: setup + factor at construction."""
 
     def __init__(self, a, bl, precond_fp32=False, warps_per_cta=0, rows_per_thread=0, no_graph=False,
-                 no_pdl=False, stream=None, factor=True, solver="auto", lane_block_max=0):
+                 no_pdl=False, stream=None, factor=True, solver="auto", lane_block_max=0, tile_mapping="auto"):
         self.n = a.n
         self.ctx = iccg_setup(a.n, a.nnz, a.rowptr, a.colind, a.val, bl["perm"], bl["block_ptr"],
                               bl["color_ptr"], bl["n_b"], bl["n_c"],
                               make_opts(precond_fp32, warps_per_cta, rows_per_thread, no_graph, no_pdl, solver,
-                                        lane_block_max),
+                                        lane_block_max, tile_mapping),
                               stream)
         if factor:
             iccg_factor(self.ctx)

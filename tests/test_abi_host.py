@@ -74,9 +74,9 @@ def test_setup_rejects_bad_inputs_before_gpu():
     # non-finite value
     a5 = gen.CSR(a.n, a.rowptr.copy(), a.colind.copy(), a.val.copy()); a5.val[7] = np.nan
     assert _setup_err(a5, perm, bp, cp, nb, nc).status == 1
-    # invalid options: solver id, warps per CTA, rows per thread, reserved words
+    # invalid options: solver id, warps per CTA, rows per thread, lane blocks, tile mapping
     for kw in (dict(solver=3), dict(solver=-1), dict(warps_per_cta=17), dict(rows_per_thread=3),
-               dict(lane_block_max=33), dict(lane_block_max=-2)):
+               dict(lane_block_max=33), dict(lane_block_max=-2), dict(tile_mapping=3), dict(tile_mapping=-1)):
         with pytest.raises(iccg.IccgError) as ei:
             iccg.iccg_setup(a.n, a.nnz, a.rowptr, a.colind, a.val, perm, bp, cp, nb, nc, iccg.make_opts(**kw))
         assert ei.value.status == 1, kw
@@ -86,11 +86,6 @@ def test_setup_rejects_bad_inputs_before_gpu():
     h = ctypes.c_void_p()
     for nsys, nrhs in ((0, 4), (1, 0), (1, 33)):
         assert L.iccg_batch_create(ctypes.byref(h), None, nsys, nrhs, None) == 1
-    o = iccg.make_opts()
-    o.reserved[0] = 1
-    with pytest.raises(iccg.IccgError) as ei:
-        iccg.iccg_setup(a.n, a.nnz, a.rowptr, a.colind, a.val, perm, bp, cp, nb, nc, o)
-    assert ei.value.status == 1
 
 
 CASES = {

@@ -41,6 +41,9 @@ CASES = {
     "grid3d_abmc8": (lambda: (gen.poisson3d_7pt(20), gen.rhs_uniform(8000, 3), None), "abmc", {"block_size": 8}),
     "grid3d_abmc32": (lambda: (gen.poisson3d_7pt(20), gen.rhs_uniform(8000, 3), None), "abmc", {"block_size": 32}),
     "grid3d_abmc100": (lambda: (gen.poisson3d_7pt(20), gen.rhs_uniform(8000, 3), None), "abmc", {"block_size": 100}),
+    "grid3d_abmc2": (lambda: (gen.poisson3d_7pt(22), gen.rhs_uniform(10648, 13), None), "abmc", {"block_size": 2}),
+    "grid3d_cpm_singletons": (lambda: (gen.poisson3d_7pt(21), gen.rhs_uniform(9261, 14), None), "leiden_cpm",
+                              {"gamma": 1.0}),
     "grid2d_leiden_md": (lambda: (gen.poisson2d_5pt(45), gen.rhs_uniform(2025, 4), None), "leiden_md", {"gamma": 1.0}),
     "grid3d_leiden_cpm": (lambda: (gen.poisson3d_7pt(15), gen.rhs_uniform(3375, 5), None), "leiden_cpm", {"gamma": 0.1}),
     "rspd_777": (lambda: (gen.random_spd_small(777, 0.01, 7), gen.rhs_uniform(777, 6), None), "abmc", {"block_size": 13}),
@@ -70,9 +73,11 @@ SHAPES = [dict(), dict(lane_block_max=8), dict(lane_block_max=-1),
           dict(lane_block_max=-1, rows_per_thread=2, warps_per_cta=4), dict(lane_block_max=-1, warps_per_cta=1),
           dict(lane_block_max=-1, warps_per_cta=16), dict(no_graph=1), dict(no_pdl=1),
           dict(solver="persistent"), dict(solver="persistent", rows_per_thread=4, warps_per_cta=4),
-          dict(solver="persistent", warps_per_cta=16)]
-LAYOUTS = {"lanes": dict(), "groups": dict(lane_block_max=-1)}
-SOLVERS = {"lanes": dict(), "groups": dict(lane_block_max=-1), "persistent": dict(solver="persistent")}
+          dict(solver="persistent", warps_per_cta=16), dict(tile_mapping="warp"), dict(tile_mapping="cta"),
+          dict(tile_mapping="warp", warps_per_cta=3, lane_block_max=16)]
+LAYOUTS = {"lanes": dict(), "groups": dict(lane_block_max=-1), "warp_tiles": dict(tile_mapping="warp")}
+SOLVERS = {"lanes": dict(), "groups": dict(lane_block_max=-1), "persistent": dict(solver="persistent"),
+           "warp_tiles": dict(tile_mapping="warp")}
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -262,6 +267,15 @@ def test_layout_choice_follows_block_sizes():
     assert info["tile_colors"] == bl["n_c"]
     assert info["tiles"] == sum((int(cp[c + 1] - cp[c]) + 31) // 32 for c in range(bl["n_c"]))
     assert info["groups"] == 0
+    assert info["warp_tile_colors"] == 0
+    S.close()
+    S = iccg.Solver(a, bl, tile_mapping="warp")
+    assert iccg.iccg_info(S.ctx)["warp_tile_colors"] == bl["n_c"]
+    S.close()
+    a2, b2, bl2, ref2 = _case("grid3d_cpm_singletons")
+    S = iccg.Solver(a2, bl2)
+    info = iccg.iccg_info(S.ctx)
+    assert info["tile_colors"] == bl2["n_c"] and info["warp_tile_colors"] == 0   # automatic: CTA per tile
     S.close()
     S = iccg.Solver(a, bl, lane_block_max=-1)
     assert iccg.iccg_info(S.ctx)["tile_colors"] == 0
