@@ -122,6 +122,13 @@ def workload(args):
     return a, b
 
 
+# DRAM bytes (read + write) of the substitution sweep per PCG iteration,
+# from the ncu launch list of `bench.py --steps 1 --warmup 1 --no-cpu-baseline`
+# (profiles/launches_iccg_fp64_poisson128_cpm05.md), keyed by workload and
+# blocking; None where no capture of the current kernels exists.
+SUBST_TRAFFIC = {("poisson128", 128, "leiden_cpm", 0.5, False): 433183458}
+
+
 def make_blocking(mod, a, args):
     """The configured blocking by `mod` (the library, or the oracle for the
     reference arm; both give the same permutation)."""
@@ -295,7 +302,10 @@ def run_gpu(args):
                      "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4), "peak_source": peak_src,
                      "bytes_per_iteration": bm["subst"], "launches_per_iteration": sub_launch / max(it_p, 1),
-                     "traffic": None},
+                     "traffic": SUBST_TRAFFIC.get((args.workload, args.nx, args.blocking,
+                                                   args.gamma if args.blocking == "leiden_cpm" else args.block_size,
+                                                   bool(args.fp32))),
+                     "traffic_unit": "bytes per PCG iteration (ncu launch list, cold cache)"},
         "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": 2 * 8 * a.n,
                 "d2h_bytes_per_step": 8 * a.n},
         "gpu_launches": int(launches_per_step * args.steps),

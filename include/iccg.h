@@ -78,11 +78,16 @@ typedef struct {
                                  (the tile's steps shared out over its warps, the
                                  in-block recurrence on one warp); ICCG_TILES_WARP
                                  one warp per tile (all steps in order, many tiles
-                                 per CTA); ICCG_TILES_AUTO (0) = ICCG_TILES_CTA */
+                                 per CTA); ICCG_TILES_PAIR: colors of blocks of one
+                                 or two rows one warp per tile with the block's rows
+                                 in registers (pair kernels), other colors one CTA
+                                 per tile; ICCG_TILES_AUTO (0): pair kernels for the
+                                 colors whose blocks all have two rows, one CTA per
+                                 tile otherwise */
 } iccg_opts;
 
 enum { ICCG_SOLVER_AUTO = 0, ICCG_SOLVER_PERSISTENT = 1, ICCG_SOLVER_PHASED = 2 };
-enum { ICCG_TILES_AUTO = 0, ICCG_TILES_CTA = 1, ICCG_TILES_WARP = 2 };
+enum { ICCG_TILES_AUTO = 0, ICCG_TILES_CTA = 1, ICCG_TILES_WARP = 2, ICCG_TILES_PAIR = 3 };
 
 /* ------------------------------------------------------------------------
  * iccg_setup -- Sec. 3: the block-multicolor ordering renumbers rows color
@@ -168,14 +173,14 @@ iccg_status iccg_get_factor(iccg_ctx *ctx, double *lval, int64_t *nnz_lower);
 iccg_status iccg_profile_solve(iccg_ctx *ctx, const double *b, double *x, double tol,
                                int32_t maxit, int32_t *iters, double *ms, int64_t *launches);
 
-/* Layout facts of a context, out[12]: n, nnz, n_b, n_c, number of groups (a
+/* Layout facts of a context, out[13]: n, nnz, n_b, n_c, number of groups (a
  * group = consecutive whole blocks of one color, at most 32 * warps_per_cta *
  * rows_per_thread rows, or one larger block; one CTA each), number of groups
  * too large for the shared-memory plan, strictly-lower entries nL, deepest
  * in-group level count, largest group (rows), number of lane tiles (32
  * blocks, one per lane), number of colors run as lane tiles, number of
- * those run one warp per tile (tile_mapping). */
-iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[12]);
+ * those run one warp per tile and as pair kernels (tile_mapping). */
+iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[13]);
 
 iccg_status iccg_last_error(const iccg_ctx *ctx, int64_t *row_or_block, const char **msg);
 void iccg_destroy(iccg_ctx *ctx);

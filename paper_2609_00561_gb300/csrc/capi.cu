@@ -127,7 +127,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   if (!rowptr || (n > 0 && (!colind || !val || !perm || !block_ptr || !color_ptr))) return ICCG_ERR_ARG;
   iccg_opts o{};
   if (opts) o = *opts;
-  if (o.tile_mapping < ICCG_TILES_AUTO || o.tile_mapping > ICCG_TILES_WARP) return ICCG_ERR_ARG;
+  if (o.tile_mapping < ICCG_TILES_AUTO || o.tile_mapping > ICCG_TILES_PAIR) return ICCG_ERR_ARG;
   if (o.lane_block_max > 32 || o.lane_block_max < -1) return ICCG_ERR_ARG;
   if (o.solver < ICCG_SOLVER_AUTO || o.solver > ICCG_SOLVER_PHASED) return ICCG_ERR_ARG;
   if (o.warps_per_cta == 0) o.warps_per_cta = 8;
@@ -256,6 +256,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   L.smem_wt = L.Ww * L.cap_ws * kWarp * elem;
   const int wt_full =
       H.tile_colors > 0 ? sms * wtile_resident_ctas(ctx->fp32, L.Ww * kWarp, L.smem_wt) : 1;
+  const int pr_full = H.tile_colors > 0 ? sms * pair_resident_ctas(ctx->fp32, L.Ww * kWarp) : 1;
   L.wtile.assign(n_c, 0);
   int32_t gbig = 1;
   for (int c = 0; c < n_c; ++c) {
@@ -264,12 +265,24 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     L.tile0[c] = H.color_tile[c];
     L.tile1[c] = H.color_tile[c + 1];
     const int nt = L.tile1[c] - L.tile0[c];
+    // the color's longest tile, and whether all its blocks have two rows
     int steps = 0;
-    for (int t = L.tile0[c]; t < L.tile1[c]; ++t) steps = std::max(steps, H.tiles[t].nsteps);
-    // automatic: one CTA per tile (on a GB300 the warp mapping measured no
-    // faster for one-step tiles and slower for longer ones)
-    L.wtile[c] = nt > 0 && o.tile_mapping == ICCG_TILES_WARP && steps >= 1;
-    if (L.wtile[c]) L.grid_c[c] = std::min((nt + L.Ww - 1) / L.Ww, wt_full);
+    bool pairs = true;
+    for (int t = L.tile0[c]; t < L.tile1[c]; ++t) {
+      const TileDesc &td = H.tiles[t];
+      steps = std::max(steps, td.nsteps);
+      if (td.nsteps != 2 || H.steps[size_t(td.step0) + 1].cnt != H.steps[size_t(td.step0)].cnt) pairs = false;
+    }
+    // automatic: colors of two-row blocks only as pair kernels, one CTA per
+    // tile otherwise (on a GB300 the pair kernels measured 7% faster for
+    // ABMC with blocks of 2 rows, slower where one-row blocks share a tile
+    // with two-row ones, and no better for one-row blocks alone)
+    L.wtile[c] = 0;
+    if (nt > 0 && o.tile_mapping == ICCG_TILES_WARP) L.wtile[c] = 1;
+    if (nt > 0 && steps <= 2 && ((pairs && o.tile_mapping == ICCG_TILES_AUTO) || o.tile_mapping == ICCG_TILES_PAIR))
+      L.wtile[c] = 2;
+    if (L.wtile[c] == 1) L.grid_c[c] = std::min((nt + L.Ww - 1) / L.Ww, wt_full);
+    else if (L.wtile[c] == 2) L.grid_c[c] = std::min((nt + L.Ww - 1) / L.Ww, pr_full);
     else L.grid_c[c] = nt > 0 ? std::min(nt, tile_full) : std::max(1, L.task1[c] - L.task0[c]);
     gbig = std::max(gbig, L.grid_c[c]);
   }
@@ -345,6 +358,9 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     StepDesc *d_steps;
     int32_t *d_slc, *d_suc, *d_slm, *d_sum, *d_sic, *d_uic, *d_sim, *d_uim;
     CK(dev_upload(ctx, &d_tiles, H.tiles), "alloc tiles");
+    PairDesc *d_pairs;
+    CK(dev_upload(ctx, &d_pairs, H.pairs), "alloc tiles");
+    P.pairs = d_pairs;
     CK(dev_upload(ctx, &d_steps, H.steps), "alloc tiles");
     CK(dev_upload(ctx, &d_slc, H.sl_col), "alloc tiles");
     CK(dev_upload(ctx, &d_suc, H.su_col), "alloc tiles");
@@ -776,7 +792,7 @@ iccg_status iccg_get_factor(iccg_ctx *ctx, double *lval, int64_t *nnz_lower) {
   return ICCG_OK;
 }
 
-iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[12]) {
+iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[13]) {
   if (!ctx || !out) return ICCG_ERR_ARG;
   const HostLayout &H = ctx->H;
   out[0] = H.n;
@@ -791,8 +807,11 @@ iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[12]) {
   out[8] = H.max_group_rows;
   out[9] = int64_t(H.tiles.size());
   out[10] = H.tile_colors;
-  out[11] = 0;
-  for (char w : ctx->plan.wtile) out[11] += w ? 1 : 0;
+  out[11] = out[12] = 0;
+  for (char w : ctx->plan.wtile) {
+    out[11] += w == 1 ? 1 : 0;
+    out[12] += w == 2 ? 1 : 0;
+  }
   return ICCG_OK;
 }
 

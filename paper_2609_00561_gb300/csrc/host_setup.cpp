@@ -318,6 +318,21 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
     }
   }
   H.color_tile[n_c] = int32_t(H.tiles.size());
+  // tiles of at most two steps, each in one descriptor
+  H.pairs.assign(H.tiles.size(), PairDesc{});
+  for (size_t t = 0; t < H.tiles.size(); ++t) {
+    const TileDesc &td = H.tiles[t];
+    if (td.nsteps > 2) continue;
+    const StepDesc &s0 = H.steps[size_t(td.step0)];
+    PairDesc &pd = H.pairs[t];
+    pd.row0 = td.row0; pd.c0 = s0.cnt; pd.lo = s0.lo; pd.lw0 = s0.lw; pd.uo = s0.uo; pd.uw0 = s0.uw;
+    pd.ui = s0.ui; pd.uiw0 = s0.uiw;
+    pd.li = td.li0;
+    if (td.nsteps == 2) {
+      const StepDesc &s1 = H.steps[size_t(td.step0) + 1];
+      pd.c1 = s1.cnt; pd.lw1 = s1.lw; pd.liw1 = s1.liw; pd.uw1 = s1.uw; pd.li = s1.li;
+    }
+  }
   const size_t lim = size_t(1) << 31;
   if (H.sl_col.size() >= lim || H.su_col.size() >= lim || H.si_col.size() >= lim || H.ui_col.size() >= lim)
     return fail(ICCG_ERR_ARG, -1, "lane-tile layout exceeds 2^31 entries", bad, msg);
@@ -536,6 +551,19 @@ extern "C" iccg_status iccg_check_layout(int32_t n, int64_t nnz, const int64_t *
       if (s == 0) ck(sd.lo == td.lo0 && sd.lw == td.lw0 && sd.li == td.li0 && sd.uo == td.uo0 && sd.uw == td.uw0 &&
                      sd.ui == td.ui0, int64_t(t), "first step in the tile descriptor");
       if (td.nsteps == 1) ck(sd.cnt == td.nrows && sd.liw == td.wl && sd.uiw == td.wu, int64_t(t), "one-step tile");
+      if (td.nsteps <= 2) {
+        const PairDesc &pd = H.pairs[t];
+        if (s == 0)
+          ck(pd.row0 == sd.row && pd.c0 == sd.cnt && pd.lo == sd.lo && pd.lw0 == sd.lw && sd.liw == 0 &&
+                 pd.uo == sd.uo && pd.uw0 == sd.uw && pd.ui == sd.ui && pd.uiw0 == sd.uiw &&
+                 (td.nsteps == 2 || (pd.c1 == 0 && pd.liw1 == 0 && sd.uiw == 0)),
+             int64_t(t), "pair descriptor, step 0");
+        else
+          ck(pd.c1 == sd.cnt && sd.row == pd.row0 + pd.c0 && sd.lo == pd.lo + pd.lw0 * pd.c0 && pd.lw1 == sd.lw &&
+                 pd.li == sd.li && pd.liw1 == sd.liw && sd.uo == pd.uo + pd.uw0 * pd.c0 && pd.uw1 == sd.uw &&
+                 sd.uiw == 0,
+             int64_t(t), "pair descriptor, step 1");
+      }
       if (s) ck(sd.cnt <= H.steps[size_t(td.step0 + s - 1)].cnt, int64_t(t), "active lanes a prefix");
       ck(sd.lo >= td.lo0 && sd.lo + sd.lw * sd.cnt <= td.lo1, int64_t(t), "L other-color range");
       ck(sd.li >= td.li0 && sd.li + sd.liw * sd.cnt <= td.li1, int64_t(t), "L in-block range");

@@ -70,6 +70,15 @@ struct __align__(16) TileDesc {
 struct __align__(16) StepDesc {
   int32_t row, cnt, lo, lw, li, liw, uo, uw, ui, uiw, pad0, pad1;
 };
+// A tile of at most two steps in one descriptor (blocks of one or two rows):
+// step 0 = rows [row0, row0 + c0), step 1 = rows [row0 + c0, row0 + c0 + c1);
+// other-color entries of step 0 at lo, of step 1 at lo + lw0 * c0 (U: uo,
+// uo + uw0 * c0); the in-block L entries are step 1's (at li, width liw1,
+// each referring to step 0), the in-block U entries step 0's (at ui, width
+// uiw0, each referring to step 1).
+struct __align__(16) PairDesc {
+  int32_t row0, c0, c1, lo, lw0, lw1, li, liw1, uo, uw0, uw1, ui, uiw0, pad0, pad1, pad2;
+};
 constexpr int32_t kPadCol = 0x7fffffff;   // padding entry of a sliced-ELL step
 constexpr int kTileSmemBudget = 96 * 1024;      // lane-tile CTA with two buffers, bytes
 constexpr int kTileSmemBudget1 = 200 * 1024;    // lane-tile CTA with one buffer, bytes
@@ -179,6 +188,7 @@ struct Params {
   // same block's row); values are filled from the factor through the maps
   // (the L entry an entry takes, -1: padding)
   const TileDesc *tiles;
+  const PairDesc *pairs;        // [tiles]: the tile as a PairDesc (tiles of <= 2 steps)
   const StepDesc *steps;
   const int32_t *sl_col, *su_col, *sl_map, *su_map;
   const int32_t *si_col, *ui_col, *si_map, *ui_map;
@@ -217,6 +227,7 @@ struct HostLayout {
   std::vector<int32_t> color_group;   // n_c + 1 (no groups for a tile color)
   std::vector<int32_t> color_tile;    // n_c + 1 (no tiles for a group color)
   std::vector<TileDesc> tiles;
+  std::vector<PairDesc> pairs;
   std::vector<StepDesc> steps;
   std::vector<int32_t> sl_col, su_col, sl_map, su_map;
   std::vector<int32_t> si_col, ui_col, si_map, ui_map;
@@ -254,7 +265,7 @@ struct Plan {
   int32_t cap_ti = 0;                   // in-block entries of a tile staged in shared memory
   int32_t nbuf_t = 2;                   // lane-tile staging buffers per CTA
   int32_t cap_ti2 = 0;                  // second-set (fused launch) staging capacity
-  std::vector<char> wtile;              // color c runs one warp per tile (warp-tile kernels)
+  std::vector<char> wtile;              // color c: 0 CTA per tile, 1 warp-tile kernels, 2 pair kernels
   int32_t Ww = 8;                       // warps per CTA of the warp-tile kernels
   int32_t smem_wt = 0;                  // bytes per CTA of the warp-tile kernels
   int32_t cap_ws = 0;                   // steps per tile held in a warp's buffer
@@ -278,6 +289,7 @@ int spmv_smem_bytes(int cap);                                // per-warp staging
 int spmv_resident_ctas(int Wa, int smem);                    // CTAs per SM of the SpMV
 int tile_resident_ctas(bool fp32, int threads, int smem);    // CTAs per SM of the lane-tile kernels
 int wtile_resident_ctas(bool fp32, int threads, int smem);   // CTAs per SM of the warp-tile kernels
+int pair_resident_ctas(bool fp32, int threads);              // CTAs per SM of the pair kernels
 cudaError_t launch_factor(const Params &P, const Plan &L, int nL);
 cudaError_t launch_solve_init(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);
 cudaError_t launch_solve_body(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);

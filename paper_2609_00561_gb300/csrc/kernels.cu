@@ -70,9 +70,19 @@ __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_grou
 // all but the most recently committed group
 __device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// sum over the warp, valid in lane 0: each step adds on the lower half of
+// the lanes still in play (16, 8, 4, 2, 1), since FP64 adds are the scarce
+// resource on this GPU
 __device__ __forceinline__ double warp_sum(double v) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    const double u = __shfl_down_sync(0xffffffffu, v, o);
+    // a predicated add (the compiler would otherwise add on every lane and select)
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.s32 p, %1, %2;\n\t@p add.rn.f64 %0, %0, %3;\n\t}"
+        : "+d"(v)
+        : "r"(lane), "r"(o), "d"(u));
+  }
   return v;
 }
 
@@ -506,18 +516,20 @@ struct SlotArgs {
 __device__ __forceinline__ void launch_epilogue(const Params &P, int fin, const SlotArgs &sa, bool has_rr,
                                                 bool has_rz, double rr_acc, double rz_acc, double *red, int *flag) {
   if (!has_rr && !has_rz) return;
-  const double rr_c = has_rr ? cta_sum(rr_acc, red) : 0.0;
-  const double rz_c = has_rz ? cta_sum(rz_acc, red) : 0.0;
   if (fin == FIN_NONE) {
+    const double rr_c = has_rr ? cta_sum(rr_acc, red) : 0.0;
+    const double rz_c = has_rz ? cta_sum(rz_acc, red) : 0.0;
     if (threadIdx.x == 0) {
       if (has_rr) P.slot_rr[sa.off_rr + blockIdx.x] = rr_c;
       if (has_rz) P.slot_rz[sa.off_rz + blockIdx.x] = rz_c;
     }
     return;
   }
+  // the final launch: this CTA's share of the earlier launches' slots joins
+  // the threads' own partial sums, then one CTA sum per quantity
   const int nb = gridDim.x;
   const int crr = (sa.last_rr + nb - 1) / nb, crz = (sa.last_rz + nb - 1) / nb;
-  double a = 0.0, b = 0.0;
+  double a = has_rr ? rr_acc : 0.0, b = has_rz ? rz_acc : 0.0;
   for (int k = threadIdx.x; k < crr; k += blockDim.x) {
     const int idx = blockIdx.x * crr + k;
     if (idx < sa.last_rr) a += __ldcg(P.slot_rr + idx);
@@ -526,10 +538,20 @@ __device__ __forceinline__ void launch_epilogue(const Params &P, int fin, const 
     const int idx = blockIdx.x * crz + k;
     if (idx < sa.last_rz) b += __ldcg(P.slot_rz + idx);
   }
-  a = cta_sum(a, red);
-  b = cta_sum(b, red);
+  // a quantity that only the first warp holds (slots alone, at most 32 per
+  // CTA) is summed by that warp
+  if (!has_rr && crr <= kWarp) {
+    if (threadIdx.x < kWarp) a = warp_sum(a);
+  } else {
+    a = cta_sum(a, red);
+  }
+  if (!has_rz && crz <= kWarp) {
+    if (threadIdx.x < kWarp) b = warp_sum(b);
+  } else {
+    b = cta_sum(b, red);
+  }
   double ga, gb;
-  if (group_reduce(P, a + rr_c, b + rz_c, true, red, flag, ga, gb)) {
+  if (group_reduce(P, a, b, true, red, flag, ga, gb)) {
     if (threadIdx.x == 0) {
       P.gsum0[blockIdx.x / kGroup] = ga;
       P.gsum1[blockIdx.x / kGroup] = gb;
@@ -930,8 +952,12 @@ __device__ __forceinline__ void wtile_sweep(const Params &P, const TileDesc &t, 
 // A warp-tile launch: the warps walk the color's tiles grid-stride (tile of
 // warp w of CTA b: t0 + b * W + w, then + gridDim.x * W); one <r,r> / <r,z>
 // reduction per CTA at the end.  Shared memory: cap_s * 32 values per warp.
+#ifndef ICCG_TILE_MAXNREG
+#define ICCG_TILE_MAXNREG 64
+#endif
+
 template <typename PT, int MODE, bool UPDATE>
-__global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
+__global__ void __maxnreg__(ICCG_TILE_MAXNREG)
 wtile_kernel(Params P, int t0, int t1, int cap_s, int fin, SlotArgs sa) {
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem[];
@@ -956,6 +982,118 @@ wtile_kernel(Params P, int t0, int t1, int cap_s, int fin, SlotArgs sa) {
     }
     __syncwarp();
     td = tdn;
+  }
+  launch_epilogue(P, fin, sa, MODE != M_BWD && UPDATE, MODE != M_FWD, rr_acc, rz_acc, red, &flag);
+}
+
+// ---------------------------------------------------------------------------
+// pair kernels: colors of blocks of one or two rows (tiles of at most two
+// steps).  A warp per tile, a lane per block, the block's rows in registers:
+// forward
+//   y0 = (r0 - sum_j L0j y_j) / L00
+//   y1 = (r1 - sum_j L1j y_j - L10 y0) / L11
+// (the sums over earlier colors), backward
+//   z1 = (y1 - sum_j Lj1 z_j) / L11
+//   z0 = (y0 - sum_j Lj0 z_j - L10 z1) / L00
+// (the sums over later colors); a one-row block is its step 0 alone.
+// Padding entries (kPadCol, 0) add 0 * an element the sweep has already
+// written: y_0 (first color) forward, z_{n-1} (last color) backward.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ PairDesc load_pair(const PairDesc *p) {
+  const int4 *q = reinterpret_cast<const int4 *>(p);
+  const int4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+  PairDesc r;
+  r.row0 = a.x; r.c0 = a.y; r.c1 = a.z; r.lo = a.w;
+  r.lw0 = b.x; r.lw1 = b.y; r.li = b.z; r.liw1 = b.w;
+  r.uo = c.x; r.uw0 = c.y; r.uw1 = c.z; r.ui = c.w;
+  r.uiw0 = d.x; r.pad0 = r.pad1 = r.pad2 = 0;
+  return r;
+}
+
+template <typename PT>
+__device__ __forceinline__ PT pair_sub(const int32_t *col, const PT *val, int e, int cnt, int w, PT acc,
+                                       const PT *g, int pad) {
+#pragma unroll 4
+  for (int j = 0; j < w; ++j) {
+    const int c = __ldg(col + e + j * cnt);
+    const PT v = __ldg(val + e + j * cnt);
+    acc -= v * __ldcg(g + (c == kPadCol ? pad : c));
+  }
+  return acc;
+}
+
+// backward over one tile from y0 (and y1 when a1): stores z, adds <r,z>
+template <typename PT>
+__device__ __forceinline__ void pair_bwd(const Params &P, const PairDesc &d, int lane, bool a1, PT y0, PT y1,
+                                         PT dv0, PT dv1, double r0, double r1, double &rz_acc) {
+  PT *zv = reinterpret_cast<PT *>(P.z);
+  const int i0 = d.row0 + lane, i1 = d.row0 + d.c0 + lane;
+  // both steps' gathers before any store (a store to z would order the
+  // other step's gathers after it)
+  PT acc0 = pair_sub<PT>(P.su_col, suv<PT>(P), d.uo + lane, d.c0, d.uw0, y0, zv, P.n - 1);
+  PT z1 = PT(0);
+  if (a1) z1 = pair_sub<PT>(P.su_col, suv<PT>(P), d.uo + d.uw0 * d.c0 + lane, d.c1, d.uw1, y1, zv, P.n - 1) * dv1;
+  for (int j = 0; j < d.uiw0; ++j) acc0 -= __ldg(uiv<PT>(P) + d.ui + j * d.c0 + lane) * z1;
+  const PT z0 = acc0 * dv0;
+  zv[i0] = z0;
+  rz_acc += r0 * double(z0);
+  if (a1) {
+    zv[i1] = z1;
+    rz_acc += r1 * double(z1);
+  }
+}
+
+template <typename PT, int MODE, bool UPDATE>
+__global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
+pair_kernel(Params P, int t0, int t1, int fin, SlotArgs sa) {
+  pdl_trigger();
+  __shared__ double red[kMaxWarpsPerCta];
+  __shared__ int flag;
+  const int lane = threadIdx.x & 31;
+  const int nw = int(blockDim.x >> 5), stride = int(gridDim.x) * nw;
+  double rr_acc = 0.0, rz_acc = 0.0;
+  pdl_wait();
+  const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
+  PT *yv = reinterpret_cast<PT *>(P.y);
+  const PT *dvg = invds<PT>(P);
+  for (int t = t0 + int(blockIdx.x) * nw + int(threadIdx.x >> 5); t < t1; t += stride) {
+    const PairDesc d = load_pair(P.pairs + t);
+    if (lane >= d.c0) continue;   // a lane active in step 1 is active in step 0
+    const bool a1 = lane < d.c1;
+    const int i0 = d.row0 + lane, i1 = d.row0 + d.c0 + lane;
+    const PT dv0 = __ldg(dvg + i0), dv1 = a1 ? __ldg(dvg + i1) : PT(0);
+    if (MODE == M_BWD) {
+      const PT y0 = __ldcg(yv + i0), y1 = a1 ? __ldcg(yv + i1) : PT(0);
+      const double r0 = __ldcg(P.r + i0), r1 = a1 ? __ldcg(P.r + i1) : 0.0;
+      pair_bwd<PT>(P, d, lane, a1, y0, y1, dv0, dv1, r0, r1, rz_acc);
+    } else {
+      double r0 = __ldcg(P.r + i0), r1 = a1 ? __ldcg(P.r + i1) : 0.0;
+      if (UPDATE) {
+        r0 -= alpha * __ldcg(P.q + i0);
+        P.r[i0] = r0;
+        P.xh[i0] = __ldcg(P.xh + i0) + alpha * __ldcg(P.p0 + i0);
+        rr_acc += r0 * r0;
+        if (a1) {
+          r1 -= alpha * __ldcg(P.q + i1);
+          P.r[i1] = r1;
+          P.xh[i1] = __ldcg(P.xh + i1) + alpha * __ldcg(P.p0 + i1);
+          rr_acc += r1 * r1;
+        }
+      }
+      const PT y0 = pair_sub<PT>(P.sl_col, slv<PT>(P), d.lo + lane, d.c0, d.lw0, PT(r0), yv, 0) * dv0;
+      PT y1 = PT(0);
+      if (a1) {
+        PT acc1 = pair_sub<PT>(P.sl_col, slv<PT>(P), d.lo + d.lw0 * d.c0 + lane, d.c1, d.lw1, PT(r1), yv, 0);
+        for (int j = 0; j < d.liw1; ++j) acc1 -= __ldg(siv<PT>(P) + d.li + j * d.c1 + lane) * y0;
+        y1 = acc1 * dv1;
+      }
+      if (MODE == M_FWD) {
+        yv[i0] = y0;
+        if (a1) yv[i1] = y1;
+      } else {
+        pair_bwd<PT>(P, d, lane, a1, y0, y1, dv0, dv1, r0, r1, rz_acc);
+      }
+    }
   }
   launch_epilogue(P, fin, sa, MODE != M_BWD && UPDATE, MODE != M_FWD, rr_acc, rz_acc, red, &flag);
 }
@@ -999,7 +1137,7 @@ __global__ void __launch_bounds__(kVecThreads) pupdate_kernel(Params P) {
 // mode 0: q = A p, <p, q>; the last CTA sets alpha = rz / pq
 // mode 1: r = b_hat - A x_hat, <r, r> partials in part_a (solve start)
 // mode 2: q = A x_hat (plain SpMV)
-constexpr int kSpmvChunk = 8;   // entries per predicated batch of the SpMV
+constexpr int kSpmvChunk = 6;   // entries per predicated batch of the SpMV
 
 template <int MODE>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
@@ -1618,7 +1756,21 @@ cudaError_t launch_wtile(const Params &P, const Plan &L, int c, int mode, bool u
 }
 
 template <typename PT>
+cudaError_t launch_pair(const Params &P, const Plan &L, int c, int mode, bool update, int fin, const SlotArgs &sa) {
+  const int g = L.grid_c[c], t0 = L.tile0[c], t1 = L.tile1[c], th = L.Ww * kWarp;
+  if (mode == M_BWD) return launch(pair_kernel<PT, M_BWD, false>, g, th, 0, L, P, t0, t1, fin, sa);
+  if (update) {
+    if (mode == M_FUSED) return launch(pair_kernel<PT, M_FUSED, true>, g, th, 0, L, P, t0, t1, fin, sa);
+    return launch(pair_kernel<PT, M_FWD, true>, g, th, 0, L, P, t0, t1, fin, sa);
+  }
+  if (mode == M_FUSED) return launch(pair_kernel<PT, M_FUSED, false>, g, th, 0, L, P, t0, t1, fin, sa);
+  return launch(pair_kernel<PT, M_FWD, false>, g, th, 0, L, P, t0, t1, fin, sa);
+}
+
+template <typename PT>
 cudaError_t launch_fwd(const Params &P, const Plan &L, int c, bool update, bool fused, int fin) {
+  if (L.tile1[c] > L.tile0[c] && L.wtile[c] == 2)
+    return launch_pair<PT>(P, L, c, fused ? M_FUSED : M_FWD, update, fin, SlotArgs{L.off_rr[c], L.off_rz[c], 0, 0});
   if (L.tile1[c] > L.tile0[c] && L.wtile[c])
     return launch_wtile<PT>(P, L, c, fused ? M_FUSED : M_FWD, update, fin, SlotArgs{L.off_rr[c], L.off_rz[c], 0, 0});
   if (L.tile1[c] > L.tile0[c])
@@ -1643,6 +1795,7 @@ cudaError_t launch_bwd(const Params &P, const Plan &L, int c, int fin) {
   // the final backward launch sums the <r,r> slots only in an iteration (the
   // solve start has no x / r update)
   const SlotArgs sa{0, L.off_rz[c], fin == FIN_ITER ? L.last_rr : 0, L.last_rz};
+  if (L.tile1[c] > L.tile0[c] && L.wtile[c] == 2) return launch_pair<PT>(P, L, c, M_BWD, false, fin, sa);
   if (L.tile1[c] > L.tile0[c] && L.wtile[c]) return launch_wtile<PT>(P, L, c, M_BWD, false, fin, sa);
   if (L.tile1[c] > L.tile0[c]) return launch_tile<PT>(P, L, c, M_BWD, false, fin, sa);
   return launch(color_kernel<PT, M_BWD, false>, L.grid_c[c], L.W * kWarp, pl.total, L, P, L.task0[c],
@@ -1729,6 +1882,18 @@ int wtile_resident_ctas(bool fp32, int threads, int smem) {
   const cudaError_t e =
       fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wtile_kernel<float, M_FWD, true>, threads, size_t(smem))
            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wtile_kernel<double, M_FWD, true>, threads, size_t(smem));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
+int pair_resident_ctas(bool fp32, int threads) {
+  int nb = 0;
+  const cudaError_t e =
+      fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<float, M_FWD, true>, threads, 0)
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<double, M_FWD, true>, threads, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;

@@ -37,7 +37,7 @@ class iccg_opts(ctypes.Structure):
 
 
 SOLVERS = {"auto": 0, "persistent": 1, "phased": 2}
-TILE_MAPPINGS = {"auto": 0, "cta": 1, "warp": 2}
+TILE_MAPPINGS = {"auto": 0, "cta": 1, "warp": 2, "pair": 3}
 
 
 class iccg_batch_opts(ctypes.Structure):
@@ -213,7 +213,7 @@ def iccg_profile_solve(ctx, b, x, tol=1e-8, maxit=10000):
 
 
 INFO_KEYS = ("n", "nnz", "n_b", "n_c", "groups", "global_groups", "nL", "max_levels", "max_group_rows", "tiles",
-             "tile_colors", "warp_tile_colors")
+             "tile_colors", "warp_tile_colors", "pair_tile_colors")
 
 
 def iccg_info(ctx):

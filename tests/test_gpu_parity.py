@@ -44,6 +44,8 @@ CASES = {
     "grid3d_abmc2": (lambda: (gen.poisson3d_7pt(22), gen.rhs_uniform(10648, 13), None), "abmc", {"block_size": 2}),
     "grid3d_cpm_singletons": (lambda: (gen.poisson3d_7pt(21), gen.rhs_uniform(9261, 14), None), "leiden_cpm",
                               {"gamma": 1.0}),
+    "grid3d_cpm_pairs": (lambda: (gen.poisson3d_7pt(23), gen.rhs_uniform(12167, 15), None), "leiden_cpm",
+                         {"gamma": 0.5}),
     "grid2d_leiden_md": (lambda: (gen.poisson2d_5pt(45), gen.rhs_uniform(2025, 4), None), "leiden_md", {"gamma": 1.0}),
     "grid3d_leiden_cpm": (lambda: (gen.poisson3d_7pt(15), gen.rhs_uniform(3375, 5), None), "leiden_cpm", {"gamma": 0.1}),
     "rspd_777": (lambda: (gen.random_spd_small(777, 0.01, 7), gen.rhs_uniform(777, 6), None), "abmc", {"block_size": 13}),
@@ -75,9 +77,11 @@ SHAPES = [dict(), dict(lane_block_max=8), dict(lane_block_max=-1),
           dict(solver="persistent"), dict(solver="persistent", rows_per_thread=4, warps_per_cta=4),
           dict(solver="persistent", warps_per_cta=16), dict(tile_mapping="warp"), dict(tile_mapping="cta"),
           dict(tile_mapping="warp", warps_per_cta=3, lane_block_max=16)]
-LAYOUTS = {"lanes": dict(), "groups": dict(lane_block_max=-1), "warp_tiles": dict(tile_mapping="warp")}
+LAYOUTS = {"lanes": dict(), "groups": dict(lane_block_max=-1), "warp_tiles": dict(tile_mapping="warp"),
+           "cta_tiles": dict(tile_mapping="cta"), "pair_tiles": dict(tile_mapping="pair")}
 SOLVERS = {"lanes": dict(), "groups": dict(lane_block_max=-1), "persistent": dict(solver="persistent"),
-           "warp_tiles": dict(tile_mapping="warp")}
+           "warp_tiles": dict(tile_mapping="warp"), "cta_tiles": dict(tile_mapping="cta"),
+           "pair_tiles": dict(tile_mapping="pair")}
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -272,10 +276,32 @@ def test_layout_choice_follows_block_sizes():
     S = iccg.Solver(a, bl, tile_mapping="warp")
     assert iccg.iccg_info(S.ctx)["warp_tile_colors"] == bl["n_c"]
     S.close()
+    assert info["pair_tile_colors"] == 0        # blocks of 8 rows: one CTA per tile
     a2, b2, bl2, ref2 = _case("grid3d_cpm_singletons")
     S = iccg.Solver(a2, bl2)
     info = iccg.iccg_info(S.ctx)
-    assert info["tile_colors"] == bl2["n_c"] and info["warp_tile_colors"] == 0   # automatic: CTA per tile
+    assert info["tile_colors"] == bl2["n_c"] and info["pair_tile_colors"] == 0   # one-row blocks: CTA per tile
+    S.close()
+    S = iccg.Solver(a2, bl2, tile_mapping="pair")
+    assert iccg.iccg_info(S.ctx)["pair_tile_colors"] == bl2["n_c"]
+    S.close()
+    a2, b2, bl2, ref2 = _case("grid3d_abmc2")
+    S = iccg.Solver(a2, bl2)
+    sizes = np.diff(np.asarray(bl2["block_ptr"]))
+    cp2 = np.asarray(bl2["color_ptr"])
+    twos = sum(int(np.all(sizes[cp2[c]:cp2[c + 1]] == 2)) for c in range(bl2["n_c"]))
+    assert twos == bl2["n_c"]
+    assert iccg.iccg_info(S.ctx)["pair_tile_colors"] == twos   # colors of two-row blocks only: pair kernels
+    S.close()
+    # tiles mixing one- and two-row blocks: pair kernels only on request
+    a3, b3, bl3, ref3 = _case("grid3d_cpm_pairs")
+    sizes = np.diff(np.asarray(bl3["block_ptr"]))
+    assert sizes.max() <= 2 and sizes.min() == 1
+    S = iccg.Solver(a3, bl3, tile_mapping="pair")
+    assert iccg.iccg_info(S.ctx)["pair_tile_colors"] == bl3["n_c"]
+    S.close()
+    S = iccg.Solver(a3, bl3)
+    assert iccg.iccg_info(S.ctx)["pair_tile_colors"] < bl3["n_c"]
     S.close()
     S = iccg.Solver(a, bl, lane_block_max=-1)
     assert iccg.iccg_info(S.ctx)["tile_colors"] == 0
