@@ -244,11 +244,25 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     L.cap_ti2 = tile_launch_bytes(tp, true) <= (nbuf == 2 ? kTileSmemBudget : kTileSmemBudget1) ? cap_i : 0;
     tp.cap_i2 = L.cap_ti2;
     L.smem_tile2 = tile_launch_bytes(tp, true);
+    // the entries to other colors and the row vectors as well, where the
+    // launch then still fits its budget
+    L.cap_to = 0;
+    if (H.tcap_o > 0) {
+      TilePlan to = tile_plan(S, H.tcap_r, cap_i, elem, H.tcap_o);
+      to.nbuf = nbuf;
+      to.cap_i2 = L.cap_ti2;
+      if (tile_launch_bytes(to, true) <= (nbuf == 2 ? kTileSmemBudget : kTileSmemBudget1)) {
+        L.cap_to = H.tcap_o;
+        L.smem_tile_x = tile_launch_bytes(to, false);
+      }
+    }
   }
   // a lane-tile launch: at most the CTAs the device holds at once, each
   // walking tiles grid-stride
   const int tile_full =
       H.tile_colors > 0 ? sms * tile_resident_ctas(ctx->fp32, L.Wt * kWarp, L.smem_tile) : 1;
+  const int tile_full_x =
+      H.tile_colors > 0 && L.cap_to > 0 ? sms * tile_resident_ctas(ctx->fp32, L.Wt * kWarp, L.smem_tile_x) : 1;
   // warp-tile kernels: W warps per CTA, one tile per warp at a time, a
   // buffer of (largest tile's steps) x 32 values per warp
   L.Ww = W;
@@ -258,6 +272,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
       H.tile_colors > 0 ? sms * wtile_resident_ctas(ctx->fp32, L.Ww * kWarp, L.smem_wt) : 1;
   const int pr_full = H.tile_colors > 0 ? sms * pair_resident_ctas(ctx->fp32, L.Ww * kWarp) : 1;
   L.wtile.assign(n_c, 0);
+  L.stage_ext.assign(n_c, 0);
   int32_t gbig = 1;
   for (int c = 0; c < n_c; ++c) {
     L.task0[c] = H.color_group[c];
@@ -281,9 +296,14 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     if (nt > 0 && o.tile_mapping == ICCG_TILES_WARP) L.wtile[c] = 1;
     if (nt > 0 && steps <= 2 && ((pairs && o.tile_mapping == ICCG_TILES_AUTO) || o.tile_mapping == ICCG_TILES_PAIR))
       L.wtile[c] = 2;
+    // one-CTA-per-tile colors of short tiles also stage their entries to
+    // other colors and row vectors (measured 3% faster in FP64 and 14% in
+    // FP32 at blocks of 1-2 rows; slower for tiles of 8 steps)
+    L.stage_ext[c] = L.cap_to > 0 && steps <= 2;
     if (L.wtile[c] == 1) L.grid_c[c] = std::min((nt + L.Ww - 1) / L.Ww, wt_full);
     else if (L.wtile[c] == 2) L.grid_c[c] = std::min((nt + L.Ww - 1) / L.Ww, pr_full);
-    else L.grid_c[c] = nt > 0 ? std::min(nt, tile_full) : std::max(1, L.task1[c] - L.task0[c]);
+    else L.grid_c[c] = nt > 0 ? std::min(nt, L.stage_ext[c] ? tile_full_x : tile_full)
+                              : std::max(1, L.task1[c] - L.task0[c]);
     gbig = std::max(gbig, L.grid_c[c]);
   }
   // slot regions: forward launches in color order (<r,r>), then the fused
@@ -383,6 +403,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     P.tcap_i = L.cap_ti;
     P.tnbuf = L.nbuf_t;
     P.tcap_i2 = L.cap_ti2;
+    P.tcap_o = L.cap_to;
     CK(dev_alloc(ctx, &P.sl_val, H.sl_col.size()), "alloc tiles");
     CK(dev_alloc(ctx, &P.su_val, H.su_col.size()), "alloc tiles");
     CK(dev_alloc(ctx, &P.si_val, H.si_col.size()), "alloc tiles");

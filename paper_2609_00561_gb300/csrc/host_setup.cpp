@@ -247,7 +247,7 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
   H.sl_col.clear(); H.su_col.clear(); H.sl_map.clear(); H.su_map.clear();
   H.si_col.clear(); H.ui_col.clear(); H.si_map.clear(); H.ui_map.clear();
   H.wi_max = 0;
-  H.tcap_r = H.tcap_i = 0;
+  H.tcap_r = H.tcap_i = H.tcap_o = 0;
   // appends, sliced-ELL, the entries of rows row .. row+cnt-1 that are
   // in-block (inb) or not; emap maps a CSR entry to its L entry (null:
   // itself); returns the width
@@ -314,6 +314,7 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
       H.wi_max = std::max(H.wi_max, std::max(td.wl, td.wu));
       H.tcap_r = std::max(H.tcap_r, td.nrows);
       H.tcap_i = std::max(H.tcap_i, std::max(td.li1 - td.li0, td.ui1 - td.ui0));
+      H.tcap_o = std::max(H.tcap_o, std::max(td.lo1 - td.lo0, td.uo1 - td.uo0));
       H.tiles.push_back(td);
     }
   }

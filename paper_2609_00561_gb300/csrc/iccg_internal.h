@@ -92,7 +92,9 @@ constexpr int kTileSmemBudget1 = 200 * 1024;    // lane-tile CTA with one buffer
 // copied into the other.  Then the row values w[step][lane].
 struct TilePlan {
   int cap_s, cap_r, cap_i;          // steps, rows, in-block entries per tile
+  int cap_o;                        // other-color entries per tile staged (0: read from global memory)
   int o_steps, o_dv, o_ic, o_iv;    // within a buffer
+  int o_oc, o_ov, o_vec;            // other-color entries (columns, values), four row vectors
   int o_ic2, o_iv2;                 // second entry set (U of a fused launch)
   int buf1, buf2;                   // buffer bytes with one / two entry sets
   int w_bytes;
@@ -102,12 +104,22 @@ struct TilePlan {
 
 __host__ __device__ inline int r16b(int bytes) { return (bytes + 15) & ~15; }
 
-__host__ __device__ inline TilePlan tile_plan(int cap_s, int cap_r, int cap_i, int elem) {
+// With cap_o > 0 a buffer also holds the tile's entries to other colors (L
+// forward, U backward) and four vectors over its rows (r, q, x, p forward;
+// y, r backward), so that a tile's loads are issued while the previous tile
+// is computed.
+__host__ __device__ inline TilePlan tile_plan(int cap_s, int cap_r, int cap_i, int elem, int cap_o = 0) {
   TilePlan p;
-  p.cap_s = cap_s; p.cap_r = cap_r; p.cap_i = cap_i;
+  p.cap_s = cap_s; p.cap_r = cap_r; p.cap_i = cap_i; p.cap_o = cap_o;
   int o = 0;
   p.o_steps = o; o += r16b(cap_s * 48);
   p.o_dv = o; o += r16b((cap_r + 8) * elem);
+  p.o_oc = p.o_ov = p.o_vec = o;
+  if (cap_o > 0) {
+    p.o_oc = o; o += r16b((cap_o + 8) * 4);
+    p.o_ov = o; o += r16b((cap_o + 8) * elem);
+    p.o_vec = o; o += 4 * r16b((cap_r + 8) * 8);
+  }
   p.o_ic = o; o += r16b((cap_i + 8) * 4);
   p.o_iv = o; o += r16b((cap_i + 8) * elem);
   p.buf1 = o;
@@ -197,6 +209,7 @@ struct Params {
   int32_t nsl, nsu, nsi, nui;
   int32_t lane_max, wi_max;     // largest tile block (steps) and in-block width
   int32_t tcap_r, tcap_i;       // largest tile rows; in-block entries staged per tile (L or U)
+  int32_t tcap_o;               // other-color entries staged per tile (0: global memory)
   int32_t tnbuf;                // lane-tile staging buffers per CTA (1 or 2)
   int32_t tcap_i2;              // fused launch: second-set staging capacity (0: global)
   // persistent solve: first group of each color [n_c + 1], grid barrier
@@ -233,6 +246,7 @@ struct HostLayout {
   std::vector<int32_t> si_col, ui_col, si_map, ui_map;
   int32_t wi_max = 0;                 // widest in-block step of any tile
   int32_t tcap_r = 0, tcap_i = 0;     // largest tile: rows, in-block entries
+  int32_t tcap_o = 0;                 // largest tile: entries to other colors (L or U)
   std::vector<int32_t> ord;           // internal row -> row of the caller's block-multicolor order
   int32_t lane_max = 0;               // largest block of a tile color
   int32_t tile_colors = 0;
@@ -262,9 +276,12 @@ struct Plan {
   std::vector<int32_t> tile0, tile1;    // tile range of each color (empty: groups)
   int32_t Wt = 8;                       // warps per CTA of the lane-tile kernels (one tile at a time)
   int32_t smem_tile = 0, smem_tile2 = 0;  // bytes per CTA of the lane-tile kernels (one / two entry sets)
+  int32_t smem_tile_x = 0;              // bytes per CTA with the entries to other colors staged as well
   int32_t cap_ti = 0;                   // in-block entries of a tile staged in shared memory
   int32_t nbuf_t = 2;                   // lane-tile staging buffers per CTA
   int32_t cap_ti2 = 0;                  // second-set (fused launch) staging capacity
+  int32_t cap_to = 0;                   // other-color entries staged per tile (0: global)
+  std::vector<char> stage_ext;          // color c's lane-tile launches stage those entries (tiles of <= 2 steps)
   std::vector<char> wtile;              // color c: 0 CTA per tile, 1 warp-tile kernels, 2 pair kernels
   int32_t Ww = 8;                       // warps per CTA of the warp-tile kernels
   int32_t smem_wt = 0;                  // bytes per CTA of the warp-tile kernels

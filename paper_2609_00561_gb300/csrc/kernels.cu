@@ -652,6 +652,10 @@ struct TileBuf {
   const PT *dv;
   const int32_t *ic, *ic2;
   const PT *iv, *iv2;
+  const int32_t *oc;     // other-color entries (cap_o > 0)
+  const PT *ov;
+  const double *vec;     // four row vectors of (cap_r + 8) doubles each
+  int vstride;
 };
 
 template <typename PT>
@@ -664,7 +668,17 @@ __device__ __forceinline__ TileBuf<PT> tile_buf(unsigned char *smem, const TileP
   t.iv = reinterpret_cast<const PT *>(b + pl.o_iv);
   t.ic2 = reinterpret_cast<const int32_t *>(b + pl.o_ic2);
   t.iv2 = reinterpret_cast<const PT *>(b + pl.o_iv2);
+  t.oc = reinterpret_cast<const int32_t *>(b + pl.o_oc);
+  t.ov = reinterpret_cast<const PT *>(b + pl.o_ov);
+  t.vec = reinterpret_cast<const double *>(b + pl.o_vec);
+  t.vstride = r16b((pl.cap_r + 8) * 8) / 8;
   return t;
+}
+
+// Whether tile t's other-color entries and row vectors are (to be) staged
+__device__ __forceinline__ bool ext_staged(const TilePlan &pl, const TileDesc &t, bool upper) {
+  const int n = upper ? t.uo1 - t.uo0 : t.lo1 - t.lo0;
+  return pl.cap_o > 0 && n <= pl.cap_o && t.nrows <= pl.cap_r;
 }
 
 // Issue (no commit) the copies of tile t's static data into buffer tb:
@@ -672,12 +686,21 @@ __device__ __forceinline__ TileBuf<PT> tile_buf(unsigned char *smem, const TileP
 // as the second set when TWO; an in-block range larger than the capacity
 // stays in global memory.
 template <typename PT, bool FIRST_UPPER, bool TWO>
-__device__ __forceinline__ void tile_stage(const Params &P, const TileDesc &t, const TileBuf<PT> &tb, int cap_i,
-                                           int cap_i2, int tid, int nthr) {
+__device__ __forceinline__ void tile_stage(const Params &P, const TileDesc &t, const TileBuf<PT> &tb,
+                                           const TilePlan &pl, int tid, int nthr) {
+  const int cap_i = pl.cap_i, cap_i2 = pl.cap_i2;
   int4 *st = reinterpret_cast<int4 *>(const_cast<StepDesc *>(tb.st));
   const int4 *gs = reinterpret_cast<const int4 *>(P.steps + t.step0);
   for (int k = tid; k < t.nsteps * 3; k += nthr) cp_async16(st + k, gs + k);
   stage_cover<PT>(invds<PT>(P), t.row0, t.row0 + t.nrows, const_cast<PT *>(tb.dv), tid, nthr);
+  // entries to other colors of the first sweep (static, like the above)
+  if (ext_staged(pl, t, FIRST_UPPER)) {
+    const int o0 = FIRST_UPPER ? t.uo0 : t.lo0, o1 = FIRST_UPPER ? t.uo1 : t.lo1;
+    if (o1 > o0) {
+      stage_cover<int32_t>(FIRST_UPPER ? P.su_col : P.sl_col, o0, o1, const_cast<int32_t *>(tb.oc), tid, nthr);
+      stage_cover<PT>(FIRST_UPPER ? suv<PT>(P) : slv<PT>(P), o0, o1, const_cast<PT *>(tb.ov), tid, nthr);
+    }
+  }
   // a set is copied only into a region the launch has (capacity > 0) and
   // only when non-empty (the cover of an empty range is still 16 bytes)
   const int i0 = FIRST_UPPER ? t.ui0 : t.li0, i1 = FIRST_UPPER ? t.ui1 : t.li1;
@@ -688,6 +711,29 @@ __device__ __forceinline__ void tile_stage(const Params &P, const TileDesc &t, c
   if (TWO && t.ui1 > t.ui0 && t.ui1 - t.ui0 <= cap_i2) {
     stage_cover<int32_t>(P.ui_col, t.ui0, t.ui1, const_cast<int32_t *>(tb.ic2), tid, nthr);
     stage_cover<PT>(uiv<PT>(P), t.ui0, t.ui1, const_cast<PT *>(tb.iv2), tid, nthr);
+  }
+}
+
+// Issue (no commit) the copies of the row vectors tile t's first sweep reads
+// (r, q, x, p forward; y, r backward) when its entries are staged.  They come
+// from earlier launches, so the first tile's are issued after
+// griddepcontrol.wait; each tile's rows are written by that tile alone.
+template <typename PT, bool FIRST_UPPER, bool UPD>
+__device__ __forceinline__ void tile_stage_vec(const Params &P, const TileDesc &t, const TileBuf<PT> &tb,
+                                               const TilePlan &pl, int tid, int nthr) {
+  if (!ext_staged(pl, t, FIRST_UPPER)) return;
+  double *v = const_cast<double *>(tb.vec);
+  const int r0 = t.row0, r1 = t.row0 + t.nrows, vs = tb.vstride;
+  if (FIRST_UPPER) {
+    stage_cover<PT>(reinterpret_cast<const PT *>(P.y), r0, r1, reinterpret_cast<PT *>(v), tid, nthr);
+    stage_cover<double>(P.r, r0, r1, v + vs, tid, nthr);
+  } else {
+    stage_cover<double>(P.r, r0, r1, v, tid, nthr);
+    if (UPD) {
+      stage_cover<double>(P.q, r0, r1, v + vs, tid, nthr);
+      stage_cover<double>(P.xh, r0, r1, v + 2 * vs, tid, nthr);
+      stage_cover<double>(P.p0, r0, r1, v + 3 * vs, tid, nthr);
+    }
   }
 }
 
@@ -709,7 +755,9 @@ __device__ __forceinline__ InBlock<PT> in_block(const int32_t *sc, const PT *sv,
 // acc -= sum over a step's sliced-ELL entries to other colors of v * g[col]
 // (coalesced loads of the entries, then the gathers; FMAs only for the
 // step's real width, a warp-uniform count; padding entries are (kPadCol, 0))
-template <typename PT>
+// (NC: col / val in global memory, read through the read-only path; else
+// shared-memory copies, plain loads)
+template <typename PT, bool NC = true>
 __device__ __forceinline__ PT ext_sub(const int32_t *col, const PT *val, int e, int stride, int width, PT acc,
                                       const PT *g) {
   for (int j0 = 0; j0 < width; j0 += kChunk) {
@@ -718,8 +766,13 @@ __device__ __forceinline__ PT ext_sub(const int32_t *col, const PT *val, int e, 
     PT vv[kChunk], xx[kChunk];
 #pragma unroll
     for (int j = 0; j < kChunk; ++j) {
-      cc[j] = j < nj ? __ldg(col + e + (j0 + j) * stride) : kPadCol;
-      vv[j] = j < nj ? __ldg(val + e + (j0 + j) * stride) : PT(0);
+      if (NC) {
+        cc[j] = j < nj ? __ldg(col + e + (j0 + j) * stride) : kPadCol;
+        vv[j] = j < nj ? __ldg(val + e + (j0 + j) * stride) : PT(0);
+      } else {
+        cc[j] = j < nj ? col[e + (j0 + j) * stride] : kPadCol;
+        vv[j] = j < nj ? val[e + (j0 + j) * stride] : PT(0);
+      }
     }
 #pragma unroll
     for (int j = 0; j < kChunk; ++j) xx[j] = cc[j] == kPadCol ? PT(0) : __ldcg(g + cc[j]);
@@ -735,11 +788,19 @@ __device__ __forceinline__ PT ext_sub(const int32_t *col, const PT *val, int e, 
 // gathers of z); the partial row value goes to w[step][lane].
 template <typename PT, bool UPPER, bool UPDATE>
 __device__ __forceinline__ void tile_phase_a(const Params &P, const TileDesc &t, const TileBuf<PT> &tb, PT *w,
-                                             double alpha, const double *pn, bool y_in_smem, double &rr_acc,
-                                             int warp, int W) {
+                                             double alpha, const double *pn, bool y_in_smem, bool staged,
+                                             double &rr_acc, int warp, int W) {
   const int lane = threadIdx.x & 31;
   PT *yv = reinterpret_cast<PT *>(P.y);
   const PT *zv = reinterpret_cast<const PT *>(P.z);
+  // entries to other colors and row vectors: the staged copies (indexed by
+  // global entry / row) or global memory
+  const int o0 = UPPER ? t.uo0 : t.lo0;
+  const int32_t *oc_s = tb.oc - cover_base<int32_t>(o0), *oc_g = UPPER ? P.su_col : P.sl_col;
+  const PT *ov_s = tb.ov - cover_base<PT>(o0), *ov_g = UPPER ? suv<PT>(P) : slv<PT>(P);
+  const int vs = tb.vstride;
+  const double *v0 = tb.vec - cover_base<double>(t.row0);
+  const PT *ys = reinterpret_cast<const PT *>(tb.vec) - cover_base<PT>(t.row0);
   for (int k = warp; k < t.nsteps; k += W) {
     const StepDesc &s = tb.st[k];
     const int cnt = s.cnt;
@@ -747,17 +808,33 @@ __device__ __forceinline__ void tile_phase_a(const Params &P, const TileDesc &t,
       const int i = s.row + lane;
       PT acc;
       if (UPPER) {
-        const PT src = y_in_smem ? w[k * kWarp + lane] : __ldcg(yv + i);
-        acc = ext_sub<PT>(P.su_col, suv<PT>(P), s.uo + lane, cnt, s.uw, src, zv);
+        PT src;
+        if (y_in_smem) src = w[k * kWarp + lane];
+        else if (staged) src = ys[i];
+        else src = __ldcg(yv + i);
+        if (staged) acc = ext_sub<PT, false>(oc_s, ov_s, s.uo + lane, cnt, s.uw, src, zv);
+        else acc = ext_sub<PT>(oc_g, ov_g, s.uo + lane, cnt, s.uw, src, zv);
       } else {
-        double ri = __ldcg(P.r + i);
-        if (UPDATE) {
-          ri -= alpha * __ldcg(P.q + i);
-          P.r[i] = ri;
-          P.xh[i] = __ldcg(P.xh + i) + alpha * __ldcg(pn + i);
-          rr_acc += ri * ri;
+        double ri;
+        if (staged) {
+          ri = v0[i];
+          if (UPDATE) {
+            ri -= alpha * v0[vs + i];
+            P.r[i] = ri;
+            P.xh[i] = v0[2 * vs + i] + alpha * v0[3 * vs + i];
+            rr_acc += ri * ri;
+          }
+          acc = ext_sub<PT, false>(oc_s, ov_s, s.lo + lane, cnt, s.lw, PT(ri), yv);
+        } else {
+          ri = __ldcg(P.r + i);
+          if (UPDATE) {
+            ri -= alpha * __ldcg(P.q + i);
+            P.r[i] = ri;
+            P.xh[i] = __ldcg(P.xh + i) + alpha * __ldcg(pn + i);
+            rr_acc += ri * ri;
+          }
+          acc = ext_sub<PT>(oc_g, ov_g, s.lo + lane, cnt, s.lw, PT(ri), yv);
         }
-        acc = ext_sub<PT>(P.sl_col, slv<PT>(P), s.lo + lane, cnt, s.lw, PT(ri), yv);
       }
       w[k * kWarp + lane] = acc;
     }
@@ -785,7 +862,7 @@ __device__ __forceinline__ void tile_phase_b(const TileDesc &t, const StepDesc *
 // Phase C: the tile's results to global memory (y or z), <r,z> (backward)
 template <typename PT, bool UPPER>
 __device__ __forceinline__ void tile_phase_c(const Params &P, const TileDesc &t, const StepDesc *st, const PT *w,
-                                             bool store, double &rz_acc, int warp, int W) {
+                                             bool store, const double *rs, double &rz_acc, int warp, int W) {
   const int lane = threadIdx.x & 31;
   PT *res = reinterpret_cast<PT *>(UPPER ? P.z : P.y);
   for (int k = warp; k < t.nsteps; k += W) {
@@ -794,7 +871,12 @@ __device__ __forceinline__ void tile_phase_c(const Params &P, const TileDesc &t,
       const int i = s.row + lane;
       const PT v = w[k * kWarp + lane];
       if (store) res[i] = v;
-      if (UPPER) rz_acc += __ldcg(P.r + i) * double(v);
+      if (UPPER) {
+        double ri;
+        if (rs) ri = rs[i];
+        else ri = __ldcg(P.r + i);
+        rz_acc += ri * double(v);
+      }
     }
   }
 }
@@ -818,17 +900,19 @@ tile_kernel(Params P, int t0, int t1, TilePlan pl, int fin, SlotArgs sa) {
   int t = t0 + int(blockIdx.x), buf = 0;
   const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   TileDesc td = load_tile(P.tiles + min(t, t1 - 1));
-  if (t < t1) tile_stage<PT, FU, TWO>(P, td, tile_buf<PT>(smem, pl, bsize, 0), pl.cap_i, pl.cap_i2, threadIdx.x, blockDim.x);
-  cp_commit();
+  if (t < t1) tile_stage<PT, FU, TWO>(P, td, tile_buf<PT>(smem, pl, bsize, 0), pl, threadIdx.x, blockDim.x);
   pdl_wait();
+  if (t < t1) tile_stage_vec<PT, FU, UPDATE>(P, td, tile_buf<PT>(smem, pl, bsize, 0), pl, threadIdx.x, blockDim.x);
+  cp_commit();
   const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
   for (; t < t1; t += gridDim.x) {
     const int tn = t + int(gridDim.x);
     TileDesc tdn = td;
     if (tn < t1) tdn = load_tile(P.tiles + tn);
-    if (tn < t1 && nbuf == 2)
-      tile_stage<PT, FU, TWO>(P, tdn, tile_buf<PT>(smem, pl, bsize, buf ^ 1), pl.cap_i, pl.cap_i2, threadIdx.x,
-                              blockDim.x);
+    if (tn < t1 && nbuf == 2) {
+      tile_stage<PT, FU, TWO>(P, tdn, tile_buf<PT>(smem, pl, bsize, buf ^ 1), pl, threadIdx.x, blockDim.x);
+      tile_stage_vec<PT, FU, UPDATE>(P, tdn, tile_buf<PT>(smem, pl, bsize, buf ^ 1), pl, threadIdx.x, blockDim.x);
+    }
     cp_commit();
     cp_wait_prev();
     __syncthreads();
@@ -836,35 +920,40 @@ tile_kernel(Params P, int t0, int t1, TilePlan pl, int fin, SlotArgs sa) {
     const PT *dv = tb.dv - cover_base<PT>(td.row0);
     const InBlock<PT> ul = in_block<PT>(tb.ic, tb.iv, P.ui_col, uiv<PT>(P), td.ui0, td.ui1, pl.cap_i);
     const InBlock<PT> ll = in_block<PT>(tb.ic, tb.iv, P.si_col, siv<PT>(P), td.li0, td.li1, pl.cap_i);
+    const bool stg = ext_staged(pl, td, MODE == M_BWD);
     if (MODE == M_BWD) {
-      tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, false, rr_acc, wid, nw);
+      tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, false, stg, rr_acc, wid, nw);
       __syncthreads();
       if (wid == 0) tile_phase_b<PT, true>(td, tb.st, dv, ul.ic, ul.iv, w, threadIdx.x);
       __syncthreads();
-      tile_phase_c<PT, true>(P, td, tb.st, w, true, rz_acc, wid, nw);
+      tile_phase_c<PT, true>(P, td, tb.st, w, true, stg ? tb.vec + tb.vstride - cover_base<double>(td.row0) : nullptr,
+                             rz_acc, wid, nw);
     } else {
-      tile_phase_a<PT, false, UPDATE>(P, td, tb, w, alpha, P.p0, false, rr_acc, wid, nw);
+      tile_phase_a<PT, false, UPDATE>(P, td, tb, w, alpha, P.p0, false, stg, rr_acc, wid, nw);
       __syncthreads();
       if (wid == 0) tile_phase_b<PT, false>(td, tb.st, dv, ll.ic, ll.iv, w, threadIdx.x);
       __syncthreads();
       if (MODE == M_FWD) {
-        tile_phase_c<PT, false>(P, td, tb.st, w, true, rz_acc, wid, nw);
+        tile_phase_c<PT, false>(P, td, tb.st, w, true, nullptr, rz_acc, wid, nw);
       } else {
         // the last color: y stays in shared memory for the backward sweep
+        // (its entries to other colors from global memory: the staged set is L's)
         const InBlock<PT> u2 = in_block<PT>(tb.ic2, tb.iv2, P.ui_col, uiv<PT>(P), td.ui0, td.ui1, pl.cap_i2);
-        tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, true, rr_acc, wid, nw);
+        tile_phase_a<PT, true, false>(P, td, tb, w, 0.0, nullptr, true, false, rr_acc, wid, nw);
         __syncthreads();
         if (wid == 0) tile_phase_b<PT, true>(td, tb.st, dv, u2.ic, u2.iv, w, threadIdx.x);
         __syncthreads();
-        tile_phase_c<PT, true>(P, td, tb.st, w, true, rz_acc, wid, nw);
+        tile_phase_c<PT, true>(P, td, tb.st, w, true, nullptr, rz_acc, wid, nw);
       }
     }
     __syncthreads();   // buffer buf and w are reused by the next tile
     if (nbuf == 1) {
       // one buffer: the next tile's copies start now (waited on by the next
       // pass's cp_wait_prev, which leaves only its own empty group pending)
-      if (tn < t1)
-        tile_stage<PT, FU, TWO>(P, tdn, tile_buf<PT>(smem, pl, bsize, 0), pl.cap_i, pl.cap_i2, threadIdx.x, blockDim.x);
+      if (tn < t1) {
+        tile_stage<PT, FU, TWO>(P, tdn, tile_buf<PT>(smem, pl, bsize, 0), pl, threadIdx.x, blockDim.x);
+        tile_stage_vec<PT, FU, UPDATE>(P, tdn, tile_buf<PT>(smem, pl, bsize, 0), pl, threadIdx.x, blockDim.x);
+      }
       cp_commit();
     } else {
       buf ^= 1;
@@ -1722,8 +1811,8 @@ GroupSmemPlan plan_of(const Params &P, bool fused, bool upper) {
 }
 
 template <typename PT>
-TilePlan tile_plan_of(const Params &P) {
-  TilePlan p = tile_plan(P.lane_max, P.tcap_r, P.tcap_i, int(sizeof(PT)));
+TilePlan tile_plan_of(const Params &P, bool stage_ext = true) {
+  TilePlan p = tile_plan(P.lane_max, P.tcap_r, P.tcap_i, int(sizeof(PT)), stage_ext ? P.tcap_o : 0);
   p.nbuf = P.tnbuf;
   p.cap_i2 = P.tcap_i2;
   return p;
@@ -1731,7 +1820,7 @@ TilePlan tile_plan_of(const Params &P) {
 
 template <typename PT>
 cudaError_t launch_tile(const Params &P, const Plan &L, int c, int mode, bool update, int fin, const SlotArgs &sa) {
-  const TilePlan pl = tile_plan_of<PT>(P);
+  const TilePlan pl = tile_plan_of<PT>(P, L.stage_ext[c] != 0);
   const int g = L.grid_c[c], t0 = L.tile0[c], t1 = L.tile1[c], th = L.Wt * kWarp;
   const int sm = tile_launch_bytes(pl, mode == M_FUSED);
   if (mode == M_BWD) return launch(tile_kernel<PT, M_BWD, false>, g, th, sm, L, P, t0, t1, pl, fin, sa);
