@@ -126,7 +126,7 @@ def workload(args):
 # from the ncu launch list of `bench.py --steps 1 --warmup 1 --no-cpu-baseline`
 # (profiles/launches_iccg_fp64_poisson128_cpm05.md), keyed by workload and
 # blocking; None where no capture of the current kernels exists.
-SUBST_TRAFFIC = {("poisson128", 128, "leiden_cpm", 0.5, False): 433183458}
+SUBST_TRAFFIC = {("poisson128", 128, "leiden_cpm", 0.5, False): 433152384}
 
 
 def make_blocking(mod, a, args):
