@@ -346,7 +346,8 @@ def run_batch(args):
                for (a, _), bl in zip(systems, blocks)]
     bs = iccg.BatchSolver(solvers, args.nrhs)
     B = [torch.tensor(b, device=dev) for _, b in systems]
-    tune_ms = bs.tune(B, args.tol, args.maxit)     # shape search on this batch (setup, untimed)
+    # shape search on this batch (setup, untimed); --no-tune keeps the default shape
+    tune_ms = None if args.no_tune else bs.tune(B, args.tol, args.maxit)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     shape = bs.info()
@@ -607,6 +608,7 @@ def main():
     p.add_argument("--nsys", type=int, default=64, help="batch64: systems")
     p.add_argument("--nrhs", type=int, default=16, help="batch64: right-hand sides per system")
     p.add_argument("--fp64-batch", action="store_true", help="batch64: FP64 preconditioner")
+    p.add_argument("--no-tune", action="store_true", help="batch64: default launch shape, no autotuning")
     args = p.parse_args()
     if args.nx is None:
         args.nx = 96 if args.workload == "diffusion96" else 128
