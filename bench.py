@@ -126,7 +126,7 @@ def workload(args):
 # from the ncu launch list of `bench.py --steps 1 --warmup 1 --no-cpu-baseline`
 # (profiles/launches_iccg_fp64_poisson128_cpm05.md), keyed by workload and
 # blocking; None where no capture of the current kernels exists.
-SUBST_TRAFFIC = {}
+SUBST_TRAFFIC = {("poisson128", 128, "leiden_cpm", 0.5, False): 433152384}
 
 
 def make_blocking(mod, a, args):
@@ -149,17 +149,16 @@ def bytes_model(n, nnz, nL, fp32):
     """Algorithmic bytes per PCG iteration (each array counted once, gathered
     vector reads assumed to hit cache), by kernel family:
       SpMV + <p,q>   values and columns 12 nnz, row pointers 4n, p in 8n, q out 8n
-      p update       the previous iteration's x += alpha p and p = z + beta p:
-                     z, p, x in, p, x out: 40n (FP32 z: 36n)
+      p update       z, p in, p out: 24n (FP32 z: 20n)
       forward sweep  L entries (value + column) per strictly-lower entry, row
-                     pointers 4n, 1/L_ii, the fused r update (r, q in, r out:
-                     24n), y out
+                     pointers 4n, 1/L_ii, the fused x/r update (r, q, x, p in,
+                     r, x out: 48n), y out
       backward sweep U entries, row pointers 4n, 1/L_ii, y in, z out, r in (dot)
     The substitution roofline uses forward + backward."""
     pe = 4 if fp32 else 8
     spmv = 12 * nnz + 4 * n + 16 * n
-    pupd = (32 + pe) * n
-    fwd = (pe + 4) * nL + 4 * n + pe * n + 24 * n + pe * n
+    pupd = (16 + pe) * n + 8 * n
+    fwd = (pe + 4) * nL + 4 * n + pe * n + 48 * n + pe * n
     bwd = (pe + 4) * nL + 4 * n + pe * n + pe * n + pe * n + 8 * n
     return {"spmv": spmv, "pupdate": pupd, "subst": fwd + bwd, "total": spmv + pupd + fwd + bwd}
 

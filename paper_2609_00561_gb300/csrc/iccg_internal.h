@@ -94,7 +94,7 @@ struct TilePlan {
   int cap_s, cap_r, cap_i;          // steps, rows, in-block entries per tile
   int cap_o;                        // other-color entries per tile staged (0: read from global memory)
   int o_steps, o_dv, o_ic, o_iv;    // within a buffer
-  int o_oc, o_ov, o_vec;            // other-color entries (columns, values), two row vectors
+  int o_oc, o_ov, o_vec;            // other-color entries (columns, values), four row vectors
   int o_ic2, o_iv2;                 // second entry set (U of a fused launch)
   int buf1, buf2;                   // buffer bytes with one / two entry sets
   int w_bytes;
@@ -105,9 +105,9 @@ struct TilePlan {
 __host__ __device__ inline int r16b(int bytes) { return (bytes + 15) & ~15; }
 
 // With cap_o > 0 a buffer also holds the tile's entries to other colors (L
-// forward, U backward) and two vectors over its rows (r, q forward; y, r
-// backward), so that a tile's loads are issued while the previous tile is
-// computed.
+// forward, U backward) and four vectors over its rows (r, q, x, p forward;
+// y, r backward), so that a tile's loads are issued while the previous tile
+// is computed.
 __host__ __device__ inline TilePlan tile_plan(int cap_s, int cap_r, int cap_i, int elem, int cap_o = 0) {
   TilePlan p;
   p.cap_s = cap_s; p.cap_r = cap_r; p.cap_i = cap_i; p.cap_o = cap_o;
@@ -118,7 +118,7 @@ __host__ __device__ inline TilePlan tile_plan(int cap_s, int cap_r, int cap_i, i
   if (cap_o > 0) {
     p.o_oc = o; o += r16b((cap_o + 8) * 4);
     p.o_ov = o; o += r16b((cap_o + 8) * elem);
-    p.o_vec = o; o += 2 * r16b((cap_r + 8) * 8);
+    p.o_vec = o; o += 4 * r16b((cap_r + 8) * 8);
   }
   p.o_ic = o; o += r16b((cap_i + 8) * 4);
   p.o_iv = o; o += r16b((cap_i + 8) * elem);
@@ -151,8 +151,6 @@ struct Scalars {
   uint32_t ticket;       // arrival counter for "last CTA reduces" epilogues
   int32_t use_cond;      // 1 when a graph conditional handle is live
   unsigned long long cond_handle;
-  int32_t xpend;         // phased solver: x += alpha p of the last SpMV not applied yet
-  int32_t pad;
 };
 
 // Everything a kernel needs; passed by value.

@@ -385,7 +385,7 @@ __device__ __forceinline__ void group_sweep(const Params &P, const GroupDesc &d,
       if (UPDATE) {
         ri -= alpha * __ldcg(P.q + i);
         P.r[i] = ri;
-        if (pn) P.xh[i] = __ldcg(P.xh + i) + alpha * __ldcg(pn + i);
+        P.xh[i] = __ldcg(P.xh + i) + alpha * __ldcg(pn + i);
         rr_acc += ri * ri;
       }
       src = PT(ri);
@@ -479,7 +479,6 @@ __device__ void finish_init(const Params &P, double rz, double *red) {
     s->bnorm = bn;
     s->iter = 0;
     s->beta = 0.0;
-    s->xpend = 0;
     s->rz = rz;
     s->rr = rr;
     int done = 0;
@@ -588,8 +587,7 @@ color_kernel(Params P, int g0, int g1, GroupSmemPlan plan, int fin, SlotArgs sa)
       group_sweep<PT, true, false>(P, d, sw, m, tid, nthr, 0.0, nullptr, false, true, rr_acc, rz_acc);
     } else {
       double alpha = 0.0;
-      // the phased solver applies x += alpha p in the next p update
-      const double *pn = nullptr;
+      const double *pn = P.p0;
       if (UPDATE) alpha = __ldcg(&P.sc->alpha);
       group_sweep<PT, false, UPDATE>(P, d, sw, m, tid, nthr, alpha, pn, false, MODE == M_FWD || !sw.fit,
                                      rr_acc, rz_acc);
@@ -656,7 +654,7 @@ struct TileBuf {
   const PT *iv, *iv2;
   const int32_t *oc;     // other-color entries (cap_o > 0)
   const PT *ov;
-  const double *vec;     // two row vectors of (cap_r + 8) doubles each
+  const double *vec;     // four row vectors of (cap_r + 8) doubles each
   int vstride;
 };
 
@@ -717,7 +715,7 @@ __device__ __forceinline__ void tile_stage(const Params &P, const TileDesc &t, c
 }
 
 // Issue (no commit) the copies of the row vectors tile t's first sweep reads
-// (r, q forward; y, r backward) when its entries are staged.  They come
+// (r, q, x, p forward; y, r backward) when its entries are staged.  They come
 // from earlier launches, so the first tile's are issued after
 // griddepcontrol.wait; each tile's rows are written by that tile alone.
 template <typename PT, bool FIRST_UPPER, bool UPD>
@@ -731,7 +729,11 @@ __device__ __forceinline__ void tile_stage_vec(const Params &P, const TileDesc &
     stage_cover<double>(P.r, r0, r1, v + vs, tid, nthr);
   } else {
     stage_cover<double>(P.r, r0, r1, v, tid, nthr);
-    if (UPD) stage_cover<double>(P.q, r0, r1, v + vs, tid, nthr);
+    if (UPD) {
+      stage_cover<double>(P.q, r0, r1, v + vs, tid, nthr);
+      stage_cover<double>(P.xh, r0, r1, v + 2 * vs, tid, nthr);
+      stage_cover<double>(P.p0, r0, r1, v + 3 * vs, tid, nthr);
+    }
   }
 }
 
@@ -819,6 +821,7 @@ __device__ __forceinline__ void tile_phase_a(const Params &P, const TileDesc &t,
           if (UPDATE) {
             ri -= alpha * v0[vs + i];
             P.r[i] = ri;
+            P.xh[i] = v0[2 * vs + i] + alpha * v0[3 * vs + i];
             rr_acc += ri * ri;
           }
           acc = ext_sub<PT, false>(oc_s, ov_s, s.lo + lane, cnt, s.lw, PT(ri), yv);
@@ -827,6 +830,7 @@ __device__ __forceinline__ void tile_phase_a(const Params &P, const TileDesc &t,
           if (UPDATE) {
             ri -= alpha * __ldcg(P.q + i);
             P.r[i] = ri;
+            P.xh[i] = __ldcg(P.xh + i) + alpha * __ldcg(pn + i);
             rr_acc += ri * ri;
           }
           acc = ext_sub<PT>(oc_g, ov_g, s.lo + lane, cnt, s.lw, PT(ri), yv);
@@ -1019,6 +1023,7 @@ __device__ __forceinline__ void wtile_sweep(const Params &P, const TileDesc &t, 
         if (UPDATE) {
           ri -= alpha * __ldcg(P.q + i);
           P.r[i] = ri;
+          P.xh[i] = __ldcg(P.xh + i) + alpha * __ldcg(P.p0 + i);
           rr_acc += ri * ri;
         }
         acc = ext_sub<PT>(P.sl_col, slv<PT>(P), s.lo + lane, s.cnt, s.lw, PT(ri), ext);
@@ -1155,10 +1160,12 @@ pair_kernel(Params P, int t0, int t1, int fin, SlotArgs sa) {
       if (UPDATE) {
         r0 -= alpha * __ldcg(P.q + i0);
         P.r[i0] = r0;
+        P.xh[i0] = __ldcg(P.xh + i0) + alpha * __ldcg(P.p0 + i0);
         rr_acc += r0 * r0;
         if (a1) {
           r1 -= alpha * __ldcg(P.q + i1);
           P.r[i1] = r1;
+          P.xh[i1] = __ldcg(P.xh + i1) + alpha * __ldcg(P.p0 + i1);
           rr_acc += r1 * r1;
         }
       }
@@ -1189,20 +1196,12 @@ __global__ void __launch_bounds__(kVecThreads) pupdate_kernel(Params P) {
   pdl_trigger();
   pdl_wait();
   const double beta = __ldcg(&P.sc->beta);
-  // the previous iteration's x += alpha p (its p is about to be overwritten)
-  const bool pend = __ldcg(&P.sc->xpend) != 0;
-  const double alpha = __ldcg(&P.sc->alpha);
   const ZT *z = reinterpret_cast<const ZT *>(P.z);
   const int n2 = P.n / 2;
   const int stride = gridDim.x * blockDim.x;
   double2 *p2 = reinterpret_cast<double2 *>(P.p0);
-  double2 *x2 = reinterpret_cast<double2 *>(P.xh);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n2; k += stride) {
     const double2 pv = __ldcg(p2 + k);
-    if (pend) {
-      const double2 xv = __ldcg(x2 + k);
-      x2[k] = make_double2(xv.x + alpha * pv.x, xv.y + alpha * pv.y);
-    }
     double z0, z1;
     if (sizeof(ZT) == 8) {
       const double2 zv = __ldcg(reinterpret_cast<const double2 *>(z) + k);
@@ -1213,11 +1212,8 @@ __global__ void __launch_bounds__(kVecThreads) pupdate_kernel(Params P) {
     }
     p2[k] = make_double2(z0 + beta * pv.x, z1 + beta * pv.y);
   }
-  if ((P.n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-    const double pl = __ldcg(P.p0 + P.n - 1);
-    if (pend) P.xh[P.n - 1] = __ldcg(P.xh + P.n - 1) + alpha * pl;
-    P.p0[P.n - 1] = double(__ldcg(z + P.n - 1)) + beta * pl;
-  }
+  if ((P.n & 1) && blockIdx.x == 0 && threadIdx.x == 0)
+    P.p0[P.n - 1] = double(__ldcg(z + P.n - 1)) + beta * __ldcg(P.p0 + P.n - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -1287,7 +1283,6 @@ spmv_kernel(Params P) {
     if (threadIdx.x == 0) {
       P.sc->pq = pq;
       P.sc->alpha = __ldcg(&P.sc->rz) / pq;
-      P.sc->xpend = 1;   // x += alpha p is applied by the next p update or at the end
     }
   }
 }
@@ -1308,13 +1303,10 @@ __global__ void __launch_bounds__(kVecThreads) perm_in_kernel(Params P) {
 }
 
 // x[perm[i]] = x_hat[i] (x = 0 when b = 0)
-// x[perm] = x_hat, with the last iteration's pending x += alpha p
 __global__ void __launch_bounds__(kVecThreads) perm_out_kernel(Params P) {
   const bool zero = P.sc->bnorm == 0.0;
-  const bool pend = P.sc->xpend != 0;
-  const double alpha = P.sc->alpha;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x)
-    P.xout[P.perm[i]] = zero ? 0.0 : (pend ? P.xh[i] + alpha * P.p0[i] : P.xh[i]);
+    P.xout[P.perm[i]] = zero ? 0.0 : P.xh[i];
 }
 
 __global__ void __launch_bounds__(kVecThreads) permute_kernel(const double *src, double *dst, const int32_t *perm,
