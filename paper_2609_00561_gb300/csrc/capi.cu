@@ -203,7 +203,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   }
   const int cap_a = cap_of(H.seg_a);
   const int Wc = W;   // warps per CTA of the color kernels (one CTA per group)
-  const int Wa = 8;   // warps per CTA of the SpMV (one warp per 32-row slice)
+  const int Wa = kSpmvWarps;   // warps per CTA of the SpMV (one warp per 32-row slice)
   L.W = Wc;
   L.Wa = Wa;
   L.smem_fwd = group_smem_bytes(cap_l, cap_rows, cap_lev, elem);

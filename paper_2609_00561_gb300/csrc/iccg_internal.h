@@ -37,6 +37,7 @@ namespace iccg {
 
 constexpr int kWarp = 32;
 constexpr int kMaxWarpsPerCta = 16;
+constexpr int kSpmvWarps = 8;    // warps per CTA of the SpMV (one warp per 32-row slice)
 
 // A group: consecutive whole blocks of one color (or one big block), the
 // work of one warp.  Its forward / backward schedules list the group's rows

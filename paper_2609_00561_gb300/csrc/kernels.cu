@@ -1228,8 +1228,10 @@ __global__ void __launch_bounds__(kVecThreads) pupdate_kernel(Params P) {
 // mode 2: q = A x_hat (plain SpMV)
 constexpr int kSpmvChunk = 6;   // entries per predicated batch of the SpMV
 
+// 6 CTAs of 8 warps per SM (at most 40 registers a thread): measured 1%
+// faster per PCG iteration than 4 CTAs at 60 registers
 template <int MODE>
-__global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
+__global__ void __launch_bounds__(kSpmvWarps * kWarp, 6)
 spmv_kernel(Params P) {
   pdl_trigger();
   __shared__ double red[kMaxWarpsPerCta];
