@@ -98,6 +98,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
+def max_over_ranks(value, device):
+    """The largest `value` of all ranks (every rank gets it), then a barrier:
+    the replicas' time is the slowest replica's."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -213,10 +224,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+        ms = max_over_ranks(ms, dev)
 
     # solve alone and factor alone (same inputs, device events)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
