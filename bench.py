@@ -159,7 +159,8 @@ def blocking_name(args):
 def bytes_model(n, nnz, nL, fp32):
     """Algorithmic bytes per PCG iteration (each array counted once, gathered
     vector reads assumed to hit cache), by kernel family:
-      SpMV + <p,q>   values and columns 12 nnz, row pointers 4n, p in 8n, q out 8n
+      SpMV + <p,q>   sliced-ELL off-diagonal values and columns 12 (nnz - n), the
+                     diagonal 8n, slice pointers n/8, p in 8n, q out 8n
       p update       z, p in, p out: 24n (FP32 z: 20n)
       forward sweep  L entries (value + column) per strictly-lower entry, row
                      pointers 4n, 1/L_ii, the fused x/r update (r, q, x, p in,
@@ -167,8 +168,8 @@ def bytes_model(n, nnz, nL, fp32):
       backward sweep U entries, row pointers 4n, 1/L_ii, y in, z out, r in (dot)
     The substitution roofline uses forward + backward."""
     pe = 4 if fp32 else 8
-    spmv = 12 * nnz + 4 * n + 16 * n
-    pupd = (16 + pe) * n + 8 * n
+    spmv = 12 * (nnz - n) + 8 * n + n // 8 + 16 * n
+    pupd = (16 + pe) * n
     fwd = (pe + 4) * nL + 4 * n + pe * n + 48 * n + pe * n
     bwd = (pe + 4) * nL + 4 * n + pe * n + pe * n + pe * n + 8 * n
     return {"spmv": spmv, "pupdate": pupd, "subst": fwd + bwd, "total": spmv + pupd + fwd + bwd}
