@@ -6,7 +6,7 @@ The labels come from the label sweep (learn/sweep.py): for every generated
 matrix, the FP64 GPU ICCG solve time to 1e-8 under ABMC with each block size
 and under Leiden CPM with each resolution; the class label is the fastest
 block size, the regression label the log of the fastest resolution.  The
-exhaustive sweep is the model's judge (regret T(prediction) / T(best of the
+exhaustive sweep is the model's yardstick (regret T(prediction) / T(best of the
 sweep)) and its fallback (`choose` returns the swept optimum when a matrix
 was swept).
 
@@ -144,7 +144,7 @@ def evaluate(model, X, ta, tc, gammas, block_sizes):
     base_a = ta[:, block_sizes.index(BASE_BLOCK)]
     base_c = tc[:, gammas.index(BASE_GAMMA)]
     # the combined choice: the faster of the two predicted blockings vs the
-    # faster of the two fixed ones (both judged by the sweep's times)
+    # faster of the two fixed ones (both measured by the sweep's times)
     pred = np.minimum(t_abmc, t_cpm)
     best = np.minimum(best_a, best_c)
     base = np.minimum(base_a, base_c)
