@@ -1,6 +1,6 @@
 """Learned blocking end to end on the committed label sweep: the MLP is
-trained on the GPU by the library's kernels (160 matrices) and measured against the
-40 held-out matrices against the exhaustive sweep: what it gains over the
+trained on the GPU by the library's kernels (160 matrices) and evaluated on
+the 40 held-out matrices against the exhaustive sweep: what it gains over the
 method without it (fixed ABMC block size 32, fixed CPM resolution 0.05),
 and its regret against the best swept setting."""
 import os
