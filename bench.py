@@ -26,8 +26,14 @@ Multi-GPU: one system does not shard (every color needs the previous
 colors' results), so N > 1 runs N independent replicas, one per rank.
 
 --impl reference times the CPU oracle (single-threaded FP64) on the same
-workload: each step is IC(0) plus a bounded number of PCG iterations, scaled
-to the full solve's iteration count.
+workload: each step is the oracle's full solve, IC(0) plus PCG to the
+tolerance (about 9 s at 128^3).
+
+The default line also carries extension 1 (the FP32-preconditioner solve of
+the same system: time, iterations, error against the FP64 solve and the
+oracle) and a compact extension 2 figure (8 systems of config 4's recipe x 16
+right-hand sides in one launch, against the plain FP64 solver); --no-ext
+leaves them out.
 """
 from __future__ import annotations
 
@@ -127,17 +133,43 @@ WORKLOADS = {
 
 def workload(args):
     if args.workload == "diffusion96":
-        a = gen.diffusion3d_27pt(args.nx, seed=args.seed)
-        return a, gen.rhs_uniform(a.n, args.seed)
+        a, b, _ = gen.config3(nx=args.nx, seed=args.seed)
+        return a, b
     a, b, _ = gen.config2(nx=args.nx, seed=args.seed)
     return a, b
 
 
-# DRAM bytes (read + write) of the substitution sweep per PCG iteration,
-# from the ncu launch list of `bench.py --steps 1 --warmup 1 --no-cpu-baseline`
-# (profiles/launches_iccg_fp64_poisson128_cpm05.md), keyed by workload and
-# blocking; None where no capture of the current kernels exists.
-SUBST_TRAFFIC = {("poisson128", 128, "leiden_cpm", 0.5, False): 433152384}
+def workload_string(args, a, bl):
+    """The workload as both arms name it (same text: same configuration)."""
+    seed_b = args.seed + 1 if args.workload == "diffusion96" else args.seed
+    return (WORKLOADS[args.workload].format(nx=args.nx) + f" (n={a.n}, nnz={a.nnz}), b~U[-1,1] seed {seed_b}, "
+            f"{blocking_name(args)} + greedy coloring (n_b={bl['n_b']}, n_c={bl['n_c']}), "
+            f"IC(0) + PCG to {args.tol:g}" + (", FP32 preconditioner" if args.fp32 else ""))
+
+
+def kernels_sha():
+    """sha256 of the CUDA sources the substitution kernels are built from."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "iccg_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2609_00561_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(key):
+    """DRAM bytes (read + write) per PCG iteration of the substitution sweep
+    from the committed ncu summary (profiles/subst_traffic.json), or None when
+    there is none for this workload or the kernels changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "subst_traffic.json")
+    if not os.path.exists(path):
+        return None, "no capture"
+    d = json.load(open(path))
+    if d.get("kernels_sha256") != kernels_sha():
+        return None, "kernels changed since the last capture"
+    e = d.get("entries", {}).get(key)
+    if e is None:
+        return None, "no capture of this workload"
+    return int(e["subst_bytes_per_iteration"]), e.get("how", "ncu")
 
 
 def make_blocking(mod, a, args):
@@ -173,6 +205,26 @@ def bytes_model(n, nnz, nL, fp32):
     fwd = (pe + 4) * nL + 4 * n + pe * n + 48 * n + pe * n
     bwd = (pe + 4) * nL + 4 * n + pe * n + pe * n + pe * n + 8 * n
     return {"spmv": spmv, "pupdate": pupd, "subst": fwd + bwd, "total": spmv + pupd + fwd + bwd}
+
+
+def hbm_peak():
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(pk_path)) if os.path.exists(pk_path) else {}
+    return float(peaks.get("hbm_gbs", 6800.0)), ("measured" if "hbm_gbs" in peaks else "fallback")
+
+
+def time_steps(step, steps, stream):
+    """Device time per step (CUDA events on the launching stream)."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    out = None
+    for _ in range(steps):
+        out = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / steps, out
 
 
 def run_gpu(args):
@@ -215,48 +267,35 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            st, iters, _ = step()
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
+        ms, (st, iters, _) = time_steps(step, args.steps, stream)
     if world > 1:
         ms = max_over_ranks(ms, dev)
 
     # solve alone and factor alone (same inputs, device events)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(max(1, args.steps)):
-        iccg.iccg_factor(S.ctx)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    factor_ms = e0.elapsed_time(e1) / max(1, args.steps)
-    xd.zero_()
-    e0.record(stream)
-    st, iters, hist = iccg.iccg_solve(S.ctx, bd, xd, args.tol, args.maxit)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    solve_ms = e0.elapsed_time(e1)
+    factor_ms, _ = time_steps(lambda: iccg.iccg_factor(S.ctx), max(1, args.steps), stream)
+    solve_reps = max(1, min(args.steps, 5))
+
+    def solve_once():
+        xd.zero_()
+        return iccg.iccg_solve(S.ctx, bd, xd, args.tol, args.maxit, want_hist=False)
+
+    solve_ms, (st, iters, _) = time_steps(solve_once, solve_reps, stream)
     x = xd.cpu().numpy()
     true_rel = float(np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b))
 
-    # per-kernel-family device time of one solve (event pair around every launch)
-    xd.zero_()
-    _, it_p, phase_ms, phase_ln = iccg.iccg_profile_solve(S.ctx, bd, xd, args.tol, args.maxit)
+    # roofline of the substitution sweep from the graph-timed solve: an
+    # iteration's time minus its SpMV phase (p update + SpMV, event-timed in
+    # the same launch configuration); the solve start (one extra sweep, the
+    # residual SpMV, permutations) is charged to the sweep as well
+    spmv_phase_ms = iccg.iccg_time_spmv_phase(S.ctx, 50)
+    sweep_ms_it = solve_ms / max(iters, 1) - spmv_phase_ms
     bm = bytes_model(info["n"], info["nnz"], info["nL"], args.fp32)
-    sub_ms = phase_ms["fwd"] + phase_ms["fused"] + phase_ms["bwd"]
-    sub_launch = phase_ln["fwd"] + phase_ln["fused"] + phase_ln["bwd"]
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    achieved = bm["subst"] * it_p / (sub_ms * 1e-3) / 1e9 if sub_ms > 0 else 0.0
+    peak, peak_src = hbm_peak()
+    achieved = bm["subst"] / (sweep_ms_it * 1e-3) / 1e9 if sweep_ms_it > 0 else 0.0
+    it_achieved = bm["total"] * iters / (solve_ms * 1e-3) / 1e9
+    tkey = f"{args.workload}|{args.nx}|{blocking_name(args)}|{'fp32' if args.fp32 else 'fp64'}"
+    traffic, traffic_src = measured_traffic(tkey)
 
     # end-to-end through the C ABI with pinned host buffers
     bh = torch.tensor(b).pin_memory().numpy()
@@ -288,10 +327,7 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32+f64" if args.fp32 else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload].format(nx=args.nx) +
-                               f" (n={a.n}, nnz={a.nnz}), b~U[-1,1] seed {args.seed}, "
-                               f"{blocking_name(args)} + greedy coloring (n_b={bl['n_b']}, n_c={n_c}), "
-                               f"IC(0) + PCG to {args.tol:g}" + (", FP32 preconditioner" if args.fp32 else ""),
+        "config": {"workload": workload_string(args, a, bl),
                    "step": "iccg_factor + iccg_solve, inputs resident",
                    "l2": "inputs larger than L2 (matrix + factors > 129 MB)",
                    "parallelism": "replicas only" if world > 1 else "1 GPU",
@@ -304,30 +340,134 @@ def run_gpu(args):
         "factor_ms": round(factor_ms, 4),
         "us_per_iteration": round(solve_ms * 1e3 / max(iters, 1), 2),
         "setup": {"gen_s": round(t_gen, 3), "blocking_s": round(t_block, 3), "setup_s": round(t_setup, 3)},
-        "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()},
-        "phase_launches": phase_ln,
+        "per_iteration_us": {"spmv_phase": round(spmv_phase_ms * 1e3, 2), "sweep": round(sweep_ms_it * 1e3, 2),
+                             "how": "sweep = graph-timed solve / iterations - event-timed SpMV phase"},
         "roofline": {"bound": "hbm", "kernel": "block-multicolor substitution sweep (forward, fused and backward "
                                                "color launches of one PCG iteration)",
-                     "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                     "frac": round(achieved / hbm_peak, 4), "peak_source": peak_src,
-                     "bytes_per_iteration": bm["subst"], "launches_per_iteration": sub_launch / max(it_p, 1),
-                     "traffic": SUBST_TRAFFIC.get((args.workload, args.nx, args.blocking,
-                                                   args.gamma if args.blocking == "leiden_cpm" else args.block_size,
-                                                   bool(args.fp32))),
-                     "traffic_unit": "bytes per PCG iteration (ncu launch list, cold cache)"},
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                     "bytes_per_iteration": bm["subst"], "traffic": traffic, "traffic_source": traffic_src,
+                     "traffic_unit": "DRAM bytes per PCG iteration (ncu, cold cache)"},
+        "iteration_roofline": {"bytes_per_iteration": bm["total"], "achieved": round(it_achieved, 1),
+                               "frac": round(it_achieved / peak, 4)},
         "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": 2 * 8 * a.n,
                 "d2h_bytes_per_step": 8 * a.n},
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clk.summary(),
     }
+    if not args.no_ext and not args.fp32 and args.workload in ("poisson128", "diffusion96"):
+        result["ext_fp32_preconditioner"] = ext_fp32(args, a, b, bl, x, ms, stream, dev)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        result["cpu_baseline"] = cpu_baseline(a, b, bl, iters, args)
+        cb, xo, it_o = cpu_baseline(a, b, bl, args)
+        result["cpu_baseline"] = cb
+        result["parity_vs_oracle"] = {"oracle_iterations": it_o, "iterations": iters,
+                                      "rel_error": float(np.linalg.norm(x - xo) / np.linalg.norm(xo)),
+                                      "bar": "rel. error <= 1e-10, iterations +-1"}
+        if "ext_fp32_preconditioner" in result:
+            xf = result["ext_fp32_preconditioner"].pop("_x")
+            result["ext_fp32_preconditioner"]["rel_error_vs_oracle"] = float(
+                np.linalg.norm(xf - xo) / np.linalg.norm(xo))
+    if "ext_fp32_preconditioner" in result:
+        result["ext_fp32_preconditioner"].pop("_x", None)
+    S.close()
+    if not args.no_ext and world == 1 and args.workload == "poisson128":
+        result["ext_batched"] = ext_batched(args, stream, dev)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
-    S.close()
     if rank == 0:
         print(json.dumps(result))
+
+
+def ext_fp32(args, a, b, bl, x64, ms64, stream, dev):
+    """Extension 1 on the same system and blocking: FP32 factors and
+    substitutions, FP64 IC(0), CG scalars and x/r updates; same step."""
+    import torch
+    from paper_2609_00561_gb300 import iccg
+    S = iccg.Solver(a, bl, precond_fp32=True, stream=stream.cuda_stream, factor=False)
+    bd = torch.tensor(b, device=dev)
+    xd = torch.zeros_like(bd)
+
+    def step():
+        iccg.iccg_factor(S.ctx)
+        xd.zero_()
+        return iccg.iccg_solve(S.ctx, bd, xd, args.tol, args.maxit, want_hist=False)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    ms, (st, it, _) = time_steps(step, args.steps, stream)
+    x = xd.cpu().numpy()
+    S.close()
+    return {"ms_per_step": round(ms, 4), "iterations": it, "status": iccg.STATUS.get(st, st),
+            "true_relres": float(np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)),
+            "rel_error_vs_fp64_gpu": float(np.linalg.norm(x - x64) / np.linalg.norm(x64)),
+            "speedup_vs_fp64": round(ms64 / ms, 3), "_x": x}
+
+
+def ext_batched(args, stream, dev, nsys=8, nrhs=16):
+    """Extension 2, compact: 8 systems of config 4's recipe (sides U{16..64},
+    shifts U[1e-4, 1e-1]) x 16 right-hand sides, ABMC 32, FP32 preconditioner,
+    one launch; against the plain FP64 single-system solver run right-hand
+    side by right-hand side."""
+    import torch
+    import oracle
+    from paper_2609_00561_gb300 import iccg
+    systems, _ = gen.config4(seed=args.seed, nsys=nsys, nrhs=nrhs)
+    blocks = [iccg.blocking(a, "abmc", 32) for a, _ in systems]
+    solvers = [iccg.Solver(a, bl, precond_fp32=True, lane_block_max=-1, stream=stream.cuda_stream)
+               for (a, _), bl in zip(systems, blocks)]
+    bs = iccg.BatchSolver(solvers, nrhs)
+    B = [torch.tensor(b, device=dev) for _, b in systems]
+    X = [torch.zeros_like(t) for t in B]
+    bs.tune(B, args.tol, args.maxit)
+
+    def step():
+        for t in X:
+            t.zero_()
+        return bs.solve(B, X, args.tol, args.maxit)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    ms, (st, its, stv, _) = time_steps(step, args.steps, stream)
+    worst = 0.0
+    for (a, b), t in zip(systems, X):
+        m = a.to_scipy()
+        xs = t.cpu().numpy()
+        for j in range(nrhs):
+            worst = max(worst, float(np.linalg.norm(b[j] - m @ xs[j]) / np.linalg.norm(b[j])))
+    # the FP64 oracle on right-hand side 0 of the smallest system
+    k0 = int(np.argmin([a.n for a, _ in systems]))
+    a0, b0 = systems[k0]
+    ref = oracle.iccg(a0, b0[0], blocks[k0]["perm"], tol=args.tol, maxit=args.maxit)
+    x0 = X[k0].cpu().numpy()[0]
+    err0 = float(np.linalg.norm(x0 - ref["x"]) / np.linalg.norm(ref["x"]))
+    # plain FP64 single-system solver, right-hand side 0 of each system, x nrhs
+    single = 0.0
+    for (a, b), bl in zip(systems, blocks):
+        S1 = iccg.Solver(a, bl, stream=stream.cuda_stream)
+        bd = torch.tensor(b[0], device=dev)
+        xd = torch.zeros_like(bd)
+        iccg.iccg_solve(S1.ctx, bd, xd, args.tol, args.maxit, want_hist=False)
+
+        def one():
+            xd.zero_()
+            return iccg.iccg_solve(S1.ctx, bd, xd, args.tol, args.maxit, want_hist=False)
+
+        t1, _ = time_steps(one, 2, stream)
+        single += t1
+        S1.close()
+    single *= nrhs
+    shape = bs.info()
+    bs.close()
+    for S in solvers:
+        S.close()
+    return {"systems": nsys, "rhs_per_system": nrhs, "rows_total": int(sum(a.n for a, _ in systems)),
+            "ms_per_step": round(ms, 4), "rhs_solves_per_s": round(nsys * nrhs / (ms * 1e-3), 1),
+            "iterations": {"min": int(its.min()), "max": int(its.max())}, "status": iccg.STATUS.get(st, st),
+            "worst_true_relres": worst, "rel_error_vs_fp64_oracle_rhs0_smallest": err0,
+            "oracle_iterations": ref["iterations"], "gpu_iterations": int(its[k0, 0]),
+            "plain_fp64_single_solves_ms": round(single, 3), "speedup_vs_plain_fp64": round(single / ms, 2),
+            "shape": shape}
 
 
 def run_batch(args):
@@ -535,30 +675,35 @@ def run_learned(args):
         print(json.dumps(result))
 
 
-def oracle_sample(a, b, perm, sample_iters):
-    """IC(0) + `sample_iters` PCG iterations of the oracle; returns seconds."""
+def oracle_solve(a, b, perm, args):
+    """The oracle's full ICCG on the permuted system: IC(0), then PCG from
+    x0 = 0 to the tolerance.  The permutation and lower-triangle extraction
+    are setup (excluded like the GPU arm's).  Returns (IC(0) s, PCG s, x in
+    the original numbering, iterations)."""
     import oracle
-    t0 = time.perf_counter()
+    perm = np.asarray(perm, dtype=np.int64)
     ah = oracle.permute(a, perm)
     lptr, lcol, aval = oracle.tril_csr(ah)
-    t_perm = time.perf_counter() - t0
+    bh = np.asarray(b)[perm]
     t0 = time.perf_counter()
     lval, _ = oracle.ic0(lptr, lcol, aval)
     t_ic = time.perf_counter() - t0
     t0 = time.perf_counter()
-    oracle.pcg(ah, lptr, lcol, lval, b[perm], tol=0.0, maxit=sample_iters)
+    xh, it, _, _ = oracle.pcg(ah, lptr, lcol, lval, bh, tol=args.tol, maxit=args.maxit)
     t_pcg = time.perf_counter() - t0
-    return t_perm, t_ic, t_pcg
+    x = np.zeros(a.n)
+    x[perm] = xh
+    return t_ic, t_pcg, x, it
 
 
-def cpu_baseline(a, b, bl, iters_full, args):
-    tp, tic, tpcg = oracle_sample(a, b, bl["perm"], args.cpu_sample_iters)
-    per_it = tpcg / args.cpu_sample_iters
-    value_ms = (tic + per_it * iters_full) * 1e3
-    return {"value": round(value_ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"IC(0) + {args.cpu_sample_iters} PCG iterations of the FP64 oracle on the same permuted "
-                      f"matrix, scaled to the {iters_full} iterations of the full solve "
-                      f"({per_it * 1e3:.1f} ms/iteration, IC(0) {tic * 1e3:.0f} ms)"}
+def cpu_baseline(a, b, bl, args):
+    t_ic, t_pcg, x, it = oracle_solve(a, b, bl["perm"], args)
+    value_ms = (t_ic + t_pcg) * 1e3
+    cb = {"value": round(value_ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+          "sample": f"one full solve of the same workload by the FP64 oracle (single thread): IC(0) "
+                    f"{t_ic * 1e3:.0f} ms + PCG to {args.tol:g} in {it} iterations "
+                    f"({t_pcg * 1e3 / max(it, 1):.1f} ms/iteration)"}
+    return cb, x, it
 
 
 def run_reference(args):
@@ -566,27 +711,26 @@ def run_reference(args):
     if rank != 0:
         return
     # the reference arm never touches the GPU; blocking comes from the oracle
+    # (bit-identical to the library's), each step is the oracle's full solve
     import oracle
     a, b = workload(args)
     bl = make_blocking(oracle, a, args)
-    iters_full = args.ref_iters
-    times = []
+    times, its = [], []
     for k in range(args.warmup + args.steps):
-        tp, tic, tpcg = oracle_sample(a, b, bl["perm"], args.cpu_sample_iters)
-        t = tic + tpcg / args.cpu_sample_iters * iters_full
+        t_ic, t_pcg, _, it = oracle_solve(a, b, bl["perm"], args)
         if k >= args.warmup:
-            times.append(t)
+            times.append(t_ic + t_pcg)
+            its.append(it)
     ms = statistics.mean(times) * 1e3
+    sample = (f"each step: one full solve by the FP64 oracle (single thread), IC(0) + PCG to {args.tol:g} "
+              f"({its[-1]} iterations); permutation and blocking excluded as in the GPU arm")
     result = {"impl": "reference", "metric": "ICCG time to 1e-8 rel. residual", "value": round(ms, 1), "unit": "ms",
               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
-              "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-              "data": "synthetic",
-              "config": {"workload": WORKLOADS[args.workload].format(nx=args.nx) +
-                                     f", {blocking_name(args)} + greedy coloring, IC(0) + PCG to {args.tol:g} "
-                                     f"(CPU oracle)"},
-              "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-                               "sample": f"each step: IC(0) + {args.cpu_sample_iters} PCG iterations, scaled to "
-                                         f"{iters_full} iterations"},
+              "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+              "dtype": "f32+f64" if args.fp32 else "f64", "data": "synthetic",
+              "config": {"workload": workload_string(args, a, bl)},
+              "iterations": its[-1],
+              "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
               "e2e": {"value": round(ms, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(result))
 
@@ -609,11 +753,9 @@ def main():
     p.add_argument("--fp32", action="store_true", help="FP32 preconditioner (extension 1)")
     p.add_argument("--warps", type=int, default=0)
     p.add_argument("--rows", type=int, default=0)
-    p.add_argument("--cpu-sample-iters", type=int, default=20)
-    p.add_argument("--ref-iters", type=int, default=None,
-                   help="iterations the full solve takes (scales the reference sample; default: 183 for the "
-                        "default poisson128 blocking, else 176)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-ext", action="store_true",
+                   help="leave out the FP32-preconditioner and batched figures of the default line")
     p.add_argument("--nsys", type=int, default=64, help="batch64: systems")
     p.add_argument("--nrhs", type=int, default=16, help="batch64: right-hand sides per system")
     p.add_argument("--fp64-batch", action="store_true", help="batch64: FP64 preconditioner")
@@ -625,8 +767,6 @@ def main():
         args.block_size = 32 if args.workload in ("diffusion96", "batch64") else 8
     if args.blocking is None:
         args.blocking = "leiden_cpm" if args.workload == "poisson128" else "abmc"
-    if args.ref_iters is None:
-        args.ref_iters = 183 if (args.blocking, args.gamma) == ("leiden_cpm", 0.5) else 176
     if args.steps < 1 or args.warmup < 0:
         raise SystemExit("steps >= 1, warmup >= 0")
     if args.impl == "reference":

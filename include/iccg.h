@@ -141,10 +141,11 @@ iccg_status iccg_factor(iccg_ctx *ctx);
  *
  * b = 0 gives x = 0 and 0 iterations.  Returns ICCG_NOT_CONVERGED when maxit
  * is reached (x and history valid) and ICCG_ERR_NONFINITE on NaN/Inf.
- * Requires a successful iccg_factor.  The persistent solver (the default
- * where the device can hold all its CTAs at once) returns ICCG_ERR_TIMEOUT
- * when a grid-barrier wait gave up (a phase longer than 4 s); the context
- * stays usable and the phased solver (opts.solver) has no such limit.
+ * Requires a successful iccg_factor.  The persistent solver (opts.solver =
+ * ICCG_SOLVER_PERSISTENT; the default is the phased solver) returns
+ * ICCG_ERR_TIMEOUT when a grid-barrier wait gave up (a phase longer than the
+ * wait limit, 4 s unless iccg_set_wait_limit set another); the context stays
+ * usable and the phased solver has no device-side waits.
  * ------------------------------------------------------------------------ */
 iccg_status iccg_solve(iccg_ctx *ctx, const double *b, double *x, double tol, int32_t maxit,
                        int32_t *iters, double *res_hist);
@@ -173,6 +174,15 @@ iccg_status iccg_get_factor(iccg_ctx *ctx, double *lval, int64_t *nnz_lower);
 iccg_status iccg_profile_solve(iccg_ctx *ctx, const double *b, double *x, double tol,
                                int32_t maxit, int32_t *iters, double *ms, int64_t *launches);
 
+/* Device time of the SpMV phase as a PCG iteration of iccg_solve launches it
+ * (p = z + beta p, then q = A p with <p,q>: Table 8's "SpMV" part of an
+ * iteration), averaged over `reps` back-to-back launches on the context's
+ * stream after one warm-up (CUDA events, same launch attributes as the
+ * solve).  *ms receives milliseconds per phase.  Requires iccg_factor;
+ * overwrites the context's solve vectors (the next iccg_solve starts from its
+ * own inputs, so results are unaffected). */
+iccg_status iccg_time_spmv_phase(iccg_ctx *ctx, int32_t reps, double *ms);
+
 /* Layout facts of a context, out[13]: n, nnz, n_b, n_c, number of groups (a
  * group = consecutive whole blocks of one color, at most 32 * warps_per_cta *
  * rows_per_thread rows, or one larger block; one CTA each), number of groups
@@ -181,6 +191,13 @@ iccg_status iccg_profile_solve(iccg_ctx *ctx, const double *b, double *x, double
  * blocks, one per lane), number of colors run as lane tiles, number of
  * those run one warp per tile and as pair kernels (tile_mapping). */
 iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[13]);
+
+/* Wall-time limit (ns) of every device-side wait of this context's
+ * persistent solver (its grid barriers; Alg. 1's colors are separated by one
+ * barrier each there).  A wait that runs past it makes the kernel stop at
+ * once and iccg_solve return ICCG_ERR_TIMEOUT; the context stays usable.
+ * 0 restores the default (4 s).  The phased solver has no device-side waits. */
+iccg_status iccg_set_wait_limit(iccg_ctx *ctx, uint64_t wait_ns);
 
 iccg_status iccg_last_error(const iccg_ctx *ctx, int64_t *row_or_block, const char **msg);
 void iccg_destroy(iccg_ctx *ctx);
@@ -218,6 +235,10 @@ void iccg_destroy(iccg_ctx *ctx);
  *                      B = NULL, random right-hand sides for 20 iterations;
  *                      the fastest is kept and *best_ms (may be NULL) gets
  *                      its time.
+ *   iccg_batch_set_wait_limit  wall-time limit (ns) of the per-system barrier
+ *                      waits inside the batched kernel (0: the default, 4 s);
+ *                      a system whose wait runs out stops and its right-hand
+ *                      sides report ICCG_ERR_TIMEOUT; the batch stays usable.
  *   iccg_batch_info    out[6]: warps per CTA, CTAs per SM, grid, padded nrhs,
  *                      largest block, 3 x the exponent e of the CTA split
  *                      (CTAs per system proportional to n^e; e = 1 or 4/3,
@@ -239,6 +260,7 @@ iccg_status iccg_batch_solve(iccg_batch *batch, const double *const *B, double *
                              int32_t maxit, int32_t *iters, int32_t *status, double *const *res_hist);
 iccg_status iccg_batch_tune(iccg_batch *batch, const double *const *B, double tol, int32_t maxit,
                             double *best_ms);
+iccg_status iccg_batch_set_wait_limit(iccg_batch *batch, uint64_t wait_ns);
 iccg_status iccg_batch_info(const iccg_batch *batch, int32_t out[6]);
 iccg_status iccg_batch_last_error(const iccg_batch *batch, const char **msg);
 void iccg_batch_destroy(iccg_batch *batch);
@@ -247,15 +269,16 @@ void iccg_batch_destroy(iccg_batch *batch);
  * iccg_spmv_dot_noalloc -- q = A p and *pq = <p, q> with no device
  * allocation at all.  The paper has no counterpart: this entry point exists
  * for callers that cannot allocate device memory where they need the
- * product (code recorded inside a CUDA stream capture, latency-critical loops
- * that must not meet the allocator's implicit synchronisation, host
- * frameworks that own all device memory through their own pool).
+ * product (latency-critical loops that must not meet the allocator's
+ * implicit device synchronisation, host frameworks that own all device
+ * memory through their own pool and forbid allocations behind their back).
  *
  *   n                       rows, 0 <= n <= ICCG_NOALLOC_MAX_ROWS (else ICCG_ERR_ARG)
  *   rowptr, colind, val     CSR of A (int64 rowptr, int32 colind, FP64), DEVICE pointers
  *   p                       double[n] device input;  q  double[n] device output
  *   pq                      one double, device output
- *   stream                  the CUDA stream to run on
+ *   stream                  the CUDA stream to run on; it must belong to the
+ *                           current device (else ICCG_ERR_ARG, nothing launched)
  *
  * Scratch (one partial per CTA and the reduction's arrival counters, about
  * 137 KB) is a fixed array in the library's device image, held by every GPU
@@ -264,6 +287,8 @@ void iccg_batch_destroy(iccg_batch *batch);
  * overlaps on the GPU race and give wrong results.  The first call on each
  * device looks up the array's address (cudaGetSymbolAddress); make that first
  * call before any stream capture.  The sum is deterministic (fixed order).
+ * ICCG_ERR_CUDA when a CUDA call of this entry point failed (an error left
+ * pending by earlier unrelated work is not consumed).
  * ------------------------------------------------------------------------ */
 #define ICCG_NOALLOC_MAX_ROWS 4194304
 iccg_status iccg_spmv_dot_noalloc(int32_t n, const int64_t *rowptr, const int32_t *colind,

@@ -35,7 +35,6 @@ namespace iccg {
 namespace {
 
 constexpr int kBatchMaxBlock = 64;   // rows of a block (a chain's scratch in shared memory)
-constexpr unsigned long long kBatchWaitNs = 4000000000ull;
 constexpr long long kBatchSpinLimit = 1ll << 27;
 
 struct BatchSys {
@@ -57,6 +56,7 @@ struct BatchSys {
   int32_t *iters;          // [kp]
   int32_t *status;         // [kp] per right-hand side
   GridBar *bar;
+  unsigned long long wait_ns;   // bounded barrier wait (ns)
 };
 
 template <typename PT> __device__ __forceinline__ const PT *b_lv(const BatchSys &S);
@@ -83,7 +83,8 @@ __device__ __forceinline__ unsigned long long b_ns() {
 
 // Barrier over the nct CTAs of one system, with a bounded wait (false for
 // the whole CTA when this or another CTA of the system gave up).
-__device__ __forceinline__ bool sys_sync(GridBar *bar, unsigned nct, unsigned &gen, int *flag) {
+__device__ __forceinline__ bool sys_sync(GridBar *bar, unsigned nct, unsigned &gen, int *flag,
+                                         unsigned long long wait_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
@@ -95,9 +96,11 @@ __device__ __forceinline__ bool sys_sync(GridBar *bar, unsigned nct, unsigned &g
       atomicExch(&bar->gen, gen + 1);
     } else {
       const unsigned long long t0 = b_ns();
+      // the clock is read on every poll (a short limit must take effect at
+      // the first poll); the error word of other CTAs every 64 polls
       for (long long k = 1; b_ld_acquire(&bar->gen) == gen; ++k) {
-        if ((k & 63) == 0 &&
-            (k > kBatchSpinLimit || b_ns() - t0 > kBatchWaitNs || b_ld_acquire(&bar->err) != 0u)) {
+        if (b_ns() - t0 > wait_ns || k > kBatchSpinLimit ||
+            ((k & 63) == 0 && b_ld_acquire(&bar->err) != 0u)) {
           atomicExch(&bar->err, 1u);
           ok = 0;
           break;
@@ -191,7 +194,7 @@ __device__ __forceinline__ bool batch_precond(const BatchSys &S, PT *w, int kp, 
     }
     // every color's results (for the last color: its z) complete before the
     // next color reads them
-    if (!sys_sync(S.bar, nct, gen, flag)) return false;
+    if (!sys_sync(S.bar, nct, gen, flag, S.wait_ns)) return false;
   }
   for (int c = nc - 2; c >= 0; --c) {
     const int b1 = __ldg(S.cblk + c + 1);
@@ -211,7 +214,7 @@ __device__ __forceinline__ bool batch_precond(const BatchSys &S, PT *w, int kp, 
         rz += __ldcg(S.r + size_t(i) * kp + j) * double(zi);
       }
     }
-    if (c > 0 && !sys_sync(S.bar, nct, gen, flag)) return false;
+    if (c > 0 && !sys_sync(S.bar, nct, gen, flag, S.wait_ns)) return false;
   }
   return true;
 }
@@ -252,7 +255,7 @@ batch_kernel(const BatchSys *sys, const int32_t *cta_sys, int k, int kp, int sma
     acc += bi * bi;
   }
   cta_rhs_sum(acc, red, kp, nchain, mypart + 0 * kp);
-  ok = sys_sync(S.bar, nct, gen, &flag);
+  ok = sys_sync(S.bar, nct, gen, &flag, S.wait_ns);
   // r0 = b - A x0, <r0, r0> (a row's b is read and r written by its own lane)
   if (ok) {
     acc = 0.0;
@@ -266,14 +269,14 @@ batch_kernel(const BatchSys *sys, const int32_t *cta_sys, int k, int kp, int sma
       acc += ri * ri;
     }
     cta_rhs_sum(acc, red, kp, nchain, mypart + 1 * kp);
-    ok = sys_sync(S.bar, nct, gen, &flag);
+    ok = sys_sync(S.bar, nct, gen, &flag, S.wait_ns);
   }
   // z0 = M^-1 r0, <r0, z0>
   double rr = 0.0, rz = 0.0;
   if (ok) ok = batch_precond<PT, false>(S, w, kp, j, gc, total, 0.0, false, rr, rz, nct, gen, &flag);
   if (ok) {
     cta_rhs_sum(rz, red, kp, nchain, mypart + 3 * kp);
-    ok = sys_sync(S.bar, nct, gen, &flag);
+    ok = sys_sync(S.bar, nct, gen, &flag, S.wait_ns);
   }
   int it = 0;
   if (ok) {
@@ -317,7 +320,7 @@ batch_kernel(const BatchSys *sys, const int32_t *cta_sys, int k, int kp, int sma
     if (act)
       for (int i = gc; i < n; i += total)
         S.p[size_t(i) * kp + j] = double(__ldcg(z + size_t(i) * kp + j)) + beta * __ldcg(S.p + size_t(i) * kp + j);
-    if (!(ok = sys_sync(S.bar, nct, gen, &flag))) break;
+    if (!(ok = sys_sync(S.bar, nct, gen, &flag, S.wait_ns))) break;
     // q = A p, <p, q>
     acc = 0.0;
     if (act) {
@@ -331,7 +334,7 @@ batch_kernel(const BatchSys *sys, const int32_t *cta_sys, int k, int kp, int sma
       }
     }
     cta_rhs_sum(acc, red, kp, nchain, mypart + 2 * kp);
-    if (!(ok = sys_sync(S.bar, nct, gen, &flag))) break;
+    if (!(ok = sys_sync(S.bar, nct, gen, &flag, S.wait_ns))) break;
     sys_rhs_sum(S.part, int(nct), kp, 2, sv[2]);
     const double alpha = act ? st_rz[j] / sv[2][j] : 0.0;
     // x / r update, z = M^-1 r, <r,r>, <r,z>
@@ -340,7 +343,7 @@ batch_kernel(const BatchSys *sys, const int32_t *cta_sys, int k, int kp, int sma
     if (!(ok = batch_precond<PT, true>(S, w, kp, j, gc, total, alpha, act, rr, rz, nct, gen, &flag))) break;
     cta_rhs_sum(rr, red, kp, nchain, mypart + 1 * kp);
     cta_rhs_sum(rz, red, kp, nchain, mypart + 3 * kp);
-    if (!(ok = sys_sync(S.bar, nct, gen, &flag))) break;
+    if (!(ok = sys_sync(S.bar, nct, gen, &flag, S.wait_ns))) break;
     sys_rhs_sum(S.part, int(nct), kp, 1, sv[1]);
     sys_rhs_sum(S.part, int(nct), kp, 3, sv[3]);
     ++it;
@@ -430,6 +433,7 @@ struct iccg_batch {
   int graph_maxit = -1;
   double graph_tol = -1.0;
   bool direct = false;   // the runtime refused to capture the cooperative launch: launch it directly
+  unsigned long long wait_ns = kDefaultWaitNs;   // barrier wait limit of the batched kernel
   std::string err_msg;
 };
 
@@ -540,6 +544,7 @@ iccg_status upload_plan(iccg_batch *b, int maxit) {
     S.iters = b->iters[s];
     S.status = b->status[s];
     S.bar = b->bars + s;
+    S.wait_ns = b->wait_ns;
     for (int g = S.cta0; g < S.cta1; ++g) cs[g] = s;
   }
   if (cudaMemcpyAsync(b->d_sys, hs.data(), sizeof(BatchSys) * hs.size(), cudaMemcpyHostToDevice, b->stream) !=
@@ -875,6 +880,13 @@ iccg_status iccg_batch_tune(iccg_batch *b, const double *const *B, double tol, i
   if (best_ms) *best_ms = best;
   b->wexp = bE;
   return set_shape(b, bW, bC, sms);
+}
+
+iccg_status iccg_batch_set_wait_limit(iccg_batch *b, uint64_t wait_ns) {
+  if (!b) return ICCG_ERR_ARG;
+  b->wait_ns = wait_ns ? wait_ns : kDefaultWaitNs;
+  destroy_batch_graph(b);   // the next solve uploads the descriptors again
+  return ICCG_OK;
 }
 
 iccg_status iccg_batch_info(const iccg_batch *b, int32_t out[6]) {

@@ -414,6 +414,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     CK(dev_alloc(ctx, &P.ui_val32, H.ui_col.size()), "alloc tiles");
   }
   CK(dev_alloc(ctx, &P.bar, 1), "alloc barrier");
+  P.wait_ns = kDefaultWaitNs;
   P.arp = d_arp; P.acol = d_acol; P.aval = d_aval;
   P.lrp = d_lrp; P.lcol = d_lcol; P.urp = d_urp; P.ucol = d_ucol; P.umap = d_umap;
   P.ainit = d_ainit; P.adiag = d_adiag;
@@ -635,7 +636,7 @@ static iccg_status solve_impl(iccg_ctx *ctx, const double *b, double *x, double 
   if (iters) *iters = it;
   if (sh->status == ICCG_ERR_TIMEOUT) {
     ctx->err_index = -1;
-    ctx->err_msg = "a grid-barrier wait of the persistent solve gave up";
+    ctx->err_msg = "a grid-barrier wait of the persistent solve gave up (iccg_set_wait_limit)";
   }
   if (res_hist) {
     CK(cudaMemcpyAsync(ctx->hist_host, ctx->hist, sizeof(double) * size_t(it + 1), cudaMemcpyDeviceToHost, s), "history");
@@ -744,6 +745,38 @@ iccg_status iccg_profile_solve(iccg_ctx *ctx, const double *b, double *x, double
   return st;
 }
 
+iccg_status iccg_time_spmv_phase(iccg_ctx *ctx, int32_t reps, double *ms) {
+  if (!ctx || reps < 1 || !ms) return ICCG_ERR_ARG;
+  DeviceGuard guard(ctx->device);
+  if (!ctx->factored) return ICCG_ERR_STATE;
+  *ms = 0.0;
+  if (ctx->H.n == 0) return ICCG_OK;
+  cudaStream_t s = ctx->stream;
+  // beta = 0: every repetition computes p = z (no growth of p across them)
+  static const double zero = 0.0;
+  CK(cudaMemcpyAsync(&ctx->P.sc->beta, &zero, sizeof(double), cudaMemcpyHostToDevice, s), "scalars");
+  CK(cudaStreamSynchronize(s), "sync");
+  cudaEvent_t a0, a1;
+  CK(cudaEventCreate(&a0), "event");
+  if (cudaEventCreate(&a1) != cudaSuccess) {
+    cudaEventDestroy(a0);
+    return cuda_fail(ctx, cudaGetLastError(), "event");
+  }
+  struct FreeEv {
+    cudaEvent_t a, b;
+    ~FreeEv() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } fe{a0, a1};
+  CK(launch_spmv_phase(ctx->P, ctx->plan, ctx->fp32), "spmv phase");   // warm-up
+  CK(cudaEventRecord(a0, s), "event");
+  for (int32_t k = 0; k < reps; ++k) CK(launch_spmv_phase(ctx->P, ctx->plan, ctx->fp32), "spmv phase");
+  CK(cudaEventRecord(a1, s), "event");
+  CK(cudaStreamSynchronize(s), "sync");
+  float t = 0.f;
+  CK(cudaEventElapsedTime(&t, a0, a1), "event");
+  *ms = double(t) / double(reps);
+  return ICCG_OK;
+}
+
 iccg_status iccg_precond(iccg_ctx *ctx, const double *r, double *z) {
   if (!ctx) return ICCG_ERR_ARG;
   DeviceGuard guard(ctx->device);
@@ -833,6 +866,12 @@ iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[13]) {
     out[11] += w == 1 ? 1 : 0;
     out[12] += w == 2 ? 1 : 0;
   }
+  return ICCG_OK;
+}
+
+iccg_status iccg_set_wait_limit(iccg_ctx *ctx, uint64_t wait_ns) {
+  if (!ctx) return ICCG_ERR_ARG;
+  ctx->P.wait_ns = wait_ns ? wait_ns : kDefaultWaitNs;
   return ICCG_OK;
 }
 

@@ -54,6 +54,7 @@ struct __align__(16) GroupDesc {
 };
 
 constexpr int kGroup = 32;   // CTAs per first-level reduction group
+constexpr unsigned long long kDefaultWaitNs = 4000000000ull;   // device-side wait limit (4 s)
 
 // A lane tile: rows [row0, row0 + nrows), step descriptors steps[step0 ..
 // step0 + nsteps); its sliced-ELL entries are the contiguous ranges
@@ -216,6 +217,7 @@ struct Params {
   // persistent solve: first group of each color [n_c + 1], grid barrier
   const int32_t *color_group;
   GridBar *bar;
+  unsigned long long wait_ns;   // bounded grid-barrier wait (ns)
   // optional phase trace of the persistent solve: (ns << 4 | phase) per
   // barrier, written by CTA 0 (null: off); trace_len receives the count
   unsigned long long *trace;
@@ -311,6 +313,8 @@ int pair_resident_ctas(bool fp32, int threads);              // CTAs per SM of t
 cudaError_t launch_factor(const Params &P, const Plan &L, int nL);
 cudaError_t launch_solve_init(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);
 cudaError_t launch_solve_body(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);
+// the SpMV phase of a PCG iteration: p = z + beta p, then q = A p and <p,q>
+cudaError_t launch_spmv_phase(const Params &P, const Plan &L, bool fp32);
 cudaError_t launch_solve_final(const Params &P, const Plan &L);
 // bytes per CTA of the persistent kernel within max(group plan, budget);
 // *cap_spmv = staged SpMV entries per warp

@@ -1432,10 +1432,10 @@ __global__ void __launch_bounds__(kVecThreads) factor_finish_kernel(Params P, in
 // across the barriers in between.
 // ---------------------------------------------------------------------------
 
-// A barrier wait gives up after kWaitNs of wall time (or kSpinLimit polls,
-// whichever comes first): long enough for any phase of a solve the shared
-// memory plan admits, short enough that a missing CTA cannot hang the device.
-constexpr unsigned long long kWaitNs = 4000000000ull;
+// A barrier wait gives up after P.wait_ns of wall time (default 4 s, settable
+// per context) or kSpinLimit polls, whichever comes first: long enough for any
+// phase of a solve the shared-memory plan admits, short enough that a missing
+// CTA cannot hang the device.
 constexpr long long kSpinLimit = 1ll << 27;
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
@@ -1452,7 +1452,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Sense-reversing grid barrier with a bounded wait.  Returns false (for the
 // whole CTA) when this CTA or another one gave up; the error word stays set.
-__device__ __forceinline__ bool grid_sync(GridBar *bar, unsigned &gen, int *flag) {
+__device__ __forceinline__ bool grid_sync(GridBar *bar, unsigned &gen, int *flag, unsigned long long wait_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
@@ -1464,9 +1464,11 @@ __device__ __forceinline__ bool grid_sync(GridBar *bar, unsigned &gen, int *flag
       atomicExch(&bar->gen, gen + 1);
     } else {
       const unsigned long long t0 = global_ns();
+      // the clock is read on every poll (a short limit must take effect at
+      // the first poll); the error word of other CTAs every 64 polls
       for (long long k = 1; ld_acquire_u32(&bar->gen) == gen; ++k) {
-        if ((k & 63) == 0 &&
-            (k > kSpinLimit || global_ns() - t0 > kWaitNs || ld_acquire_u32(&bar->err) != 0u)) {
+        if (global_ns() - t0 > wait_ns || k > kSpinLimit ||
+            ((k & 63) == 0 && ld_acquire_u32(&bar->err) != 0u)) {
           atomicExch(&bar->err, 1u);
           ok = 0;
           break;
@@ -1490,10 +1492,11 @@ struct GridSync {
   int *flag;
   unsigned long long *trace;
   int tk, cap;
+  unsigned long long wait_ns;
 };
 
 __device__ __forceinline__ bool phase_end(GridSync &s, int tag) {
-  const bool ok = grid_sync(s.bar, s.gen, s.flag);
+  const bool ok = grid_sync(s.bar, s.gen, s.flag, s.wait_ns);
   if (s.trace && blockIdx.x == 0 && threadIdx.x == 0 && s.tk < s.cap)
     s.trace[s.tk++] = (global_ns() << 4) | unsigned(tag);
   return ok;
@@ -1667,7 +1670,7 @@ persistent_kernel(Params P, GroupSmemPlan plan, int cap_a) {
   const int tid = threadIdx.x, nthr = blockDim.x, nb = gridDim.x, b = blockIdx.x;
   const int gstride = nb * nthr, gi = b * nthr + tid;
   unsigned char *smem_a = smem + plan.o_w + plan.total;   // SpMV staging
-  GridSync gs{P.bar, 0u, &flag, P.trace, 0, P.trace_cap};
+  GridSync gs{P.bar, 0u, &flag, P.trace, 0, P.trace_cap, P.wait_ns};
   Scalars *S = P.sc;
   const double tol = __ldcg(&S->tol);
   const int maxit = __ldcg(&S->maxit);
@@ -2075,11 +2078,16 @@ cudaError_t launch_solve_init(const Params &P, const Plan &L, bool fp32, PhaseHo
   return e;
 }
 
-cudaError_t launch_solve_body(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u) {
-  if (h) h(u, PH_SPMV, 1);
+cudaError_t launch_spmv_phase(const Params &P, const Plan &L, bool fp32) {
   cudaError_t e = fp32 ? launch(pupdate_kernel<float>, L.grid_v, kVecThreads, 0, L, P)
                        : launch(pupdate_kernel<double>, L.grid_v, kVecThreads, 0, L, P);
   if (e == cudaSuccess) e = launch_spmv<0>(P, L);
+  return e;
+}
+
+cudaError_t launch_solve_body(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u) {
+  if (h) h(u, PH_SPMV, 1);
+  cudaError_t e = launch_spmv_phase(P, L, fp32);
   if (h) h(u, PH_SPMV, 0);
   if (e != cudaSuccess) return e;
   return fp32 ? sweep<float>(P, L, true, FIN_ITER, h, u) : sweep<double>(P, L, true, FIN_ITER, h, u);

@@ -1,11 +1,11 @@
 // iccg_spmv_dot_noalloc: q = A p and <p, q> without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// sparse product: code recorded inside a CUDA stream capture (an allocation
-// there either breaks the capture or is not allowed), latency-critical loops
-// that must not pay for the allocator's implicit synchronisation, and host
-// frameworks that own all device memory through their own pool and forbid
-// raw cudaMalloc.  This entry point serves them: the caller passes every
+// sparse product: latency-critical loops that must not pay for the
+// allocator's implicit device synchronisation, and host frameworks that own
+// all device memory through their own pool and forbid raw cudaMalloc (an
+// allocation behind their back would break their accounting or fail under
+// their memory cap).  This entry point serves them: the caller passes every
 // input and output as device pointers, and the only scratch the kernel needs
 // (one partial sum per CTA plus the arrival counters of the deterministic
 // two-level reduction) lives in a fixed file-scope __device__ array.
@@ -19,7 +19,8 @@
 //
 // The first call on each device looks up the array's device address with
 // cudaGetSymbolAddress (with that device current) and caches it; make that
-// first call before any stream capture starts.
+// first call before any stream capture starts.  The stream must belong to the
+// current device (the cached address is that device's copy of the array).
 #include <mutex>
 
 #include "iccg_internal.h"
@@ -115,20 +116,22 @@ extern "C" iccg_status iccg_spmv_dot_noalloc(int32_t n, const int64_t *rowptr, c
   if (!pq || (n > 0 && (!rowptr || !colind || !val || !p || !q))) return ICCG_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ICCG_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the scratch address below is the current device's copy: a stream of
+  // another device would run the kernel against the wrong GPU's memory
+  int sdev = -1;
+  if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) return ICCG_ERR_ARG;
+  if (sdev != dev) return ICCG_ERR_ARG;
   NaScratch *s = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_na_mutex);
     if (!g_na_ptr[dev]) {
       void *addr = nullptr;
-      if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) {
-        cudaGetLastError();
-        return ICCG_ERR_CUDA;
-      }
+      if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) return ICCG_ERR_CUDA;
       g_na_ptr[dev] = static_cast<NaScratch *>(addr);
     }
     s = g_na_ptr[dev];
   }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (n == 0) return cudaMemsetAsync(pq, 0, sizeof(double), st) == cudaSuccess ? ICCG_OK : ICCG_ERR_CUDA;
   const int grid = (n + kNaRowsPerCta - 1) / kNaRowsPerCta;
   const int ngroups = (grid + kNaGroup - 1) / kNaGroup;
@@ -137,6 +140,13 @@ extern "C" iccg_status iccg_spmv_dot_noalloc(int32_t n, const int64_t *rowptr, c
   if (cudaMemsetAsync(s->gticket, 0, sizeof(unsigned int) * size_t(ngroups), st) != cudaSuccess ||
       cudaMemsetAsync(&s->ticket, 0, sizeof(unsigned int), st) != cudaSuccess)
     return ICCG_ERR_CUDA;
-  spmv_dot_noalloc_kernel<<<grid, kNaRowsPerCta, 0, st>>>(n, rowptr, colind, val, p, q, pq, s);
-  return cudaGetLastError() == cudaSuccess ? ICCG_OK : ICCG_ERR_CUDA;
+  // the launch's own status (cudaGetLastError would also report, and clear,
+  // an error that earlier unrelated work of the caller left pending)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(unsigned(kNaRowsPerCta));
+  cfg.stream = st;
+  return cudaLaunchKernelEx(&cfg, spmv_dot_noalloc_kernel, n, rowptr, colind, val, p, q, pq, s) == cudaSuccess
+             ? ICCG_OK
+             : ICCG_ERR_CUDA;
 }

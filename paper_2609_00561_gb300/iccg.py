@@ -67,7 +67,9 @@ def load():
         "iccg_get_factor": [vp, vp, P(i64)],
         "iccg_profile_solve": [vp, vp, vp, d, i32, P(i32), vp, vp],
         "iccg_info": [vp, vp],
+        "iccg_time_spmv_phase": [vp, i32, P(d)],
         "iccg_last_error": [vp, P(i64), P(ctypes.c_char_p)],
+        "iccg_set_wait_limit": [vp, u64],
         "iccg_graph": [i32, vp, vp, vp, vp, P(i64)],
         "iccg_block_abmc": [i32, vp, vp, i32, vp, P(i32)],
         "iccg_block_leiden": [i32, vp, vp, i32, d, i32, d, u64, vp, P(i32)],
@@ -84,6 +86,7 @@ def load():
         "iccg_batch_solve": [vp, vp, vp, d, i32, vp, vp, vp],
         "iccg_batch_tune": [vp, vp, d, i32, P(d)],
         "iccg_batch_info": [vp, vp],
+        "iccg_batch_set_wait_limit": [vp, u64],
         "iccg_batch_last_error": [vp, P(ctypes.c_char_p)],
     }
     for name, args in sig.items():
@@ -212,6 +215,14 @@ def iccg_profile_solve(ctx, b, x, tol=1e-8, maxit=10000):
     return st, it.value, dict(zip(PHASES, ms.tolist())), dict(zip(PHASES, ln.tolist()))
 
 
+def iccg_time_spmv_phase(ctx, reps=50):
+    """Milliseconds of one SpMV phase (p update + SpMV with <p,q>) of a PCG
+    iteration, averaged over `reps` back-to-back launches."""
+    ms = ctypes.c_double(0.0)
+    _check(load().iccg_time_spmv_phase(ctx, int(reps), ctypes.byref(ms)), "iccg_time_spmv_phase", ctx)
+    return ms.value
+
+
 INFO_KEYS = ("n", "nnz", "n_b", "n_c", "groups", "global_groups", "nL", "max_levels", "max_group_rows", "tiles",
              "tile_colors", "warp_tile_colors", "pair_tile_colors")
 
@@ -227,6 +238,11 @@ def iccg_last_error(ctx):
     m = ctypes.c_char_p()
     load().iccg_last_error(ctx, ctypes.byref(i), ctypes.byref(m))
     return i.value, (m.value or b"").decode()
+
+
+def iccg_set_wait_limit(ctx, wait_ns):
+    """Device-side wait limit (ns) of the persistent solver; 0 = default."""
+    return _check(load().iccg_set_wait_limit(ctx, int(wait_ns)), "iccg_set_wait_limit", ctx)
 
 
 def iccg_destroy(ctx):
@@ -389,6 +405,10 @@ class BatchSolver:
         out = np.zeros(6, dtype=np.int32)
         _batch_check(load().iccg_batch_info(self.h, _ptr(out)), "iccg_batch_info", self.h)
         return dict(zip(("warps_per_cta", "ctas_per_sm", "grid", "kp", "smax", "split_exp_x3"), out.tolist()))
+
+    def set_wait_limit(self, wait_ns):
+        """iccg_batch_set_wait_limit: barrier wait limit (ns); 0 = default."""
+        _batch_check(load().iccg_batch_set_wait_limit(self.h, int(wait_ns)), "iccg_batch_set_wait_limit", self.h)
 
     def tune(self, B=None, tol=1e-8, maxit=10000):
         """Shape search on B (x0 = 0, to tol) or, without B, a random probe."""

@@ -46,14 +46,18 @@ def test_max_over_ranks_two_gloo_ranks():
 def test_reference_arm_prints_on_rank_zero_only():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--nx", "16",
-                        "--steps", "1", "--warmup", "0", "--cpu-sample-iters", "2"],
+                        "--steps", "1", "--warmup", "0"],
                        capture_output=True, text=True, env=env, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == ""
     env.update(RANK="0", LOCAL_RANK="0")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--nx", "16",
-                        "--steps", "1", "--warmup", "0", "--cpu-sample-iters", "2"],
+                        "--steps", "1", "--warmup", "0"],
                        capture_output=True, text=True, env=env, timeout=300)
     assert r.returncode == 0
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "ms" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    # the full workload (sizes, blocking, colors) as the GPU arm names it
+    wl = line["config"]["workload"]
+    assert "n=4096" in wl and "n_b=" in wl and "n_c=" in wl and "Leiden CPM resolution 0.5" in wl
+    assert line["iterations"] > 0
