@@ -249,7 +249,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
     S = iccg.Solver(a, bl, precond_fp32=args.fp32, warps_per_cta=args.warps, rows_per_thread=args.rows,
-                    stream=stream.cuda_stream, factor=False)
+                    stream=stream.cuda_stream, factor=False, no_graph=args.no_graph, lane_block_max=args.lane_max,
+                    tile_mapping=args.tile_mapping)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     info = S.info()
@@ -332,7 +333,7 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (matrix + factors > 129 MB)",
                    "parallelism": "replicas only" if world > 1 else "1 GPU",
                    "layout": f"{info['tile_colors']} of {n_c} colors as lane tiles ({info['tiles']} tiles), "
-                             f"{info['groups']} CTA groups"},
+                             f"{info['unit_colors']} as warp units, {info['groups']} CTA groups"},
         "iterations": iters,
         "status": iccg.STATUS.get(st, st),
         "true_relres": true_rel,
@@ -751,9 +752,14 @@ def main():
     p.add_argument("--tol", type=float, default=1e-8)
     p.add_argument("--maxit", type=int, default=5000)
     p.add_argument("--fp32", action="store_true", help="FP32 preconditioner (extension 1)")
-    p.add_argument("--warps", type=int, default=0)
-    p.add_argument("--rows", type=int, default=0)
+    p.add_argument("--warps", type=int, default=0, help="warps per CTA of the substitution kernels (0: 8)")
+    p.add_argument("--rows", type=int, default=0, help="rows per thread of a CTA group (0: 1)")
+    p.add_argument("--lane-max", type=int, default=0,
+                   help="largest block run as lane tiles (0: 32, -1: none, every color as CTA groups)")
+    p.add_argument("--tile-mapping", default="auto", choices=["auto", "cta", "warp", "pair", "units"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-graph", action="store_true",
+                   help="drive the PCG loop from the host (every kernel a separate launch, e.g. for ncu)")
     p.add_argument("--no-ext", action="store_true",
                    help="leave out the FP32-preconditioner and batched figures of the default line")
     p.add_argument("--nsys", type=int, default=64, help="batch64: systems")

@@ -74,20 +74,28 @@ typedef struct {
                                  one CTA per group of blocks, level by level; 1..32,
                                  0 = 32, -1 = never (the persistent solver never
                                  uses lanes) */
-  int32_t tile_mapping;       /* lane-tile colors: ICCG_TILES_CTA runs one CTA per tile
-                                 (the tile's steps shared out over its warps, the
-                                 in-block recurrence on one warp); ICCG_TILES_WARP
-                                 one warp per tile (all steps in order, many tiles
-                                 per CTA); ICCG_TILES_PAIR: colors of blocks of one
-                                 or two rows one warp per tile with the block's rows
-                                 in registers (pair kernels), other colors one CTA
-                                 per tile; ICCG_TILES_AUTO (0): pair kernels for the
+  int32_t tile_mapping;       /* colors whose blocks have at most lane_block_max rows:
+                                 ICCG_TILES_UNITS runs the colors of blocks of 3..32
+                                 rows as warp units (one warp per block, a lane per
+                                 row, the in-block recurrence as a shuffle-broadcast
+                                 column sweep; blocks of up to 4, 8 or 16 rows share
+                                 a warp) and the others as lane tiles like
+                                 ICCG_TILES_AUTO; lane tiles (32 blocks, one per
+                                 lane): ICCG_TILES_CTA runs one CTA per tile (the
+                                 tile's steps shared out over its warps, the in-block
+                                 recurrence on one warp); ICCG_TILES_WARP one warp
+                                 per tile (all steps in order, many tiles per CTA);
+                                 ICCG_TILES_PAIR: colors of blocks of one or two rows
+                                 one warp per tile with the block's rows in registers
+                                 (pair kernels), other colors one CTA per tile;
+                                 ICCG_TILES_AUTO (0): warp units for colors whose
+                                 largest block has 5..32 rows, pair kernels for the
                                  colors whose blocks all have two rows, one CTA per
                                  tile otherwise */
 } iccg_opts;
 
 enum { ICCG_SOLVER_AUTO = 0, ICCG_SOLVER_PERSISTENT = 1, ICCG_SOLVER_PHASED = 2 };
-enum { ICCG_TILES_AUTO = 0, ICCG_TILES_CTA = 1, ICCG_TILES_WARP = 2, ICCG_TILES_PAIR = 3 };
+enum { ICCG_TILES_AUTO = 0, ICCG_TILES_CTA = 1, ICCG_TILES_WARP = 2, ICCG_TILES_PAIR = 3, ICCG_TILES_UNITS = 4 };
 
 /* ------------------------------------------------------------------------
  * iccg_setup -- Sec. 3: the block-multicolor ordering renumbers rows color
@@ -183,14 +191,15 @@ iccg_status iccg_profile_solve(iccg_ctx *ctx, const double *b, double *x, double
  * own inputs, so results are unaffected). */
 iccg_status iccg_time_spmv_phase(iccg_ctx *ctx, int32_t reps, double *ms);
 
-/* Layout facts of a context, out[13]: n, nnz, n_b, n_c, number of groups (a
+/* Layout facts of a context, out[14]: n, nnz, n_b, n_c, number of groups (a
  * group = consecutive whole blocks of one color, at most 32 * warps_per_cta *
  * rows_per_thread rows, or one larger block; one CTA each), number of groups
  * too large for the shared-memory plan, strictly-lower entries nL, deepest
  * in-group level count, largest group (rows), number of lane tiles (32
  * blocks, one per lane), number of colors run as lane tiles, number of
- * those run one warp per tile and as pair kernels (tile_mapping). */
-iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[13]);
+ * those run one warp per tile and as pair kernels (tile_mapping), number of
+ * colors run as warp units. */
+iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[14]);
 
 /* Wall-time limit (ns) of every device-side wait of this context's
  * persistent solver (its grid barriers; Alg. 1's colors are separated by one
@@ -335,15 +344,16 @@ iccg_status iccg_color_order(int32_t n, const int64_t *gptr, const int32_t *gadj
 
 /* Diagnostics (host only, no device): builds the layout iccg_setup would
  * build for these inputs (groups of at most group_rows rows, lane tiles for
- * colors of blocks of at most lane_max rows, 0 = none) and checks the index
- * ranges the kernels rely on.  report[4]: lane tiles, groups, failed checks,
- * the tile / group / color of the first failure (-1 none); *what (may be
- * NULL) names the first failed check.  ICCG_OK, ICCG_ERR_STATE when a check
- * failed, or the validation error of iccg_setup. */
+ * colors of blocks of at most lane_max rows, 0 = none; with use_units, warp
+ * units for colors of blocks of 3..32 rows) and checks the index ranges and
+ * orderings the kernels rely on.  report[4]: lane tiles plus warp units,
+ * groups, failed checks, the tile / unit / group / color of the first failure
+ * (-1 none); *what (may be NULL) names the first failed check.  ICCG_OK,
+ * ICCG_ERR_STATE when a check failed, or the validation error of iccg_setup. */
 iccg_status iccg_check_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
                               const double *val, const int32_t *perm, const int32_t *block_ptr,
                               const int32_t *color_ptr, int32_t n_b, int32_t n_c, int32_t group_rows,
-                              int32_t lane_max, int64_t report[4], const char **what);
+                              int32_t lane_max, int32_t use_units, int64_t report[4], const char **what);
 
 /* ------------------------------------------------------------------------
  * Learned blocking (extension; the paper selects block sizes and

@@ -127,7 +127,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   if (!rowptr || (n > 0 && (!colind || !val || !perm || !block_ptr || !color_ptr))) return ICCG_ERR_ARG;
   iccg_opts o{};
   if (opts) o = *opts;
-  if (o.tile_mapping < ICCG_TILES_AUTO || o.tile_mapping > ICCG_TILES_PAIR) return ICCG_ERR_ARG;
+  if (o.tile_mapping < ICCG_TILES_AUTO || o.tile_mapping > ICCG_TILES_UNITS) return ICCG_ERR_ARG;
   if (o.lane_block_max > 32 || o.lane_block_max < -1) return ICCG_ERR_ARG;
   if (o.solver < ICCG_SOLVER_AUTO || o.solver > ICCG_SOLVER_PHASED) return ICCG_ERR_ARG;
   if (o.warps_per_cta == 0) o.warps_per_cta = 8;
@@ -162,8 +162,14 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   // lane tiles for colors of small blocks; the persistent kernel runs groups only
   const int lane_max = o.solver == ICCG_SOLVER_PERSISTENT || o.lane_block_max < 0 ? 0
                        : (o.lane_block_max == 0 ? 32 : o.lane_block_max);
+  // warp units (one warp per block, a lane per row): automatically for colors
+  // of blocks of 5..32 rows (on a GB300 12% faster than lane tiles at 8 rows,
+  // 2.7x at 32, 2.5% slower at 4), explicitly from 3 rows
+  const int32_t unit_min = lane_max <= 0 ? 0
+                           : o.tile_mapping == ICCG_TILES_UNITS ? 3
+                           : o.tile_mapping == ICCG_TILES_AUTO ? 5 : 0;
   iccg_status st = build_layout(n, nnz, hrp.data(), hci.data(), hval.data(), hperm.data(), hbp.data(),
-                                hcp.data(), n_b, n_c, G, lane_max, ctx->H, ctx->err_index, ctx->err_msg);
+                                hcp.data(), n_b, n_c, G, lane_max, unit_min, ctx->H, ctx->err_index, ctx->err_msg);
   if (st != ICCG_OK) return st;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaGetDevice");
   {
@@ -273,6 +279,10 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   const int pr_full = H.tile_colors > 0 ? sms * pair_resident_ctas(ctx->fp32, L.Ww * kWarp) : 1;
   L.wtile.assign(n_c, 0);
   L.stage_ext.assign(n_c, 0);
+  L.unit0.assign(n_c, 0);
+  L.unit1.assign(n_c, 0);
+  L.unit_S.assign(n_c, 0);
+  L.Wu = 8;
   int32_t gbig = 1;
   for (int c = 0; c < n_c; ++c) {
     L.task0[c] = H.color_group[c];
@@ -300,7 +310,15 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     // other colors and row vectors (measured 3% faster in FP64 and 14% in
     // FP32 at blocks of 1-2 rows; slower for tiles of 8 steps)
     L.stage_ext[c] = L.cap_to > 0 && steps <= 2;
-    if (L.wtile[c] == 1) L.grid_c[c] = std::min((nt + L.Ww - 1) / L.Ww, wt_full);
+    L.unit0[c] = H.color_unit[c];
+    L.unit1[c] = H.color_unit[c + 1];
+    L.unit_S[c] = H.unit_S[c];
+    const int nu = L.unit1[c] - L.unit0[c];
+    if (nu > 0) {
+      L.wtile[c] = 3;
+      const int full = sms * unit_resident_ctas(ctx->fp32, L.unit_S[c], L.Wu * kWarp);
+      L.grid_c[c] = std::max(1, std::min((nu + L.Wu - 1) / L.Wu, full));
+    } else if (L.wtile[c] == 1) L.grid_c[c] = std::min((nt + L.Ww - 1) / L.Ww, wt_full);
     else if (L.wtile[c] == 2) L.grid_c[c] = std::min((nt + L.Ww - 1) / L.Ww, pr_full);
     else L.grid_c[c] = nt > 0 ? std::min(nt, L.stage_ext[c] ? tile_full_x : tile_full)
                               : std::max(1, L.task1[c] - L.task0[c]);
@@ -370,9 +388,40 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   CK(dev_upload(ctx, &d_sb, H.sched_b), "alloc groups");
   CK(dev_upload(ctx, &d_levp, H.levp), "alloc groups");
   CK(dev_upload(ctx, &d_perm, H.perm), "alloc perm");
+  {
+    int32_t *d_fr;
+    CK(dev_upload(ctx, &d_fr, H.fac_rows), "alloc factor schedule");
+    P.fac_rows = d_fr;
+    L.fac_ptr = H.fac_ptr;
+    L.fac_lev0 = H.fac_lev0;
+    L.fac_nlev = H.fac_nlev;
+  }
   int32_t *d_cg;
   CK(dev_upload(ctx, &d_cg, H.color_group), "alloc groups");
   P.color_group = d_cg;
+  {
+    WarpUnit *d_units;
+    uint32_t *d_wlm, *d_wum;
+    int32_t *d_wlmap, *d_wlsr, *d_wumap, *d_wusr, *d_bptr;
+    CK(dev_upload(ctx, &d_units, H.units), "alloc units");
+    CK(dev_upload(ctx, &d_wlm, H.wl_mask), "alloc units");
+    CK(dev_upload(ctx, &d_wum, H.wu_mask), "alloc units");
+    CK(dev_upload(ctx, &d_wlmap, H.wl_map), "alloc units");
+    CK(dev_upload(ctx, &d_wlsr, H.wl_srow), "alloc units");
+    CK(dev_upload(ctx, &d_wumap, H.wu_map), "alloc units");
+    CK(dev_upload(ctx, &d_wusr, H.wu_srow), "alloc units");
+    CK(dev_upload(ctx, &d_bptr, H.block_ptr), "alloc units");
+    P.units = d_units;
+    P.wl_mask = d_wlm; P.wu_mask = d_wum;
+    P.wl_map = d_wlmap; P.wl_srow = d_wlsr; P.wu_map = d_wumap; P.wu_srow = d_wusr;
+    P.bptr = d_bptr;
+    P.nwl = int32_t(H.wl_map.size());
+    P.nwu = int32_t(H.wu_map.size());
+    CK(dev_alloc(ctx, &P.wl_val, H.wl_map.size()), "alloc units");
+    CK(dev_alloc(ctx, &P.wu_val, H.wu_map.size()), "alloc units");
+    CK(dev_alloc(ctx, &P.wl_val32, H.wl_map.size()), "alloc units");
+    CK(dev_alloc(ctx, &P.wu_val32, H.wu_map.size()), "alloc units");
+  }
   {
     TileDesc *d_tiles;
     StepDesc *d_steps;
@@ -846,7 +895,7 @@ iccg_status iccg_get_factor(iccg_ctx *ctx, double *lval, int64_t *nnz_lower) {
   return ICCG_OK;
 }
 
-iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[13]) {
+iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[14]) {
   if (!ctx || !out) return ICCG_ERR_ARG;
   const HostLayout &H = ctx->H;
   out[0] = H.n;
@@ -866,6 +915,7 @@ iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[13]) {
     out[11] += w == 1 ? 1 : 0;
     out[12] += w == 2 ? 1 : 0;
   }
+  out[13] = H.unit_colors;
   return ICCG_OK;
 }
 

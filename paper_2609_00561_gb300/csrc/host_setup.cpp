@@ -26,7 +26,7 @@ iccg_status fail(iccg_status st, int64_t idx, const char *what, int64_t &bad, st
 iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
                          const double *val, const int32_t *perm, const int32_t *block_ptr,
                          const int32_t *color_ptr, int32_t n_b, int32_t n_c, int32_t group_rows,
-                         int32_t lane_max, HostLayout &H, int64_t &bad, std::string &msg) {
+                         int32_t lane_max, int32_t unit_min, HostLayout &H, int64_t &bad, std::string &msg) {
   bad = -1;
   if (n < 0 || nnz < 0 || nnz >= (int64_t(1) << 31)) return fail(ICCG_ERR_ARG, -1, "n or nnz out of range", bad, msg);
   if (n > 0 && (n_b < 1 || n_c < 1 || n_b > n || n_c > n_b)) return fail(ICCG_ERR_ARG, -1, "n_b / n_c out of range", bad, msg);
@@ -126,6 +126,18 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
   // active at a step are a prefix), its rows stored step-major per tile
   lane_max = std::max(0, std::min(lane_max, 32));
   std::vector<char> tcol(n_c > 0 ? n_c : 1, 0);
+  // warp units: colors whose largest block has unit_min..32 rows (when
+  // enabled, unit_min >= 3); they keep the caller's row order
+  std::vector<char> wcol(n_c > 0 ? n_c : 1, 0);
+  H.unit_colors = 0;
+  for (int32_t c = 0; c < n_c && unit_min > 0; ++c) {
+    int32_t mb = 0;
+    for (int32_t j = color_ptr[c]; j < color_ptr[c + 1]; ++j) mb = std::max(mb, block_ptr[j + 1] - block_ptr[j]);
+    if (mb >= std::max(unit_min, 3) && mb <= kWarp) {
+      wcol[c] = 1;
+      H.unit_colors++;
+    }
+  }
   H.ord.resize(n);
   for (int32_t i = 0; i < n; ++i) H.ord[i] = i;
   H.lane_max = 0;
@@ -133,6 +145,7 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
   struct TileRows { int32_t row0, nsteps, nlanes; std::vector<int32_t> cnt; };
   std::vector<std::vector<TileRows>> ctiles(n_c > 0 ? n_c : 1);
   for (int32_t c = 0; c < n_c && lane_max > 0; ++c) {
+    if (wcol[c]) continue;
     int32_t mb = 0;
     for (int32_t j = color_ptr[c]; j < color_ptr[c + 1]; ++j) mb = std::max(mb, block_ptr[j + 1] - block_ptr[j]);
     if (mb > lane_max) continue;
@@ -319,6 +332,40 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
     }
   }
   H.color_tile[n_c] = int32_t(H.tiles.size());
+  // IC(0) schedule of the lane-tile and warp-unit colors: a row's in-block level is one
+  // more than the deepest earlier row of its block it refers to (internal
+  // numbering: earlier steps of a block have smaller indices); the rows of a
+  // level depend only on earlier levels and earlier colors
+  H.fac_rows.clear();
+  H.fac_ptr.assign(1, 0);
+  H.fac_lev0.assign(n_c + 1, 0);
+  H.fac_nlev.assign(n_c + 1, 0);
+  {
+    std::vector<int32_t> lev(n, 0), cnt;
+    for (int32_t c = 0; c < n_c; ++c) {
+      H.fac_lev0[c] = int32_t(H.fac_ptr.size()) - 1;
+      if (!tcol[c] && !wcol[c]) continue;
+      const int32_t r0 = block_ptr[color_ptr[c]], r1 = block_ptr[color_ptr[c + 1]];
+      int32_t depth = 0;
+      for (int32_t i = r0; i < r1; ++i) {
+        int32_t lv = 0;
+        for (int32_t e = H.lrp[i]; e < H.lrp[i + 1]; ++e)
+          if (H.lcol[e] >= r0 && iblk[H.lcol[e]] == iblk[i]) lv = std::max(lv, lev[H.lcol[e]] + 1);
+        lev[i] = lv;
+        depth = std::max(depth, lv + 1);
+      }
+      cnt.assign(size_t(depth) + 1, 0);
+      for (int32_t i = r0; i < r1; ++i) cnt[size_t(lev[i]) + 1]++;
+      for (int32_t v = 0; v < depth; ++v) cnt[size_t(v) + 1] += cnt[size_t(v)];
+      const int32_t base = int32_t(H.fac_rows.size());
+      H.fac_rows.resize(size_t(base) + size_t(r1 - r0));
+      std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+      for (int32_t i = r0; i < r1; ++i) H.fac_rows[size_t(base + fill[size_t(lev[i])]++)] = i;
+      for (int32_t v = 1; v <= depth; ++v) H.fac_ptr.push_back(base + cnt[size_t(v)]);
+      H.fac_nlev[c] = depth;
+    }
+    H.fac_lev0[n_c] = int32_t(H.fac_ptr.size()) - 1;
+  }
   // tiles of at most two steps, each in one descriptor
   H.pairs.assign(H.tiles.size(), PairDesc{});
   for (size_t t = 0; t < H.tiles.size(); ++t) {
@@ -334,7 +381,91 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
       pd.c1 = s1.cnt; pd.lw1 = s1.lw; pd.liw1 = s1.liw; pd.uw1 = s1.uw; pd.li = s1.li;
     }
   }
+  // warp units: 32 / S blocks per warp, lane l = row l % S of block l / S
+  H.color_unit.assign(n_c + 1, 0);
+  H.unit_S.assign(n_c + 1, 0);
+  H.units.clear();
+  H.wl_mask.clear(); H.wu_mask.clear();
+  H.wl_map.clear(); H.wl_srow.clear(); H.wu_map.clear(); H.wu_srow.clear();
+  {
+    std::vector<std::vector<int32_t>> se(kWarp), sw(kWarp);
+    // appends the per-lane lists sliced-ELL over 32 lanes, padding (pad, -1)
+    auto slab = [&](std::vector<std::vector<int32_t>> &a, std::vector<std::vector<int32_t>> &b,
+                    std::vector<int32_t> &oa, std::vector<int32_t> &ob, int32_t pad) {
+      int32_t w = 0;
+      for (int l = 0; l < kWarp; ++l) w = std::max(w, int32_t(a[size_t(l)].size()));
+      for (int32_t j = 0; j < w; ++j)
+        for (int l = 0; l < kWarp; ++l) {
+          const bool ok = j < int32_t(a[size_t(l)].size());
+          oa.push_back(ok ? a[size_t(l)][size_t(j)] : pad);
+          ob.push_back(ok ? b[size_t(l)][size_t(j)] : -1);
+        }
+      return w;
+    };
+    for (int32_t c = 0; c < n_c; ++c) {
+      H.color_unit[c] = int32_t(H.units.size());
+      if (!wcol[c]) continue;
+      int32_t mb = 0;
+      for (int32_t j = color_ptr[c]; j < color_ptr[c + 1]; ++j) mb = std::max(mb, block_ptr[j + 1] - block_ptr[j]);
+      int32_t S = 4;
+      while (S < mb) S <<= 1;
+      H.unit_S[c] = S;
+      const int32_t per = kWarp / S;
+      for (int32_t j = color_ptr[c]; j < color_ptr[c + 1]; j += per) {
+        WarpUnit u{};
+        u.blk0 = j;
+        u.nblk = std::min(per, color_ptr[c + 1] - j);
+        u.row0 = block_ptr[j];
+        u.nrows = block_ptr[j + u.nblk] - u.row0;
+        std::vector<int32_t> lrow(kWarp, -1);
+        for (int l = 0; l < kWarp; ++l) {
+          const int32_t b = j + l / S;
+          if (l / S < u.nblk && block_ptr[b] + l % S < block_ptr[b + 1]) lrow[size_t(l)] = block_ptr[b] + l % S;
+        }
+        for (int pass = 0; pass < 2; ++pass) {
+          const std::vector<int32_t> &rp = pass ? H.urp : H.lrp, &cols = pass ? H.ucol : H.lcol;
+          // entries to other colors
+          for (int l = 0; l < kWarp; ++l) {
+            se[size_t(l)].clear();
+            sw[size_t(l)].clear();
+            const int32_t i = lrow[size_t(l)];
+            if (i < 0) continue;
+            for (int32_t e = rp[size_t(i)]; e < rp[size_t(i) + 1]; ++e)
+              if (iblk[cols[size_t(e)]] != iblk[i]) {
+                se[size_t(l)].push_back(cols[size_t(e)]);
+                sw[size_t(l)].push_back(pass ? H.umap[size_t(e)] : e);
+              }
+          }
+          if (pass == 0) { u.lo = int32_t(H.sl_col.size()); u.lw = slab(se, sw, H.sl_col, H.sl_map, kPadCol); }
+          else { u.uo = int32_t(H.su_col.size()); u.uw = slab(se, sw, H.su_col, H.su_map, kPadCol); }
+          // in-block coefficients (ascending column) and the lane masks
+          for (int l = 0; l < kWarp; ++l) {
+            se[size_t(l)].clear();
+            sw[size_t(l)].clear();
+            uint32_t mask = 0;
+            const int32_t i = lrow[size_t(l)];
+            if (i >= 0) {
+              const int32_t base = block_ptr[iblk[i]];
+              for (int32_t e = rp[size_t(i)]; e < rp[size_t(i) + 1]; ++e) {
+                const int32_t k = cols[size_t(e)];
+                if (iblk[k] != iblk[i]) continue;
+                mask |= 1u << (k - base);
+                se[size_t(l)].push_back(pass ? H.umap[size_t(e)] : e);
+                sw[size_t(l)].push_back(k);
+              }
+            }
+            (pass ? H.wu_mask : H.wl_mask).push_back(mask);
+          }
+          if (pass == 0) { u.li = int32_t(H.wl_map.size()); u.liw = slab(se, sw, H.wl_map, H.wl_srow, -1); }
+          else { u.ui = int32_t(H.wu_map.size()); u.uiw = slab(se, sw, H.wu_map, H.wu_srow, -1); }
+        }
+        H.units.push_back(u);
+      }
+    }
+    H.color_unit[n_c] = int32_t(H.units.size());
+  }
   const size_t lim = size_t(1) << 31;
+  if (H.wl_map.size() >= lim || H.wu_map.size() >= lim) return fail(ICCG_ERR_ARG, -1, "warp-unit layout exceeds 2^31 entries", bad, msg);
   if (H.sl_col.size() >= lim || H.su_col.size() >= lim || H.si_col.size() >= lim || H.ui_col.size() >= lim)
     return fail(ICCG_ERR_ARG, -1, "lane-tile layout exceeds 2^31 entries", bad, msg);
 
@@ -345,7 +476,7 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
   H.color_group.assign(n_c + 1, 0);
   for (int32_t c = 0; c < n_c; ++c) {
     H.color_group[c] = int32_t(gr0.size());
-    if (tcol[c]) continue;
+    if (tcol[c] || wcol[c]) continue;
     int32_t j = color_ptr[c];
     while (j < color_ptr[c + 1]) {
       int32_t end = j + 1;
@@ -496,14 +627,15 @@ struct Checker {
 extern "C" iccg_status iccg_check_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
                                          const double *val, const int32_t *perm, const int32_t *block_ptr,
                                          const int32_t *color_ptr, int32_t n_b, int32_t n_c, int32_t group_rows,
-                                         int32_t lane_max, int64_t report[4], const char **what) {
+                                         int32_t lane_max, int32_t use_units, int64_t report[4],
+                                         const char **what) {
   using namespace iccg;
   if (!report || !rowptr) return ICCG_ERR_ARG;
   HostLayout H;
   int64_t bad = -1;
   std::string msg;
   const iccg_status st = build_layout(n, nnz, rowptr, colind, val, perm, block_ptr, color_ptr, n_b, n_c,
-                                      std::max(group_rows, 1), lane_max, H, bad, msg);
+                                      std::max(group_rows, 1), lane_max, use_units ? 3 : 0, H, bad, msg);
   report[0] = report[1] = report[2] = report[3] = 0;
   if (st != ICCG_OK) {
     report[3] = bad;
@@ -616,13 +748,84 @@ extern "C" iccg_status iccg_check_layout(int32_t n, int64_t nnz, const int64_t *
       }
     }
   }
-  // every color either tiles or groups, covering its rows
+  // IC(0) schedule of the lane-tile colors: every row of the color once, and
+  // every in-block reference of a row at an earlier level
+  {
+    std::vector<int32_t> level(size_t(n), -1);
+    for (int c = 0; c < n_c; ++c) {
+      const bool tile = H.color_tile[size_t(c) + 1] > H.color_tile[size_t(c)] ||
+                        H.color_unit[size_t(c) + 1] > H.color_unit[size_t(c)];
+      if (!tile) { ck(H.fac_nlev[size_t(c)] == 0, c, "factor schedule of a group color"); continue; }
+      const int32_t r0 = H.block_ptr[size_t(H.color_ptr[size_t(c)])], r1 = H.block_ptr[size_t(H.color_ptr[size_t(c) + 1])];
+      int64_t seen = 0;
+      for (int v = 0; v < H.fac_nlev[size_t(c)]; ++v) {
+        const int32_t k0 = H.fac_ptr[size_t(H.fac_lev0[size_t(c)] + v)], k1 = H.fac_ptr[size_t(H.fac_lev0[size_t(c)] + v + 1)];
+        ck(k0 <= k1, c, "factor level pointers");
+        for (int32_t k = k0; k < k1; ++k) {
+          const int32_t i = H.fac_rows[size_t(k)];
+          const bool in = i >= r0 && i < r1;
+          ck(in && level[size_t(std::max(0, std::min(i, n - 1)))] < 0, c, "factor schedule rows");
+          if (in) level[size_t(i)] = v;
+          ++seen;
+        }
+      }
+      ck(seen == r1 - r0, c, "factor schedule covers the color");
+      for (int32_t i = r0; i < r1; ++i)
+        for (int32_t e = H.lrp[size_t(i)]; e < H.lrp[size_t(i) + 1]; ++e) {
+          const int32_t j = H.lcol[size_t(e)];
+          if (j >= r0) ck(level[size_t(j)] >= 0 && level[size_t(j)] < level[size_t(i)], c, "factor schedule order");
+        }
+    }
+  }
+  // warp units: lanes on the rows of their blocks, masks naming earlier (L)
+  // or later (U) rows of the lane's own block, one coefficient per set bit in
+  // ascending column order, entries to other colors outside the block
+  for (int c = 0; c < n_c; ++c) {
+    const int S = H.unit_S[size_t(c)];
+    for (int32_t t = H.color_unit[size_t(c)]; t < H.color_unit[size_t(c) + 1]; ++t) {
+      const WarpUnit &u = H.units[size_t(t)];
+      ck(S >= 4 && S <= kWarp && (S & (S - 1)) == 0 && u.nblk >= 1 && u.nblk <= kWarp / S, t, "unit shape");
+      ck(u.blk0 >= H.color_ptr[size_t(c)] && u.blk0 + u.nblk <= H.color_ptr[size_t(c) + 1], t, "unit blocks");
+      ck(u.row0 == H.block_ptr[size_t(u.blk0)] && u.row0 + u.nrows == H.block_ptr[size_t(u.blk0 + u.nblk)], t, "unit rows");
+      for (int l = 0; l < kWarp; ++l) {
+        const int32_t b = u.blk0 + l / S;
+        const bool on = l / S < u.nblk && H.block_ptr[size_t(b)] + l % S < H.block_ptr[size_t(b) + 1];
+        const int32_t i = on ? H.block_ptr[size_t(b)] + l % S : -1;
+        for (int pass = 0; pass < 2; ++pass) {
+          const uint32_t m = (pass ? H.wu_mask : H.wl_mask)[size_t(t) * kWarp + l];
+          const int32_t off = pass ? u.ui : u.li, w = pass ? u.uiw : u.liw;
+          const std::vector<int32_t> &mp = pass ? H.wu_map : H.wl_map, &sr = pass ? H.wu_srow : H.wl_srow;
+          if (!on) { ck(m == 0u, t, "idle lane mask"); continue; }
+          const int step = l % S;
+          ck(pass ? (m & ((2u << step) - 1u)) == 0u : (m >> step) == 0u, t, "mask direction");
+          int j = 0;
+          for (int k = 0; k < S; ++k) {
+            if (!((m >> k) & 1u)) continue;
+            const size_t e = size_t(off) + size_t(j) * kWarp + size_t(l);
+            ck(j < w && sr[e] == H.block_ptr[size_t(b)] + k && mp[e] >= 0 && mp[e] < H.nL, t, "unit coefficient");
+            ++j;
+          }
+          for (; j < w; ++j) ck(mp[size_t(off) + size_t(j) * kWarp + size_t(l)] == -1, t, "unit coefficient padding");
+          const int32_t eo = pass ? u.uo : u.lo, ew = pass ? u.uw : u.lw;
+          const std::vector<int32_t> &ec = pass ? H.su_col : H.sl_col;
+          for (int32_t q = 0; q < ew; ++q) {
+            const int32_t col = ec[size_t(eo) + size_t(q) * kWarp + size_t(l)];
+            ck(col == kPadCol || (col >= 0 && col < n && (pass ? col > i : col < i) &&
+                                  (col < H.block_ptr[size_t(b)] || col >= H.block_ptr[size_t(b) + 1])),
+               t, "unit entry to another color");
+          }
+        }
+      }
+    }
+  }
+  // every color tiles, groups or units, covering its rows
   for (int c = 0; c < n_c; ++c) {
     const bool tile = H.color_tile[size_t(c) + 1] > H.color_tile[size_t(c)];
     const bool grp = H.color_group[size_t(c) + 1] > H.color_group[size_t(c)];
-    ck(tile != grp, c, "color layout");
+    const bool unit = H.color_unit[size_t(c) + 1] > H.color_unit[size_t(c)];
+    ck(int(tile) + int(grp) + int(unit) == 1, c, "color layout");
   }
-  report[0] = int64_t(H.tiles.size());
+  report[0] = int64_t(H.tiles.size() + H.units.size());
   report[1] = int64_t(H.groups.size());
   report[2] = ck.failed;
   report[3] = ck.first;

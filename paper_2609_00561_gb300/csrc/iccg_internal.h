@@ -81,6 +81,18 @@ struct __align__(16) StepDesc {
 struct __align__(16) PairDesc {
   int32_t row0, c0, c1, lo, lw0, lw1, li, liw1, uo, uw0, uw1, ui, uiw0, pad0, pad1, pad2;
 };
+// A warp unit (colors whose blocks have 3..32 rows): 32 / S consecutive
+// blocks of one color, each at most S rows (S a power of two), one warp;
+// lane l holds row l % S of block blk0 + l / S (rows of a block are
+// consecutive in the caller's order, which these colors keep).  Its entries
+// to other colors are sliced-ELL over the 32 lanes (entry j of lane l at
+// off + 32 j + l; L at (lo, lw), U at (uo, uw)); its in-block coefficients
+// likewise at (li, liw) / (ui, uiw), entry m of a lane being its m-th
+// in-block column in ascending order, whose steps are the set bits of the
+// lane's mask (wl_mask / wu_mask).
+struct __align__(16) WarpUnit {
+  int32_t blk0, nblk, lo, lw, uo, uw, li, liw, ui, uiw, row0, nrows;
+};
 constexpr int32_t kPadCol = 0x7fffffff;   // padding entry of a sliced-ELL step
 constexpr int kTileSmemBudget = 96 * 1024;      // lane-tile CTA with two buffers, bytes
 constexpr int kTileSmemBudget1 = 200 * 1024;    // lane-tile CTA with one buffer, bytes
@@ -225,6 +237,17 @@ struct Params {
   int32_t trace_cap;
   double *hist;
   unsigned long long *err_row;  // IC(0) breakdown row (new numbering), ~0 = none
+  const int32_t *fac_rows;      // IC(0) rows of the lane-tile colors, level by level
+  // warp units: descriptors, per-lane in-block masks, in-block coefficients
+  // (forward: L_lk / L_kk; backward: L_kl / L_kk, k the source step's row),
+  // filled from the factor through (entry map, scaling row); block pointers
+  const WarpUnit *units;
+  const uint32_t *wl_mask, *wu_mask;
+  const int32_t *wl_map, *wl_srow, *wu_map, *wu_srow;
+  double *wl_val, *wu_val;
+  float *wl_val32, *wu_val32;
+  int32_t nwl, nwu;
+  const int32_t *bptr;
 };
 
 // ---- host-side layout built by iccg_setup --------------------------------
@@ -251,6 +274,18 @@ struct HostLayout {
   int32_t tcap_r = 0, tcap_i = 0;     // largest tile: rows, in-block entries
   int32_t tcap_o = 0;                 // largest tile: entries to other colors (L or U)
   std::vector<int32_t> ord;           // internal row -> row of the caller's block-multicolor order
+  // IC(0) schedule of the lane-tile colors: the color's rows by in-block
+  // dependency level (level 0: no earlier row of the same block in the
+  // pattern); rows of level v of color c are fac_rows[fac_ptr[fac_lev0[c] + v]
+  // .. fac_ptr[fac_lev0[c] + v + 1]), fac_nlev[c] levels (0 for a group color)
+  std::vector<int32_t> fac_rows, fac_ptr, fac_lev0, fac_nlev;
+  // warp units (colors of blocks of 3..32 rows when enabled): color c's units
+  // [color_unit[c], color_unit[c + 1]), unit_S[c] rows per segment
+  std::vector<WarpUnit> units;
+  std::vector<int32_t> color_unit, unit_S;
+  std::vector<uint32_t> wl_mask, wu_mask;
+  std::vector<int32_t> wl_map, wl_srow, wu_map, wu_srow;
+  int32_t unit_colors = 0;
   int32_t lane_max = 0;               // largest block of a tile color
   int32_t tile_colors = 0;
   std::vector<int32_t> block_ptr, color_ptr;
@@ -263,10 +298,13 @@ struct HostLayout {
 // returns ICCG_OK or an error with (bad_index, message) filled in.
 // Colors whose blocks all have at most lane_max rows (<= 32; 0 = none) use
 // lane tiles.
+// Colors whose largest block has unit_min..32 rows use warp units instead
+// of lane tiles (unit_min = 0: no warp units).
 iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
                          const double *val, const int32_t *perm, const int32_t *block_ptr,
                          const int32_t *color_ptr, int32_t n_b, int32_t n_c, int32_t group_rows,
-                         int32_t lane_max, HostLayout &out, int64_t &bad_index, std::string &msg);
+                         int32_t lane_max, int32_t unit_min, HostLayout &out, int64_t &bad_index,
+                         std::string &msg);
 
 // ---- launch plan (host side) ---------------------------------------------
 struct Plan {
@@ -285,11 +323,14 @@ struct Plan {
   int32_t cap_ti2 = 0;                  // second-set (fused launch) staging capacity
   int32_t cap_to = 0;                   // other-color entries staged per tile (0: global)
   std::vector<char> stage_ext;          // color c's lane-tile launches stage those entries (tiles of <= 2 steps)
-  std::vector<char> wtile;              // color c: 0 CTA per tile, 1 warp-tile kernels, 2 pair kernels
+  std::vector<char> wtile;              // color c: 0 CTA per tile, 1 warp-tile kernels, 2 pair kernels, 3 warp units
+  std::vector<int32_t> unit0, unit1, unit_S;   // warp-unit range and segment size of each color
+  int32_t Wu = 8;                       // warps per CTA of the warp-unit kernels
   int32_t Ww = 8;                       // warps per CTA of the warp-tile kernels
   int32_t smem_wt = 0;                  // bytes per CTA of the warp-tile kernels
   int32_t cap_ws = 0;                   // steps per tile held in a warp's buffer
   std::vector<int32_t> off_rr, off_rz;  // slot regions of the color-c forward / backward launches
+  std::vector<int32_t> fac_ptr, fac_lev0, fac_nlev;   // IC(0) level schedule (host copy)
   int32_t last_rr = 0, last_rz = 0;     // slots written before the final launch of an iteration
   int32_t grid_a = 0;                   // CTAs of the SpMV-shaped kernels
   int32_t grid_v = 0;                   // CTAs of the vector kernels
@@ -310,6 +351,7 @@ int spmv_resident_ctas(int Wa, int smem);                    // CTAs per SM of t
 int tile_resident_ctas(bool fp32, int threads, int smem);    // CTAs per SM of the lane-tile kernels
 int wtile_resident_ctas(bool fp32, int threads, int smem);   // CTAs per SM of the warp-tile kernels
 int pair_resident_ctas(bool fp32, int threads);              // CTAs per SM of the pair kernels
+int unit_resident_ctas(bool fp32, int S, int threads);       // CTAs per SM of the warp-unit kernels
 cudaError_t launch_factor(const Params &P, const Plan &L, int nL);
 cudaError_t launch_solve_init(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);
 cudaError_t launch_solve_body(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);

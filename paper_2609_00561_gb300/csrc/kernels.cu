@@ -1188,6 +1188,169 @@ pair_kernel(Params P, int t0, int t1, int fin, SlotArgs sa) {
 }
 
 // ---------------------------------------------------------------------------
+// warp-unit kernels: colors of blocks of 3..32 rows.  One warp holds 32 / S
+// whole blocks, a lane per row (Alg. 1: the blocks of a color in parallel,
+// the rows of a block in order).  A sweep over a unit:
+//   A  every lane: its source (r with the x / r update, or y) minus its
+//      entries to other colors (sliced-ELL over the warp: coalesced);
+//   B  the in-block recurrence as a column sweep: at step k the value t_k of
+//      row k of each block is final and is broadcast to its block's lanes
+//      (shuffle); every later (forward) or earlier (backward) row of the
+//      block with an entry in column k subtracts coefficient x t_k, the
+//      coefficient being the entry divided by the pivot of row k, so the
+//      division of Alg. 1 is applied to each row once, at the end;
+//   C  y = t / L_ii (times 1/L_ii), stored; <r,z> for the backward sweep.
+// Every static datum of a unit (descriptor, masks, coefficients, 1/L_ii) is
+// loaded before the first dependent access (griddepcontrol.wait).  A step at
+// which no lane of the warp has a coefficient issues no FP64 instruction.
+// ---------------------------------------------------------------------------
+template <typename PT> __device__ __forceinline__ const PT *wlv(const Params &P);
+template <> __device__ __forceinline__ const double *wlv<double>(const Params &P) { return P.wl_val; }
+template <> __device__ __forceinline__ const float *wlv<float>(const Params &P) { return P.wl_val32; }
+template <typename PT> __device__ __forceinline__ const PT *wuv(const Params &P);
+template <> __device__ __forceinline__ const double *wuv<double>(const Params &P) { return P.wu_val; }
+template <> __device__ __forceinline__ const float *wuv<float>(const Params &P) { return P.wu_val32; }
+
+__device__ __forceinline__ WarpUnit load_unit(const WarpUnit *u) {
+  const int4 *p = reinterpret_cast<const int4 *>(u);
+  const int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+  WarpUnit r;
+  r.blk0 = a.x; r.nblk = a.y; r.lo = a.z; r.lw = a.w;
+  r.uo = b.x; r.uw = b.y; r.li = b.z; r.liw = b.w;
+  r.ui = c.x; r.uiw = c.y; r.row0 = c.z; r.nrows = c.w;
+  return r;
+}
+
+constexpr int kUnitChunk = 8;   // entries to other colors per batch of loads
+
+// acc -= sum over the lane's entries to other colors (width w, stride 32)
+template <typename PT>
+__device__ __forceinline__ PT unit_ext(const int32_t *col, const PT *val, int e, int w, PT acc, const PT *g) {
+  for (int j0 = 0; j0 < w; j0 += kUnitChunk) {
+    const int nj = min(kUnitChunk, w - j0);
+    int cc[kUnitChunk];
+    PT vv[kUnitChunk], xx[kUnitChunk];
+#pragma unroll
+    for (int j = 0; j < kUnitChunk; ++j) {
+      cc[j] = j < nj ? __ldg(col + e + (j0 + j) * kWarp) : kPadCol;
+      vv[j] = j < nj ? __ldg(val + e + (j0 + j) * kWarp) : PT(0);
+    }
+#pragma unroll
+    for (int j = 0; j < kUnitChunk; ++j) xx[j] = cc[j] == kPadCol ? PT(0) : __ldcg(g + cc[j]);
+#pragma unroll
+    for (int j = 0; j < kUnitChunk; ++j)
+      if (j < nj) acc -= vv[j] * xx[j];
+  }
+  return acc;
+}
+
+// the lane's in-block coefficients by step (0 where its mask has no bit)
+template <typename PT, int S>
+__device__ __forceinline__ void unit_coef(const PT *v, int off, uint32_t mask, int lane, PT (&cf)[S]) {
+  int m = 0;
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    cf[k] = PT(0);
+    if ((mask >> k) & 1u) {
+      cf[k] = __ldg(v + off + m * kWarp + lane);
+      ++m;
+    }
+  }
+}
+
+// phase B of a unit: the column sweep (ascending steps forward, descending
+// backward); wmask = OR of the warp's lane masks
+template <typename PT, int S, bool UPPER>
+__device__ __forceinline__ PT unit_chain(PT t, uint32_t mask, uint32_t wmask, const PT (&cf)[S], int seg) {
+#pragma unroll
+  for (int kk = 0; kk < S; ++kk) {
+    const int k = UPPER ? S - 1 - kk : kk;
+    const PT tk = __shfl_sync(0xffffffffu, t, seg + k);
+    if ((wmask >> k) & 1u) {
+      if ((mask >> k) & 1u) t -= cf[k] * tk;
+    }
+  }
+  return t;
+}
+
+constexpr int kUnitWarps = 8;   // warps (units in flight) per CTA of the warp-unit kernels
+
+template <typename PT, int MODE, bool UPDATE, int S>
+__global__ void __launch_bounds__(kUnitWarps * kWarp)
+unit_kernel(Params P, int u0, int u1, int fin, SlotArgs sa) {
+  pdl_trigger();
+  __shared__ double red[kMaxWarpsPerCta];
+  __shared__ int flag;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int seg = lane & ~(S - 1), step = lane & (S - 1);
+  constexpr bool FWD = MODE != M_BWD;
+  PT *yv = reinterpret_cast<PT *>(P.y);
+  PT *zv = reinterpret_cast<PT *>(P.z);
+  const PT *dvg = invds<PT>(P);
+  double rr_acc = 0.0, rz_acc = 0.0;
+  bool waited = false;
+  double alpha = 0.0;
+  for (int u = u0 + int(blockIdx.x) * nw + wid; u < u1; u += int(gridDim.x) * nw) {
+    // static data of the unit
+    const WarpUnit d = load_unit(P.units + u);
+    int row = -1;
+    if (lane / S < d.nblk) {
+      const int b = d.blk0 + lane / S;
+      const int r = __ldg(P.bptr + b) + step;
+      if (r < __ldg(P.bptr + b + 1)) row = r;
+    }
+    const bool on = row >= 0;
+    const uint32_t mf = FWD ? __ldg(P.wl_mask + size_t(u) * kWarp + lane) : 0u;
+    const uint32_t mb = MODE != M_FWD ? __ldg(P.wu_mask + size_t(u) * kWarp + lane) : 0u;
+    PT cf[S];
+    if (FWD) unit_coef<PT, S>(wlv<PT>(P), d.li, mf, lane, cf);
+    else unit_coef<PT, S>(wuv<PT>(P), d.ui, mb, lane, cf);
+    const PT dv = on ? __ldg(dvg + row) : PT(0);
+    if (!waited) {
+      pdl_wait();
+      waited = true;
+      if (UPDATE) alpha = __ldcg(&P.sc->alpha);
+    }
+    PT t = PT(0);
+    if (FWD) {
+      // A: source r (with the x / r update), entries to earlier colors
+      if (on) {
+        double ri = __ldcg(P.r + row);
+        if (UPDATE) {
+          ri -= alpha * __ldcg(P.q + row);
+          P.r[row] = ri;
+          P.xh[row] = __ldcg(P.xh + row) + alpha * __ldcg(P.p0 + row);
+          rr_acc += ri * ri;
+        }
+        t = PT(ri);
+      }
+      t = unit_ext<PT>(P.sl_col, slv<PT>(P), d.lo + lane, d.lw, t, yv);
+      // B, C
+      t = unit_chain<PT, S, false>(t, mf, __reduce_or_sync(0xffffffffu, mf), cf, seg);
+      const PT y = t * dv;
+      if (MODE == M_FWD) {
+        if (on) yv[row] = y;
+        continue;
+      }
+      // the last color: its backward sweep at once (y stays in registers)
+      unit_coef<PT, S>(wuv<PT>(P), d.ui, mb, lane, cf);
+      t = y;
+    } else {
+      if (on) t = __ldcg(yv + row);
+    }
+    t = unit_ext<PT>(P.su_col, suv<PT>(P), d.uo + lane, d.uw, t, zv);
+    t = unit_chain<PT, S, true>(t, mb, __reduce_or_sync(0xffffffffu, mb), cf, seg);
+    const PT z = t * dv;
+    if (on) {
+      zv[row] = z;
+      rz_acc += __ldcg(P.r + row) * double(z);
+    }
+  }
+  if (!waited) pdl_wait();
+  launch_epilogue(P, fin, sa, MODE != M_BWD && UPDATE, MODE != M_FWD, rr_acc, rz_acc, red, &flag);
+}
+
+// ---------------------------------------------------------------------------
 // p = z + beta p (start of an iteration; beta = 0 on the first)
 // ---------------------------------------------------------------------------
 // (two rows per thread per pass: 16-byte loads of p and, for FP64 z, of z)
@@ -1326,7 +1489,12 @@ __global__ void __launch_bounds__(kVecThreads) widen_kernel(const float *src, do
 // ---------------------------------------------------------------------------
 // IC(0) (up-looking, rows of a group level by level, one row per lane)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void factor_row(const Params &P, int i) {
+// Row i of the up-looking IC(0): for every j < i in the pattern, ascending,
+//   L_ij = (a_ij - sum_{k < j, k in pat(i) and pat(j)} L_ik L_jk) / L_jj,
+// then L_ii = sqrt(a_ii - sum_j L_ij^2); rows j are final when row i runs.
+// General form: the common columns by a merge of the two sorted rows (a
+// chain of dependent loads).
+__device__ __forceinline__ void factor_row_merge(const Params &P, int i) {
   const int rb = P.lrp[i], re = P.lrp[i + 1];
   double d = P.adiag[i];
   for (int p = rb; p < re; ++p) {
@@ -1351,26 +1519,86 @@ __device__ __forceinline__ void factor_row(const Params &P, int i) {
   P.ldiag[i] = sqrt(d);
 }
 
+// Rows of at most kFacRow strictly-lower entries whose referenced rows have
+// at most kFacRow as well: row i's columns and computed values sit in the
+// thread's slice of shared memory (sc, sv), each row j is loaded with
+// independent loads into registers, and the common columns are found by
+// compare-and-select, so no load waits on another.  The terms are
+// subtracted in ascending k, as in the general form.
+constexpr int kFacRow = 32;
+constexpr int kFacThreads = 64;    // small CTAs: a level's rows spread over many SMs' FP64 units
+
+__device__ __forceinline__ void factor_row(const Params &P, int i, int32_t *sc, double *sv) {
+  const int rb = P.lrp[i], ni = P.lrp[i + 1] - rb;
+  if (ni > kFacRow) { factor_row_merge(P, i); return; }
+  // the row's columns and the longest referenced row (all loads issued at once)
+  int nmax = 0;
+#pragma unroll
+  for (int t = 0; t < kFacRow; ++t) {
+    if (t < ni) {
+      const int j = __ldg(P.lcol + rb + t);
+      sc[t] = j;
+      nmax = max(nmax, __ldg(P.lrp + j + 1) - __ldg(P.lrp + j));
+    }
+  }
+  if (nmax > kFacRow) { factor_row_merge(P, i); return; }
+  double d = P.adiag[i];
+  for (int p = 0; p < ni; ++p) {
+    const int j = sc[p];
+    const int jb = __ldg(P.lrp + j), nj = __ldg(P.lrp + j + 1) - jb;
+    int cj[kFacRow];
+    double vj[kFacRow];
+#pragma unroll
+    for (int u = 0; u < kFacRow; ++u) {
+      cj[u] = u < nj ? __ldg(P.lcol + jb + u) : -2;
+      vj[u] = u < nj ? __ldcg(P.lval + jb + u) : 0.0;
+    }
+    double s = __ldg(P.ainit + rb + p);
+    for (int t = 0; t < p; ++t) {
+      const int c = sc[t];
+      double v = 0.0;
+      bool hit = false;
+#pragma unroll
+      for (int u = 0; u < kFacRow; ++u) {
+        const bool m = cj[u] == c;
+        v = m ? vj[u] : v;
+        hit = hit || m;
+      }
+      if (hit) s -= sv[t] * v;
+    }
+    const double lij = s / __ldcg(P.ldiag + j);
+    sv[p] = lij;
+    d -= lij * lij;
+  }
+  for (int t = 0; t < ni; ++t) P.lval[rb + t] = sv[t];
+  if (!(d > 0.0) || !isfinite(d)) {
+    atomicMin(P.err_row, (unsigned long long)i);
+    d = 1.0;
+  }
+  P.ldiag[i] = sqrt(d);
+}
+
+// the rows of one in-block level of a lane-tile color, one row per thread
+__global__ void __launch_bounds__(kFacThreads) factor_rows_kernel(Params P, int k0, int k1) {
+  __shared__ int32_t sc[kFacThreads * kFacRow];
+  __shared__ double sv[kFacThreads * kFacRow];
+  for (int k = k0 + int(blockIdx.x * blockDim.x + threadIdx.x); k < k1; k += int(gridDim.x * blockDim.x))
+    factor_row(P, __ldg(P.fac_rows + k), sc + threadIdx.x * kFacRow, sv + threadIdx.x * kFacRow);
+}
+
+// group colors: one CTA per group, its rows level by level of the in-group
+// schedule (dynamic shared memory: a kFacRow slice per thread)
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp) factor_color_kernel(Params P, int g0, int g1) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  int32_t *sc = reinterpret_cast<int32_t *>(fsm) + threadIdx.x * kFacRow;
+  double *sv = reinterpret_cast<double *>(fsm + size_t(blockDim.x) * kFacRow * 4) + threadIdx.x * kFacRow;
   const int g = g0 + blockIdx.x;
   if (g >= g1) return;
   const GroupDesc d = P.groups[g];
   for (int lv = 0; lv < d.nlf; ++lv) {
     const int p0 = P.levp[d.lf + lv], p1 = P.levp[d.lf + lv + 1];
-    for (int p = p0 + int(threadIdx.x); p < p1; p += blockDim.x) factor_row(P, d.r0 + P.sched_f[d.r0 + p]);
+    for (int p = p0 + int(threadIdx.x); p < p1; p += blockDim.x) factor_row(P, d.r0 + P.sched_f[d.r0 + p], sc, sv);
     __syncthreads();
-  }
-}
-
-// lane tiles: a thread factors its block's rows in order
-__global__ void __launch_bounds__(kVecThreads) factor_tile_kernel(Params P, int t0, int t1) {
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int t = t0 + gt / kWarp, lane = gt % kWarp;
-  if (t >= t1) return;
-  const TileDesc td = P.tiles[t];
-  for (int k = 0; k < td.nsteps; ++k) {
-    const StepDesc s = P.steps[td.step0 + k];
-    if (lane < s.cnt) factor_row(P, s.row + lane);
   }
 }
 
@@ -1411,6 +1639,19 @@ __global__ void __launch_bounds__(kVecThreads) factor_finish_kernel(Params P, in
     const double v = m >= 0 ? P.lval[m] : 0.0;
     P.ui_val[e] = v;
     P.ui_val32[e] = float(v);
+  }
+  // warp-unit coefficients: the entry divided by the pivot of its source row
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.nwl; e += stride) {
+    const int m = P.wl_map[e];
+    const double v = m >= 0 ? P.lval[m] / P.ldiag[P.wl_srow[e]] : 0.0;
+    P.wl_val[e] = v;
+    P.wl_val32[e] = float(v);
+  }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.nwu; e += stride) {
+    const int m = P.wu_map[e];
+    const double v = m >= 0 ? P.lval[m] / P.ldiag[P.wu_srow[e]] : 0.0;
+    P.wu_val[e] = v;
+    P.wu_val32[e] = float(v);
   }
 }
 
@@ -1861,8 +2102,32 @@ cudaError_t launch_pair(const Params &P, const Plan &L, int c, int mode, bool up
   return launch(pair_kernel<PT, M_FWD, false>, g, th, 0, L, P, t0, t1, fin, sa);
 }
 
+template <typename PT, int S>
+cudaError_t launch_unit_s(const Params &P, const Plan &L, int c, int mode, bool update, int fin, const SlotArgs &sa) {
+  const int g = L.grid_c[c], t0 = L.unit0[c], t1 = L.unit1[c], th = kUnitWarps * kWarp;
+  if (mode == M_BWD) return launch(unit_kernel<PT, M_BWD, false, S>, g, th, 0, L, P, t0, t1, fin, sa);
+  if (update) {
+    if (mode == M_FUSED) return launch(unit_kernel<PT, M_FUSED, true, S>, g, th, 0, L, P, t0, t1, fin, sa);
+    return launch(unit_kernel<PT, M_FWD, true, S>, g, th, 0, L, P, t0, t1, fin, sa);
+  }
+  if (mode == M_FUSED) return launch(unit_kernel<PT, M_FUSED, false, S>, g, th, 0, L, P, t0, t1, fin, sa);
+  return launch(unit_kernel<PT, M_FWD, false, S>, g, th, 0, L, P, t0, t1, fin, sa);
+}
+
+template <typename PT>
+cudaError_t launch_unit(const Params &P, const Plan &L, int c, int mode, bool update, int fin, const SlotArgs &sa) {
+  switch (L.unit_S[c]) {
+    case 4: return launch_unit_s<PT, 4>(P, L, c, mode, update, fin, sa);
+    case 8: return launch_unit_s<PT, 8>(P, L, c, mode, update, fin, sa);
+    case 16: return launch_unit_s<PT, 16>(P, L, c, mode, update, fin, sa);
+    default: return launch_unit_s<PT, 32>(P, L, c, mode, update, fin, sa);
+  }
+}
+
 template <typename PT>
 cudaError_t launch_fwd(const Params &P, const Plan &L, int c, bool update, bool fused, int fin) {
+  if (L.unit1[c] > L.unit0[c])
+    return launch_unit<PT>(P, L, c, fused ? M_FUSED : M_FWD, update, fin, SlotArgs{L.off_rr[c], L.off_rz[c], 0, 0});
   if (L.tile1[c] > L.tile0[c] && L.wtile[c] == 2)
     return launch_pair<PT>(P, L, c, fused ? M_FUSED : M_FWD, update, fin, SlotArgs{L.off_rr[c], L.off_rz[c], 0, 0});
   if (L.tile1[c] > L.tile0[c] && L.wtile[c])
@@ -1889,6 +2154,7 @@ cudaError_t launch_bwd(const Params &P, const Plan &L, int c, int fin) {
   // the final backward launch sums the <r,r> slots only in an iteration (the
   // solve start has no x / r update)
   const SlotArgs sa{0, L.off_rz[c], fin == FIN_ITER ? L.last_rr : 0, L.last_rz};
+  if (L.unit1[c] > L.unit0[c]) return launch_unit<PT>(P, L, c, M_BWD, false, fin, sa);
   if (L.tile1[c] > L.tile0[c] && L.wtile[c] == 2) return launch_pair<PT>(P, L, c, M_BWD, false, fin, sa);
   if (L.tile1[c] > L.tile0[c] && L.wtile[c]) return launch_wtile<PT>(P, L, c, M_BWD, false, fin, sa);
   if (L.tile1[c] > L.tile0[c]) return launch_tile<PT>(P, L, c, M_BWD, false, fin, sa);
@@ -1995,6 +2261,23 @@ int pair_resident_ctas(bool fp32, int threads) {
   return nb > 0 ? nb : 1;
 }
 
+int unit_resident_ctas(bool fp32, int S, int threads) {
+  int nb = 0;
+  cudaError_t e;
+  if (fp32) {
+    e = S <= 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, unit_kernel<float, M_FWD, true, 8>, threads, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, unit_kernel<float, M_FWD, true, 32>, threads, 0);
+  } else {
+    e = S <= 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, unit_kernel<double, M_FWD, true, 8>, threads, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, unit_kernel<double, M_FWD, true, 32>, threads, 0);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
 int spmv_resident_ctas(int Wa, int smem) {
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_kernel<0>, Wa * kWarp, size_t(smem)) != cudaSuccess) {
@@ -2040,22 +2323,30 @@ cudaError_t launch_solve_persistent(const Params &P, const Plan &L, bool fp32) {
 }
 
 cudaError_t configure_kernels() {
-  cudaError_t e = configure_pt<double>();
+  cudaError_t e = cudaFuncSetAttribute(factor_color_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kMaxWarpsPerCta * kWarp * kFacRow * 12);
+  if (e == cudaSuccess) e = configure_pt<double>();
   if (e == cudaSuccess) e = configure_pt<float>();
   return e;
 }
 
 cudaError_t launch_factor(const Params &P, const Plan &L, int nL) {
   for (int c = 0; c < L.n_c; ++c) {
-    if (L.tile1[c] > L.tile0[c]) {
-      const int nt = L.tile1[c] - L.tile0[c];
-      factor_tile_kernel<<<(nt * kWarp + kVecThreads - 1) / kVecThreads, kVecThreads, 0, L.stream>>>(P, L.tile0[c],
-                                                                                                    L.tile1[c]);
+    if (L.tile1[c] > L.tile0[c] || L.unit1[c] > L.unit0[c]) {
+      // lane-tile and warp-unit colors: one launch per in-block level, a thread per row
+      for (int v = 0; v < L.fac_nlev[c]; ++v) {
+        const int k0 = L.fac_ptr[size_t(L.fac_lev0[c] + v)], k1 = L.fac_ptr[size_t(L.fac_lev0[c] + v + 1)];
+        const int grid = std::max(1, std::min((k1 - k0 + kFacThreads - 1) / kFacThreads, L.grid_v));
+        factor_rows_kernel<<<grid, kFacThreads, 0, L.stream>>>(P, k0, k1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
     } else {
-      factor_color_kernel<<<L.grid_c[c], L.W * kWarp, 0, L.stream>>>(P, L.task0[c], L.task1[c]);
+      const int threads = L.W * kWarp;
+      factor_color_kernel<<<L.grid_c[c], threads, size_t(threads) * kFacRow * 12, L.stream>>>(P, L.task0[c], L.task1[c]);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
   }
   factor_finish_kernel<<<L.grid_v, kVecThreads, 0, L.stream>>>(P, nL);
   return cudaGetLastError();

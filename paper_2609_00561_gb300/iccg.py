@@ -37,7 +37,7 @@ class iccg_opts(ctypes.Structure):
 
 
 SOLVERS = {"auto": 0, "persistent": 1, "phased": 2}
-TILE_MAPPINGS = {"auto": 0, "cta": 1, "warp": 2, "pair": 3}
+TILE_MAPPINGS = {"auto": 0, "cta": 1, "warp": 2, "pair": 3, "units": 4}
 
 
 class iccg_batch_opts(ctypes.Structure):
@@ -78,7 +78,7 @@ def load():
         "iccg_spmv_dot_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp],
         "iccg_batch_create": [P(vp), vp, i32, i32, P(iccg_batch_opts)],
         "iccg_features": [i32, vp, vp, vp, vp],
-        "iccg_check_layout": [i32, i64, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, P(ctypes.c_char_p)],
+        "iccg_check_layout": [i32, i64, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, vp, P(ctypes.c_char_p)],
         "iccg_mlp_forward": [vp, i32, i32, i32, vp, i32, vp, vp, vp],
         "iccg_mlp_grad": [vp, i32, i32, i32, vp, vp, vp, ctypes.c_float, i32, vp, vp, vp, vp],
         "iccg_mlp_adam": [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i32,
@@ -224,7 +224,7 @@ def iccg_time_spmv_phase(ctx, reps=50):
 
 
 INFO_KEYS = ("n", "nnz", "n_b", "n_c", "groups", "global_groups", "nL", "max_levels", "max_group_rows", "tiles",
-             "tile_colors", "warp_tile_colors", "pair_tile_colors")
+             "tile_colors", "warp_tile_colors", "pair_tile_colors", "unit_colors")
 
 
 def iccg_info(ctx):
@@ -484,14 +484,14 @@ def mlp_adam(params, grad, m, v, lr, beta1, beta2, eps, step, stream=None):
            "iccg_mlp_adam")
 
 
-def check_layout(a, bl, group_rows=256, lane_max=32):
+def check_layout(a, bl, group_rows=256, lane_max=32, use_units=False):
     """Host-only check of the device layout (iccg_check_layout): returns
-    (status, tiles, groups, failed checks, first failure, message)."""
+    (status, tiles + warp units, groups, failed checks, first failure, message)."""
     keep = [_as(a.rowptr, np.int64), _as(a.colind, np.int32), _as(a.val, np.float64), _as(bl["perm"], np.int32),
             _as(bl["block_ptr"], np.int32), _as(np.asarray(bl["color_ptr"])[:bl["n_c"] + 1], np.int32)]
     rep = np.zeros(4, dtype=np.int64)
     m = ctypes.c_char_p()
     st = load().iccg_check_layout(int(a.n), int(a.nnz), *[_ptr(k) for k in keep], int(bl["n_b"]), int(bl["n_c"]),
-                                  int(group_rows), int(lane_max), _ptr(rep), ctypes.byref(m))
+                                  int(group_rows), int(lane_max), int(bool(use_units)), _ptr(rep), ctypes.byref(m))
     return st, int(rep[0]), int(rep[1]), int(rep[2]), int(rep[3]), (m.value or b"").decode()
 

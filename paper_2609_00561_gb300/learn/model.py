@@ -49,21 +49,46 @@ def add_features(data):
     return data
 
 
+TIE = 0.01   # settings within 1% of the fastest count as tied (timing noise)
+
+
 def labels(data):
-    """(features [N, F], class [N], log gamma [N], ABMC times [N, 5], CPM times [N, 6])."""
+    """(features [N, F], class [N], log gamma [N], ABMC times [N, S], CPM times [N, G]).
+    The class is the smallest block size within TIE of the fastest ABMC
+    setting; the regression target the log of the largest resolution within
+    TIE of the fastest CPM setting (ties go to the simpler, smaller-block
+    setting, so timing noise between equal blockings does not flip labels)."""
     bs, gs = data["meta"]["block_sizes"], data["meta"]["gammas"]
     X, yc, yr, ta, tc = [], [], [], [], []
     for rec in data["records"]:
         runs = rec["runs"]
-        a = [r["ms"] if r["status"] == 0 else math.inf for r in runs[:len(bs)]]
-        c = [r["ms"] if r["status"] == 0 else math.inf for r in runs[len(bs):]]
+        a = np.array([r["ms"] if r["status"] == 0 else math.inf for r in runs[:len(bs)]])
+        c = np.array([r["ms"] if r["status"] == 0 else math.inf for r in runs[len(bs):]])
         X.append(rec["features"])
-        yc.append(int(np.argmin(a)))
-        yr.append(math.log(gs[int(np.argmin(c))]))
+        yc.append(int(np.flatnonzero(a <= (1 + TIE) * a.min())[0]))
+        yr.append(math.log(gs[int(np.flatnonzero(c <= (1 + TIE) * c.min())[-1])]))
         ta.append(a)
         tc.append(c)
     return (np.array(X, dtype=np.float64), np.array(yc, dtype=np.int32), np.array(yr, dtype=np.float64),
             np.array(ta), np.array(tc))
+
+
+def best_constants(ta, tc):
+    """The constant settings (block-size index, resolution index) with the
+    lowest mean regret on the given records (chosen on the training set)."""
+    ra = (ta / ta.min(axis=1, keepdims=True)).mean(axis=0)
+    rc = (tc / tc.min(axis=1, keepdims=True)).mean(axis=0)
+    return int(np.argmin(ra)), int(np.argmin(rc))
+
+
+def evaluate_constant(ta, tc, ia, ic):
+    """Regret of constant settings (indices into the swept block sizes and
+    resolutions) on the given records."""
+    best_a, best_c = ta.min(axis=1), tc.min(axis=1)
+    t_a, t_c = ta[:, ia], tc[:, ic]
+    return {"abmc_regret_mean": float(np.mean(t_a / best_a)), "abmc_within_5pct": float(np.mean(t_a <= 1.05 * best_a)),
+            "cpm_regret_mean": float(np.mean(t_c / best_c)), "cpm_within_5pct": float(np.mean(t_c <= 1.05 * best_c)),
+            "combined_regret_mean": float(np.mean(np.minimum(t_a, t_c) / np.minimum(best_a, best_c)))}
 
 
 def split(n, seed=0, n_test=40):

@@ -76,7 +76,7 @@ def test_setup_rejects_bad_inputs_before_gpu():
     assert _setup_err(a5, perm, bp, cp, nb, nc).status == 1
     # invalid options: solver id, warps per CTA, rows per thread, lane blocks, tile mapping
     for kw in (dict(solver=3), dict(solver=-1), dict(warps_per_cta=17), dict(rows_per_thread=3),
-               dict(lane_block_max=33), dict(lane_block_max=-2), dict(tile_mapping=4), dict(tile_mapping=-1)):
+               dict(lane_block_max=33), dict(lane_block_max=-2), dict(tile_mapping=5), dict(tile_mapping=-1)):
         with pytest.raises(iccg.IccgError) as ei:
             iccg.iccg_setup(a.n, a.nnz, a.rowptr, a.colind, a.val, perm, bp, cp, nb, nc, iccg.make_opts(**kw))
         assert ei.value.status == 1, kw

@@ -8,10 +8,11 @@ Bars (element by element on the same seeded inputs):
   * blockings / permutations are inputs and bit-exact by construction.
 Cases span several tiles, ragged tails, multi-tile blocks (ABMC s > 32R,
 Leiden modularity blocks of hundreds of rows), one-color and one-row systems,
-and every launch shape: lane tiles (one block per lane) and CTA groups
-(level by level) under several rows-per-thread / warps-per-CTA choices, the
-phased solve as a CUDA graph or a host loop, with or without programmatic
-dependent launch, and the persistent single-launch solve.
+and every launch shape: warp units (one warp per block of 3..32 rows, a lane
+per row), lane tiles (one block per lane) and CTA groups (level by level)
+under several rows-per-thread / warps-per-CTA choices, the phased solve as a
+CUDA graph or a host loop, with or without programmatic dependent launch, and
+the persistent single-launch solve.
 """
 import numpy as np
 import pytest
@@ -76,12 +77,14 @@ SHAPES = [dict(), dict(lane_block_max=8), dict(lane_block_max=-1),
           dict(lane_block_max=-1, warps_per_cta=16), dict(no_graph=1), dict(no_pdl=1),
           dict(solver="persistent"), dict(solver="persistent", rows_per_thread=4, warps_per_cta=4),
           dict(solver="persistent", warps_per_cta=16), dict(tile_mapping="warp"), dict(tile_mapping="cta"),
-          dict(tile_mapping="warp", warps_per_cta=3, lane_block_max=16)]
+          dict(tile_mapping="warp", warps_per_cta=3, lane_block_max=16), dict(tile_mapping="units"),
+          dict(tile_mapping="units", lane_block_max=16), dict(tile_mapping="units", no_graph=1)]
 LAYOUTS = {"lanes": dict(), "groups": dict(lane_block_max=-1), "warp_tiles": dict(tile_mapping="warp"),
-           "cta_tiles": dict(tile_mapping="cta"), "pair_tiles": dict(tile_mapping="pair")}
+           "cta_tiles": dict(tile_mapping="cta"), "pair_tiles": dict(tile_mapping="pair"),
+           "units": dict(tile_mapping="units"), "units16": dict(tile_mapping="units", lane_block_max=16)}
 SOLVERS = {"lanes": dict(), "groups": dict(lane_block_max=-1), "persistent": dict(solver="persistent"),
            "warp_tiles": dict(tile_mapping="warp"), "cta_tiles": dict(tile_mapping="cta"),
-           "pair_tiles": dict(tile_mapping="pair")}
+           "pair_tiles": dict(tile_mapping="pair"), "units": dict(tile_mapping="units")}
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -262,21 +265,30 @@ def test_production_blocking_drives_the_same_solve():
 
 
 def test_layout_choice_follows_block_sizes():
-    """Colors of blocks up to lane_block_max rows run as lane tiles (32 blocks
-    per tile); larger blocks run as CTA groups."""
+    """Colors of blocks of 5..32 rows run as warp units (a warp per block, a
+    lane per row) by default and as lane tiles (32 blocks per tile) when asked;
+    larger blocks run as CTA groups."""
     a, b, bl, ref = _case("grid3d_abmc8")
     cp = np.asarray(bl["color_ptr"])
     S = iccg.Solver(a, bl)
     info = iccg.iccg_info(S.ctx)
-    assert info["tile_colors"] == bl["n_c"]
+    assert info["unit_colors"] == bl["n_c"] and info["tile_colors"] == 0 and info["groups"] == 0
+    S.close()
+    S = iccg.Solver(a, bl, tile_mapping="cta")
+    info = iccg.iccg_info(S.ctx)
+    assert info["tile_colors"] == bl["n_c"] and info["unit_colors"] == 0
     assert info["tiles"] == sum((int(cp[c + 1] - cp[c]) + 31) // 32 for c in range(bl["n_c"]))
     assert info["groups"] == 0
     assert info["warp_tile_colors"] == 0
+    assert info["pair_tile_colors"] == 0        # blocks of 8 rows: one CTA per tile
     S.close()
     S = iccg.Solver(a, bl, tile_mapping="warp")
     assert iccg.iccg_info(S.ctx)["warp_tile_colors"] == bl["n_c"]
     S.close()
-    assert info["pair_tile_colors"] == 0        # blocks of 8 rows: one CTA per tile
+    a4, b4, bl4, ref4 = _case("grid3d_abmc100")
+    S = iccg.Solver(a4, bl4)
+    assert iccg.iccg_info(S.ctx)["groups"] > 0     # blocks above 32 rows: CTA groups
+    S.close()
     a2, b2, bl2, ref2 = _case("grid3d_cpm_singletons")
     S = iccg.Solver(a2, bl2)
     info = iccg.iccg_info(S.ctx)

@@ -32,16 +32,18 @@ BLOCKINGS = [("abmc", dict(block_size=s)) for s in (1, 2, 8, 32, 100)] + \
 @pytest.mark.parametrize("mat", sorted(MATS))
 @pytest.mark.parametrize("blk", range(len(BLOCKINGS)))
 @pytest.mark.parametrize("lane_max", [32, 8, 0])
-def test_layout_invariants(mat, blk, lane_max):
+@pytest.mark.parametrize("units", [False, True])
+def test_layout_invariants(mat, blk, lane_max, units):
     a = MATS[mat]()
     method, kw = BLOCKINGS[blk]
     bl = iccg.blocking(a, method, **kw)
-    st, tiles, groups, failed, first, what = iccg.check_layout(a, bl, group_rows=256, lane_max=lane_max)
+    st, tiles, groups, failed, first, what = iccg.check_layout(a, bl, group_rows=256, lane_max=lane_max,
+                                                               use_units=units)
     assert st == 0 and failed == 0, (what, first)
-    if lane_max == 0:
-        assert tiles == 0
     sizes = np.diff(np.asarray(bl["block_ptr"]))
-    if lane_max and sizes.max() <= lane_max:
+    if lane_max == 0 and not units:
+        assert tiles == 0
+    if (lane_max and sizes.max() <= lane_max) or (units and lane_max >= 2 and sizes.max() <= 32):
         assert groups == 0
 
 
