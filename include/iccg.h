@@ -75,12 +75,11 @@ typedef struct {
                                  0 = 32, -1 = never (the persistent solver never
                                  uses lanes) */
   int32_t tile_mapping;       /* colors whose blocks have at most lane_block_max rows:
-                                 ICCG_TILES_UNITS runs the colors of blocks of 3..32
-                                 rows as warp units (one warp per block, a lane per
-                                 row, the in-block recurrence as a shuffle-broadcast
-                                 column sweep; blocks of up to 4, 8 or 16 rows share
-                                 a warp) and the others as lane tiles like
-                                 ICCG_TILES_AUTO; lane tiles (32 blocks, one per
+                                 ICCG_TILES_UNITS runs every such color as warp units
+                                 (one warp per block, a lane per row, the in-block
+                                 recurrence as a shuffle-broadcast column sweep;
+                                 blocks of up to 1, 2, 4, 8 or 16 rows share a warp);
+                                 lane tiles (32 blocks, one per
                                  lane): ICCG_TILES_CTA runs one CTA per tile (the
                                  tile's steps shared out over its warps, the in-block
                                  recurrence on one warp); ICCG_TILES_WARP one warp
@@ -345,7 +344,7 @@ iccg_status iccg_color_order(int32_t n, const int64_t *gptr, const int32_t *gadj
 /* Diagnostics (host only, no device): builds the layout iccg_setup would
  * build for these inputs (groups of at most group_rows rows, lane tiles for
  * colors of blocks of at most lane_max rows, 0 = none; with use_units, warp
- * units for colors of blocks of 3..32 rows) and checks the index ranges and
+ * units for every color of blocks of at most 32 rows) and checks the index ranges and
  * orderings the kernels rely on.  report[4]: lane tiles plus warp units,
  * groups, failed checks, the tile / unit / group / color of the first failure
  * (-1 none); *what (may be NULL) names the first failed check.  ICCG_OK,

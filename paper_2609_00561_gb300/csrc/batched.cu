@@ -681,7 +681,7 @@ iccg_status iccg_batch_create(iccg_batch **out, iccg_ctx *const *ctxs, int32_t n
   for (int s = 0; s < nsys; ++s) {
     const iccg_ctx *c = ctxs[s];
     if (!c || !c->factored || c->H.n < 1) return ICCG_ERR_STATE;
-    if (c->H.tile_colors != 0) return ICCG_ERR_ARG;   // contexts set up with lane_block_max = -1
+    if (c->H.tile_colors != 0 || c->H.unit_colors != 0) return ICCG_ERR_ARG;   // set up with lane_block_max = -1
     if (c->device != ctxs[0]->device || c->fp32 != ctxs[0]->fp32) return ICCG_ERR_ARG;
     for (int j = 0; j < c->H.n_b; ++j)
       if (c->H.block_ptr[j + 1] - c->H.block_ptr[j] > kBatchMaxBlock) return ICCG_ERR_ARG;

@@ -164,9 +164,9 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
                        : (o.lane_block_max == 0 ? 32 : o.lane_block_max);
   // warp units (one warp per block, a lane per row): automatically for colors
   // of blocks of 5..32 rows (on a GB300 12% faster than lane tiles at 8 rows,
-  // 2.7x at 32, 2.5% slower at 4), explicitly from 3 rows
+  // 2.7x at 32, 2.5% slower at 4), explicitly for every color of at most 32
   const int32_t unit_min = lane_max <= 0 ? 0
-                           : o.tile_mapping == ICCG_TILES_UNITS ? 3
+                           : o.tile_mapping == ICCG_TILES_UNITS ? 1
                            : o.tile_mapping == ICCG_TILES_AUTO ? 5 : 0;
   iccg_status st = build_layout(n, nnz, hrp.data(), hci.data(), hval.data(), hperm.data(), hbp.data(),
                                 hcp.data(), n_b, n_c, G, lane_max, unit_min, ctx->H, ctx->err_index, ctx->err_msg);
@@ -406,6 +406,10 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     CK(dev_upload(ctx, &d_units, H.units), "alloc units");
     CK(dev_upload(ctx, &d_wlm, H.wl_mask), "alloc units");
     CK(dev_upload(ctx, &d_wum, H.wu_mask), "alloc units");
+    uint32_t *d_wls, *d_wus;
+    CK(dev_upload(ctx, &d_wls, H.wl_src), "alloc units");
+    CK(dev_upload(ctx, &d_wus, H.wu_src), "alloc units");
+    P.wl_src = d_wls; P.wu_src = d_wus;
     CK(dev_upload(ctx, &d_wlmap, H.wl_map), "alloc units");
     CK(dev_upload(ctx, &d_wlsr, H.wl_srow), "alloc units");
     CK(dev_upload(ctx, &d_wumap, H.wu_map), "alloc units");

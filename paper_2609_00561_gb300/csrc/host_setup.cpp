@@ -127,13 +127,13 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
   lane_max = std::max(0, std::min(lane_max, 32));
   std::vector<char> tcol(n_c > 0 ? n_c : 1, 0);
   // warp units: colors whose largest block has unit_min..32 rows (when
-  // enabled, unit_min >= 3); they keep the caller's row order
+  // enabled, unit_min >= 1); they keep the caller's row order
   std::vector<char> wcol(n_c > 0 ? n_c : 1, 0);
   H.unit_colors = 0;
   for (int32_t c = 0; c < n_c && unit_min > 0; ++c) {
     int32_t mb = 0;
     for (int32_t j = color_ptr[c]; j < color_ptr[c + 1]; ++j) mb = std::max(mb, block_ptr[j + 1] - block_ptr[j]);
-    if (mb >= std::max(unit_min, 3) && mb <= kWarp) {
+    if (mb >= unit_min && mb <= kWarp) {
       wcol[c] = 1;
       H.unit_colors++;
     }
@@ -385,7 +385,7 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
   H.color_unit.assign(n_c + 1, 0);
   H.unit_S.assign(n_c + 1, 0);
   H.units.clear();
-  H.wl_mask.clear(); H.wu_mask.clear();
+  H.wl_mask.clear(); H.wu_mask.clear(); H.wl_src.clear(); H.wu_src.clear();
   H.wl_map.clear(); H.wl_srow.clear(); H.wu_map.clear(); H.wu_srow.clear();
   {
     std::vector<std::vector<int32_t>> se(kWarp), sw(kWarp);
@@ -407,7 +407,7 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
       if (!wcol[c]) continue;
       int32_t mb = 0;
       for (int32_t j = color_ptr[c]; j < color_ptr[c + 1]; ++j) mb = std::max(mb, block_ptr[j + 1] - block_ptr[j]);
-      int32_t S = 4;
+      int32_t S = 1;
       while (S < mb) S <<= 1;
       H.unit_S[c] = S;
       const int32_t per = kWarp / S;
@@ -438,26 +438,70 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
           }
           if (pass == 0) { u.lo = int32_t(H.sl_col.size()); u.lw = slab(se, sw, H.sl_col, H.sl_map, kPadCol); }
           else { u.uo = int32_t(H.su_col.size()); u.uw = slab(se, sw, H.su_col, H.su_map, kPadCol); }
-          // in-block coefficients (ascending column) and the lane masks
+          // in-block terms as a chain schedule: lane l's terms (source row
+          // k, coefficient) in the order their sources become final, one per
+          // step (a source is final the step after its own last term; rows
+          // are visited in dependency order: ascending forward, descending
+          // backward), each at the earliest step both it and the lane allow
+          std::vector<int32_t> ready(size_t(kWarp), 0);
+          std::vector<std::vector<std::pair<int32_t, int32_t>>> sched(kWarp);   // (step, term index)
+          std::vector<std::vector<int32_t>> tsrc(kWarp), tmap(kWarp), trow(kWarp);
           for (int l = 0; l < kWarp; ++l) {
-            se[size_t(l)].clear();
-            sw[size_t(l)].clear();
-            uint32_t mask = 0;
             const int32_t i = lrow[size_t(l)];
-            if (i >= 0) {
-              const int32_t base = block_ptr[iblk[i]];
-              for (int32_t e = rp[size_t(i)]; e < rp[size_t(i) + 1]; ++e) {
-                const int32_t k = cols[size_t(e)];
-                if (iblk[k] != iblk[i]) continue;
-                mask |= 1u << (k - base);
-                se[size_t(l)].push_back(pass ? H.umap[size_t(e)] : e);
-                sw[size_t(l)].push_back(k);
-              }
+            if (i < 0) continue;
+            for (int32_t e = rp[size_t(i)]; e < rp[size_t(i) + 1]; ++e) {
+              const int32_t k = cols[size_t(e)];
+              if (iblk[k] != iblk[i]) continue;
+              tsrc[size_t(l)].push_back((l / S) * S + (k - block_ptr[iblk[i]]));
+              tmap[size_t(l)].push_back(pass ? H.umap[size_t(e)] : e);
+              trow[size_t(l)].push_back(k);
             }
-            (pass ? H.wu_mask : H.wl_mask).push_back(mask);
           }
-          if (pass == 0) { u.li = int32_t(H.wl_map.size()); u.liw = slab(se, sw, H.wl_map, H.wl_srow, -1); }
-          else { u.ui = int32_t(H.wu_map.size()); u.uiw = slab(se, sw, H.wu_map, H.wu_srow, -1); }
+          int32_t M = 0;
+          for (int q = 0; q < kWarp; ++q) {
+            const int l = pass ? kWarp - 1 - q : q;   // sources before their targets within a block
+            const size_t nt = tsrc[size_t(l)].size();
+            std::vector<int32_t> ord(nt);
+            for (size_t x = 0; x < nt; ++x) ord[x] = int32_t(x);
+            std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+              return ready[size_t(tsrc[size_t(l)][size_t(a)])] < ready[size_t(tsrc[size_t(l)][size_t(b)])];
+            });
+            int32_t t = 0;
+            for (int32_t x : ord) {
+              const int32_t st = std::max(t, ready[size_t(tsrc[size_t(l)][size_t(x)])]);
+              sched[size_t(l)].push_back({st, x});
+              t = st + 1;
+            }
+            ready[size_t(l)] = t;
+            M = std::max(M, t);
+          }
+          if (M > kWarp) return fail(ICCG_ERR_ARG, u.blk0, "warp-unit chain longer than 32 steps", bad, msg);
+          const int32_t co = int32_t((pass ? H.wu_map : H.wl_map).size());
+          const int32_t so = int32_t((pass ? H.wu_src : H.wl_src).size());
+          std::vector<int32_t> &mp = pass ? H.wu_map : H.wl_map, &sr = pass ? H.wu_srow : H.wl_srow;
+          std::vector<uint32_t> &swd = pass ? H.wu_src : H.wl_src, &mk = pass ? H.wu_mask : H.wl_mask;
+          mp.resize(size_t(co) + size_t(M) * kWarp, -1);
+          sr.resize(size_t(co) + size_t(M) * kWarp, -1);
+          const int32_t nw = (M + 3) / 4;
+          swd.resize(size_t(so) + size_t(nw) * kWarp, 0u);
+          for (int l = 0; l < kWarp; ++l) {
+            uint32_t mask = 0;
+            for (int m = 0; m < nw * 4; ++m) {   // idle steps read the lane itself
+              const size_t w = size_t(so) + size_t(m / 4) * kWarp + size_t(l);
+              swd[w] |= uint32_t(l) << (8 * (m % 4));
+            }
+            for (const auto &pr : sched[size_t(l)]) {
+              const int32_t m = pr.first, x = pr.second;
+              mask |= 1u << m;
+              mp[size_t(co) + size_t(m) * kWarp + size_t(l)] = tmap[size_t(l)][size_t(x)];
+              sr[size_t(co) + size_t(m) * kWarp + size_t(l)] = trow[size_t(l)][size_t(x)];
+              const size_t w = size_t(so) + size_t(m / 4) * kWarp + size_t(l);
+              swd[w] = (swd[w] & ~(0xffu << (8 * (m % 4)))) | (uint32_t(tsrc[size_t(l)][size_t(x)]) << (8 * (m % 4)));
+            }
+            mk.push_back(mask);
+          }
+          if (pass == 0) { u.li = co; u.lm = M; u.ls = so; }
+          else { u.ui = co; u.um = M; u.us = so; }
         }
         H.units.push_back(u);
       }
@@ -635,7 +679,7 @@ extern "C" iccg_status iccg_check_layout(int32_t n, int64_t nnz, const int64_t *
   int64_t bad = -1;
   std::string msg;
   const iccg_status st = build_layout(n, nnz, rowptr, colind, val, perm, block_ptr, color_ptr, n_b, n_c,
-                                      std::max(group_rows, 1), lane_max, use_units ? 3 : 0, H, bad, msg);
+                                      std::max(group_rows, 1), lane_max, use_units ? 1 : 0, H, bad, msg);
   report[0] = report[1] = report[2] = report[3] = 0;
   if (st != ICCG_OK) {
     report[3] = bad;
@@ -777,14 +821,14 @@ extern "C" iccg_status iccg_check_layout(int32_t n, int64_t nnz, const int64_t *
         }
     }
   }
-  // warp units: lanes on the rows of their blocks, masks naming earlier (L)
-  // or later (U) rows of the lane's own block, one coefficient per set bit in
-  // ascending column order, entries to other colors outside the block
+  // warp units: lanes on the rows of their blocks; each chain holds every
+  // in-block term of a row once, from a lane of the same block whose own last
+  // term comes at an earlier step; entries to other colors outside the block
   for (int c = 0; c < n_c; ++c) {
     const int S = H.unit_S[size_t(c)];
     for (int32_t t = H.color_unit[size_t(c)]; t < H.color_unit[size_t(c) + 1]; ++t) {
       const WarpUnit &u = H.units[size_t(t)];
-      ck(S >= 4 && S <= kWarp && (S & (S - 1)) == 0 && u.nblk >= 1 && u.nblk <= kWarp / S, t, "unit shape");
+      ck(S >= 1 && S <= kWarp && (S & (S - 1)) == 0 && u.nblk >= 1 && u.nblk <= kWarp / S, t, "unit shape");
       ck(u.blk0 >= H.color_ptr[size_t(c)] && u.blk0 + u.nblk <= H.color_ptr[size_t(c) + 1], t, "unit blocks");
       ck(u.row0 == H.block_ptr[size_t(u.blk0)] && u.row0 + u.nrows == H.block_ptr[size_t(u.blk0 + u.nblk)], t, "unit rows");
       for (int l = 0; l < kWarp; ++l) {
@@ -793,19 +837,33 @@ extern "C" iccg_status iccg_check_layout(int32_t n, int64_t nnz, const int64_t *
         const int32_t i = on ? H.block_ptr[size_t(b)] + l % S : -1;
         for (int pass = 0; pass < 2; ++pass) {
           const uint32_t m = (pass ? H.wu_mask : H.wl_mask)[size_t(t) * kWarp + l];
-          const int32_t off = pass ? u.ui : u.li, w = pass ? u.uiw : u.liw;
+          const int32_t off = pass ? u.ui : u.li, M = pass ? u.um : u.lm, so = pass ? u.us : u.ls;
           const std::vector<int32_t> &mp = pass ? H.wu_map : H.wl_map, &sr = pass ? H.wu_srow : H.wl_srow;
+          const std::vector<uint32_t> &swd = pass ? H.wu_src : H.wl_src;
+          ck(M >= 0 && M <= kWarp && (M == kWarp || (m >> M) == 0u), t, "chain steps");
           if (!on) { ck(m == 0u, t, "idle lane mask"); continue; }
-          const int step = l % S;
-          ck(pass ? (m & ((2u << step) - 1u)) == 0u : (m >> step) == 0u, t, "mask direction");
-          int j = 0;
-          for (int k = 0; k < S; ++k) {
-            if (!((m >> k) & 1u)) continue;
-            const size_t e = size_t(off) + size_t(j) * kWarp + size_t(l);
-            ck(j < w && sr[e] == H.block_ptr[size_t(b)] + k && mp[e] >= 0 && mp[e] < H.nL, t, "unit coefficient");
-            ++j;
+          // every in-block entry of the row exactly once, from its own block,
+          // after the source lane's last term
+          std::vector<int32_t> want;
+          const std::vector<int32_t> &rp = pass ? H.urp : H.lrp, &cols = pass ? H.ucol : H.lcol;
+          for (int32_t e = rp[size_t(i)]; e < rp[size_t(i) + 1]; ++e)
+            if (cols[size_t(e)] >= H.block_ptr[size_t(b)] && cols[size_t(e)] < H.block_ptr[size_t(b) + 1])
+              want.push_back(pass ? H.umap[size_t(e)] : e);
+          std::vector<int32_t> got;
+          for (int k = 0; k < M; ++k) {
+            const size_t e = size_t(off) + size_t(k) * kWarp + size_t(l);
+            const uint32_t src = (swd[size_t(so) + size_t(k / 4) * kWarp + size_t(l)] >> (8 * (k % 4))) & 0xffu;
+            if (!((m >> k) & 1u)) { ck(mp[e] == -1, t, "chain padding"); continue; }
+            got.push_back(mp[e]);
+            const int32_t srow = H.block_ptr[size_t(b)] + int32_t(src) % S;
+            ck(int32_t(src) / S == l / S && sr[e] == srow && (pass ? srow > i : srow < i), t, "chain source");
+            // the source lane has no term at this step or later
+            const uint32_t ms = (pass ? H.wu_mask : H.wl_mask)[size_t(t) * kWarp + src];
+            ck((ms >> k) == 0u, t, "chain order");
           }
-          for (; j < w; ++j) ck(mp[size_t(off) + size_t(j) * kWarp + size_t(l)] == -1, t, "unit coefficient padding");
+          std::sort(want.begin(), want.end());
+          std::sort(got.begin(), got.end());
+          ck(want == got, t, "chain terms");
           const int32_t eo = pass ? u.uo : u.lo, ew = pass ? u.uw : u.lw;
           const std::vector<int32_t> &ec = pass ? H.su_col : H.sl_col;
           for (int32_t q = 0; q < ew; ++q) {

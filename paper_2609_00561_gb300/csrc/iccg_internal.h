@@ -81,17 +81,19 @@ struct __align__(16) StepDesc {
 struct __align__(16) PairDesc {
   int32_t row0, c0, c1, lo, lw0, lw1, li, liw1, uo, uw0, uw1, ui, uiw0, pad0, pad1, pad2;
 };
-// A warp unit (colors whose blocks have 3..32 rows): 32 / S consecutive
+// A warp unit (a color whose blocks have at most 32 rows): 32 / S consecutive
 // blocks of one color, each at most S rows (S a power of two), one warp;
 // lane l holds row l % S of block blk0 + l / S (rows of a block are
 // consecutive in the caller's order, which these colors keep).  Its entries
 // to other colors are sliced-ELL over the 32 lanes (entry j of lane l at
-// off + 32 j + l; L at (lo, lw), U at (uo, uw)); its in-block coefficients
-// likewise at (li, liw) / (ui, uiw), entry m of a lane being its m-th
-// in-block column in ascending order, whose steps are the set bits of the
-// lane's mask (wl_mask / wu_mask).
+// off + 32 j + l; L at (lo, lw), U at (uo, uw)).  Its in-block recurrence runs
+// as lm (forward) / um (backward) chain steps: at step m a lane subtracts at
+// most one in-block term, coefficient x the final value of the source lane;
+// coefficient m of lane l at li + 32 m + l (ui for U), the source lanes as
+// bytes, four steps per word, word w of lane l at ls + 32 w + l (us for U),
+// and bit m of the lane's mask (wl_mask / wu_mask) marks a step with a term.
 struct __align__(16) WarpUnit {
-  int32_t blk0, nblk, lo, lw, uo, uw, li, liw, ui, uiw, row0, nrows;
+  int32_t blk0, nblk, lo, lw, uo, uw, li, lm, ui, um, row0, nrows, ls, us, pad0, pad1;
 };
 constexpr int32_t kPadCol = 0x7fffffff;   // padding entry of a sliced-ELL step
 constexpr int kTileSmemBudget = 96 * 1024;      // lane-tile CTA with two buffers, bytes
@@ -243,6 +245,7 @@ struct Params {
   // filled from the factor through (entry map, scaling row); block pointers
   const WarpUnit *units;
   const uint32_t *wl_mask, *wu_mask;
+  const uint32_t *wl_src, *wu_src;    // chain-step source lanes, four bytes a word
   const int32_t *wl_map, *wl_srow, *wu_map, *wu_srow;
   double *wl_val, *wu_val;
   float *wl_val32, *wu_val32;
@@ -279,11 +282,11 @@ struct HostLayout {
   // pattern); rows of level v of color c are fac_rows[fac_ptr[fac_lev0[c] + v]
   // .. fac_ptr[fac_lev0[c] + v + 1]), fac_nlev[c] levels (0 for a group color)
   std::vector<int32_t> fac_rows, fac_ptr, fac_lev0, fac_nlev;
-  // warp units (colors of blocks of 3..32 rows when enabled): color c's units
+  // warp units (colors of blocks of at most 32 rows when enabled): color c's units
   // [color_unit[c], color_unit[c + 1]), unit_S[c] rows per segment
   std::vector<WarpUnit> units;
   std::vector<int32_t> color_unit, unit_S;
-  std::vector<uint32_t> wl_mask, wu_mask;
+  std::vector<uint32_t> wl_mask, wu_mask, wl_src, wu_src;
   std::vector<int32_t> wl_map, wl_srow, wu_map, wu_srow;
   int32_t unit_colors = 0;
   int32_t lane_max = 0;               // largest block of a tile color

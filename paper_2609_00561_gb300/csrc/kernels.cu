@@ -1188,17 +1188,20 @@ pair_kernel(Params P, int t0, int t1, int fin, SlotArgs sa) {
 }
 
 // ---------------------------------------------------------------------------
-// warp-unit kernels: colors of blocks of 3..32 rows.  One warp holds 32 / S
+// warp-unit kernels: colors of blocks of at most 32 rows.  One warp holds 32 / S
 // whole blocks, a lane per row (Alg. 1: the blocks of a color in parallel,
 // the rows of a block in order).  A sweep over a unit:
 //   A  every lane: its source (r with the x / r update, or y) minus its
 //      entries to other colors (sliced-ELL over the warp: coalesced);
-//   B  the in-block recurrence as a column sweep: at step k the value t_k of
-//      row k of each block is final and is broadcast to its block's lanes
-//      (shuffle); every later (forward) or earlier (backward) row of the
-//      block with an entry in column k subtracts coefficient x t_k, the
-//      coefficient being the entry divided by the pivot of row k, so the
-//      division of Alg. 1 is applied to each row once, at the end;
+//   B  the in-block recurrence as a chain of steps: at every step a lane
+//      subtracts at most one in-block term, coefficient x t_k, where t_k is
+//      the final value of the term's source row k (read from its lane by a
+//      shuffle) and the coefficient is the entry divided by the pivot of
+//      row k, so the division of Alg. 1 is applied to each row once, at the
+//      end.  The host orders each lane's terms by the step their sources
+//      become final, so independent terms of different rows share a step:
+//      the chain is about as long as the in-block dependency depth or the
+//      widest row, not the block size;
 //   C  y = t / L_ii (times 1/L_ii), stored; <r,z> for the backward sweep.
 // Every static datum of a unit (descriptor, masks, coefficients, 1/L_ii) is
 // loaded before the first dependent access (griddepcontrol.wait).  A step at
@@ -1213,11 +1216,12 @@ template <> __device__ __forceinline__ const float *wuv<float>(const Params &P) 
 
 __device__ __forceinline__ WarpUnit load_unit(const WarpUnit *u) {
   const int4 *p = reinterpret_cast<const int4 *>(u);
-  const int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+  const int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), e = __ldg(p + 3);
   WarpUnit r;
   r.blk0 = a.x; r.nblk = a.y; r.lo = a.z; r.lw = a.w;
-  r.uo = b.x; r.uw = b.y; r.li = b.z; r.liw = b.w;
-  r.ui = c.x; r.uiw = c.y; r.row0 = c.z; r.nrows = c.w;
+  r.uo = b.x; r.uw = b.y; r.li = b.z; r.lm = b.w;
+  r.ui = c.x; r.um = c.y; r.row0 = c.z; r.nrows = c.w;
+  r.ls = e.x; r.us = e.y; r.pad0 = r.pad1 = 0;
   return r;
 }
 
@@ -1244,30 +1248,31 @@ __device__ __forceinline__ PT unit_ext(const int32_t *col, const PT *val, int e,
   return acc;
 }
 
-// the lane's in-block coefficients by step (0 where its mask has no bit)
+// the lane's chain coefficients by step (0 where its mask has no bit) and the
+// source lanes (four bytes a word)
 template <typename PT, int S>
-__device__ __forceinline__ void unit_coef(const PT *v, int off, uint32_t mask, int lane, PT (&cf)[S]) {
-  int m = 0;
+__device__ __forceinline__ void unit_coef(const PT *v, const uint32_t *sw, int off, int soff, int M, uint32_t mask,
+                                          int lane, PT (&cf)[S], uint32_t (&src)[(S + 3) / 4]) {
 #pragma unroll
-  for (int k = 0; k < S; ++k) {
-    cf[k] = PT(0);
-    if ((mask >> k) & 1u) {
-      cf[k] = __ldg(v + off + m * kWarp + lane);
-      ++m;
-    }
-  }
+  for (int k = 0; k < S; ++k) cf[k] = ((mask >> k) & 1u) ? __ldg(v + off + k * kWarp + lane) : PT(0);
+#pragma unroll
+  for (int w = 0; w < (S + 3) / 4; ++w) src[w] = 4 * w < M ? __ldg(sw + soff + w * kWarp + lane) : 0u;
 }
 
-// phase B of a unit: the column sweep (ascending steps forward, descending
-// backward); wmask = OR of the warp's lane masks
-template <typename PT, int S, bool UPPER>
-__device__ __forceinline__ PT unit_chain(PT t, uint32_t mask, uint32_t wmask, const PT (&cf)[S], int seg) {
+// phase B of a unit: M chain steps; at step k every lane with a term
+// subtracts coefficient x the (final) value of its source lane; wmask = OR
+// of the warp's lane masks (a step no lane uses issues no FP64 instruction)
+template <typename PT, int S>
+__device__ __forceinline__ PT unit_chain(PT t, int M, uint32_t mask, uint32_t wmask, const PT (&cf)[S],
+                                         const uint32_t (&src)[(S + 3) / 4]) {
 #pragma unroll
-  for (int kk = 0; kk < S; ++kk) {
-    const int k = UPPER ? S - 1 - kk : kk;
-    const PT tk = __shfl_sync(0xffffffffu, t, seg + k);
-    if ((wmask >> k) & 1u) {
-      if ((mask >> k) & 1u) t -= cf[k] * tk;
+  for (int k = 0; k < S; ++k) {
+    if (k < M) {
+      const int sl = int((src[k / 4] >> (8 * (k % 4))) & 0xffu);
+      const PT tk = __shfl_sync(0xffffffffu, t, sl);
+      if ((wmask >> k) & 1u) {
+        if ((mask >> k) & 1u) t -= cf[k] * tk;
+      }
     }
   }
   return t;
@@ -1282,7 +1287,7 @@ unit_kernel(Params P, int u0, int u1, int fin, SlotArgs sa) {
   __shared__ double red[kMaxWarpsPerCta];
   __shared__ int flag;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int seg = lane & ~(S - 1), step = lane & (S - 1);
+  const int step = lane & (S - 1);
   constexpr bool FWD = MODE != M_BWD;
   PT *yv = reinterpret_cast<PT *>(P.y);
   PT *zv = reinterpret_cast<PT *>(P.z);
@@ -1303,8 +1308,9 @@ unit_kernel(Params P, int u0, int u1, int fin, SlotArgs sa) {
     const uint32_t mf = FWD ? __ldg(P.wl_mask + size_t(u) * kWarp + lane) : 0u;
     const uint32_t mb = MODE != M_FWD ? __ldg(P.wu_mask + size_t(u) * kWarp + lane) : 0u;
     PT cf[S];
-    if (FWD) unit_coef<PT, S>(wlv<PT>(P), d.li, mf, lane, cf);
-    else unit_coef<PT, S>(wuv<PT>(P), d.ui, mb, lane, cf);
+    uint32_t src[(S + 3) / 4];
+    if (FWD) unit_coef<PT, S>(wlv<PT>(P), P.wl_src, d.li, d.ls, d.lm, mf, lane, cf, src);
+    else unit_coef<PT, S>(wuv<PT>(P), P.wu_src, d.ui, d.us, d.um, mb, lane, cf, src);
     const PT dv = on ? __ldg(dvg + row) : PT(0);
     if (!waited) {
       pdl_wait();
@@ -1326,20 +1332,20 @@ unit_kernel(Params P, int u0, int u1, int fin, SlotArgs sa) {
       }
       t = unit_ext<PT>(P.sl_col, slv<PT>(P), d.lo + lane, d.lw, t, yv);
       // B, C
-      t = unit_chain<PT, S, false>(t, mf, __reduce_or_sync(0xffffffffu, mf), cf, seg);
+      t = unit_chain<PT, S>(t, d.lm, mf, __reduce_or_sync(0xffffffffu, mf), cf, src);
       const PT y = t * dv;
       if (MODE == M_FWD) {
         if (on) yv[row] = y;
         continue;
       }
       // the last color: its backward sweep at once (y stays in registers)
-      unit_coef<PT, S>(wuv<PT>(P), d.ui, mb, lane, cf);
+      unit_coef<PT, S>(wuv<PT>(P), P.wu_src, d.ui, d.us, d.um, mb, lane, cf, src);
       t = y;
     } else {
       if (on) t = __ldcg(yv + row);
     }
     t = unit_ext<PT>(P.su_col, suv<PT>(P), d.uo + lane, d.uw, t, zv);
-    t = unit_chain<PT, S, true>(t, mb, __reduce_or_sync(0xffffffffu, mb), cf, seg);
+    t = unit_chain<PT, S>(t, d.um, mb, __reduce_or_sync(0xffffffffu, mb), cf, src);
     const PT z = t * dv;
     if (on) {
       zv[row] = z;
@@ -2117,6 +2123,8 @@ cudaError_t launch_unit_s(const Params &P, const Plan &L, int c, int mode, bool 
 template <typename PT>
 cudaError_t launch_unit(const Params &P, const Plan &L, int c, int mode, bool update, int fin, const SlotArgs &sa) {
   switch (L.unit_S[c]) {
+    case 1: return launch_unit_s<PT, 1>(P, L, c, mode, update, fin, sa);
+    case 2: return launch_unit_s<PT, 2>(P, L, c, mode, update, fin, sa);
     case 4: return launch_unit_s<PT, 4>(P, L, c, mode, update, fin, sa);
     case 8: return launch_unit_s<PT, 8>(P, L, c, mode, update, fin, sa);
     case 16: return launch_unit_s<PT, 16>(P, L, c, mode, update, fin, sa);

@@ -147,7 +147,12 @@ def test_batched_device_buffers_and_autotune():
 def test_batched_rejects_lane_tile_contexts():
     a = gen.poisson3d_7pt(6)
     bl = oracle.blocking(a, "abmc", 8)
-    S = iccg.Solver(a, bl)                          # lane tiles (default)
+    S = iccg.Solver(a, bl)                          # warp units (default for 8-row blocks)
+    with pytest.raises(iccg.IccgError) as ei:
+        iccg.BatchSolver([S], 2)
+    assert ei.value.status == 1
+    S.close()
+    S = iccg.Solver(a, bl, tile_mapping="cta")      # lane tiles
     with pytest.raises(iccg.IccgError) as ei:
         iccg.BatchSolver([S], 2)
     assert ei.value.status == 1

@@ -8,7 +8,7 @@ Bars (element by element on the same seeded inputs):
   * blockings / permutations are inputs and bit-exact by construction.
 Cases span several tiles, ragged tails, multi-tile blocks (ABMC s > 32R,
 Leiden modularity blocks of hundreds of rows), one-color and one-row systems,
-and every launch shape: warp units (one warp per block of 3..32 rows, a lane
+and every launch shape: warp units (one warp per block of up to 32 rows, a lane
 per row), lane tiles (one block per lane) and CTA groups (level by level)
 under several rows-per-thread / warps-per-CTA choices, the phased solve as a
 CUDA graph or a host loop, with or without programmatic dependent launch, and
@@ -347,11 +347,18 @@ def test_fused_color_without_in_block_entries():
     b = gen.rhs_uniform(a.n, 12)
     ref = oracle.iccg(a, b, bl["perm"])
     for fp32 in (False, True):
-        S = iccg.Solver(a, bl, precond_fp32=fp32)
-        assert iccg.iccg_info(S.ctx)["tile_colors"] == bl["n_c"]
-        x = np.zeros(a.n)
-        st, it, _ = iccg.iccg_solve(S.ctx, b, x)
-        assert st == iccg.ICCG_OK
-        if not fp32:
-            assert abs(it - ref["iterations"]) <= 1 and _rel(x, ref["x"]) <= 1e-10
-        S.close()
+        # the lane-tile layout the regression concerns, then the default
+        # (warp units for the 32-row blocks)
+        for mapping in ("cta", "auto"):
+            S = iccg.Solver(a, bl, precond_fp32=fp32, tile_mapping=mapping)
+            info = iccg.iccg_info(S.ctx)
+            if mapping == "cta":
+                assert info["tile_colors"] == bl["n_c"]
+            else:
+                assert info["unit_colors"] + info["tile_colors"] == bl["n_c"]
+            x = np.zeros(a.n)
+            st, it, _ = iccg.iccg_solve(S.ctx, b, x)
+            assert st == iccg.ICCG_OK
+            if not fp32:
+                assert abs(it - ref["iterations"]) <= 1 and _rel(x, ref["x"]) <= 1e-10
+            S.close()

@@ -43,7 +43,7 @@ def test_layout_invariants(mat, blk, lane_max, units):
     sizes = np.diff(np.asarray(bl["block_ptr"]))
     if lane_max == 0 and not units:
         assert tiles == 0
-    if (lane_max and sizes.max() <= lane_max) or (units and lane_max >= 2 and sizes.max() <= 32):
+    if (lane_max and sizes.max() <= lane_max) or (units and sizes.max() <= 32):
         assert groups == 0
 
 
