@@ -177,15 +177,19 @@ def make_blocking(mod, a, args):
     reference arm; both give the same permutation)."""
     if args.blocking == "abmc":
         return mod.blocking(a, "abmc", args.block_size)
+    if args.blocking == "levels":
+        return mod.blocking(a, "levels")
     return mod.blocking(a, args.blocking, gamma=args.gamma)
 
 
 def blocking_name(args):
     if args.blocking == "abmc":
         return f"ABMC s={args.block_size}"
+    if args.blocking == "levels":
+        return "level sets of the natural order (level scheduling)"
     if args.blocking == "leiden_cpm":
         return f"Leiden CPM resolution {args.gamma:g}"
-    return "Leiden modularity"
+    return f"Leiden modularity resolution {args.gamma:g}"
 
 
 def bytes_model(n, nnz, nL, fp32):
@@ -745,7 +749,7 @@ def main():
     p.add_argument("--workload", default="poisson128", choices=sorted(WORKLOADS))
     p.add_argument("--nx", type=int, default=None, help="grid side (default 128, or 96 for diffusion96)")
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--blocking", default=None, choices=["abmc", "leiden_cpm", "leiden_md"],
+    p.add_argument("--blocking", default=None, choices=["abmc", "leiden_cpm", "leiden_md", "levels"],
                    help="default: leiden_cpm for poisson128, abmc otherwise")
     p.add_argument("--gamma", type=float, default=0.5, help="Leiden CPM resolution")
     p.add_argument("--block-size", type=int, default=None, help="ABMC block size (default 8, or 32 for diffusion96)")

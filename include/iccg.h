@@ -91,6 +91,14 @@ typedef struct {
                                  largest block has 5..32 rows, pair kernels for the
                                  colors whose blocks all have two rows, one CTA per
                                  tile otherwise */
+  int32_t fuse_sweep;         /* layouts whose colors are all lane tiles of blocks of
+                                 one or two rows: 1 runs each preconditioner sweep
+                                 (every color forward and backward) as one
+                                 cooperative launch with bounded grid barriers
+                                 between colors (a wait longer than the limit of
+                                 iccg_set_wait_limit ends the solve with
+                                 ICCG_ERR_TIMEOUT); 0 (default) or -1 one launch per
+                                 color; other layouts ignore it */
 } iccg_opts;
 
 enum { ICCG_SOLVER_AUTO = 0, ICCG_SOLVER_PERSISTENT = 1, ICCG_SOLVER_PHASED = 2 };
@@ -190,21 +198,22 @@ iccg_status iccg_profile_solve(iccg_ctx *ctx, const double *b, double *x, double
  * own inputs, so results are unaffected). */
 iccg_status iccg_time_spmv_phase(iccg_ctx *ctx, int32_t reps, double *ms);
 
-/* Layout facts of a context, out[14]: n, nnz, n_b, n_c, number of groups (a
+/* Layout facts of a context, out[15]: n, nnz, n_b, n_c, number of groups (a
  * group = consecutive whole blocks of one color, at most 32 * warps_per_cta *
  * rows_per_thread rows, or one larger block; one CTA each), number of groups
  * too large for the shared-memory plan, strictly-lower entries nL, deepest
  * in-group level count, largest group (rows), number of lane tiles (32
  * blocks, one per lane), number of colors run as lane tiles, number of
  * those run one warp per tile and as pair kernels (tile_mapping), number of
- * colors run as warp units. */
-iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[14]);
+ * colors run as warp units, 1 when each sweep is one cooperative launch. */
+iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[15]);
 
-/* Wall-time limit (ns) of every device-side wait of this context's
- * persistent solver (its grid barriers; Alg. 1's colors are separated by one
- * barrier each there).  A wait that runs past it makes the kernel stop at
- * once and iccg_solve return ICCG_ERR_TIMEOUT; the context stays usable.
- * 0 restores the default (4 s).  The phased solver has no device-side waits. */
+/* Wall-time limit (ns) of every device-side wait of this context: the grid
+ * barriers of the persistent solver and of the cooperative sweep
+ * (opts.fuse_sweep; Alg. 1's colors are separated by one barrier each
+ * there).  A wait that runs past it makes the kernel stop at once and
+ * iccg_solve return ICCG_ERR_TIMEOUT; the context stays usable.  0 restores
+ * the default (4 s).  Per-color launches have no device-side waits. */
 iccg_status iccg_set_wait_limit(iccg_ctx *ctx, uint64_t wait_ns);
 
 iccg_status iccg_last_error(const iccg_ctx *ctx, int64_t *row_or_block, const char **msg);
@@ -340,6 +349,19 @@ iccg_status iccg_sort_blocks_desc(int32_t n, int32_t n_b, int32_t *block_of);
 iccg_status iccg_color_order(int32_t n, const int64_t *gptr, const int32_t *gadj, int32_t n_b,
                              const int32_t *block_of, int32_t *color_of, int32_t *n_c,
                              int32_t *perm, int32_t *block_ptr, int32_t *color_ptr);
+
+/* Level-set ordering, the level scheduling of the triangular solves (Sec. 2)
+ * expressed as a block-multicolor ordering: level_of[i] = 0 when no
+ * neighbour j < i exists, else 1 + max level_of[j] over the neighbours j < i;
+ * rows of one level are never adjacent, so each level is a color of one-row
+ * blocks.  perm int32[n] (levels ascending, rows ascending within a level),
+ * block_ptr int32[n+1] (= 0..n), color_ptr int32[n+1] (first n_lev+1 used),
+ * *n_lev the number of levels.  The IC(0) factor and the substitutions in
+ * this order are those of the natural order (every adjacent pair keeps its
+ * relative order), so iccg_setup with these arrays gives the GPU
+ * level-scheduled ICCG of the natural ordering. */
+iccg_status iccg_level_order(int32_t n, const int64_t *gptr, const int32_t *gadj, int32_t *level_of,
+                             int32_t *n_lev, int32_t *perm, int32_t *block_ptr, int32_t *color_ptr);
 
 /* Diagnostics (host only, no device): builds the layout iccg_setup would
  * build for these inputs (groups of at most group_rows rows, lane tiles for

@@ -60,6 +60,8 @@ def lib():
         L.orc_delta_quality.restype = c_d
         L.orc_sort_blocks_desc.argtypes = [c_i32, c_i32, _i32p]
         L.orc_order.argtypes = [c_i32, c_i32, c_i32, _i32p, _i32p, _i32p, _i32p, _i32p]
+        L.orc_level_order.argtypes = [c_i32, _i64p, _i32p, _i32p, _i32p, _i32p, _i32p]
+        L.orc_level_order.restype = c_i32
         L.orc_ic0.argtypes = [c_i32, _i64p, _i32p, _f64p, _f64p]
         L.orc_ic0.restype = c_i64
         L.orc_forward.argtypes = [c_i32, _i64p, _i32p, _f64p, _f64p, _f64p]
@@ -154,12 +156,28 @@ def order(n, n_b, n_c, block_of, color_of):
     return perm[:n], bptr, cptr
 
 
+def level_order(n, gptr, gadj):
+    """Level sets of the natural order (level scheduling, Sec. 2): returns
+    (level [n], n_levels, perm, block_ptr [n+1], color_ptr [n_levels+1])."""
+    lev = np.zeros(max(n, 1), dtype=np.int32)
+    perm = np.zeros(max(n, 1), dtype=np.int32)
+    bptr = np.zeros(n + 1, dtype=np.int32)
+    cptr = np.zeros(n + 1, dtype=np.int32)
+    nl = lib().orc_level_order(n, _c(gptr, np.int64), _c(gadj, np.int32), lev, perm, bptr, cptr)
+    return lev[:n], int(nl), perm[:n], bptr, cptr[:nl + 1]
+
+
 def blocking(a, method: str = "abmc", block_size: int = 32, gamma: float = 1.0,
              n_iter: int = 2, beta: float = 0.01, seed: int = 42):
     """Full blocking pipeline: graph -> blocks -> (Leiden: size sort) -> colors ->
-    ordering.  Returns dict(perm, block_ptr, color_ptr, n_b, n_c, block_of, color_of)."""
+    ordering, or the level-set ordering of the natural order ("levels").
+    Returns dict(perm, block_ptr, color_ptr, n_b, n_c, block_of, color_of)."""
     n = a.n
     gptr, gadj = graph(n, a.rowptr, a.colind)
+    if method == "levels":
+        lev, nl, perm, bptr, cptr = level_order(n, gptr, gadj)
+        return {"perm": perm, "block_ptr": bptr, "color_ptr": cptr, "n_b": n, "n_c": nl,
+                "block_of": np.arange(n, dtype=np.int32), "color_of": lev}
     if method == "abmc":
         block_of, nb = abmc(n, gptr, gadj, block_size)
     elif method in ("leiden_md", "leiden_cpm"):

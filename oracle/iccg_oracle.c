@@ -12,6 +12,7 @@
  *   - greedy block coloring ........................... Sec. 3; Sec. 5.1 (Saad's greedy)
  *   - Leiden with modularity (Eq. 1) / CPM (Eq. 2) .... Sec. 4; Sec. 6.1 (2 iterations, beta 0.01)
  *   - block ordering (Leiden: size descending) ........ Sec. 6.1
+ *   - level-set ordering (level scheduling baseline) .. Sec. 2
  *   - IC(0) factor, L L^T form ........................ Sec. 3 (Alg. 1 divides by L_ii)
  *   - forward / backward substitution ................. Sec. 3, Alg. 1 and the text after it
  *   - PCG, stop at ||r||_2/||b||_2 <= tol .............. Sec. 1; Sec. 4 (tol 1e-8)
@@ -693,6 +694,34 @@ void orc_order(int32_t n, int32_t n_b, int32_t n_c, const int32_t *block_of,
   block_ptr[n_b] = pos;
   for (int32_t i = 0; i < n; ++i) perm[start[block_of[i]]++] = i;
   free(border); free(size); free(start);
+}
+
+/* Level sets of the natural order (level scheduling, Sec. 2): a row's level
+ * is the length of the longest chain of preceding neighbours ending at it,
+ * i.e. 0 with no neighbour j < i, else 1 + the largest level of such j.  The
+ * ordering lists levels ascending, rows ascending within a level; every row
+ * is its own block and every level a color.  Returns the number of levels. */
+int32_t orc_level_order(int32_t n, const int64_t *gptr, const int32_t *gadj, int32_t *level,
+                        int32_t *perm, int32_t *block_ptr, int32_t *color_ptr) {
+  int32_t nl = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t lv = 0;
+    for (int64_t e = gptr[i]; e < gptr[i + 1]; ++e) {
+      const int32_t j = gadj[e];
+      if (j < i && level[j] + 1 > lv) lv = level[j] + 1;
+    }
+    level[i] = lv;
+    if (lv + 1 > nl) nl = lv + 1;
+  }
+  int32_t pos = 0;
+  for (int32_t v = 0; v < nl; ++v) {
+    color_ptr[v] = pos;
+    for (int32_t i = 0; i < n; ++i)
+      if (level[i] == v) perm[pos++] = i;
+  }
+  color_ptr[nl] = pos;
+  for (int32_t k = 0; k <= n; ++k) block_ptr[k] = k;
+  return nl;
 }
 
 /* ------------------------------------------------------------------------- */

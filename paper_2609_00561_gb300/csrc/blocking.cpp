@@ -492,4 +492,34 @@ iccg_status iccg_color_order(int32_t n, const int64_t *gptr, const int32_t *gadj
   return ICCG_OK;
 }
 
+// Level-set ordering (the level scheduling of Sec. 2): the level of row i is
+// 0 when no neighbour precedes it in the natural order, else one more than
+// the deepest preceding neighbour.  Rows of one level are never adjacent, so
+// the levels are colors of one-row blocks; ordering rows by level (ascending
+// index within a level) keeps the relative order of every adjacent pair, so
+// IC(0) and its substitutions are those of the natural order.
+iccg_status iccg_level_order(int32_t n, const int64_t *gptr, const int32_t *gadj, int32_t *level_of, int32_t *n_lev,
+                             int32_t *perm, int32_t *block_ptr, int32_t *color_ptr) {
+  if (n < 0 || !gptr || !level_of || !n_lev || !perm || !block_ptr || !color_ptr) return ICCG_ERR_ARG;
+  int32_t nl = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t lv = 0;
+    for (int64_t e = gptr[i]; e < gptr[i + 1]; ++e) {
+      const int32_t j = gadj[e];
+      if (j < 0 || j >= n) return ICCG_ERR_ARG;
+      if (j < i) lv = std::max(lv, level_of[j] + 1);
+    }
+    level_of[i] = lv;
+    nl = std::max(nl, lv + 1);
+  }
+  *n_lev = nl;
+  std::vector<int32_t> cnt(size_t(nl) + 1, 0);
+  for (int32_t i = 0; i < n; ++i) cnt[size_t(level_of[i]) + 1]++;
+  for (int32_t v = 0; v < nl; ++v) cnt[size_t(v) + 1] += cnt[size_t(v)];
+  for (int32_t v = 0; v <= nl; ++v) color_ptr[v] = cnt[size_t(v)];
+  for (int32_t i = 0; i < n; ++i) perm[cnt[size_t(level_of[i])]++] = i;
+  for (int32_t k = 0; k <= n; ++k) block_ptr[k] = k;
+  return ICCG_OK;
+}
+
 }  // extern "C"

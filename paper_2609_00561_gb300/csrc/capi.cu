@@ -130,6 +130,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   if (o.tile_mapping < ICCG_TILES_AUTO || o.tile_mapping > ICCG_TILES_UNITS) return ICCG_ERR_ARG;
   if (o.lane_block_max > 32 || o.lane_block_max < -1) return ICCG_ERR_ARG;
   if (o.solver < ICCG_SOLVER_AUTO || o.solver > ICCG_SOLVER_PHASED) return ICCG_ERR_ARG;
+  if (o.fuse_sweep < -1 || o.fuse_sweep > 1) return ICCG_ERR_ARG;
   if (o.warps_per_cta == 0) o.warps_per_cta = 8;
   if (o.rows_per_thread == 0) o.rows_per_thread = 1;
   if (o.warps_per_cta < 1 || o.warps_per_cta > kMaxWarpsPerCta) return ICCG_ERR_ARG;
@@ -324,6 +325,21 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
                               : std::max(1, L.task1[c] - L.task0[c]);
     gbig = std::max(gbig, L.grid_c[c]);
   }
+  // one cooperative launch per sweep when every color is pair tiles (blocks
+  // of one or two rows) and every CTA of that launch can be resident
+  {
+    bool pairs_only = n_c > 0 && H.groups.empty() && H.units.empty();
+    for (const TileDesc &td : H.tiles) pairs_only = pairs_only && td.nsteps <= 2;
+    for (int c = 0; c < n_c; ++c) pairs_only = pairs_only && L.tile1[c] > L.tile0[c];
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+    // on request only: at 128^3 with Leiden CPM 0.5 (8 colors) its grid
+    // barriers cost more than the launch boundaries they replace
+    const int per_sm = pairs_only && coop && o.fuse_sweep > 0 ? coop_sweep_resident_ctas(ctx->fp32) : 0;
+    L.coop = per_sm > 0;
+    L.grid_coop = L.coop ? sms * per_sm : 0;
+    gbig = std::max(gbig, L.grid_coop);
+  }
   // slot regions: forward launches in color order (<r,r>), then the fused
   // launch and the backward launches in launch order (<r,z>); the final
   // launch (backward color 0, or the fused launch of a one-color ordering)
@@ -399,6 +415,11 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   int32_t *d_cg;
   CK(dev_upload(ctx, &d_cg, H.color_group), "alloc groups");
   P.color_group = d_cg;
+  {
+    int32_t *d_ct;
+    CK(dev_upload(ctx, &d_ct, H.color_tile), "alloc tiles");
+    P.ctile = d_ct;
+  }
   {
     WarpUnit *d_units;
     uint32_t *d_wlm, *d_wum;
@@ -656,6 +677,14 @@ static iccg_status solve_impl(iccg_ctx *ctx, const double *b, double *x, double 
   const bool use_graph = !persistent && ctx->opts.no_graph == 0 && prof == nullptr;
   if (use_graph && !ctx->gexec) {
     st = build_graph(ctx);
+    if (st != ICCG_OK && ctx->plan.coop) {
+      // the runtime would not capture the cooperative sweep into the graph:
+      // one launch per color instead
+      destroy_graph(ctx);
+      cudaGetLastError();
+      ctx->plan.coop = false;
+      st = build_graph(ctx);
+    }
     if (st != ICCG_OK) { destroy_graph(ctx); return st; }
   }
   CK(copy_in(ctx, ctx->bin, b, size_t(n)), "copy b");
@@ -899,7 +928,7 @@ iccg_status iccg_get_factor(iccg_ctx *ctx, double *lval, int64_t *nnz_lower) {
   return ICCG_OK;
 }
 
-iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[14]) {
+iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[15]) {
   if (!ctx || !out) return ICCG_ERR_ARG;
   const HostLayout &H = ctx->H;
   out[0] = H.n;
@@ -920,12 +949,15 @@ iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[14]) {
     out[12] += w == 2 ? 1 : 0;
   }
   out[13] = H.unit_colors;
+  out[14] = ctx->plan.coop ? 1 : 0;
   return ICCG_OK;
 }
 
 iccg_status iccg_set_wait_limit(iccg_ctx *ctx, uint64_t wait_ns) {
   if (!ctx) return ICCG_ERR_ARG;
+  DeviceGuard guard(ctx->device);
   ctx->P.wait_ns = wait_ns ? wait_ns : kDefaultWaitNs;
+  destroy_graph(ctx);   // the captured launches hold the old limit
   return ICCG_OK;
 }
 

@@ -251,6 +251,7 @@ struct Params {
   float *wl_val32, *wu_val32;
   int32_t nwl, nwu;
   const int32_t *bptr;
+  const int32_t *ctile;         // first lane tile of each color [n_c + 1] (cooperative sweep)
 };
 
 // ---- host-side layout built by iccg_setup --------------------------------
@@ -329,6 +330,8 @@ struct Plan {
   std::vector<char> wtile;              // color c: 0 CTA per tile, 1 warp-tile kernels, 2 pair kernels, 3 warp units
   std::vector<int32_t> unit0, unit1, unit_S;   // warp-unit range and segment size of each color
   int32_t Wu = 8;                       // warps per CTA of the warp-unit kernels
+  bool coop = false;                    // every sweep as one cooperative launch (pair-tile layouts)
+  int32_t grid_coop = 0;                // CTAs of that launch (all resident)
   int32_t Ww = 8;                       // warps per CTA of the warp-tile kernels
   int32_t smem_wt = 0;                  // bytes per CTA of the warp-tile kernels
   int32_t cap_ws = 0;                   // steps per tile held in a warp's buffer
@@ -355,6 +358,7 @@ int tile_resident_ctas(bool fp32, int threads, int smem);    // CTAs per SM of t
 int wtile_resident_ctas(bool fp32, int threads, int smem);   // CTAs per SM of the warp-tile kernels
 int pair_resident_ctas(bool fp32, int threads);              // CTAs per SM of the pair kernels
 int unit_resident_ctas(bool fp32, int S, int threads);       // CTAs per SM of the warp-unit kernels
+int coop_sweep_resident_ctas(bool fp32);                     // CTAs per SM of the cooperative sweep (0: none)
 cudaError_t launch_factor(const Params &P, const Plan &L, int nL);
 cudaError_t launch_solve_init(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);
 cudaError_t launch_solve_body(const Params &P, const Plan &L, bool fp32, PhaseHook h, void *u);

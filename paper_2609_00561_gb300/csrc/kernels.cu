@@ -1132,6 +1132,51 @@ __device__ __forceinline__ void pair_bwd(const Params &P, const PairDesc &d, int
   }
 }
 
+// one tile of a pair color, warp-wide (lanes beyond the tile's blocks idle)
+template <typename PT, int MODE, bool UPDATE>
+__device__ __forceinline__ void pair_tile(const Params &P, int t, int lane, double alpha, double &rr_acc,
+                                          double &rz_acc) {
+  PT *yv = reinterpret_cast<PT *>(P.y);
+  const PT *dvg = invds<PT>(P);
+  const PairDesc d = load_pair(P.pairs + t);
+  if (lane >= d.c0) return;   // a lane active in step 1 is active in step 0
+  const bool a1 = lane < d.c1;
+  const int i0 = d.row0 + lane, i1 = d.row0 + d.c0 + lane;
+  const PT dv0 = __ldg(dvg + i0), dv1 = a1 ? __ldg(dvg + i1) : PT(0);
+  if (MODE == M_BWD) {
+    const PT y0 = __ldcg(yv + i0), y1 = a1 ? __ldcg(yv + i1) : PT(0);
+    const double r0 = __ldcg(P.r + i0), r1 = a1 ? __ldcg(P.r + i1) : 0.0;
+    pair_bwd<PT>(P, d, lane, a1, y0, y1, dv0, dv1, r0, r1, rz_acc);
+  } else {
+    double r0 = __ldcg(P.r + i0), r1 = a1 ? __ldcg(P.r + i1) : 0.0;
+    if (UPDATE) {
+      r0 -= alpha * __ldcg(P.q + i0);
+      P.r[i0] = r0;
+      P.xh[i0] = __ldcg(P.xh + i0) + alpha * __ldcg(P.p0 + i0);
+      rr_acc += r0 * r0;
+      if (a1) {
+        r1 -= alpha * __ldcg(P.q + i1);
+        P.r[i1] = r1;
+        P.xh[i1] = __ldcg(P.xh + i1) + alpha * __ldcg(P.p0 + i1);
+        rr_acc += r1 * r1;
+      }
+    }
+    const PT y0 = pair_sub<PT>(P.sl_col, slv<PT>(P), d.lo + lane, d.c0, d.lw0, PT(r0), yv, 0) * dv0;
+    PT y1 = PT(0);
+    if (a1) {
+      PT acc1 = pair_sub<PT>(P.sl_col, slv<PT>(P), d.lo + d.lw0 * d.c0 + lane, d.c1, d.lw1, PT(r1), yv, 0);
+      for (int j = 0; j < d.liw1; ++j) acc1 -= __ldg(siv<PT>(P) + d.li + j * d.c1 + lane) * y0;
+      y1 = acc1 * dv1;
+    }
+    if (MODE == M_FWD) {
+      yv[i0] = y0;
+      if (a1) yv[i1] = y1;
+    } else {
+      pair_bwd<PT>(P, d, lane, a1, y0, y1, dv0, dv1, r0, r1, rz_acc);
+    }
+  }
+}
+
 template <typename PT, int MODE, bool UPDATE>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
 pair_kernel(Params P, int t0, int t1, int fin, SlotArgs sa) {
@@ -1143,47 +1188,8 @@ pair_kernel(Params P, int t0, int t1, int fin, SlotArgs sa) {
   double rr_acc = 0.0, rz_acc = 0.0;
   pdl_wait();
   const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
-  PT *yv = reinterpret_cast<PT *>(P.y);
-  const PT *dvg = invds<PT>(P);
-  for (int t = t0 + int(blockIdx.x) * nw + int(threadIdx.x >> 5); t < t1; t += stride) {
-    const PairDesc d = load_pair(P.pairs + t);
-    if (lane >= d.c0) continue;   // a lane active in step 1 is active in step 0
-    const bool a1 = lane < d.c1;
-    const int i0 = d.row0 + lane, i1 = d.row0 + d.c0 + lane;
-    const PT dv0 = __ldg(dvg + i0), dv1 = a1 ? __ldg(dvg + i1) : PT(0);
-    if (MODE == M_BWD) {
-      const PT y0 = __ldcg(yv + i0), y1 = a1 ? __ldcg(yv + i1) : PT(0);
-      const double r0 = __ldcg(P.r + i0), r1 = a1 ? __ldcg(P.r + i1) : 0.0;
-      pair_bwd<PT>(P, d, lane, a1, y0, y1, dv0, dv1, r0, r1, rz_acc);
-    } else {
-      double r0 = __ldcg(P.r + i0), r1 = a1 ? __ldcg(P.r + i1) : 0.0;
-      if (UPDATE) {
-        r0 -= alpha * __ldcg(P.q + i0);
-        P.r[i0] = r0;
-        P.xh[i0] = __ldcg(P.xh + i0) + alpha * __ldcg(P.p0 + i0);
-        rr_acc += r0 * r0;
-        if (a1) {
-          r1 -= alpha * __ldcg(P.q + i1);
-          P.r[i1] = r1;
-          P.xh[i1] = __ldcg(P.xh + i1) + alpha * __ldcg(P.p0 + i1);
-          rr_acc += r1 * r1;
-        }
-      }
-      const PT y0 = pair_sub<PT>(P.sl_col, slv<PT>(P), d.lo + lane, d.c0, d.lw0, PT(r0), yv, 0) * dv0;
-      PT y1 = PT(0);
-      if (a1) {
-        PT acc1 = pair_sub<PT>(P.sl_col, slv<PT>(P), d.lo + d.lw0 * d.c0 + lane, d.c1, d.lw1, PT(r1), yv, 0);
-        for (int j = 0; j < d.liw1; ++j) acc1 -= __ldg(siv<PT>(P) + d.li + j * d.c1 + lane) * y0;
-        y1 = acc1 * dv1;
-      }
-      if (MODE == M_FWD) {
-        yv[i0] = y0;
-        if (a1) yv[i1] = y1;
-      } else {
-        pair_bwd<PT>(P, d, lane, a1, y0, y1, dv0, dv1, r0, r1, rz_acc);
-      }
-    }
-  }
+  for (int t = t0 + int(blockIdx.x) * nw + int(threadIdx.x >> 5); t < t1; t += stride)
+    pair_tile<PT, MODE, UPDATE>(P, t, lane, alpha, rr_acc, rz_acc);
   launch_epilogue(P, fin, sa, MODE != M_BWD && UPDATE, MODE != M_FWD, rr_acc, rz_acc, red, &flag);
 }
 
@@ -2024,6 +2030,59 @@ persistent_kernel(Params P, GroupSmemPlan plan, int cap_a) {
 }
 
 // ---------------------------------------------------------------------------
+// Cooperative sweep: a whole preconditioner application in one launch for a
+// layout whose colors are all pair tiles (blocks of one or two rows): the
+// forward colors, the fused last color and the backward colors (Alg. 1 and
+// the reverse sweep) one after another, each color's tiles taken grid-stride
+// by every warp of the grid, a bounded grid barrier where a color needs the
+// previous one's results; one reduction closes the launch.  It replaces the
+// 2 n_c - 1 color launches of the sweep, whose fixed cost (launch, ramp-up,
+// tail, per-launch reduction) dominates colors of few rows.
+// ---------------------------------------------------------------------------
+constexpr int kCoopWarps = 8;
+
+template <typename PT, bool UPDATE>
+__global__ void __launch_bounds__(kCoopWarps * kWarp)
+coop_sweep_kernel(Params P, int fin) {
+  __shared__ double red[kMaxWarpsPerCta];
+  __shared__ int flag;
+  const int lane = threadIdx.x & 31;
+  const int nw = int(blockDim.x >> 5), gw = int(blockIdx.x) * nw + int(threadIdx.x >> 5);
+  const int NW = int(gridDim.x) * nw, nc = P.n_c;
+  double rr_acc = 0.0, rz_acc = 0.0;
+  pdl_wait();
+  const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
+  GridSync gs{P.bar, 0u, &flag, nullptr, 0, 0, P.wait_ns};
+  bool ok = true;
+  for (int c = 0; c < nc - 1 && ok; ++c) {
+    const int t1 = __ldg(P.ctile + c + 1);
+    for (int t = __ldg(P.ctile + c) + gw; t < t1; t += NW) pair_tile<PT, M_FWD, UPDATE>(P, t, lane, alpha, rr_acc, rz_acc);
+    ok = phase_end(gs, PH_FWD);
+  }
+  if (ok) {
+    const int t1 = __ldg(P.ctile + nc);
+    for (int t = __ldg(P.ctile + nc - 1) + gw; t < t1; t += NW)
+      pair_tile<PT, M_FUSED, UPDATE>(P, t, lane, alpha, rr_acc, rz_acc);
+  }
+  for (int c = nc - 2; c >= 0 && ok; --c) {
+    if (!(ok = phase_end(gs, PH_BWD))) break;
+    const int t1 = __ldg(P.ctile + c + 1);
+    for (int t = __ldg(P.ctile + c) + gw; t < t1; t += NW) pair_tile<PT, M_BWD, false>(P, t, lane, alpha, rr_acc, rz_acc);
+  }
+  if (!ok) {
+    // a barrier wait gave up: the solve stops with ICCG_ERR_TIMEOUT
+    if (threadIdx.x == 0) {
+      P.sc->status = ICCG_ERR_TIMEOUT;
+      P.sc->done = 1;
+      set_condition(P.sc, 0);
+    }
+    return;
+  }
+  if (fin == FIN_NONE) return;
+  launch_epilogue(P, fin, SlotArgs{0, 0, 0, 0}, UPDATE, true, rr_acc, rz_acc, red, &flag);
+}
+
+// ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
 template <typename... KArgs, typename... Args>
@@ -2173,9 +2232,23 @@ cudaError_t launch_bwd(const Params &P, const Plan &L, int c, int fin) {
 // Forward sweep (with or without the x/r update), fused last color, backward
 // sweep.  fin_last: the epilogue run by the last launch.
 template <typename PT>
+cudaError_t launch_coop_sweep(const Params &P, const Plan &L, bool update, int fin) {
+  cudaError_t e = cudaMemsetAsync(P.bar, 0, sizeof(GridBar), L.stream);
+  if (e != cudaSuccess) return e;
+  if (update) return launch_coop(coop_sweep_kernel<PT, true>, L.grid_coop, kCoopWarps * kWarp, 0, L.stream, P, fin);
+  return launch_coop(coop_sweep_kernel<PT, false>, L.grid_coop, kCoopWarps * kWarp, 0, L.stream, P, fin);
+}
+
+template <typename PT>
 cudaError_t sweep(const Params &P, const Plan &L, bool update, int fin_last, PhaseHook h, void *u) {
   cudaError_t e = cudaSuccess;
   const int nc = L.n_c;
+  if (L.coop) {
+    if (h) h(u, PH_FWD, 1);
+    e = launch_coop_sweep<PT>(P, L, update, fin_last);
+    if (h) h(u, PH_FWD, 0);
+    return e;
+  }
   for (int c = 0; c < nc - 1 && e == cudaSuccess; ++c) {
     if (h) h(u, PH_FWD, 1);
     e = launch_fwd<PT>(P, L, c, update, false, FIN_NONE);
@@ -2267,6 +2340,18 @@ int pair_resident_ctas(bool fp32, int threads) {
     return 1;
   }
   return nb > 0 ? nb : 1;
+}
+
+int coop_sweep_resident_ctas(bool fp32) {
+  int nb = 0;
+  const cudaError_t e =
+      fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop_sweep_kernel<float, true>, kCoopWarps * kWarp, 0)
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop_sweep_kernel<double, true>, kCoopWarps * kWarp, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
 }
 
 int unit_resident_ctas(bool fp32, int S, int threads) {

@@ -33,7 +33,7 @@ class iccg_opts(ctypes.Structure):
     _fields_ = [("precond_fp32", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("rows_per_thread", ctypes.c_int32), ("no_graph", ctypes.c_int32),
                 ("no_pdl", ctypes.c_int32), ("solver", ctypes.c_int32), ("lane_block_max", ctypes.c_int32),
-                ("tile_mapping", ctypes.c_int32)]
+                ("tile_mapping", ctypes.c_int32), ("fuse_sweep", ctypes.c_int32)]
 
 
 SOLVERS = {"auto": 0, "persistent": 1, "phased": 2}
@@ -75,6 +75,7 @@ def load():
         "iccg_block_leiden": [i32, vp, vp, i32, d, i32, d, u64, vp, P(i32)],
         "iccg_sort_blocks_desc": [i32, i32, vp],
         "iccg_color_order": [i32, vp, vp, i32, vp, vp, P(i32), vp, vp, vp],
+        "iccg_level_order": [i32, vp, vp, vp, P(i32), vp, vp, vp],
         "iccg_spmv_dot_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp],
         "iccg_batch_create": [P(vp), vp, i32, i32, P(iccg_batch_opts)],
         "iccg_features": [i32, vp, vp, vp, vp],
@@ -137,13 +138,14 @@ def _as(a, dt):
 
 
 def make_opts(precond_fp32=0, warps_per_cta=0, rows_per_thread=0, no_graph=0, no_pdl=0, solver="auto",
-              lane_block_max=0, tile_mapping="auto"):
+              lane_block_max=0, tile_mapping="auto", fuse_sweep=0):
     o = iccg_opts()
     o.precond_fp32, o.warps_per_cta, o.rows_per_thread, o.no_graph, o.no_pdl = (
         int(precond_fp32), int(warps_per_cta), int(rows_per_thread), int(no_graph), int(no_pdl))
     o.solver = SOLVERS[solver] if isinstance(solver, str) else int(solver)
     o.lane_block_max = int(lane_block_max)
     o.tile_mapping = TILE_MAPPINGS[tile_mapping] if isinstance(tile_mapping, str) else int(tile_mapping)
+    o.fuse_sweep = int(fuse_sweep)
     return o
 
 
@@ -224,7 +226,7 @@ def iccg_time_spmv_phase(ctx, reps=50):
 
 
 INFO_KEYS = ("n", "nnz", "n_b", "n_c", "groups", "global_groups", "nL", "max_levels", "max_group_rows", "tiles",
-             "tile_colors", "warp_tile_colors", "pair_tile_colors", "unit_colors")
+             "tile_colors", "warp_tile_colors", "pair_tile_colors", "unit_colors", "fused_sweep")
 
 
 def iccg_info(ctx):
@@ -299,6 +301,19 @@ def iccg_color_order(n, gptr, gadj, n_b, block_of):
     return color_of[:n_b], nc.value, perm[:n], bptr, cptr[: nc.value + 1]
 
 
+def iccg_level_order(n, gptr, gadj):
+    """Returns (level_of, n_lev, perm, block_ptr, color_ptr)."""
+    gptr, gadj = _as(gptr, np.int64), _as(gadj, np.int32)
+    lev = np.zeros(max(n, 1), dtype=np.int32)
+    perm = np.zeros(max(n, 1), dtype=np.int32)
+    bptr = np.zeros(n + 1, dtype=np.int32)
+    cptr = np.zeros(n + 1, dtype=np.int32)
+    nl = ctypes.c_int32(0)
+    _check(load().iccg_level_order(int(n), _ptr(gptr), _ptr(gadj), _ptr(lev), ctypes.byref(nl), _ptr(perm),
+                                   _ptr(bptr), _ptr(cptr)), "iccg_level_order")
+    return lev[:n], nl.value, perm[:n], bptr, cptr[: nl.value + 1]
+
+
 NOALLOC_MAX_ROWS = 4194304
 
 
@@ -314,9 +329,15 @@ def iccg_spmv_dot_noalloc(n, rowptr, colind, val, p, q, pq, stream=None):
 # conveniences built only from the entry points above
 # ---------------------------------------------------------------------------
 def blocking(a, method="abmc", block_size=32, gamma=1.0, n_iter=2, beta=0.01, seed=42):
-    """graph -> ABMC or Leiden (+ size sort) -> greedy coloring -> ordering.
-    `a` has fields n, rowptr, colind.  Returns a dict like the oracle's."""
+    """graph -> ABMC or Leiden (+ size sort) -> greedy coloring -> ordering,
+    or the level-set ordering of the natural order ("levels": one-row blocks,
+    colors = levels).  `a` has fields n, rowptr, colind.  Returns a dict like
+    the oracle's."""
     gptr, gadj = iccg_graph(a.n, a.rowptr, a.colind)
+    if method == "levels":
+        lev, nl, perm, bptr, cptr = iccg_level_order(a.n, gptr, gadj)
+        return {"perm": perm, "block_ptr": bptr, "color_ptr": cptr, "n_b": a.n, "n_c": nl,
+                "block_of": np.arange(a.n, dtype=np.int32), "color_of": lev}
     if method == "abmc":
         block_of, nb = iccg_block_abmc(a.n, gptr, gadj, block_size)
     elif method in ("leiden_md", "leiden_cpm"):
@@ -334,12 +355,13 @@ class Solver:
     """Owns one iccg context: setup + factor at construction."""
 
     def __init__(self, a, bl, precond_fp32=False, warps_per_cta=0, rows_per_thread=0, no_graph=False,
-                 no_pdl=False, stream=None, factor=True, solver="auto", lane_block_max=0, tile_mapping="auto"):
+                 no_pdl=False, stream=None, factor=True, solver="auto", lane_block_max=0, tile_mapping="auto",
+                 fuse_sweep=0):
         self.n = a.n
         self.ctx = iccg_setup(a.n, a.nnz, a.rowptr, a.colind, a.val, bl["perm"], bl["block_ptr"],
                               bl["color_ptr"], bl["n_b"], bl["n_c"],
                               make_opts(precond_fp32, warps_per_cta, rows_per_thread, no_graph, no_pdl, solver,
-                                        lane_block_max, tile_mapping),
+                                        lane_block_max, tile_mapping, fuse_sweep),
                               stream)
         if factor:
             iccg_factor(self.ctx)

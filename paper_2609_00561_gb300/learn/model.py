@@ -212,6 +212,24 @@ def evaluate_fixed(ta, tc, gammas, block_sizes):
             "combined_regret_mean": float(np.mean(np.minimum(base_a, base_c) / np.minimum(best_a, best_c)))}
 
 
+def report(data, epochs=3000, seed=0):
+    """Train on the training split and evaluate on the held-out split: the
+    model, the best constant settings chosen on the training labels, and the
+    method without the model (fixed ABMC 32 / CPM 0.05)."""
+    X, yc, yr, ta, tc = labels(data)
+    tr, te = split(len(yc))
+    g, b = data["meta"]["gammas"], data["meta"]["block_sizes"]
+    m = Model(X.shape[1], len(b), seed=seed)
+    hist = m.fit(X[tr], yc[tr], yr[tr], epochs=epochs)
+    ia, ic = best_constants(ta[tr], tc[tr])
+    return m, {"train": evaluate(m, X[tr], ta[tr], tc[tr], g, b), "test": evaluate(m, X[te], ta[te], tc[te], g, b),
+               "test_best_constant": dict(evaluate_constant(ta[te], tc[te], ia, ic),
+                                          block_size=b[ia], gamma=g[ic]),
+               "test_fixed": evaluate_fixed(ta[te], tc[te], g, b), "loss": hist[::5],
+               "labels": {"block_size": {str(v): int(np.sum(yc == k)) for k, v in enumerate(b)},
+                          "gamma": {str(v): int(np.sum(np.isclose(np.exp(yr), v))) for v in g}}}
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--sweep", required=True)
@@ -225,13 +243,7 @@ def main():
         with open(args.sweep, "w") as f:
             json.dump(data, f)
         return
-    X, yc, yr, ta, tc = labels(data)
-    tr, te = split(len(yc))
-    m = Model(X.shape[1], len(data["meta"]["block_sizes"]))
-    hist = m.fit(X[tr], yc[tr], yr[tr], epochs=args.epochs)
-    g, b = data["meta"]["gammas"], data["meta"]["block_sizes"]
-    res = {"train": evaluate(m, X[tr], ta[tr], tc[tr], g, b), "test": evaluate(m, X[te], ta[te], tc[te], g, b),
-           "test_fixed": evaluate_fixed(ta[te], tc[te], g, b), "loss": hist[::5]}
+    m, res = report(data, args.epochs)
     print(json.dumps(res, indent=1))
     if args.out:
         m.save(args.out)

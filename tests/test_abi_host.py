@@ -137,3 +137,14 @@ def test_leiden_iteration_count_and_beta_are_honoured():
             m1, k1 = iccg.iccg_block_leiden(a.n, gptr, gadj, "cpm", 0.05, n_iter, beta, 7)
             m2, k2 = oracle.leiden(a.n, gptr, gadj, "cpm", 0.05, n_iter, beta, 7)
             assert k1 == k2 and np.array_equal(m1, m2)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_level_order_equals_oracle(name):
+    a = CASES[name]()
+    gptr, gadj = iccg.iccg_graph(a.n, a.rowptr, a.colind)
+    lev, nl, perm, bptr, cptr = iccg.iccg_level_order(a.n, gptr, gadj)
+    og, oa = oracle.graph(a.n, a.rowptr, a.colind)
+    olev, onl, operm, obptr, ocptr = oracle.level_order(a.n, og, oa)
+    assert nl == onl and np.array_equal(lev, olev) and np.array_equal(perm, operm)
+    assert np.array_equal(bptr, obptr) and np.array_equal(cptr, ocptr)

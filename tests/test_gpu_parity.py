@@ -53,6 +53,9 @@ CASES = {
     "aniso27": (lambda: (gen.stencil_aniso("27pt", 3375, 4.0), gen.rhs_uniform(3375, 8), None), "abmc", {"block_size": 32}),
     "elast27": (lambda: (gen.elasticity_like(700, 27, 3.0), gen.rhs_uniform(2187, 9), None), "abmc", {"block_size": 24}),
     "diff27": (lambda: (gen.diffusion3d_27pt(14, seed=2), gen.rhs_uniform(2744, 10), None), "abmc", {"block_size": 32}),
+    # level scheduling of the natural order: one-row blocks, a color per level
+    "grid3d_levels": (lambda: (gen.poisson3d_7pt(13), gen.rhs_uniform(2197, 16), None), "levels", {}),
+    "rgg_levels": (lambda: (gen.rgg_laplacian(1500, 10.0, 5), gen.rhs_uniform(1500, 17), None), "levels", {}),
 }
 
 _cache = {}
@@ -78,13 +81,16 @@ SHAPES = [dict(), dict(lane_block_max=8), dict(lane_block_max=-1),
           dict(solver="persistent"), dict(solver="persistent", rows_per_thread=4, warps_per_cta=4),
           dict(solver="persistent", warps_per_cta=16), dict(tile_mapping="warp"), dict(tile_mapping="cta"),
           dict(tile_mapping="warp", warps_per_cta=3, lane_block_max=16), dict(tile_mapping="units"),
-          dict(tile_mapping="units", lane_block_max=16), dict(tile_mapping="units", no_graph=1)]
+          dict(tile_mapping="units", lane_block_max=16), dict(tile_mapping="units", no_graph=1),
+          dict(fuse_sweep=1), dict(fuse_sweep=1, no_graph=1), dict(fuse_sweep=1, precond_fp32=0, warps_per_cta=4)]
 LAYOUTS = {"lanes": dict(), "groups": dict(lane_block_max=-1), "warp_tiles": dict(tile_mapping="warp"),
            "cta_tiles": dict(tile_mapping="cta"), "pair_tiles": dict(tile_mapping="pair"),
-           "units": dict(tile_mapping="units"), "units16": dict(tile_mapping="units", lane_block_max=16)}
+           "units": dict(tile_mapping="units"), "units16": dict(tile_mapping="units", lane_block_max=16),
+           "fused": dict(fuse_sweep=1)}
 SOLVERS = {"lanes": dict(), "groups": dict(lane_block_max=-1), "persistent": dict(solver="persistent"),
            "warp_tiles": dict(tile_mapping="warp"), "cta_tiles": dict(tile_mapping="cta"),
-           "pair_tiles": dict(tile_mapping="pair"), "units": dict(tile_mapping="units")}
+           "pair_tiles": dict(tile_mapping="pair"), "units": dict(tile_mapping="units"),
+           "fused": dict(fuse_sweep=1)}
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -288,6 +294,15 @@ def test_layout_choice_follows_block_sizes():
     a4, b4, bl4, ref4 = _case("grid3d_abmc100")
     S = iccg.Solver(a4, bl4)
     assert iccg.iccg_info(S.ctx)["groups"] > 0     # blocks above 32 rows: CTA groups
+    assert iccg.iccg_info(S.ctx)["fused_sweep"] == 0
+    S.close()
+    # blocks of one or two rows: each sweep one cooperative launch on request
+    a5, b5, bl5, ref5 = _case("grid3d_cpm_pairs")
+    S = iccg.Solver(a5, bl5, fuse_sweep=1)
+    assert iccg.iccg_info(S.ctx)["fused_sweep"] == 1
+    S.close()
+    S = iccg.Solver(a5, bl5)
+    assert iccg.iccg_info(S.ctx)["fused_sweep"] == 0
     S.close()
     a2, b2, bl2, ref2 = _case("grid3d_cpm_singletons")
     S = iccg.Solver(a2, bl2)

@@ -1,8 +1,8 @@
 """Bounded device-side waits: a wait that runs out returns an error status.
 
-The persistent solver separates the phases of Alg. 1 (colors, SpMV, the
-closing reduction) by grid barriers, and the batched solver separates them by
-per-system barriers.  Every barrier wait gives up after a wall-time limit,
+The persistent solver and the cooperative sweep (layouts of one- and two-row
+blocks) separate the colors of Alg. 1 by grid barriers, and the batched
+solver separates its phases by per-system barriers.  Every barrier wait gives up after a wall-time limit,
 sets an error word, and the kernel returns; the host reads ICCG_ERR_TIMEOUT.
 Here the limit is set to 1 ns, so the first CTA that has to wait at all gives
 up (no fault, no hang: the kernel ends normally with an error status).  The
@@ -52,6 +52,29 @@ def test_persistent_wait_runs_out_then_context_solves():
     assert st == iccg.ICCG_OK
     assert abs(it - ref["iterations"]) <= 1
     assert _rel(x, ref["x"]) <= 1e-10
+    S.close()
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_cooperative_sweep_wait_runs_out_then_context_solves(fp32):
+    a = gen.poisson3d_7pt(18)
+    b = gen.rhs_uniform(a.n, 5)
+    bl = oracle.blocking(a, "leiden_cpm", gamma=0.5)
+    ref = oracle.iccg(a, b, bl["perm"], tol=1e-8, maxit=5000)
+    S = iccg.Solver(a, bl, precond_fp32=fp32, fuse_sweep=1)
+    assert iccg.iccg_info(S.ctx)["fused_sweep"] == 1
+    iccg.iccg_set_wait_limit(S.ctx, 1)
+    x = np.zeros(a.n)
+    with pytest.raises(iccg.IccgError) as ei:
+        iccg.iccg_solve(S.ctx, b, x, 1e-8, 5000)
+    assert ei.value.status == TIMEOUT
+    iccg.iccg_set_wait_limit(S.ctx, 0)
+    x = np.zeros(a.n)
+    st, it, _ = iccg.iccg_solve(S.ctx, b, x, 1e-8, 5000)
+    assert st == iccg.ICCG_OK
+    if not fp32:
+        assert abs(it - ref["iterations"]) <= 1
+        assert _rel(x, ref["x"]) <= 1e-10
     S.close()
 
 

@@ -168,3 +168,74 @@ def test_leiden_block_sort_descending():
             assert first[j] < first[j + 1]
     # same partition, relabelled
     assert len(set(zip(memb.tolist(), b.tolist()))) == k
+
+
+# ---------------------------------------------------------------------------
+# level-set ordering (the level-scheduling baseline of Sec. 2)
+# ---------------------------------------------------------------------------
+def _levels_by_relaxation(n, gptr, gadj):
+    """Longest chain of preceding neighbours, by repeated relaxation until no
+    level changes (an algorithm other than the oracle's single pass)."""
+    lev = np.zeros(n, dtype=np.int64)
+    changed = True
+    while changed:
+        changed = False
+        for i in range(n):
+            nb = gadj[gptr[i]:gptr[i + 1]]
+            lower = nb[nb < i]
+            want = int(lev[lower].max()) + 1 if lower.size else 0
+            if want != lev[i]:
+                lev[i] = want
+                changed = True
+    return lev
+
+
+@pytest.mark.parametrize("kind", ["rspd", "rgg", "grid2d"])
+def test_level_order_is_longest_chain_and_independent(kind):
+    a = {"rspd": lambda: gen.random_spd_small(300, 0.02, 5), "rgg": lambda: gen.rgg_laplacian(400, 9.0, 3),
+         "grid2d": lambda: gen.poisson2d_5pt(13)}[kind]()
+    gptr, gadj = oracle.graph(a.n, a.rowptr, a.colind)
+    lev, nl, perm, bptr, cptr = oracle.level_order(a.n, gptr, gadj)
+    assert np.array_equal(lev, _levels_by_relaxation(a.n, gptr, gadj))
+    assert nl == lev.max() + 1
+    # rows of a level are never adjacent (a valid coloring of one-row blocks)
+    src = np.repeat(np.arange(a.n), np.diff(gptr))
+    assert not np.any(lev[src] == lev[gadj])
+    # levels ascending, rows ascending within a level
+    assert np.array_equal(perm, np.lexsort((np.arange(a.n), lev)))
+    assert np.array_equal(bptr, np.arange(a.n + 1)) and np.array_equal(np.diff(cptr), np.bincount(lev))
+
+
+@pytest.mark.parametrize("nx", [5, 9])
+def test_level_order_grid_closed_form(nx):
+    """Natural order of a 3D 7-point grid: the level of node (i, j, k) is
+    i + j + k, so there are 3 nx - 2 levels."""
+    a = gen.poisson3d_7pt(nx)
+    gptr, gadj = oracle.graph(a.n, a.rowptr, a.colind)
+    lev, nl, *_ = oracle.level_order(a.n, gptr, gadj)
+    idx = np.arange(a.n)
+    i, j, k = idx % nx, (idx // nx) % nx, idx // (nx * nx)
+    assert np.array_equal(lev, i + j + k) and nl == 3 * nx - 2
+
+
+def test_level_order_gives_the_natural_order_ic0_and_iccg():
+    """Every adjacent pair keeps its relative order, so IC(0) in the level
+    order is the natural-order IC(0) permuted, and ICCG converges alike."""
+    a = gen.rgg_laplacian(500, 8.0, 7)
+    b = gen.rhs_uniform(a.n, 2)
+    gptr, gadj = oracle.graph(a.n, a.rowptr, a.colind)
+    lev, nl, perm, *_ = oracle.level_order(a.n, gptr, gadj)
+    ident = np.arange(a.n, dtype=np.int32)
+    an = oracle.permute(a, ident)
+    ap = oracle.permute(a, perm)
+    ln, _ = oracle.ic0(*oracle.tril_csr(an))
+    lp, _ = oracle.ic0(*oracle.tril_csr(ap))
+    import scipy.sparse as sps
+    Ln = sps.csr_matrix((ln, oracle.tril_csr(an)[1], oracle.tril_csr(an)[0]), shape=(a.n, a.n))
+    Lp = sps.csr_matrix((lp, oracle.tril_csr(ap)[1], oracle.tril_csr(ap)[0]), shape=(a.n, a.n))
+    back = Lp[np.argsort(perm)][:, np.argsort(perm)]
+    assert abs(back - Ln).max() <= 1e-13 * abs(Ln).max()
+    rn = oracle.iccg(a, b, ident)
+    rp = oracle.iccg(a, b, perm)
+    assert rn["iterations"] == rp["iterations"]
+    assert np.linalg.norm(rn["x"] - rp["x"]) <= 1e-10 * np.linalg.norm(rn["x"])
