@@ -174,15 +174,27 @@ def measured_traffic(key):
 
 def make_blocking(mod, a, args):
     """The configured blocking by `mod` (the library, or the oracle for the
-    reference arm; both give the same permutation)."""
+    reference arm; both give the same permutation), with blocks above
+    --split-levels rows split into in-block levels when asked."""
     if args.blocking == "abmc":
-        return mod.blocking(a, "abmc", args.block_size)
-    if args.blocking == "levels":
-        return mod.blocking(a, "levels")
-    return mod.blocking(a, args.blocking, gamma=args.gamma)
+        bl = mod.blocking(a, "abmc", args.block_size)
+    elif args.blocking == "levels":
+        bl = mod.blocking(a, "levels")
+    else:
+        bl = mod.blocking(a, args.blocking, gamma=args.gamma)
+    if args.split_levels:
+        bl = mod.iccg_split_levels(a, bl, args.split_levels) if hasattr(mod, "iccg_split_levels") \
+            else mod.split_levels(a, bl, args.split_levels)
+    return bl
 
 
 def blocking_name(args):
+    if args.split_levels:
+        return _blocking_name(args) + f", blocks above {args.split_levels} rows split into in-block levels"
+    return _blocking_name(args)
+
+
+def _blocking_name(args):
     if args.blocking == "abmc":
         return f"ABMC s={args.block_size}"
     if args.blocking == "levels":
@@ -751,7 +763,9 @@ def main():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--blocking", default=None, choices=["abmc", "leiden_cpm", "leiden_md", "levels"],
                    help="default: leiden_cpm for poisson128, abmc otherwise")
-    p.add_argument("--gamma", type=float, default=0.5, help="Leiden CPM resolution")
+    p.add_argument("--gamma", type=float, default=0.5, help="Leiden resolution (CPM threshold or modularity gamma)")
+    p.add_argument("--split-levels", type=int, default=0,
+                   help="split blocks above this many rows into in-block levels (0: no)")
     p.add_argument("--block-size", type=int, default=None, help="ABMC block size (default 8, or 32 for diffusion96)")
     p.add_argument("--tol", type=float, default=1e-8)
     p.add_argument("--maxit", type=int, default=5000)

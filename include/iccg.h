@@ -363,6 +363,23 @@ iccg_status iccg_color_order(int32_t n, const int64_t *gptr, const int32_t *gadj
 iccg_status iccg_level_order(int32_t n, const int64_t *gptr, const int32_t *gadj, int32_t *level_of,
                              int32_t *n_lev, int32_t *perm, int32_t *block_ptr, int32_t *color_ptr);
 
+/* Intra-block level sets for oversized blocks: a block-multicolor ordering
+ * (perm, block_ptr, color_ptr, as for iccg_setup; CSR host arrays of A) is
+ * refined by splitting every block of more than max_rows rows into its
+ * in-block dependency levels (level 0: rows with no earlier row of their
+ * block in the pattern; otherwise one more than the deepest such row), each
+ * level of a color becoming a color of one-row blocks placed after the
+ * color's small blocks.  Rows of one such level are never adjacent and every
+ * adjacent pair keeps its relative order, so the IC(0) factor and the
+ * substitutions of the refined ordering are those of the input ordering,
+ * with all rows of a level of a color resolved in parallel.  Outputs:
+ * perm_out int32[n], block_ptr_out int32[n+1], color_ptr_out int32[n+1]
+ * (first *n_c_out + 1 used), *n_b_out, *n_c_out. */
+iccg_status iccg_split_levels(int32_t n, const int64_t *rowptr, const int32_t *colind, const int32_t *perm,
+                              const int32_t *block_ptr, const int32_t *color_ptr, int32_t n_b, int32_t n_c,
+                              int32_t max_rows, int32_t *perm_out, int32_t *block_ptr_out,
+                              int32_t *color_ptr_out, int32_t *n_b_out, int32_t *n_c_out);
+
 /* Diagnostics (host only, no device): builds the layout iccg_setup would
  * build for these inputs (groups of at most group_rows rows, lane tiles for
  * colors of blocks of at most lane_max rows, 0 = none; with use_units, warp

@@ -167,6 +167,57 @@ def level_order(n, gptr, gadj):
     return lev[:n], int(nl), perm[:n], bptr, cptr[:nl + 1]
 
 
+def split_levels(a, bl, max_rows=32):
+    """Intra-block level sets for oversized blocks (blocks as the unit of
+    parallelism of Sec. 3, made finer for blocks too large for one warp):
+    every block of more than max_rows rows is split by in-block level (the
+    longest chain of earlier rows of the same block, through the pattern,
+    ending at the row); each level of a color becomes a color of one-row
+    blocks, after the color's small blocks.  Plain loops; returns a blocking
+    dict (perm, block_ptr, color_ptr, n_b, n_c)."""
+    n = a.n
+    perm = np.asarray(bl["perm"])
+    bptr = np.asarray(bl["block_ptr"])
+    cptr = np.asarray(bl["color_ptr"])[:bl["n_c"] + 1]
+    iperm = np.empty(n, dtype=np.int64)
+    iperm[perm] = np.arange(n)
+    lev = {}
+    for b in range(bl["n_b"]):
+        r0, r1 = int(bptr[b]), int(bptr[b + 1])
+        if r1 - r0 <= max_rows:
+            continue
+        for i in range(r0, r1):
+            o = perm[i]
+            lv = 0
+            for e in range(a.rowptr[o], a.rowptr[o + 1]):
+                j = int(iperm[a.colind[e]])
+                if r0 <= j < i:
+                    lv = max(lv, lev[j] + 1)
+            lev[i] = lv
+    out_perm, out_bptr, out_cptr = [], [], []
+    for c in range(bl["n_c"]):
+        blocks = range(int(cptr[c]), int(cptr[c + 1]))
+        small = [b for b in blocks if bptr[b + 1] - bptr[b] <= max_rows]
+        big = [b for b in blocks if bptr[b + 1] - bptr[b] > max_rows]
+        if small:
+            out_cptr.append(len(out_bptr))
+            for b in small:
+                out_bptr.append(len(out_perm))
+                out_perm.extend(int(v) for v in perm[bptr[b]:bptr[b + 1]])
+        depth = max([lev[i] + 1 for b in big for i in range(bptr[b], bptr[b + 1])], default=0)
+        for v in range(depth):
+            out_cptr.append(len(out_bptr))
+            for b in big:
+                for i in range(int(bptr[b]), int(bptr[b + 1])):
+                    if lev[i] == v:
+                        out_bptr.append(len(out_perm))
+                        out_perm.append(int(perm[i]))
+    out_cptr.append(len(out_bptr))
+    out_bptr.append(len(out_perm))
+    return {"perm": np.array(out_perm, dtype=np.int32), "block_ptr": np.array(out_bptr, dtype=np.int32),
+            "color_ptr": np.array(out_cptr, dtype=np.int32), "n_b": len(out_bptr) - 1, "n_c": len(out_cptr) - 1}
+
+
 def blocking(a, method: str = "abmc", block_size: int = 32, gamma: float = 1.0,
              n_iter: int = 2, beta: float = 0.01, seed: int = 42):
     """Full blocking pipeline: graph -> blocks -> (Leiden: size sort) -> colors ->

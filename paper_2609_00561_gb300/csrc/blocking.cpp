@@ -522,4 +522,80 @@ iccg_status iccg_level_order(int32_t n, const int64_t *gptr, const int32_t *gadj
   return ICCG_OK;
 }
 
+// Intra-block level sets for oversized blocks: every block of more than
+// max_rows rows is split into its in-block dependency levels (level 0: rows
+// with no earlier row of the block in the pattern; a row one deeper than its
+// deepest earlier in-block neighbour), each level of each color becoming a
+// color of one-row blocks.  Rows of one level of one color are never
+// adjacent (blocks of a color share no edge; in a block, adjacent rows sit at
+// different levels), and ordering a block's rows by level keeps the relative
+// order of every adjacent pair, so IC(0) and the substitutions are those of
+// the input ordering.  Blocks of at most max_rows rows are kept; every color
+// of the input keeps its position.  Outputs sized n, n+1, n+1.
+iccg_status iccg_split_levels(int32_t n, const int64_t *rowptr, const int32_t *colind, const int32_t *perm,
+                              const int32_t *block_ptr, const int32_t *color_ptr, int32_t n_b, int32_t n_c,
+                              int32_t max_rows, int32_t *perm_out, int32_t *block_ptr_out,
+                              int32_t *color_ptr_out, int32_t *n_b_out, int32_t *n_c_out) {
+  if (n < 0 || n_b < 0 || n_c < 0 || max_rows < 1 || !rowptr || !perm || !block_ptr || !color_ptr || !perm_out ||
+      !block_ptr_out || !color_ptr_out || !n_b_out || !n_c_out)
+    return ICCG_ERR_ARG;
+  std::vector<int32_t> iperm(size_t(n), -1), blk(size_t(n), 0);
+  for (int32_t i = 0; i < n; ++i) {
+    if (perm[i] < 0 || perm[i] >= n || iperm[size_t(perm[i])] >= 0) return ICCG_ERR_ARG;
+    iperm[size_t(perm[i])] = i;
+  }
+  for (int32_t b = 0; b < n_b; ++b)
+    for (int32_t i = block_ptr[b]; i < block_ptr[b + 1]; ++i) blk[size_t(i)] = b;
+  // in-block level of every (new) row of an oversized block
+  std::vector<int32_t> lev(size_t(n), 0);
+  for (int32_t b = 0; b < n_b; ++b) {
+    if (block_ptr[b + 1] - block_ptr[b] <= max_rows) continue;
+    for (int32_t i = block_ptr[b]; i < block_ptr[b + 1]; ++i) {
+      const int32_t o = perm[i];
+      int32_t lv = 0;
+      for (int64_t e = rowptr[o]; e < rowptr[o + 1]; ++e) {
+        const int32_t c = colind[e];
+        if (c < 0 || c >= n) return ICCG_ERR_ARG;
+        const int32_t j = iperm[size_t(c)];
+        if (j < i && blk[size_t(j)] == b) lv = std::max(lv, lev[size_t(j)] + 1);
+      }
+      lev[size_t(i)] = lv;
+    }
+  }
+  int32_t nb = 0, nc = 0, row = 0;
+  for (int32_t c = 0; c < n_c; ++c) {
+    // the color's small blocks stay one color; its oversized blocks give one
+    // color per level
+    color_ptr_out[nc++] = nb;
+    int32_t depth = 0;
+    bool small = false;
+    for (int32_t b = color_ptr[c]; b < color_ptr[c + 1]; ++b) {
+      if (block_ptr[b + 1] - block_ptr[b] <= max_rows) {
+        small = true;
+        block_ptr_out[nb++] = row;
+        for (int32_t i = block_ptr[b]; i < block_ptr[b + 1]; ++i) perm_out[row++] = perm[i];
+      } else {
+        for (int32_t i = block_ptr[b]; i < block_ptr[b + 1]; ++i) depth = std::max(depth, lev[size_t(i)] + 1);
+      }
+    }
+    if (!small) --nc;
+    for (int32_t v = 0; v < depth; ++v) {
+      color_ptr_out[nc++] = nb;
+      for (int32_t b = color_ptr[c]; b < color_ptr[c + 1]; ++b) {
+        if (block_ptr[b + 1] - block_ptr[b] <= max_rows) continue;
+        for (int32_t i = block_ptr[b]; i < block_ptr[b + 1]; ++i)
+          if (lev[size_t(i)] == v) {
+            block_ptr_out[nb++] = row;
+            perm_out[row++] = perm[i];
+          }
+      }
+    }
+  }
+  color_ptr_out[nc] = nb;
+  block_ptr_out[nb] = row;
+  *n_b_out = nb;
+  *n_c_out = nc;
+  return ICCG_OK;
+}
+
 }  // extern "C"

@@ -1504,6 +1504,7 @@ __global__ void __launch_bounds__(kVecThreads) widen_kernel(const float *src, do
 // Row i of the up-looking IC(0): for every j < i in the pattern, ascending,
 //   L_ij = (a_ij - sum_{k < j, k in pat(i) and pat(j)} L_ik L_jk) / L_jj,
 // then L_ii = sqrt(a_ii - sum_j L_ij^2); rows j are final when row i runs.
+// A finished row also stores 1/L_ii, and later rows multiply by it.
 // General form: the common columns by a merge of the two sorted rows (a
 // chain of dependent loads).
 __device__ __forceinline__ void factor_row_merge(const Params &P, int i) {
@@ -1520,7 +1521,7 @@ __device__ __forceinline__ void factor_row_merge(const Params &P, int i) {
       else if (ca < cb) ++a;
       else ++b;
     }
-    const double lij = s / P.ldiag[j];
+    const double lij = s * __ldcg(P.invd + j);
     P.lval[p] = lij;
     d -= lij * lij;
   }
@@ -1528,7 +1529,9 @@ __device__ __forceinline__ void factor_row_merge(const Params &P, int i) {
     atomicMin(P.err_row, (unsigned long long)i);
     d = 1.0;
   }
-  P.ldiag[i] = sqrt(d);
+  const double lii = sqrt(d);
+  P.ldiag[i] = lii;
+  P.invd[i] = 1.0 / lii;
 }
 
 // Rows of at most kFacRow strictly-lower entries whose referenced rows have
@@ -1578,7 +1581,9 @@ __device__ __forceinline__ void factor_row(const Params &P, int i, int32_t *sc, 
       }
       if (hit) s -= sv[t] * v;
     }
-    const double lij = s / __ldcg(P.ldiag + j);
+    // times 1/L_jj (one division per row, at its end, instead of one per
+    // entry: FP64 division is a multi-instruction sequence on this GPU)
+    const double lij = s * __ldcg(P.invd + j);
     sv[p] = lij;
     d -= lij * lij;
   }
@@ -1587,7 +1592,9 @@ __device__ __forceinline__ void factor_row(const Params &P, int i, int32_t *sc, 
     atomicMin(P.err_row, (unsigned long long)i);
     d = 1.0;
   }
-  P.ldiag[i] = sqrt(d);
+  const double lii = sqrt(d);
+  P.ldiag[i] = lii;
+  P.invd[i] = 1.0 / lii;
 }
 
 // the rows of one in-block level of a lane-tile color, one row per thread

@@ -76,6 +76,7 @@ def load():
         "iccg_sort_blocks_desc": [i32, i32, vp],
         "iccg_color_order": [i32, vp, vp, i32, vp, vp, P(i32), vp, vp, vp],
         "iccg_level_order": [i32, vp, vp, vp, P(i32), vp, vp, vp],
+        "iccg_split_levels": [i32, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, P(i32), P(i32)],
         "iccg_spmv_dot_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp],
         "iccg_batch_create": [P(vp), vp, i32, i32, P(iccg_batch_opts)],
         "iccg_features": [i32, vp, vp, vp, vp],
@@ -312,6 +313,24 @@ def iccg_level_order(n, gptr, gadj):
     _check(load().iccg_level_order(int(n), _ptr(gptr), _ptr(gadj), _ptr(lev), ctypes.byref(nl), _ptr(perm),
                                    _ptr(bptr), _ptr(cptr)), "iccg_level_order")
     return lev[:n], nl.value, perm[:n], bptr, cptr[: nl.value + 1]
+
+
+def iccg_split_levels(a, bl, max_rows=32):
+    """Refines a blocking dict (perm, block_ptr, color_ptr, n_b, n_c): blocks
+    above max_rows rows become their in-block levels, one color of one-row
+    blocks per level.  Returns a blocking dict of the same form."""
+    n = a.n
+    keep = [_as(a.rowptr, np.int64), _as(a.colind, np.int32), _as(bl["perm"], np.int32),
+            _as(bl["block_ptr"], np.int32), _as(np.asarray(bl["color_ptr"])[:bl["n_c"] + 1], np.int32)]
+    perm = np.zeros(max(n, 1), dtype=np.int32)
+    bptr = np.zeros(n + 1, dtype=np.int32)
+    cptr = np.zeros(n + 1, dtype=np.int32)
+    nb, nc = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().iccg_split_levels(int(n), *[_ptr(k) for k in keep], int(bl["n_b"]), int(bl["n_c"]), int(max_rows),
+                                    _ptr(perm), _ptr(bptr), _ptr(cptr), ctypes.byref(nb), ctypes.byref(nc)),
+           "iccg_split_levels")
+    return {"perm": perm[:n], "block_ptr": bptr[:nb.value + 1], "color_ptr": cptr[:nc.value + 1], "n_b": nb.value,
+            "n_c": nc.value}
 
 
 NOALLOC_MAX_ROWS = 4194304

@@ -148,3 +148,23 @@ def test_level_order_equals_oracle(name):
     olev, onl, operm, obptr, ocptr = oracle.level_order(a.n, og, oa)
     assert nl == onl and np.array_equal(lev, olev) and np.array_equal(perm, operm)
     assert np.array_equal(bptr, obptr) and np.array_equal(cptr, ocptr)
+
+
+@pytest.mark.parametrize("case", ["md2d", "md3d", "abmc100"])
+def test_split_levels_equals_oracle(case):
+    if case == "md2d":
+        a = gen.poisson2d_5pt(30)
+        bl = oracle.blocking(a, "leiden_md", gamma=1.0)
+    elif case == "md3d":
+        a = gen.poisson3d_7pt(12)
+        bl = oracle.blocking(a, "leiden_md", gamma=1.0)
+    else:
+        a = gen.stencil_aniso("27pt", 2000, 5.0)
+        bl = oracle.blocking(a, "abmc", 100)
+    got = iccg.iccg_split_levels(a, bl, 32)
+    want = oracle.split_levels(a, bl, 32)
+    for k in ("perm", "block_ptr", "color_ptr"):
+        assert np.array_equal(got[k], want[k]), k
+    assert got["n_b"] == want["n_b"] and got["n_c"] == want["n_c"]
+    st, *_ = iccg.check_layout(a, got)
+    assert st == 0

@@ -130,3 +130,26 @@ def test_solve_fp32_preconditioner_at_full_size(problem, oracle_solve):
     assert st == iccg.ICCG_OK and abs(it - ref["iterations"]) <= 2, (it, ref["iterations"])
     assert np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b) <= 1e-8
     assert np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-6
+
+
+def test_leiden_md_split_levels_at_full_size(problem):
+    """Leiden modularity on 128^3 gives tens of blocks of tens of thousands of
+    rows; split into in-block levels (one color of one-row blocks per level of
+    a color) the solve runs all rows of a level in parallel and matches the
+    oracle's solve on the same ordering (the IC(0) of the unsplit ordering,
+    pinned on the host)."""
+    a, b = problem
+    bo = oracle.blocking(a, "leiden_md", gamma=1.0)
+    bp = iccg.blocking(a, "leiden_md", gamma=1.0)
+    for k in ("perm", "block_ptr", "color_ptr"):
+        assert np.array_equal(np.asarray(bo[k]), np.asarray(bp[k])), k
+    assert np.diff(bp["block_ptr"]).max() > 1000
+    sl = iccg.iccg_split_levels(a, bp, 32)
+    ref = oracle.iccg(a, b, sl["perm"], tol=1e-8, maxit=5000)
+    S = iccg.Solver(a, sl)
+    x = np.zeros(a.n)
+    st, it, _ = iccg.iccg_solve(S.ctx, b, x, 1e-8, 5000)
+    S.close()
+    assert st == iccg.ICCG_OK
+    assert abs(it - ref["iterations"]) <= 1, (it, ref["iterations"])
+    assert np.linalg.norm(x - ref["x"]) <= 1e-10 * np.linalg.norm(ref["x"])

@@ -56,6 +56,9 @@ CASES = {
     # level scheduling of the natural order: one-row blocks, a color per level
     "grid3d_levels": (lambda: (gen.poisson3d_7pt(13), gen.rhs_uniform(2197, 16), None), "levels", {}),
     "rgg_levels": (lambda: (gen.rgg_laplacian(1500, 10.0, 5), gen.rhs_uniform(1500, 17), None), "levels", {}),
+    # Leiden modularity blocks of hundreds of rows split into in-block levels
+    "grid2d_leiden_md_split": (lambda: (gen.poisson2d_5pt(45), gen.rhs_uniform(2025, 4), None), "leiden_md_split",
+                               {"gamma": 1.0}),
 }
 
 _cache = {}
@@ -65,7 +68,10 @@ def _case(name):
     if name not in _cache:
         mk, method, kw = CASES[name]
         a, b, _ = mk()
-        bl = oracle.blocking(a, method, **kw)
+        if method == "leiden_md_split":
+            bl = oracle.split_levels(a, oracle.blocking(a, "leiden_md", **kw), 32)
+        else:
+            bl = oracle.blocking(a, method, **kw)
         ref = oracle.iccg(a, b, bl["perm"], tol=1e-8, maxit=20000)
         _cache[name] = (a, b, bl, ref)
     return _cache[name]

@@ -239,3 +239,51 @@ def test_level_order_gives_the_natural_order_ic0_and_iccg():
     rp = oracle.iccg(a, b, perm)
     assert rn["iterations"] == rp["iterations"]
     assert np.linalg.norm(rn["x"] - rp["x"]) <= 1e-10 * np.linalg.norm(rn["x"])
+
+
+# ---------------------------------------------------------------------------
+# intra-block level sets for oversized blocks
+# ---------------------------------------------------------------------------
+def test_split_levels_keeps_the_factor_and_the_solve():
+    """Splitting Leiden-modularity blocks (hundreds of rows) by in-block level
+    gives a valid block-multicolor ordering whose IC(0) is the original one
+    permuted (adjacent pairs keep their order) and whose ICCG converges alike."""
+    a = gen.poisson2d_5pt(30)
+    b = gen.rhs_uniform(a.n, 3)
+    bl = oracle.blocking(a, "leiden_md", gamma=1.0)
+    assert np.diff(bl["block_ptr"]).max() > 32
+    sp_ = oracle.split_levels(a, bl, 32)
+    assert sorted(sp_["perm"].tolist()) == list(range(a.n))
+    # coloring invariant: no edge inside a color between different blocks
+    n = a.n
+    gptr, gadj = oracle.graph(n, a.rowptr, a.colind)
+    newpos = np.empty(n, dtype=np.int64)
+    newpos[sp_["perm"]] = np.arange(n)
+    blk = np.repeat(np.arange(sp_["n_b"]), np.diff(sp_["block_ptr"]))
+    col = np.repeat(np.arange(sp_["n_c"]), np.diff(sp_["color_ptr"]))
+    src = np.repeat(np.arange(n), np.diff(gptr))
+    bi, bj = blk[newpos[src]], blk[newpos[gadj]]
+    assert not np.any((bi != bj) & (col[bi] == col[bj]))
+    # factor: the original one, permuted
+    import scipy.sparse as sps
+    def lfac(perm):
+        ah = oracle.permute(a, perm)
+        lp, lc, av = oracle.tril_csr(ah)
+        lv, br = oracle.ic0(lp, lc, av)
+        assert br == -1
+        m = sps.csr_matrix((lv, lc, lp), shape=(n, n))
+        inv = np.argsort(perm)
+        return m[inv][:, inv]
+    f0, f1 = lfac(bl["perm"]), lfac(sp_["perm"])
+    assert abs(f0 - f1).max() <= 1e-13 * abs(f0).max()
+    r0, r1 = oracle.iccg(a, b, bl["perm"]), oracle.iccg(a, b, sp_["perm"])
+    assert r0["iterations"] == r1["iterations"]
+    assert np.linalg.norm(r0["x"] - r1["x"]) <= 1e-10 * np.linalg.norm(r0["x"])
+
+
+def test_split_levels_leaves_small_blocks_alone():
+    a = gen.poisson3d_7pt(8)
+    bl = oracle.blocking(a, "abmc", 16)
+    sp_ = oracle.split_levels(a, bl, 32)
+    assert np.array_equal(sp_["perm"], bl["perm"]) and sp_["n_c"] == bl["n_c"]
+    assert np.array_equal(sp_["block_ptr"], bl["block_ptr"])
