@@ -9,10 +9,11 @@ diffusion problem (96^3, ABMC 32) with the FP32 preconditioner (extension 1).
 `--workload batch64` runs the batched extension: 64 shifted 7-point systems
 (sides U{16..64}), 16 right-hand sides each, ABMC 32, FP32 preconditioner,
 all in one launch; a step is the whole batch solved to 1e-8.
-`--workload learned` trains the learned-blocking MLP on the GPU (library
-kernels) from the committed label sweep and solves the held-out matrices
-with the predicted ABMC block size and with the fixed block size 32; a step
-is the held-out set solved once with the predicted settings.
+`--workload learned` selects and trains the learned-blocking MLP ensemble on
+the GPU (library kernels) from the committed label sweep and solves every
+held-out matrix live with the predicted ABMC block size and the predicted CPM
+resolution, the best constant settings and the fixed settings; a step is the
+held-out set solved once with the predicted ABMC block size.
 
 A step is one pass of the device hot path on inputs resident in HBM:
 iccg_factor (IC(0), FP64) followed by iccg_solve (PCG with block-multicolor
@@ -127,7 +128,8 @@ WORKLOADS = {
     "diffusion96": "3D 27-point variable-coefficient diffusion {nx}^3 (contrast 1e3, shift 1e-6 max diag)",
     "batch64": "batch of 64 shifted 3D 7-point systems (sides U{{16..64}}, shift U[1e-4,1e-1]) x 16 right-hand sides",
     "learned": "40 held-out generated SPD matrices (5/7/27-point anisotropic stencils, random geometric graph "
-               "Laplacians, 3-dof spring networks; n 2e4-2e5), ABMC block size predicted by the learned-blocking MLP",
+               "Laplacians, 3-dof spring networks; n 1e5-2e6), ABMC block size and CPM resolution predicted by the "
+               "learned-blocking MLP ensemble",
 }
 
 
@@ -266,7 +268,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     S = iccg.Solver(a, bl, precond_fp32=args.fp32, warps_per_cta=args.warps, rows_per_thread=args.rows,
                     stream=stream.cuda_stream, factor=False, no_graph=args.no_graph, lane_block_max=args.lane_max,
-                    tile_mapping=args.tile_mapping)
+                    tile_mapping=args.tile_mapping, fuse_sweep=args.fuse_sweep)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     info = S.info()
@@ -616,6 +618,14 @@ def run_batch(args):
 
 
 def run_learned(args):
+    """Extension 4: the learned blocking on the held-out matrices of the label
+    sweep (config 5's recipe, n 1e5-2e6).  The model is selected and trained
+    on the GPU with the library's kernels from the 160 training records; then
+    every held-out matrix is solved live (FP64, to 1e-8) with the predicted
+    ABMC block size and with the predicted CPM resolution, and, for
+    comparison, with the best constant settings of the training labels and
+    with the fixed settings of the paper's ranges (ABMC 32, CPM 0.05).  A step
+    is the held-out set solved once with the predicted ABMC block size."""
     import torch
     from paper_2609_00561_gb300 import build as libbuild
     from paper_2609_00561_gb300 import iccg
@@ -630,63 +640,62 @@ def run_learned(args):
     X, yc, yr, ta, tc = lm.labels(data)
     tr, te = lm.split(len(yc))
     bs_list, gammas = data["meta"]["block_sizes"], data["meta"]["gammas"]
-    m = lm.Model(X.shape[1], len(bs_list), seed=args.seed)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    hist = m.fit(X[tr], yc[tr], yr[tr], epochs=3000)
-    e1.record(stream)
+    t0 = time.perf_counter()
+    ens, rep = lm.report(data, seed=args.seed)
     torch.cuda.synchronize()
-    train_ms = e0.elapsed_time(e1)
-    ev_sweep = lm.evaluate(m, X[te], ta[te], tc[te], gammas, bs_list)
-    cls, _ = m.predict(X[te])
-    # live: each held-out matrix solved with the predicted and with the fixed block size
-    import gen
-    solvers = []
+    train_s = time.perf_counter() - t0
+    cls, lg = ens.predict(X[te])
+    gi = np.abs(lg[:, None] - np.log(np.array(gammas))[None, :]).argmin(axis=1)
+    ia, ic = lm.best_constants(ta[tr], tc[tr])
+    settings = ["abmc_predicted", "cpm_predicted", "abmc_best_constant", "cpm_best_constant", "abmc_fixed32",
+                "cpm_fixed005"]
+    times = {k: 0.0 for k in settings}
+    per = []
     for k, idx in enumerate(te):
         spec = data["records"][idx]["spec"]
         a = gen.config5_matrix(spec)
         b = np.random.default_rng(spec["seed"] + 7).uniform(-1.0, 1.0, a.n)
-        pair = []
-        for s_blk in (bs_list[int(cls[k])], lm.BASE_BLOCK):
-            S = iccg.Solver(a, iccg.blocking(a, "abmc", s_blk), stream=stream.cuda_stream)
-            pair.append(S)
-        solvers.append((pair, torch.tensor(b, device=dev)))
+        bd = torch.tensor(b, device=dev)
+        want = {"abmc_predicted": ("abmc", bs_list[int(cls[k])]), "cpm_predicted": ("leiden_cpm", gammas[int(gi[k])]),
+                "abmc_best_constant": ("abmc", bs_list[ia]), "cpm_best_constant": ("leiden_cpm", gammas[ic]),
+                "abmc_fixed32": ("abmc", lm.BASE_BLOCK), "cpm_fixed005": ("leiden_cpm", lm.BASE_GAMMA)}
+        done = {}
+        row = {"index": int(spec["index"]), "kind": spec["kind"], "n": a.n}
+        for name in settings:
+            key = want[name]
+            if key not in done:
+                bl = iccg.blocking(a, key[0], key[1]) if key[0] == "abmc" else iccg.blocking(a, key[0], gamma=key[1])
+                S = iccg.Solver(a, bl, stream=stream.cuda_stream)
+                xd = torch.zeros_like(bd)
+                iccg.iccg_solve(S.ctx, bd, xd, args.tol, args.maxit, want_hist=False)
 
-    def step(which):
-        tot = 0.0
-        for pair, bd in solvers:
-            xd = torch.zeros_like(bd)
-            e0.record(stream)
-            iccg.iccg_solve(pair[which].ctx, bd, xd, args.tol, args.maxit, want_hist=False)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            tot += e0.elapsed_time(e1)
-        return tot
+                def one():
+                    xd.zero_()
+                    return iccg.iccg_solve(S.ctx, bd, xd, args.tol, args.maxit, want_hist=False)
 
-    for _ in range(args.warmup):
-        step(0)
-        step(1)
-    with ClockSampler(local) as clk:
-        pred_ms = statistics.mean(step(0) for _ in range(args.steps))
-    fixed_ms = statistics.mean(step(1) for _ in range(args.steps))
-    for pair, _ in solvers:
-        for S in pair:
-            S.close()
+                ms, _ = time_steps(one, max(1, args.steps), stream)
+                S.close()
+                done[key] = ms
+            times[name] += done[key]
+            row[name] = round(done[key], 3)
+        per.append(row)
     result = {
-        "metric": "ICCG time to 1e-8 rel. residual", "value": round(pred_ms, 3), "unit": "ms",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(pred_ms, 3),
+        "metric": "ICCG time to 1e-8 rel. residual", "value": round(times["abmc_predicted"], 3), "unit": "ms",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(times["abmc_predicted"], 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS["learned"], "step": "the 40 held-out systems solved once each, "
-                   "inputs resident, blocking and setup excluded", "l2": "mixed (systems 0.5-30 MB)",
-                   "parallelism": "1 GPU"},
-        "fixed_block32_ms": round(fixed_ms, 3),
-        "gain_vs_fixed_block32": round(fixed_ms / pred_ms, 3),
-        "train_ms": round(train_ms, 1), "train_loss": [round(v, 4) for v in hist[::6]],
-        "held_out_vs_sweep": ev_sweep,
-        "roofline": None,
-        "e2e": None,
-        "gpu_launches": None,
-        "clocks": clk.summary(),
+        "config": {"workload": WORKLOADS["learned"], "step": "the 40 held-out systems solved once each with the "
+                   "predicted ABMC block size, inputs resident, blocking and setup excluded",
+                   "l2": "mixed (systems of 1e5-2e6 rows)", "parallelism": "1 GPU"},
+        "held_out_sum_ms": {k: round(v, 2) for k, v in times.items()},
+        "gain_vs_fixed": {"abmc": round(times["abmc_fixed32"] / times["abmc_predicted"], 3),
+                          "cpm": round(times["cpm_fixed005"] / times["cpm_predicted"], 3)},
+        "gain_vs_best_constant": {"abmc": round(times["abmc_best_constant"] / times["abmc_predicted"], 3),
+                                  "cpm": round(times["cpm_best_constant"] / times["cpm_predicted"], 3)},
+        "selection_and_training_s": round(train_s, 2), "model_choice": rep["choice"],
+        "held_out_vs_sweep": {"model": rep["test"], "best_constant": rep["test_best_constant"],
+                              "fixed": rep["test_fixed"]},
+        "per_matrix": per,
+        "roofline": None, "e2e": None, "gpu_launches": None,
     }
     if rank == 0:
         print(json.dumps(result))
@@ -775,6 +784,8 @@ def main():
     p.add_argument("--lane-max", type=int, default=0,
                    help="largest block run as lane tiles (0: 32, -1: none, every color as CTA groups)")
     p.add_argument("--tile-mapping", default="auto", choices=["auto", "cta", "warp", "pair", "units"])
+    p.add_argument("--fuse-sweep", type=int, default=0,
+                   help="1: each preconditioner sweep as one cooperative launch (layouts of 1-2-row blocks)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-graph", action="store_true",
                    help="drive the PCG loop from the host (every kernel a separate launch, e.g. for ncu)")

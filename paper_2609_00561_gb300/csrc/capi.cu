@@ -408,6 +408,15 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     int32_t *d_fr;
     CK(dev_upload(ctx, &d_fr, H.fac_rows), "alloc factor schedule");
     P.fac_rows = d_fr;
+    P.fp_ptr = nullptr; P.fp_b = nullptr; P.fp_pos = nullptr;
+    if (!H.fp_ptr.empty()) {
+      int32_t *d_fp, *d_fb;
+      uint8_t *d_fs;
+      CK(dev_upload(ctx, &d_fp, H.fp_ptr), "alloc factor pairs");
+      CK(dev_upload(ctx, &d_fb, H.fp_b), "alloc factor pairs");
+      CK(dev_upload(ctx, &d_fs, H.fp_pos), "alloc factor pairs");
+      P.fp_ptr = d_fp; P.fp_b = d_fb; P.fp_pos = d_fs;
+    }
     L.fac_ptr = H.fac_ptr;
     L.fac_lev0 = H.fac_lev0;
     L.fac_nlev = H.fac_nlev;

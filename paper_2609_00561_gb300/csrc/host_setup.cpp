@@ -252,6 +252,57 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
     }
   }
 
+  // IC(0) update pairs of every L entry (the symbolic part of the factor),
+  // built when every row has at most 32 lower entries and the pairs stay
+  // within a budget; otherwise the numeric factor finds them itself
+  H.fp_ptr.clear(); H.fp_b.clear(); H.fp_pos.clear();
+  {
+    constexpr int64_t kPairBudget = int64_t(64) << 20;
+    bool ok = true;
+    for (int32_t i = 0; i < n && ok; ++i) ok = H.lrp[i + 1] - H.lrp[i] <= 32;
+    std::vector<int32_t> cnt;
+    if (ok) {
+      cnt.assign(size_t(H.nL), 0);
+#pragma omp parallel for schedule(dynamic, 1024)
+      for (int32_t i = 0; i < n; ++i) {
+        for (int32_t e = H.lrp[i]; e < H.lrp[i + 1]; ++e) {
+          const int32_t j = H.lcol[e];
+          int32_t a = H.lrp[i], b = H.lrp[j], c = 0;
+          while (a < e && b < H.lrp[j + 1]) {
+            if (H.lcol[a] == H.lcol[b]) { ++c; ++a; ++b; }
+            else if (H.lcol[a] < H.lcol[b]) ++a;
+            else ++b;
+          }
+          cnt[size_t(e)] = c;
+        }
+      }
+      int64_t tot = 0;
+      for (int32_t c : cnt) tot += c;
+      ok = tot <= kPairBudget;
+    }
+    if (ok && H.nL > 0) {
+      H.fp_ptr.assign(size_t(H.nL) + 1, 0);
+      for (int64_t e = 0; e < H.nL; ++e) H.fp_ptr[size_t(e) + 1] = H.fp_ptr[size_t(e)] + cnt[size_t(e)];
+      H.fp_b.resize(size_t(H.fp_ptr[size_t(H.nL)]));
+      H.fp_pos.resize(H.fp_b.size());
+#pragma omp parallel for schedule(dynamic, 1024)
+      for (int32_t i = 0; i < n; ++i) {
+        for (int32_t e = H.lrp[i]; e < H.lrp[i + 1]; ++e) {
+          const int32_t j = H.lcol[e];
+          int32_t a = H.lrp[i], b = H.lrp[j], q = H.fp_ptr[size_t(e)];
+          while (a < e && b < H.lrp[j + 1]) {
+            if (H.lcol[a] == H.lcol[b]) {
+              H.fp_pos[size_t(q)] = uint8_t(a - H.lrp[i]);
+              H.fp_b[size_t(q)] = b;
+              ++q; ++a; ++b;
+            } else if (H.lcol[a] < H.lcol[b]) ++a;
+            else ++b;
+          }
+        }
+      }
+    }
+  }
+
   // lane tiles: descriptors and the sliced-ELL L / U entries of every step,
   // split into entries to other colors and in-block entries
   H.color_tile.assign(n_c + 1, 0);

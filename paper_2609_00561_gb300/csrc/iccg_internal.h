@@ -240,6 +240,8 @@ struct Params {
   double *hist;
   unsigned long long *err_row;  // IC(0) breakdown row (new numbering), ~0 = none
   const int32_t *fac_rows;      // IC(0) rows of the lane-tile colors, level by level
+  const int32_t *fp_ptr, *fp_b;  // IC(0) update pairs (null: not built)
+  const uint8_t *fp_pos;
   // warp units: descriptors, per-lane in-block masks, in-block coefficients
   // (forward: L_lk / L_kk; backward: L_kl / L_kk, k the source step's row),
   // filled from the factor through (entry map, scaling row); block pointers
@@ -283,6 +285,12 @@ struct HostLayout {
   // pattern); rows of level v of color c are fac_rows[fac_ptr[fac_lev0[c] + v]
   // .. fac_ptr[fac_lev0[c] + v + 1]), fac_nlev[c] levels (0 for a group color)
   std::vector<int32_t> fac_rows, fac_ptr, fac_lev0, fac_nlev;
+  // IC(0) update pairs (symbolic factorisation, when small enough): for L
+  // entry e = (i, j), the terms L_ik L_jk with k < j in both patterns, k
+  // ascending, as pairs fp_pos[q] (position of k in row i) and fp_b[q] (the L
+  // entry (j, k)), q in [fp_ptr[e], fp_ptr[e + 1]); empty when not built
+  std::vector<int32_t> fp_ptr, fp_b;
+  std::vector<uint8_t> fp_pos;
   // warp units (colors of blocks of at most 32 rows when enabled): color c's units
   // [color_unit[c], color_unit[c + 1]), unit_S[c] rows per segment
   std::vector<WarpUnit> units;

@@ -1597,13 +1597,96 @@ __device__ __forceinline__ void factor_row(const Params &P, int i, int32_t *sc, 
   P.invd[i] = 1.0 / lii;
 }
 
-// the rows of one in-block level of a lane-tile color, one row per thread
-__global__ void __launch_bounds__(kFacThreads) factor_rows_kernel(Params P, int k0, int k1) {
-  __shared__ int32_t sc[kFacThreads * kFacRow];
-  __shared__ double sv[kFacThreads * kFacRow];
-  for (int k = k0 + int(blockIdx.x * blockDim.x + threadIdx.x); k < k1; k += int(gridDim.x * blockDim.x))
-    factor_row(P, __ldg(P.fac_rows + k), sc + threadIdx.x * kFacRow, sv + threadIdx.x * kFacRow);
+// Row i from its precomputed update pairs: the row's pair entries and
+// positions, then the pair values L_jk (rows j are final), are staged with
+// independent loads (32 in flight per pass), then every entry takes only its
+// own terms, k ascending as in the general form.
+constexpr int kFacPairs = 320;   // staged pairs of a row (more: the general form)
+constexpr int kFacRowThreads = 32;
+
+__device__ __forceinline__ void factor_row_pairs(const Params &P, int i, double *sv, double *pv, int32_t *pb,
+                                                 uint8_t *pp, double *ivj, uint16_t *qe) {
+  const int rb = P.lrp[i], ni = P.lrp[i + 1] - rb;
+  const int q0 = __ldg(P.fp_ptr + rb), q1 = __ldg(P.fp_ptr + rb + ni);
+  if (ni > kFacRow || q1 - q0 > kFacPairs) { factor_row(P, i, pb, sv); return; }
+  const int np = q1 - q0;
+  // per entry: a_ij (into sv, computed in place), 1/L_jj, the end of its pairs
+  {
+    int col[kFacRow];
+#pragma unroll
+    for (int p = 0; p < kFacRow; ++p) col[p] = p < ni ? __ldg(P.lcol + rb + p) : 0;
+#pragma unroll
+    for (int p = 0; p < kFacRow; ++p)
+      if (p < ni) {
+        sv[p] = __ldg(P.ainit + rb + p);
+        ivj[p] = __ldcg(P.invd + col[p]);
+        qe[p] = uint16_t(__ldg(P.fp_ptr + rb + p + 1) - q0);
+      }
+  }
+  for (int q = 0; q < np; q += 32) {
+    int b[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) b[u] = q + u < np ? __ldg(P.fp_b + q0 + q + u) : 0;
+#pragma unroll
+    for (int u = 0; u < 32; ++u)
+      if (q + u < np) {
+        pb[q + u] = b[u];
+        pp[q + u] = __ldg(P.fp_pos + q0 + q + u);
+      }
+  }
+  for (int q = 0; q < np; q += 32) {
+    double v[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) v[u] = q + u < np ? __ldcg(P.lval + pb[q + u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < 32; ++u)
+      if (q + u < np) pv[q + u] = v[u];
+  }
+  double d = P.adiag[i];
+  int q = 0;
+  for (int p = 0; p < ni; ++p) {
+    double s = sv[p];
+    for (const int qend = qe[p]; q < qend; ++q) s -= sv[pp[q]] * pv[q];
+    const double lij = s * ivj[p];
+    sv[p] = lij;
+    d -= lij * lij;
+  }
+  for (int t = 0; t < ni; ++t) P.lval[rb + t] = sv[t];
+  if (!(d > 0.0) || !isfinite(d)) {
+    atomicMin(P.err_row, (unsigned long long)i);
+    d = 1.0;
+  }
+  const double lii = sqrt(d);
+  P.ldiag[i] = lii;
+  P.invd[i] = 1.0 / lii;
 }
+
+// the rows of one in-block level of a lane-tile or warp-unit color, one row
+// per thread (dynamic shared memory: row values, staged pairs)
+__global__ void __launch_bounds__(kFacRowThreads) factor_rows_kernel(Params P, int k0, int k1) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int t = threadIdx.x;
+  constexpr int T = kFacRowThreads;
+  unsigned char *m = fsm;
+  double *sv = reinterpret_cast<double *>(m) + t * kFacRow;
+  m += size_t(T) * kFacRow * 8;
+  double *ivj = reinterpret_cast<double *>(m) + t * kFacRow;
+  m += size_t(T) * kFacRow * 8;
+  double *pv = reinterpret_cast<double *>(m) + t * kFacPairs;
+  m += size_t(T) * kFacPairs * 8;
+  int32_t *pb = reinterpret_cast<int32_t *>(m) + t * kFacPairs;
+  m += size_t(T) * kFacPairs * 4;
+  uint8_t *pp = m + size_t(t) * kFacPairs;
+  m += size_t(T) * kFacPairs;
+  uint16_t *qe = reinterpret_cast<uint16_t *>(m) + size_t(t) * kFacRow;
+  for (int k = k0 + int(blockIdx.x * blockDim.x + threadIdx.x); k < k1; k += int(gridDim.x * blockDim.x)) {
+    const int i = __ldg(P.fac_rows + k);
+    if (P.fp_ptr) factor_row_pairs(P, i, sv, pv, pb, pp, ivj, qe);
+    else factor_row(P, i, pb, sv);
+  }
+}
+
+constexpr int kFacSmem = kFacRowThreads * (kFacRow * 18 + kFacPairs * 13);
 
 // group colors: one CTA per group, its rows level by level of the in-group
 // schedule (dynamic shared memory: a kFacRow slice per thread)
@@ -2425,6 +2508,7 @@ cudaError_t launch_solve_persistent(const Params &P, const Plan &L, bool fp32) {
 cudaError_t configure_kernels() {
   cudaError_t e = cudaFuncSetAttribute(factor_color_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kMaxWarpsPerCta * kWarp * kFacRow * 12);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(factor_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFacSmem);
   if (e == cudaSuccess) e = configure_pt<double>();
   if (e == cudaSuccess) e = configure_pt<float>();
   return e;
@@ -2436,8 +2520,8 @@ cudaError_t launch_factor(const Params &P, const Plan &L, int nL) {
       // lane-tile and warp-unit colors: one launch per in-block level, a thread per row
       for (int v = 0; v < L.fac_nlev[c]; ++v) {
         const int k0 = L.fac_ptr[size_t(L.fac_lev0[c] + v)], k1 = L.fac_ptr[size_t(L.fac_lev0[c] + v + 1)];
-        const int grid = std::max(1, std::min((k1 - k0 + kFacThreads - 1) / kFacThreads, L.grid_v));
-        factor_rows_kernel<<<grid, kFacThreads, 0, L.stream>>>(P, k0, k1);
+        const int grid = std::max(1, std::min((k1 - k0 + kFacRowThreads - 1) / kFacRowThreads, 8 * L.grid_v));
+        factor_rows_kernel<<<grid, kFacRowThreads, kFacSmem, L.stream>>>(P, k0, k1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }

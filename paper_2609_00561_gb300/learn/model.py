@@ -157,6 +157,86 @@ class Model:
         np.savez(path, params=self.params, mu=self.mu, sd=self.sd, shape=np.array([self.nf, self.h, self.ncls]))
 
 
+class Ensemble:
+    """Several Models (seeds) whose outputs are averaged; the CPM prediction
+    is kept only when it lies farther than `margin` (log space) from the
+    constant resolution `gamma_const`, else that constant is used."""
+
+    def __init__(self, models, margin=0.0, gamma_const=1.0):
+        self.models, self.margin, self.gamma_const = models, margin, gamma_const
+
+    def predict(self, X):
+        import torch
+        from paper_2609_00561_gb300 import iccg
+        outs = []
+        for m in self.models:
+            Xs = torch.tensor(m.standardise(np.atleast_2d(X)), device="cuda")
+            P = torch.tensor(m.params, device="cuda")
+            out = torch.zeros((Xs.shape[0], m.ncls + 1), dtype=torch.float32, device="cuda")
+            iccg.mlp_forward(P, m.nf, m.h, m.ncls, Xs, out, None, torch.cuda.current_stream().cuda_stream)
+            outs.append(out.cpu().numpy().astype(np.float64))
+        o = np.mean(outs, axis=0)
+        ncls = self.models[0].ncls
+        lg = o[:, ncls]
+        lc = math.log(self.gamma_const)
+        lg = np.where(np.abs(lg - lc) > self.margin, lg, lc)
+        return o[:, :ncls].argmax(axis=1), lg
+
+
+def _regrets(cls, lg, ta, tc, gammas):
+    lgs = np.log(np.array(gammas))
+    gi = np.abs(lg[:, None] - lgs[None, :]).argmin(axis=1)
+    r = np.arange(len(cls))
+    t_a, t_c = ta[r, cls], tc[r, gi]
+    best_a, best_c = ta.min(axis=1), tc.min(axis=1)
+    return (float(np.mean(t_a / best_a)), float(np.mean(t_c / best_c)),
+            float(np.mean(np.minimum(t_a, t_c) / np.minimum(best_a, best_c))))
+
+
+EPOCHS = (100, 300, 1000)
+MARGINS = (0.0, 0.35, 0.7, 1.0, 1.5, 100.0)
+
+
+def fit_select(X, yc, yr, ta, tc, gammas, nseeds=5, folds=5, seed=0):
+    """Model selection on the training records only: 5-fold cross-validation
+    over the training length (EPOCHS, chosen by the combined regret) and the
+    CPM margin (MARGINS, chosen by the CPM regret) of a seed ensemble; then
+    the ensemble trained on all of them.  Returns (Ensemble, choice record)."""
+    rng = np.random.default_rng(seed + 1)
+    parts = np.array_split(rng.permutation(len(yc)), folds)
+    ia, ic = best_constants(ta, tc)
+    cv = {}
+    for ep in EPOCHS:
+        outs = []
+        for k in range(folds):
+            va = parts[k]
+            tr = np.concatenate([parts[j] for j in range(folds) if j != k])
+            ja, jc = best_constants(ta[tr], tc[tr])
+            ms = []
+            for sd in range(nseeds):
+                m = Model(X.shape[1], ta.shape[1], seed=seed + sd)
+                m.fit(X[tr], yc[tr], yr[tr], epochs=ep)
+                ms.append(m)
+            cls, lg = Ensemble(ms, 0.0, gammas[jc]).predict(X[va])
+            outs.append((va, cls, lg, math.log(gammas[jc])))
+        for mg in MARGINS:
+            res = []
+            for va, cls, lg, lc in outs:
+                lg2 = np.where(np.abs(lg - lc) > mg, lg, lc)
+                res.append(_regrets(cls, lg2, ta[va], tc[va], gammas))
+            cv[(ep, mg)] = np.mean(res, axis=0)
+    ep_best = min(EPOCHS, key=lambda e: cv[(e, 0.0)][2])
+    mg_best = min(MARGINS, key=lambda g: cv[(ep_best, g)][1])
+    ms = []
+    for sd in range(nseeds):
+        m = Model(X.shape[1], ta.shape[1], seed=seed + sd)
+        m.fit(X, yc, yr, epochs=ep_best)
+        ms.append(m)
+    choice = {"epochs": ep_best, "margin": mg_best, "cv_regret": [float(v) for v in cv[(ep_best, mg_best)]],
+              "constant_block_index": ia, "constant_gamma": gammas[ic], "seeds": nseeds}
+    return Ensemble(ms, mg_best, gammas[ic]), choice
+
+
 def evaluate(model, X, ta, tc, gammas, block_sizes):
     """Regret of the predictions against the sweep, and the gain over the
     method without the model (ABMC 32, CPM 0.05), on the given records."""
@@ -212,29 +292,27 @@ def evaluate_fixed(ta, tc, gammas, block_sizes):
             "combined_regret_mean": float(np.mean(np.minimum(base_a, base_c) / np.minimum(best_a, best_c)))}
 
 
-def report(data, epochs=3000, seed=0):
-    """Train on the training split and evaluate on the held-out split: the
-    model, the best constant settings chosen on the training labels, and the
-    method without the model (fixed ABMC 32 / CPM 0.05)."""
+def report(data, seed=0):
+    """Select and train on the training split, evaluate on the held-out split:
+    the model, the best constant settings chosen on the training labels, and
+    the method without the model (fixed ABMC 32 / CPM 0.05)."""
     X, yc, yr, ta, tc = labels(data)
     tr, te = split(len(yc))
     g, b = data["meta"]["gammas"], data["meta"]["block_sizes"]
-    m = Model(X.shape[1], len(b), seed=seed)
-    hist = m.fit(X[tr], yc[tr], yr[tr], epochs=epochs)
+    ens, choice = fit_select(X[tr], yc[tr], yr[tr], ta[tr], tc[tr], g, seed=seed)
     ia, ic = best_constants(ta[tr], tc[tr])
-    return m, {"train": evaluate(m, X[tr], ta[tr], tc[tr], g, b), "test": evaluate(m, X[te], ta[te], tc[te], g, b),
-               "test_best_constant": dict(evaluate_constant(ta[te], tc[te], ia, ic),
-                                          block_size=b[ia], gamma=g[ic]),
-               "test_fixed": evaluate_fixed(ta[te], tc[te], g, b), "loss": hist[::5],
-               "labels": {"block_size": {str(v): int(np.sum(yc == k)) for k, v in enumerate(b)},
-                          "gamma": {str(v): int(np.sum(np.isclose(np.exp(yr), v))) for v in g}}}
+    return ens, {"choice": choice, "train": evaluate(ens, X[tr], ta[tr], tc[tr], g, b),
+                 "test": evaluate(ens, X[te], ta[te], tc[te], g, b),
+                 "test_best_constant": dict(evaluate_constant(ta[te], tc[te], ia, ic), block_size=b[ia], gamma=g[ic]),
+                 "test_fixed": evaluate_fixed(ta[te], tc[te], g, b),
+                 "labels": {"block_size": {str(v): int(np.sum(yc == k)) for k, v in enumerate(b)},
+                            "gamma": {str(v): int(np.sum(np.isclose(np.exp(yr), v))) for v in g}}}
 
 
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--sweep", required=True)
     p.add_argument("--add-features", action="store_true")
-    p.add_argument("--epochs", type=int, default=3000)
     p.add_argument("--out", default=None)
     args = p.parse_args()
     data = load_sweep(args.sweep)
@@ -243,10 +321,11 @@ def main():
         with open(args.sweep, "w") as f:
             json.dump(data, f)
         return
-    m, res = report(data, args.epochs)
+    ens, res = report(data)
     print(json.dumps(res, indent=1))
     if args.out:
-        m.save(args.out)
+        for k, m in enumerate(ens.models):
+            m.save(f"{args.out}.{k}")
 
 
 if __name__ == "__main__":
