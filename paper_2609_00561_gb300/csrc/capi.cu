@@ -420,6 +420,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     L.fac_ptr = H.fac_ptr;
     L.fac_lev0 = H.fac_lev0;
     L.fac_nlev = H.fac_nlev;
+    L.fac_wide = H.fac_wide;
   }
   int32_t *d_cg;
   CK(dev_upload(ctx, &d_cg, H.color_group), "alloc groups");

@@ -388,6 +388,7 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
   // numbering: earlier steps of a block have smaller indices); the rows of a
   // level depend only on earlier levels and earlier colors
   H.fac_rows.clear();
+  H.fac_wide.clear();
   H.fac_ptr.assign(1, 0);
   H.fac_lev0.assign(n_c + 1, 0);
   H.fac_nlev.assign(n_c + 1, 0);
@@ -414,6 +415,9 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
       for (int32_t i = r0; i < r1; ++i) H.fac_rows[size_t(base + fill[size_t(lev[i])]++)] = i;
       for (int32_t v = 1; v <= depth; ++v) H.fac_ptr.push_back(base + cnt[size_t(v)]);
       H.fac_nlev[c] = depth;
+      std::vector<int32_t> wide(size_t(depth), 0);
+      for (int32_t i = r0; i < r1; ++i) wide[size_t(lev[i])] = std::max(wide[size_t(lev[i])], H.lrp[i + 1] - H.lrp[i]);
+      H.fac_wide.insert(H.fac_wide.end(), wide.begin(), wide.end());
     }
     H.fac_lev0[n_c] = int32_t(H.fac_ptr.size()) - 1;
   }

@@ -285,6 +285,7 @@ struct HostLayout {
   // pattern); rows of level v of color c are fac_rows[fac_ptr[fac_lev0[c] + v]
   // .. fac_ptr[fac_lev0[c] + v + 1]), fac_nlev[c] levels (0 for a group color)
   std::vector<int32_t> fac_rows, fac_ptr, fac_lev0, fac_nlev;
+  std::vector<int32_t> fac_wide;      // per level: the widest row's lower entries
   // IC(0) update pairs (symbolic factorisation, when small enough): for L
   // entry e = (i, j), the terms L_ik L_jk with k < j in both patterns, k
   // ascending, as pairs fp_pos[q] (position of k in row i) and fp_b[q] (the L
@@ -344,7 +345,7 @@ struct Plan {
   int32_t smem_wt = 0;                  // bytes per CTA of the warp-tile kernels
   int32_t cap_ws = 0;                   // steps per tile held in a warp's buffer
   std::vector<int32_t> off_rr, off_rz;  // slot regions of the color-c forward / backward launches
-  std::vector<int32_t> fac_ptr, fac_lev0, fac_nlev;   // IC(0) level schedule (host copy)
+  std::vector<int32_t> fac_ptr, fac_lev0, fac_nlev, fac_wide;   // IC(0) level schedule (host copy)
   int32_t last_rr = 0, last_rz = 0;     // slots written before the final launch of an iteration
   int32_t grid_a = 0;                   // CTAs of the SpMV-shaped kernels
   int32_t grid_v = 0;                   // CTAs of the vector kernels

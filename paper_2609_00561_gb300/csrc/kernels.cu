@@ -1604,11 +1604,20 @@ __device__ __forceinline__ void factor_row(const Params &P, int i, int32_t *sc, 
 constexpr int kFacPairs = 320;   // staged pairs of a row (more: the general form)
 constexpr int kFacRowThreads = 32;
 
-__device__ __forceinline__ void factor_row_pairs(const Params &P, int i, double *sv, double *pv, int32_t *pb,
-                                                 uint8_t *pp, double *ivj, uint16_t *qe) {
+// Shared-memory arrays of the row kernels are thread-interleaved: element q
+// of thread t at q * T + t, so a warp's accesses to one q hit 32 banks.
+template <typename T>
+struct Strided {
+  T *base;
+  __device__ __forceinline__ T &operator[](int q) const { return base[q * kFacRowThreads]; }
+};
+
+__device__ __forceinline__ void factor_row_pairs(const Params &P, int i, Strided<double> sv, Strided<double> pv,
+                                                 Strided<uint8_t> pp, Strided<double> ivj, Strided<uint16_t> qe,
+                                                 int32_t *scratch) {
   const int rb = P.lrp[i], ni = P.lrp[i + 1] - rb;
   const int q0 = __ldg(P.fp_ptr + rb), q1 = __ldg(P.fp_ptr + rb + ni);
-  if (ni > kFacRow || q1 - q0 > kFacPairs) { factor_row(P, i, pb, sv); return; }
+  if (ni > kFacRow || q1 - q0 > kFacPairs) { factor_row_merge(P, i); return; }
   const int np = q1 - q0;
   // per entry: a_ij (into sv, computed in place), 1/L_jj, the end of its pairs
   {
@@ -1623,25 +1632,19 @@ __device__ __forceinline__ void factor_row_pairs(const Params &P, int i, double 
         qe[p] = uint16_t(__ldg(P.fp_ptr + rb + p + 1) - q0);
       }
   }
+  // the pair values L_jk (rows j are final) and positions, 32 in flight
   for (int q = 0; q < np; q += 32) {
     int b[32];
 #pragma unroll
-    for (int u = 0; u < 32; ++u) b[u] = q + u < np ? __ldg(P.fp_b + q0 + q + u) : 0;
+    for (int u = 0; u < 32; ++u) b[u] = q + u < np ? __ldg(P.fp_b + q0 + q + u) : -1;
 #pragma unroll
     for (int u = 0; u < 32; ++u)
-      if (q + u < np) {
-        pb[q + u] = b[u];
+      if (b[u] >= 0) {
+        pv[q + u] = __ldcg(P.lval + b[u]);
         pp[q + u] = __ldg(P.fp_pos + q0 + q + u);
       }
   }
-  for (int q = 0; q < np; q += 32) {
-    double v[32];
-#pragma unroll
-    for (int u = 0; u < 32; ++u) v[u] = q + u < np ? __ldcg(P.lval + pb[q + u]) : 0.0;
-#pragma unroll
-    for (int u = 0; u < 32; ++u)
-      if (q + u < np) pv[q + u] = v[u];
-  }
+  (void)scratch;
   double d = P.adiag[i];
   int q = 0;
   for (int p = 0; p < ni; ++p) {
@@ -1662,31 +1665,38 @@ __device__ __forceinline__ void factor_row_pairs(const Params &P, int i, double 
 }
 
 // the rows of one in-block level of a lane-tile or warp-unit color, one row
-// per thread (dynamic shared memory: row values, staged pairs)
+// per thread (dynamic shared memory, thread-interleaved: row values, 1/L_jj,
+// staged pair values and positions, pair offsets)
 __global__ void __launch_bounds__(kFacRowThreads) factor_rows_kernel(Params P, int k0, int k1) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int t = threadIdx.x;
   constexpr int T = kFacRowThreads;
   unsigned char *m = fsm;
-  double *sv = reinterpret_cast<double *>(m) + t * kFacRow;
+  Strided<double> sv{reinterpret_cast<double *>(m) + t};
   m += size_t(T) * kFacRow * 8;
-  double *ivj = reinterpret_cast<double *>(m) + t * kFacRow;
+  Strided<double> ivj{reinterpret_cast<double *>(m) + t};
   m += size_t(T) * kFacRow * 8;
-  double *pv = reinterpret_cast<double *>(m) + t * kFacPairs;
+  Strided<double> pv{reinterpret_cast<double *>(m) + t};
   m += size_t(T) * kFacPairs * 8;
-  int32_t *pb = reinterpret_cast<int32_t *>(m) + t * kFacPairs;
-  m += size_t(T) * kFacPairs * 4;
-  uint8_t *pp = m + size_t(t) * kFacPairs;
-  m += size_t(T) * kFacPairs;
-  uint16_t *qe = reinterpret_cast<uint16_t *>(m) + size_t(t) * kFacRow;
+  Strided<uint16_t> qe{reinterpret_cast<uint16_t *>(m) + t};
+  m += size_t(T) * kFacRow * 2;
+  Strided<uint8_t> pp{m + t};
   for (int k = k0 + int(blockIdx.x * blockDim.x + threadIdx.x); k < k1; k += int(gridDim.x * blockDim.x)) {
     const int i = __ldg(P.fac_rows + k);
-    if (P.fp_ptr) factor_row_pairs(P, i, sv, pv, pb, pp, ivj, qe);
-    else factor_row(P, i, pb, sv);
+    if (P.fp_ptr) factor_row_pairs(P, i, sv, pv, pp, ivj, qe, nullptr);
+    else factor_row_merge(P, i);
   }
 }
 
-constexpr int kFacSmem = kFacRowThreads * (kFacRow * 18 + kFacPairs * 13);
+// levels of short rows (at most kFacShort lower entries): one row per thread,
+// the general form (short merges), no staging, full CTAs
+constexpr int kFacShort = 8;
+__global__ void __launch_bounds__(kVecThreads) factor_short_kernel(Params P, int k0, int k1) {
+  for (int k = k0 + int(blockIdx.x * blockDim.x + threadIdx.x); k < k1; k += int(gridDim.x * blockDim.x))
+    factor_row_merge(P, __ldg(P.fac_rows + k));
+}
+
+constexpr int kFacSmem = kFacRowThreads * (kFacRow * 18 + kFacPairs * 9);
 
 // group colors: one CTA per group, its rows level by level of the in-group
 // schedule (dynamic shared memory: a kFacRow slice per thread)
@@ -1707,11 +1717,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp) factor_color_kernel(P
 // invd = 1/L_ii, U values mirrored from L, FP32 copies, sliced-ELL values
 __global__ void __launch_bounds__(kVecThreads) factor_finish_kernel(Params P, int nL) {
   const int stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
-    const double iv = 1.0 / P.ldiag[i];
-    P.invd[i] = iv;
-    P.invd32[i] = float(iv);
-  }
+  // 1/L_ii was stored with each row; its FP32 copy
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) P.invd32[i] = float(P.invd[i]);
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nL; u += stride) {
     const double lv = P.lval[P.umap[u]];
     P.uval[u] = lv;
@@ -1743,15 +1750,16 @@ __global__ void __launch_bounds__(kVecThreads) factor_finish_kernel(Params P, in
     P.ui_val32[e] = float(v);
   }
   // warp-unit coefficients: the entry divided by the pivot of its source row
+  // (times the stored 1/L_kk)
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.nwl; e += stride) {
     const int m = P.wl_map[e];
-    const double v = m >= 0 ? P.lval[m] / P.ldiag[P.wl_srow[e]] : 0.0;
+    const double v = m >= 0 ? P.lval[m] * P.invd[P.wl_srow[e]] : 0.0;
     P.wl_val[e] = v;
     P.wl_val32[e] = float(v);
   }
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.nwu; e += stride) {
     const int m = P.wu_map[e];
-    const double v = m >= 0 ? P.lval[m] / P.ldiag[P.wu_srow[e]] : 0.0;
+    const double v = m >= 0 ? P.lval[m] * P.invd[P.wu_srow[e]] : 0.0;
     P.wu_val[e] = v;
     P.wu_val32[e] = float(v);
   }
@@ -2520,8 +2528,13 @@ cudaError_t launch_factor(const Params &P, const Plan &L, int nL) {
       // lane-tile and warp-unit colors: one launch per in-block level, a thread per row
       for (int v = 0; v < L.fac_nlev[c]; ++v) {
         const int k0 = L.fac_ptr[size_t(L.fac_lev0[c] + v)], k1 = L.fac_ptr[size_t(L.fac_lev0[c] + v + 1)];
-        const int grid = std::max(1, std::min((k1 - k0 + kFacRowThreads - 1) / kFacRowThreads, 8 * L.grid_v));
-        factor_rows_kernel<<<grid, kFacRowThreads, kFacSmem, L.stream>>>(P, k0, k1);
+        if (L.fac_wide[size_t(L.fac_lev0[c] + v)] <= kFacShort) {
+          const int grid = std::max(1, std::min((k1 - k0 + kVecThreads - 1) / kVecThreads, L.grid_v));
+          factor_short_kernel<<<grid, kVecThreads, 0, L.stream>>>(P, k0, k1);
+        } else {
+          const int grid = std::max(1, std::min((k1 - k0 + kFacRowThreads - 1) / kFacRowThreads, 8 * L.grid_v));
+          factor_rows_kernel<<<grid, kFacRowThreads, kFacSmem, L.stream>>>(P, k0, k1);
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }
