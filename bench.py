@@ -145,7 +145,8 @@ def workload_string(args, a, bl):
     """The workload as both arms name it (same text: same configuration)."""
     seed_b = args.seed + 1 if args.workload == "diffusion96" else args.seed
     return (WORKLOADS[args.workload].format(nx=args.nx) + f" (n={a.n}, nnz={a.nnz}), b~U[-1,1] seed {seed_b}, "
-            f"{blocking_name(args)} + greedy coloring (n_b={bl['n_b']}, n_c={bl['n_c']}), "
+            f"{blocking_name(args)}{'' if args.blocking == 'levels' and not args.split_levels else ' + greedy coloring'} "
+            f"(n_b={bl['n_b']}, n_c={bl['n_c']}), "
             f"IC(0) + PCG to {args.tol:g}" + (", FP32 preconditioner" if args.fp32 else ""))
 
 
@@ -200,7 +201,7 @@ def _blocking_name(args):
     if args.blocking == "abmc":
         return f"ABMC s={args.block_size}"
     if args.blocking == "levels":
-        return "level sets of the natural order (level scheduling)"
+        return "level sets of the natural order (level scheduling, a color per level)"
     if args.blocking == "leiden_cpm":
         return f"Leiden CPM resolution {args.gamma:g}"
     return f"Leiden modularity resolution {args.gamma:g}"
@@ -328,11 +329,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
 
-    n_c = info["n_c"]
-    # iccg_factor: one launch per color + finish; iccg_solve: perm_in, the
-    # residual SpMV, the 2 n_c - 1 color launches of z0, then per iteration
-    # p update + SpMV + 2 n_c - 1 color launches, and perm_out
-    launches_per_step = (n_c + 1) + (2 + 2 * n_c - 1) + iters * (2 + 2 * n_c - 1) + 1
+    # the library's own count of the kernels one iccg_factor and one
+    # iccg_solve of `iters` iterations launch
+    launches_per_step = info["factor_launches"] + info["solve_fixed_launches"] + iters * info["launches_per_iteration"]
     result = {
         "metric": "ICCG time to 1e-8 rel. residual",
         "value": round(ms, 4),
@@ -350,7 +349,7 @@ def run_gpu(args):
                    "step": "iccg_factor + iccg_solve, inputs resident",
                    "l2": "inputs larger than L2 (matrix + factors > 129 MB)",
                    "parallelism": "replicas only" if world > 1 else "1 GPU",
-                   "layout": f"{info['tile_colors']} of {n_c} colors as lane tiles ({info['tiles']} tiles), "
+                   "layout": f"{info['tile_colors']} of {info['n_c']} colors as lane tiles ({info['tiles']} tiles), "
                              f"{info['unit_colors']} as warp units, {info['groups']} CTA groups"},
         "iterations": iters,
         "status": iccg.STATUS.get(st, st),

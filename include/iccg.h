@@ -198,15 +198,20 @@ iccg_status iccg_profile_solve(iccg_ctx *ctx, const double *b, double *x, double
  * own inputs, so results are unaffected). */
 iccg_status iccg_time_spmv_phase(iccg_ctx *ctx, int32_t reps, double *ms);
 
-/* Layout facts of a context, out[15]: n, nnz, n_b, n_c, number of groups (a
+/* Layout facts of a context, out[18]: n, nnz, n_b, n_c, number of groups (a
  * group = consecutive whole blocks of one color, at most 32 * warps_per_cta *
  * rows_per_thread rows, or one larger block; one CTA each), number of groups
  * too large for the shared-memory plan, strictly-lower entries nL, deepest
  * in-group level count, largest group (rows), number of lane tiles (32
  * blocks, one per lane), number of colors run as lane tiles, number of
  * those run one warp per tile and as pair kernels (tile_mapping), number of
- * colors run as warp units, 1 when each sweep is one cooperative launch. */
-iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[15]);
+ * colors run as warp units, 1 when each sweep is one cooperative launch,
+ * then the library's kernel launches: of one iccg_factor (one per in-block
+ * level of the lane-tile and warp-unit colors, one per group color, and the
+ * finishing pass), of one PCG iteration of iccg_solve (p update, SpMV and the
+ * sweep's color launches), and of an iccg_solve's start and end (input
+ * permutation, residual SpMV, the first sweep, output permutation). */
+iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[18]);
 
 /* Wall-time limit (ns) of every device-side wait of this context: the grid
  * barriers of the persistent solver and of the cooperative sweep

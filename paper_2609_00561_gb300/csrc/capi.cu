@@ -938,7 +938,7 @@ iccg_status iccg_get_factor(iccg_ctx *ctx, double *lval, int64_t *nnz_lower) {
   return ICCG_OK;
 }
 
-iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[15]) {
+iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[18]) {
   if (!ctx || !out) return ICCG_ERR_ARG;
   const HostLayout &H = ctx->H;
   out[0] = H.n;
@@ -960,6 +960,14 @@ iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[15]) {
   }
   out[13] = H.unit_colors;
   out[14] = ctx->plan.coop ? 1 : 0;
+  const Plan &L = ctx->plan;
+  int64_t fac = 1;    // factor_finish
+  for (int c = 0; c < L.n_c; ++c)
+    fac += (L.tile1[c] > L.tile0[c] || L.unit1[c] > L.unit0[c]) ? L.fac_nlev[c] : 1;
+  const int64_t sw = L.n_c == 0 ? 0 : (L.coop ? 1 : 2 * int64_t(L.n_c) - 1);
+  out[15] = fac;
+  out[16] = 2 + sw;
+  out[17] = 3 + sw;
   return ICCG_OK;
 }
 

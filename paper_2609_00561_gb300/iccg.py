@@ -227,7 +227,8 @@ def iccg_time_spmv_phase(ctx, reps=50):
 
 
 INFO_KEYS = ("n", "nnz", "n_b", "n_c", "groups", "global_groups", "nL", "max_levels", "max_group_rows", "tiles",
-             "tile_colors", "warp_tile_colors", "pair_tile_colors", "unit_colors", "fused_sweep")
+             "tile_colors", "warp_tile_colors", "pair_tile_colors", "unit_colors", "fused_sweep",
+             "factor_launches", "launches_per_iteration", "solve_fixed_launches")
 
 
 def iccg_info(ctx):
