@@ -388,6 +388,8 @@ def run_gpu(args):
     if "ext_fp32_preconditioner" in result:
         result["ext_fp32_preconditioner"].pop("_x", None)
     S.close()
+    if not args.no_ext and world == 1 and args.blocking in ("leiden_cpm", "leiden_md") and not args.split_levels:
+        result["ext_device_blocking"] = ext_device_blocking(args, a, b, ms, iters, stream, dev)
     if not args.no_ext and world == 1 and args.workload == "poisson128":
         result["ext_batched"] = ext_batched(args, stream, dev)
     if world > 1:
@@ -395,6 +397,39 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(result))
+
+
+def ext_device_blocking(args, a, b, ms_host, it_host, stream, dev):
+    """The same Leiden blocking computed on the device (graph, parallel
+    Leiden, size order, greedy coloring, ordering), its time against the
+    host's, and the step (IC(0) + solve) with that blocking."""
+    import torch
+    from paper_2609_00561_gb300 import iccg
+    iccg.dev_blocking(a, args.blocking, args.gamma, stream=stream.cuda_stream)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bl = iccg.dev_blocking(a, args.blocking, args.gamma, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_dev = time.perf_counter() - t0
+    S = iccg.Solver(a, bl, stream=stream.cuda_stream, factor=False)
+    bd = torch.tensor(b, device=dev)
+    xd = torch.zeros_like(bd)
+
+    def step():
+        iccg.iccg_factor(S.ctx)
+        xd.zero_()
+        return iccg.iccg_solve(S.ctx, bd, xd, args.tol, args.maxit, want_hist=False)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    ms, (st, it, _) = time_steps(step, args.steps, stream)
+    x = xd.cpu().numpy()
+    S.close()
+    return {"blocking_s": round(t_dev, 4), "n_b": int(bl["n_b"]), "n_c": int(bl["n_c"]),
+            "ms_per_step": round(ms, 4), "iterations": it, "status": iccg.STATUS.get(st, st),
+            "true_relres": float(np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)),
+            "vs_host_blocking": {"ms_per_step": round(ms_host, 4), "iterations": it_host},
+            "how": "wall time of the device pipeline (synchronised), second call"}
 
 
 def ext_fp32(args, a, b, bl, x64, ms64, stream, dev):

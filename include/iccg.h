@@ -97,8 +97,12 @@ typedef struct {
                                  cooperative launch with bounded grid barriers
                                  between colors (a wait longer than the limit of
                                  iccg_set_wait_limit ends the solve with
-                                 ICCG_ERR_TIMEOUT); 0 (default) or -1 one launch per
-                                 color; other layouts ignore it */
+                                 ICCG_ERR_TIMEOUT); 2 runs only the tail of each
+                                 sweep that way (the last colors, together at most
+                                 n/32 rows, when they are such lane tiles: forward,
+                                 fused and backward in one launch of one CTA per SM);
+                                 0 (default) or -1 one launch per color; other
+                                 layouts ignore it */
 } iccg_opts;
 
 enum { ICCG_SOLVER_AUTO = 0, ICCG_SOLVER_PERSISTENT = 1, ICCG_SOLVER_PHASED = 2 };
@@ -354,6 +358,54 @@ iccg_status iccg_sort_blocks_desc(int32_t n, int32_t n_b, int32_t *block_of);
 iccg_status iccg_color_order(int32_t n, const int64_t *gptr, const int32_t *gadj, int32_t n_b,
                              const int32_t *block_of, int32_t *color_of, int32_t *n_c,
                              int32_t *perm, int32_t *block_ptr, int32_t *color_ptr);
+
+/* ------------------------------------------------------------------------
+ * Device-side blocking (the same results as the host helpers above, computed
+ * on the GPU).  All array arguments are device pointers on `stream`; scalar
+ * outputs (m, n_c) are host pointers, filled before return (each call
+ * synchronizes `stream`).  Scratch is allocated stream-ordered and freed
+ * before return.  ICCG_ERR_ARG on invalid input (checked on the device
+ * before use), ICCG_ERR_CUDA on a CUDA error.
+ *
+ *   iccg_dev_graph        the graph of Sec. 3 (edge {i,j} iff a_ij or a_ji is
+ *                         stored, i != j), rows sorted: gptr int64[n+1],
+ *                         gadj int32 of capacity 2 nnz, *m = gptr[n]; equal
+ *                         to iccg_graph's.
+ *   iccg_dev_color_order  greedy block coloring (Sec. 3, Sec. 5.1: blocks
+ *                         in index order, the smallest color no adjacent
+ *                         block with a smaller index has) and the
+ *                         block-multicolor ordering; outputs as for
+ *                         iccg_color_order (color_of int32[n_b], perm
+ *                         int32[n], block_ptr int32[n_b+1], color_ptr
+ *                         int32[n_b+1], *n_c), equal to its results.  The
+ *                         blocks are colored in waves: a block as soon as
+ *                         all its smaller neighbours are.
+ *   iccg_dev_sort_blocks_desc  Leiden block order (Sec. 6.1): blocks
+ *                         relabelled by size descending, ties by smallest
+ *                         row; equal to iccg_sort_blocks_desc.
+ *   iccg_dev_block_leiden Leiden blocking (Sec. 4, Sec. 6.1) on the device:
+ *                         quality 0 = modularity (Eq. 1), 1 = CPM (Eq. 2),
+ *                         resolution gamma, n_iter passes.  The same quality
+ *                         and gains as iccg_block_leiden, in a parallel form
+ *                         that does not reproduce the host's partition:
+ *                         local moving in synchronous sub-rounds (moves to
+ *                         smaller labels, then to larger ones, no two nodes
+ *                         swapping), refinement choosing the largest
+ *                         non-negative gain (no randomness), aggregation as
+ *                         on the host; every community is then split into
+ *                         its connected components.  Deterministic.
+ *                         block_of int32[n] (device, labels 0..n_b-1, not
+ *                         size-sorted), *n_b (host).
+ * ------------------------------------------------------------------------ */
+iccg_status iccg_dev_graph(int32_t n, const int64_t *rowptr, const int32_t *colind, int64_t nnz, int64_t *gptr,
+                           int32_t *gadj, int64_t *m, iccg_stream_t stream);
+iccg_status iccg_dev_color_order(int32_t n, const int64_t *gptr, const int32_t *gadj, int64_t m, int32_t n_b,
+                                 const int32_t *block_of, int32_t *color_of, int32_t *n_c, int32_t *perm,
+                                 int32_t *block_ptr, int32_t *color_ptr, iccg_stream_t stream);
+iccg_status iccg_dev_sort_blocks_desc(int32_t n, int32_t n_b, int32_t *block_of, iccg_stream_t stream);
+iccg_status iccg_dev_block_leiden(int32_t n, const int64_t *gptr, const int32_t *gadj, int64_t m, int32_t quality,
+                                  double gamma, int32_t n_iter, int32_t *block_of, int32_t *n_b,
+                                  iccg_stream_t stream);
 
 /* Level-set ordering, the level scheduling of the triangular solves (Sec. 2)
  * expressed as a block-multicolor ordering: level_of[i] = 0 when no

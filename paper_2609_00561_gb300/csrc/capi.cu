@@ -130,7 +130,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   if (o.tile_mapping < ICCG_TILES_AUTO || o.tile_mapping > ICCG_TILES_UNITS) return ICCG_ERR_ARG;
   if (o.lane_block_max > 32 || o.lane_block_max < -1) return ICCG_ERR_ARG;
   if (o.solver < ICCG_SOLVER_AUTO || o.solver > ICCG_SOLVER_PHASED) return ICCG_ERR_ARG;
-  if (o.fuse_sweep < -1 || o.fuse_sweep > 1) return ICCG_ERR_ARG;
+  if (o.fuse_sweep < -1 || o.fuse_sweep > 2) return ICCG_ERR_ARG;
   if (o.warps_per_cta == 0) o.warps_per_cta = 8;
   if (o.rows_per_thread == 0) o.rows_per_thread = 1;
   if (o.warps_per_cta < 1 || o.warps_per_cta > kMaxWarpsPerCta) return ICCG_ERR_ARG;
@@ -335,10 +335,32 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
     // on request only: at 128^3 with Leiden CPM 0.5 (8 colors) its grid
     // barriers cost more than the launch boundaries they replace
-    const int per_sm = pairs_only && coop && o.fuse_sweep > 0 ? coop_sweep_resident_ctas(ctx->fp32) : 0;
+    const int per_sm = pairs_only && coop && o.fuse_sweep == 1 ? coop_sweep_resident_ctas(ctx->fp32) : 0;
     L.coop = per_sm > 0;
     L.grid_coop = L.coop ? sms * per_sm : 0;
     gbig = std::max(gbig, L.grid_coop);
+    // the tail of every sweep (the last colors, together at most n / 32 rows,
+    // all of them lane tiles of at most two steps) in one cooperative launch,
+    // one CTA per SM
+    L.tail_c = 0;
+    L.grid_tail = 0;
+    if (!L.coop && coop && o.fuse_sweep == 2 && n_c >= 3 && coop_sweep_resident_ctas(ctx->fp32) > 0) {
+      int ct = n_c;
+      int64_t rows = 0;
+      for (int c = n_c - 1; c >= 1; --c) {
+        bool short_tiles = L.tile1[c] > L.tile0[c] && L.unit1[c] == L.unit0[c];
+        for (int t = L.tile0[c]; t < L.tile1[c] && short_tiles; ++t) short_tiles = H.tiles[t].nsteps <= 2;
+        rows += int64_t(H.color_ptr[c + 1] > H.color_ptr[c]
+                            ? H.block_ptr[H.color_ptr[c + 1]] - H.block_ptr[H.color_ptr[c]] : 0);
+        if (!short_tiles || rows * 32 > int64_t(n)) break;
+        ct = c;
+      }
+      if (ct <= n_c - 2) {
+        L.tail_c = ct;
+        L.grid_tail = sms;
+        for (int c = ct; c < n_c; ++c) L.grid_c[c] = L.grid_tail;
+      }
+    }
   }
   // slot regions: forward launches in color order (<r,r>), then the fused
   // launch and the backward launches in launch order (<r,z>); the final
@@ -687,12 +709,13 @@ static iccg_status solve_impl(iccg_ctx *ctx, const double *b, double *x, double 
   const bool use_graph = !persistent && ctx->opts.no_graph == 0 && prof == nullptr;
   if (use_graph && !ctx->gexec) {
     st = build_graph(ctx);
-    if (st != ICCG_OK && ctx->plan.coop) {
+    if (st != ICCG_OK && (ctx->plan.coop || ctx->plan.tail_c > 0)) {
       // the runtime would not capture the cooperative sweep into the graph:
       // one launch per color instead
       destroy_graph(ctx);
       cudaGetLastError();
       ctx->plan.coop = false;
+      ctx->plan.tail_c = 0;
       st = build_graph(ctx);
     }
     if (st != ICCG_OK) { destroy_graph(ctx); return st; }
@@ -959,12 +982,12 @@ iccg_status iccg_info(const iccg_ctx *ctx, int64_t out[18]) {
     out[12] += w == 2 ? 1 : 0;
   }
   out[13] = H.unit_colors;
-  out[14] = ctx->plan.coop ? 1 : 0;
+  out[14] = ctx->plan.coop ? 1 : (ctx->plan.tail_c > 0 ? 2 : 0);
   const Plan &L = ctx->plan;
   int64_t fac = 1;    // factor_finish
   for (int c = 0; c < L.n_c; ++c)
     fac += (L.tile1[c] > L.tile0[c] || L.unit1[c] > L.unit0[c]) ? L.fac_nlev[c] : 1;
-  const int64_t sw = L.n_c == 0 ? 0 : (L.coop ? 1 : 2 * int64_t(L.n_c) - 1);
+  const int64_t sw = L.n_c == 0 ? 0 : (L.coop ? 1 : (L.tail_c > 0 ? 2 * int64_t(L.tail_c) + 1 : 2 * int64_t(L.n_c) - 1));
   out[15] = fac;
   out[16] = 2 + sw;
   out[17] = 3 + sw;

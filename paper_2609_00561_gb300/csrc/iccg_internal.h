@@ -341,6 +341,8 @@ struct Plan {
   int32_t Wu = 8;                       // warps per CTA of the warp-unit kernels
   bool coop = false;                    // every sweep as one cooperative launch (pair-tile layouts)
   int32_t grid_coop = 0;                // CTAs of that launch (all resident)
+  int32_t tail_c = 0;                   // > 0: colors tail_c.. of every sweep in one cooperative launch
+  int32_t grid_tail = 0;                // CTAs of that launch (one per SM)
   int32_t Ww = 8;                       // warps per CTA of the warp-tile kernels
   int32_t smem_wt = 0;                  // bytes per CTA of the warp-tile kernels
   int32_t cap_ws = 0;                   // steps per tile held in a warp's buffer

@@ -457,7 +457,10 @@ __device__ void finish_iteration(const Params &P, double rr, double rz) {
     s->iter = k + 1;
     s->rr = rr;
     int done = 0;
-    if (!isfinite(rn) || !isfinite(rz)) { s->status = ICCG_ERR_NONFINITE; done = 1; }
+    // a bounded wait of this iteration gave up (a cooperative launch of the
+    // sweep): the solve stops with that status
+    if (s->status == ICCG_ERR_TIMEOUT) done = 1;
+    else if (!isfinite(rn) || !isfinite(rz)) { s->status = ICCG_ERR_NONFINITE; done = 1; }
     else if (rn <= s->tol) { s->status = ICCG_OK; done = 1; }
     else if (k + 1 >= s->maxit) { s->status = ICCG_NOT_CONVERGED; done = 1; }
     else { s->beta = rz / s->rz; s->rz = rz; }
@@ -482,7 +485,8 @@ __device__ void finish_init(const Params &P, double rz, double *red) {
     s->rz = rz;
     s->rr = rr;
     int done = 0;
-    if (bn == 0.0) { P.hist[0] = 0.0; s->status = ICCG_OK; done = 1; }
+    if (s->status == ICCG_ERR_TIMEOUT) done = 1;
+    else if (bn == 0.0) { P.hist[0] = 0.0; s->status = ICCG_OK; done = 1; }
     else {
       const double rn = sqrt(rr) / bn;
       P.hist[0] = rn;
@@ -1597,29 +1601,42 @@ __device__ __forceinline__ void factor_row(const Params &P, int i, int32_t *sc, 
   P.invd[i] = 1.0 / lii;
 }
 
-// Row i from its precomputed update pairs: the row's pair entries and
-// positions, then the pair values L_jk (rows j are final), are staged with
-// independent loads (32 in flight per pass), then every entry takes only its
-// own terms, k ascending as in the general form.
-constexpr int kFacPairs = 320;   // staged pairs of a row (more: the general form)
+// Row i from its precomputed update pairs (per entry L_ij, the pairs
+// (position of k in row i, index of L_jk) for the common columns k < j,
+// ascending k).  A level has few rows, so each row's latency is the cost:
+// all pair indices and positions of a pass are copied into shared memory
+// with cp.async at once, then all pair values L_jk (rows j are final)
+// gathered the same way, then every entry takes its own terms from shared
+// memory, k ascending as in the general form.  Shared memory is
+// thread-interleaved (element q of thread t at q T + t: no bank conflicts).
 constexpr int kFacRowThreads = 32;
+constexpr int kFacStage = 160;   // pairs per pass
 
-// Shared-memory arrays of the row kernels are thread-interleaved: element q
-// of thread t at q * T + t, so a warp's accesses to one q hit 32 banks.
 template <typename T>
 struct Strided {
   T *base;
   __device__ __forceinline__ T &operator[](int q) const { return base[q * kFacRowThreads]; }
 };
 
-__device__ __forceinline__ void factor_row_pairs(const Params &P, int i, Strided<double> sv, Strided<double> pv,
-                                                 Strided<uint8_t> pp, Strided<double> ivj, Strided<uint16_t> qe,
-                                                 int32_t *scratch) {
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+struct FacSmem {
+  Strided<double> sv, ivj, pv;
+  Strided<int32_t> qe, pb;
+  Strided<uint32_t> pw;   // fp_pos bytes, as the 4-byte words covering the pass
+};
+
+__device__ __forceinline__ void factor_row_pairs(const Params &P, int i, const FacSmem &m) {
   const int rb = P.lrp[i], ni = P.lrp[i + 1] - rb;
-  const int q0 = __ldg(P.fp_ptr + rb), q1 = __ldg(P.fp_ptr + rb + ni);
-  if (ni > kFacRow || q1 - q0 > kFacPairs) { factor_row_merge(P, i); return; }
-  const int np = q1 - q0;
-  // per entry: a_ij (into sv, computed in place), 1/L_jj, the end of its pairs
+  if (ni > kFacRow) { factor_row_merge(P, i); return; }
+  const int q0 = __ldg(P.fp_ptr + rb), np = ni > 0 ? __ldg(P.fp_ptr + rb + ni) - q0 : 0;
   {
     int col[kFacRow];
 #pragma unroll
@@ -1627,34 +1644,52 @@ __device__ __forceinline__ void factor_row_pairs(const Params &P, int i, Strided
 #pragma unroll
     for (int p = 0; p < kFacRow; ++p)
       if (p < ni) {
-        sv[p] = __ldg(P.ainit + rb + p);
-        ivj[p] = __ldcg(P.invd + col[p]);
-        qe[p] = uint16_t(__ldg(P.fp_ptr + rb + p + 1) - q0);
+        m.sv[p] = __ldg(P.ainit + rb + p);
+        m.ivj[p] = __ldcg(P.invd + col[p]);
+        m.qe[p] = __ldg(P.fp_ptr + rb + p + 1) - q0;
       }
   }
-  // the pair values L_jk (rows j are final) and positions, 32 in flight
-  for (int q = 0; q < np; q += 32) {
-    int b[32];
-#pragma unroll
-    for (int u = 0; u < 32; ++u) b[u] = q + u < np ? __ldg(P.fp_b + q0 + q + u) : -1;
-#pragma unroll
-    for (int u = 0; u < 32; ++u)
-      if (b[u] >= 0) {
-        pv[q + u] = __ldcg(P.lval + b[u]);
-        pp[q + u] = __ldg(P.fp_pos + q0 + q + u);
-      }
-  }
-  (void)scratch;
   double d = P.adiag[i];
-  int q = 0;
-  for (int p = 0; p < ni; ++p) {
-    double s = sv[p];
-    for (const int qend = qe[p]; q < qend; ++q) s -= sv[pp[q]] * pv[q];
-    const double lij = s * ivj[p];
-    sv[p] = lij;
+  int p = 0;
+  double s = 0.0;
+  // entries without terms before the first pair
+  while (p < ni && m.qe[p] == 0) {
+    const double lij = m.sv[p] * m.ivj[p];
+    m.sv[p] = lij;
     d -= lij * lij;
+    ++p;
   }
-  for (int t = 0; t < ni; ++t) P.lval[rb + t] = sv[t];
+  if (p < ni) s = m.sv[p];
+  const uint32_t *posw = reinterpret_cast<const uint32_t *>(P.fp_pos);
+  for (int qa = 0; qa < np; qa += kFacStage) {
+    const int nq = min(kFacStage, np - qa);
+    // indices and the words holding the positions
+    const int g0 = q0 + qa, w0 = g0 >> 2, w1 = (g0 + nq + 3) >> 2;
+    for (int q = 0; q < nq; ++q) cp_async4(&m.pb[q], P.fp_b + g0 + q);
+    for (int w = w0; w < w1; ++w) cp_async4(&m.pw[w - w0], posw + w);
+    cp_commit();
+    cp_wait_all();
+    // the pair values
+    for (int q = 0; q < nq; ++q) cp_async8(&m.pv[q], P.lval + m.pb[q]);
+    cp_commit();
+    cp_wait_all();
+    const int sh = g0 & 3;
+    for (int q = 0; q < nq; ++q) {
+      const int bq = q + sh;
+      const int pos = int((m.pw[bq >> 2] >> (8 * (bq & 3))) & 0xffu);
+      s -= m.sv[pos] * m.pv[q];
+      // the entry is complete after its last pair; then the following
+      // entries up to the next one with pairs left
+      while (p < ni && m.qe[p] == qa + q + 1) {
+        const double lij = s * m.ivj[p];
+        m.sv[p] = lij;
+        d -= lij * lij;
+        ++p;
+        s = p < ni ? m.sv[p] : 0.0;
+      }
+    }
+  }
+  for (int t = 0; t < ni; ++t) P.lval[rb + t] = m.sv[t];
   if (!(d > 0.0) || !isfinite(d)) {
     atomicMin(P.err_row, (unsigned long long)i);
     d = 1.0;
@@ -1664,26 +1699,31 @@ __device__ __forceinline__ void factor_row_pairs(const Params &P, int i, Strided
   P.invd[i] = 1.0 / lii;
 }
 
+constexpr int kFacPosWords = kFacStage / 4 + 2;
+constexpr int kFacSmem = kFacRowThreads * (kFacRow * 20 + kFacStage * 12 + kFacPosWords * 4);
+
 // the rows of one in-block level of a lane-tile or warp-unit color, one row
-// per thread (dynamic shared memory, thread-interleaved: row values, 1/L_jj,
-// staged pair values and positions, pair offsets)
+// per thread (dynamic shared memory, thread-interleaved)
 __global__ void __launch_bounds__(kFacRowThreads) factor_rows_kernel(Params P, int k0, int k1) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int t = threadIdx.x;
   constexpr int T = kFacRowThreads;
-  unsigned char *m = fsm;
-  Strided<double> sv{reinterpret_cast<double *>(m) + t};
-  m += size_t(T) * kFacRow * 8;
-  Strided<double> ivj{reinterpret_cast<double *>(m) + t};
-  m += size_t(T) * kFacRow * 8;
-  Strided<double> pv{reinterpret_cast<double *>(m) + t};
-  m += size_t(T) * kFacPairs * 8;
-  Strided<uint16_t> qe{reinterpret_cast<uint16_t *>(m) + t};
-  m += size_t(T) * kFacRow * 2;
-  Strided<uint8_t> pp{m + t};
+  unsigned char *q = fsm;
+  FacSmem m;
+  m.sv.base = reinterpret_cast<double *>(q) + t;
+  q += size_t(T) * kFacRow * 8;
+  m.ivj.base = reinterpret_cast<double *>(q) + t;
+  q += size_t(T) * kFacRow * 8;
+  m.pv.base = reinterpret_cast<double *>(q) + t;
+  q += size_t(T) * kFacStage * 8;
+  m.qe.base = reinterpret_cast<int32_t *>(q) + t;
+  q += size_t(T) * kFacRow * 4;
+  m.pb.base = reinterpret_cast<int32_t *>(q) + t;
+  q += size_t(T) * kFacStage * 4;
+  m.pw.base = reinterpret_cast<uint32_t *>(q) + t;
   for (int k = k0 + int(blockIdx.x * blockDim.x + threadIdx.x); k < k1; k += int(gridDim.x * blockDim.x)) {
     const int i = __ldg(P.fac_rows + k);
-    if (P.fp_ptr) factor_row_pairs(P, i, sv, pv, pp, ivj, qe, nullptr);
+    if (P.fp_ptr) factor_row_pairs(P, i, m);
     else factor_row_merge(P, i);
   }
 }
@@ -1696,7 +1736,6 @@ __global__ void __launch_bounds__(kVecThreads) factor_short_kernel(Params P, int
     factor_row_merge(P, __ldg(P.fac_rows + k));
 }
 
-constexpr int kFacSmem = kFacRowThreads * (kFacRow * 18 + kFacPairs * 9);
 
 // group colors: one CTA per group, its rows level by level of the in-group
 // schedule (dynamic shared memory: a kFacRow slice per thread)
@@ -2139,9 +2178,14 @@ persistent_kernel(Params P, GroupSmemPlan plan, int cap_a) {
 // ---------------------------------------------------------------------------
 constexpr int kCoopWarps = 8;
 
+// c_lo > 0: the tail of a sweep (forward colors c_lo .. n_c - 2, the fused
+// last color, backward colors n_c - 2 .. c_lo), between per-color launches;
+// its <r,r> / <r,z> partials go to the slot regions of those colors (one per
+// CTA in the first region of each, zeros in the others), which the
+// iteration's last launch sums.
 template <typename PT, bool UPDATE>
 __global__ void __launch_bounds__(kCoopWarps * kWarp)
-coop_sweep_kernel(Params P, int fin) {
+coop_sweep_kernel(Params P, int c_lo, int fin, int rr0, int ntail) {
   __shared__ double red[kMaxWarpsPerCta];
   __shared__ int flag;
   const int lane = threadIdx.x & 31;
@@ -2152,7 +2196,7 @@ coop_sweep_kernel(Params P, int fin) {
   const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
   GridSync gs{P.bar, 0u, &flag, nullptr, 0, 0, P.wait_ns};
   bool ok = true;
-  for (int c = 0; c < nc - 1 && ok; ++c) {
+  for (int c = c_lo; c < nc - 1 && ok; ++c) {
     const int t1 = __ldg(P.ctile + c + 1);
     for (int t = __ldg(P.ctile + c) + gw; t < t1; t += NW) pair_tile<PT, M_FWD, UPDATE>(P, t, lane, alpha, rr_acc, rz_acc);
     ok = phase_end(gs, PH_FWD);
@@ -2162,7 +2206,7 @@ coop_sweep_kernel(Params P, int fin) {
     for (int t = __ldg(P.ctile + nc - 1) + gw; t < t1; t += NW)
       pair_tile<PT, M_FUSED, UPDATE>(P, t, lane, alpha, rr_acc, rz_acc);
   }
-  for (int c = nc - 2; c >= 0 && ok; --c) {
+  for (int c = nc - 2; c >= c_lo && ok; --c) {
     if (!(ok = phase_end(gs, PH_BWD))) break;
     const int t1 = __ldg(P.ctile + c + 1);
     for (int t = __ldg(P.ctile + c) + gw; t < t1; t += NW) pair_tile<PT, M_BWD, false>(P, t, lane, alpha, rr_acc, rz_acc);
@@ -2173,6 +2217,18 @@ coop_sweep_kernel(Params P, int fin) {
       P.sc->status = ICCG_ERR_TIMEOUT;
       P.sc->done = 1;
       set_condition(P.sc, 0);
+    }
+    return;
+  }
+  if (c_lo > 0) {
+    const double rr_c = UPDATE ? cta_sum(rr_acc, red) : 0.0;
+    const double rz_c = cta_sum(rz_acc, red);
+    if (threadIdx.x == 0) {
+      const int G = int(gridDim.x), b = int(blockIdx.x);
+      for (int k = 0; k < ntail; ++k) {
+        if (UPDATE) P.slot_rr[rr0 + k * G + b] = k == 0 ? rr_c : 0.0;
+        P.slot_rz[k * G + b] = k == 0 ? rz_c : 0.0;
+      }
     }
     return;
   }
@@ -2333,8 +2389,21 @@ template <typename PT>
 cudaError_t launch_coop_sweep(const Params &P, const Plan &L, bool update, int fin) {
   cudaError_t e = cudaMemsetAsync(P.bar, 0, sizeof(GridBar), L.stream);
   if (e != cudaSuccess) return e;
-  if (update) return launch_coop(coop_sweep_kernel<PT, true>, L.grid_coop, kCoopWarps * kWarp, 0, L.stream, P, fin);
-  return launch_coop(coop_sweep_kernel<PT, false>, L.grid_coop, kCoopWarps * kWarp, 0, L.stream, P, fin);
+  if (update) return launch_coop(coop_sweep_kernel<PT, true>, L.grid_coop, kCoopWarps * kWarp, 0, L.stream, P, 0, fin, 0, 0);
+  return launch_coop(coop_sweep_kernel<PT, false>, L.grid_coop, kCoopWarps * kWarp, 0, L.stream, P, 0, fin, 0, 0);
+}
+
+// the sweep's tail colors (tail_c .. n_c - 1) in one cooperative launch
+template <typename PT>
+cudaError_t launch_coop_tail(const Params &P, const Plan &L, bool update) {
+  cudaError_t e = cudaMemsetAsync(P.bar, 0, sizeof(GridBar), L.stream);
+  if (e != cudaSuccess) return e;
+  const int ct = L.tail_c, nt = L.n_c - ct, rr0 = L.off_rr[ct];
+  if (update)
+    return launch_coop(coop_sweep_kernel<PT, true>, L.grid_tail, kCoopWarps * kWarp, 0, L.stream, P, ct, int(FIN_NONE),
+                       rr0, nt);
+  return launch_coop(coop_sweep_kernel<PT, false>, L.grid_tail, kCoopWarps * kWarp, 0, L.stream, P, ct, int(FIN_NONE),
+                     rr0, nt);
 }
 
 template <typename PT>
@@ -2345,6 +2414,23 @@ cudaError_t sweep(const Params &P, const Plan &L, bool update, int fin_last, Pha
     if (h) h(u, PH_FWD, 1);
     e = launch_coop_sweep<PT>(P, L, update, fin_last);
     if (h) h(u, PH_FWD, 0);
+    return e;
+  }
+  if (L.tail_c > 0) {
+    for (int c = 0; c < L.tail_c && e == cudaSuccess; ++c) {
+      if (h) h(u, PH_FWD, 1);
+      e = launch_fwd<PT>(P, L, c, update, false, FIN_NONE);
+      if (h) h(u, PH_FWD, 0);
+    }
+    if (e != cudaSuccess) return e;
+    if (h) h(u, PH_FUSED, 1);
+    e = launch_coop_tail<PT>(P, L, update);
+    if (h) h(u, PH_FUSED, 0);
+    for (int c = L.tail_c - 1; c >= 0 && e == cudaSuccess; --c) {
+      if (h) h(u, PH_BWD, 1);
+      e = launch_bwd<PT>(P, L, c, c == 0 ? fin_last : FIN_NONE);
+      if (h) h(u, PH_BWD, 0);
+    }
     return e;
   }
   for (int c = 0; c < nc - 1 && e == cudaSuccess; ++c) {

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libiccg.so")
 STATUS = {0: "ICCG_OK", 1: "ICCG_ERR_ARG", 2: "ICCG_ERR_COLORING", 3: "ICCG_ERR_BREAKDOWN",
           4: "ICCG_NOT_CONVERGED", 5: "ICCG_ERR_CUDA", 6: "ICCG_ERR_TIMEOUT", 7: "ICCG_ERR_NONFINITE",
           8: "ICCG_ERR_UNIMPLEMENTED", 9: "ICCG_ERR_STATE"}
-ICCG_OK, ICCG_NOT_CONVERGED = 0, 4
+ICCG_OK, ICCG_ERR_ARG, ICCG_NOT_CONVERGED = 0, 1, 4
 
 
 class IccgError(RuntimeError):
@@ -76,6 +76,10 @@ def load():
         "iccg_sort_blocks_desc": [i32, i32, vp],
         "iccg_color_order": [i32, vp, vp, i32, vp, vp, P(i32), vp, vp, vp],
         "iccg_level_order": [i32, vp, vp, vp, P(i32), vp, vp, vp],
+        "iccg_dev_graph": [i32, vp, vp, i64, vp, vp, P(i64), vp],
+        "iccg_dev_color_order": [i32, vp, vp, i64, i32, vp, vp, P(i32), vp, vp, vp, vp],
+        "iccg_dev_sort_blocks_desc": [i32, i32, vp, vp],
+        "iccg_dev_block_leiden": [i32, vp, vp, i64, i32, d, i32, vp, P(i32), vp],
         "iccg_split_levels": [i32, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, P(i32), P(i32)],
         "iccg_spmv_dot_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp],
         "iccg_batch_create": [P(vp), vp, i32, i32, P(iccg_batch_opts)],
@@ -301,6 +305,70 @@ def iccg_color_order(n, gptr, gadj, n_b, block_of):
     _check(load().iccg_color_order(int(n), _ptr(gptr), _ptr(gadj), int(n_b), _ptr(block_of), _ptr(color_of),
                                    ctypes.byref(nc), _ptr(perm), _ptr(bptr), _ptr(cptr)), "iccg_color_order")
     return color_of[:n_b], nc.value, perm[:n], bptr, cptr[: nc.value + 1]
+
+
+def iccg_dev_graph(rowptr, colind, stream=None):
+    """Device graph: rowptr int64[n+1], colind int32[nnz] CUDA tensors ->
+    (gptr int64[n+1], gadj int32[m]) CUDA tensors."""
+    import torch
+    n, nnz = rowptr.numel() - 1, colind.numel()
+    gptr = torch.empty(n + 1, dtype=torch.int64, device=rowptr.device)
+    gadj = torch.empty(max(2 * nnz, 1), dtype=torch.int32, device=rowptr.device)
+    m = ctypes.c_int64(0)
+    _check(load().iccg_dev_graph(int(n), _ptr(rowptr), _ptr(colind), int(nnz), _ptr(gptr), _ptr(gadj),
+                                 ctypes.byref(m), ctypes.c_void_p(stream or 0)), "iccg_dev_graph")
+    return gptr, gadj[: m.value]
+
+
+def iccg_dev_color_order(gptr, gadj, n_b, block_of, stream=None):
+    """Device greedy block coloring + ordering (CUDA tensors in and out).
+    Returns (color_of, n_c, perm, block_ptr, color_ptr)."""
+    import torch
+    n, dev = gptr.numel() - 1, gptr.device
+    color_of = torch.empty(max(n_b, 1), dtype=torch.int32, device=dev)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    bptr = torch.empty(n_b + 1, dtype=torch.int32, device=dev)
+    cptr = torch.empty(n_b + 1, dtype=torch.int32, device=dev)
+    nc = ctypes.c_int32(0)
+    _check(load().iccg_dev_color_order(int(n), _ptr(gptr), _ptr(gadj), int(gadj.numel()), int(n_b), _ptr(block_of),
+                                       _ptr(color_of), ctypes.byref(nc), _ptr(perm), _ptr(bptr), _ptr(cptr),
+                                       ctypes.c_void_p(stream or 0)), "iccg_dev_color_order")
+    return color_of[:n_b], nc.value, perm[:n], bptr, cptr[: nc.value + 1]
+
+
+def iccg_dev_sort_blocks_desc(n_b, block_of, stream=None):
+    """Relabels the CUDA tensor block_of in place (Leiden block order)."""
+    _check(load().iccg_dev_sort_blocks_desc(int(block_of.numel()), int(n_b), _ptr(block_of),
+                                            ctypes.c_void_p(stream or 0)), "iccg_dev_sort_blocks_desc")
+    return block_of
+
+
+def iccg_dev_block_leiden(gptr, gadj, quality, gamma, n_iter=2, stream=None):
+    """Device Leiden blocking (CUDA tensors).  Returns (block_of, n_b)."""
+    import torch
+    q = {"modularity": 0, "md": 0, "cpm": 1, "cp": 1}[quality] if isinstance(quality, str) else int(quality)
+    n = gptr.numel() - 1
+    block_of = torch.empty(max(n, 1), dtype=torch.int32, device=gptr.device)
+    nb = ctypes.c_int32(0)
+    _check(load().iccg_dev_block_leiden(int(n), _ptr(gptr), _ptr(gadj), int(gadj.numel()), q, float(gamma),
+                                        int(n_iter), _ptr(block_of), ctypes.byref(nb), ctypes.c_void_p(stream or 0)),
+           "iccg_dev_block_leiden")
+    return block_of[:n], nb.value
+
+
+def dev_blocking(a, method="leiden_cpm", gamma=0.5, n_iter=2, stream=None):
+    """The blocking pipeline on the device (graph -> Leiden -> size order ->
+    greedy coloring -> ordering); returns the host dict of `blocking`."""
+    import torch
+    rp = torch.as_tensor(np.asarray(a.rowptr, dtype=np.int64)).cuda()
+    ci = torch.as_tensor(np.asarray(a.colind, dtype=np.int32)).cuda()
+    gptr, gadj = iccg_dev_graph(rp, ci, stream)
+    q = {"leiden_md": "modularity", "leiden_cpm": "cpm"}[method]
+    block_of, nb = iccg_dev_block_leiden(gptr, gadj, q, gamma, n_iter, stream)
+    iccg_dev_sort_blocks_desc(nb, block_of, stream)
+    color_of, nc, perm, bptr, cptr = iccg_dev_color_order(gptr, gadj, nb, block_of, stream)
+    return {"perm": perm.cpu().numpy(), "block_ptr": bptr.cpu().numpy(), "color_ptr": cptr.cpu().numpy(),
+            "n_b": nb, "n_c": nc, "block_of": block_of.cpu().numpy(), "color_of": color_of.cpu().numpy()}
 
 
 def iccg_level_order(n, gptr, gadj):

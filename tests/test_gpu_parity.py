@@ -88,15 +88,16 @@ SHAPES = [dict(), dict(lane_block_max=8), dict(lane_block_max=-1),
           dict(solver="persistent", warps_per_cta=16), dict(tile_mapping="warp"), dict(tile_mapping="cta"),
           dict(tile_mapping="warp", warps_per_cta=3, lane_block_max=16), dict(tile_mapping="units"),
           dict(tile_mapping="units", lane_block_max=16), dict(tile_mapping="units", no_graph=1),
-          dict(fuse_sweep=1), dict(fuse_sweep=1, no_graph=1), dict(fuse_sweep=1, precond_fp32=0, warps_per_cta=4)]
+          dict(fuse_sweep=1), dict(fuse_sweep=1, no_graph=1), dict(fuse_sweep=1, precond_fp32=0, warps_per_cta=4),
+          dict(fuse_sweep=2), dict(fuse_sweep=2, no_graph=1)]
 LAYOUTS = {"lanes": dict(), "groups": dict(lane_block_max=-1), "warp_tiles": dict(tile_mapping="warp"),
            "cta_tiles": dict(tile_mapping="cta"), "pair_tiles": dict(tile_mapping="pair"),
            "units": dict(tile_mapping="units"), "units16": dict(tile_mapping="units", lane_block_max=16),
-           "fused": dict(fuse_sweep=1)}
+           "fused": dict(fuse_sweep=1), "tail": dict(fuse_sweep=2)}
 SOLVERS = {"lanes": dict(), "groups": dict(lane_block_max=-1), "persistent": dict(solver="persistent"),
            "warp_tiles": dict(tile_mapping="warp"), "cta_tiles": dict(tile_mapping="cta"),
            "pair_tiles": dict(tile_mapping="pair"), "units": dict(tile_mapping="units"),
-           "fused": dict(fuse_sweep=1)}
+           "fused": dict(fuse_sweep=1), "tail": dict(fuse_sweep=2)}
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -383,3 +384,29 @@ def test_fused_color_without_in_block_entries():
             if not fp32:
                 assert abs(it - ref["iterations"]) <= 1 and _rel(x, ref["x"]) <= 1e-10
             S.close()
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("no_graph", [0, 1])
+def test_tail_colors_in_one_cooperative_launch(fp32, no_graph):
+    """fuse_sweep = 2: the last colors of every sweep (at most n/32 rows, blocks
+    of one or two rows) run forward, fused and backward in one cooperative
+    launch between the per-color launches; the solve equals the oracle's."""
+    a = gen.poisson3d_7pt(40)
+    b = gen.rhs_uniform(a.n, 6)
+    bl = oracle.blocking(a, "leiden_cpm", gamma=0.5)
+    ref = oracle.iccg(a, b, bl["perm"], tol=1e-8, maxit=5000)
+    S = iccg.Solver(a, bl, fuse_sweep=2, precond_fp32=fp32, no_graph=no_graph)
+    info = iccg.iccg_info(S.ctx)
+    assert info["fused_sweep"] == 2
+    assert info["launches_per_iteration"] < 2 + 2 * bl["n_c"] - 1
+    x = np.zeros(a.n)
+    st, it, hist = iccg.iccg_solve(S.ctx, b, x, 1e-8, 5000)
+    S.close()
+    assert st == iccg.ICCG_OK
+    if fp32:
+        assert np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b) <= 1e-7
+        assert abs(it - ref["iterations"]) <= 3 + ref["iterations"] // 10
+    else:
+        assert abs(it - ref["iterations"]) <= 1
+        assert _rel(x, ref["x"]) <= 1e-10

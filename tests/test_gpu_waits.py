@@ -55,14 +55,15 @@ def test_persistent_wait_runs_out_then_context_solves():
     S.close()
 
 
+@pytest.mark.parametrize("fuse", [1, 2])
 @pytest.mark.parametrize("fp32", [False, True])
-def test_cooperative_sweep_wait_runs_out_then_context_solves(fp32):
-    a = gen.poisson3d_7pt(18)
+def test_cooperative_sweep_wait_runs_out_then_context_solves(fp32, fuse):
+    a = gen.poisson3d_7pt(40)
     b = gen.rhs_uniform(a.n, 5)
     bl = oracle.blocking(a, "leiden_cpm", gamma=0.5)
     ref = oracle.iccg(a, b, bl["perm"], tol=1e-8, maxit=5000)
-    S = iccg.Solver(a, bl, precond_fp32=fp32, fuse_sweep=1)
-    assert iccg.iccg_info(S.ctx)["fused_sweep"] == 1
+    S = iccg.Solver(a, bl, precond_fp32=fp32, fuse_sweep=fuse)
+    assert iccg.iccg_info(S.ctx)["fused_sweep"] == fuse
     iccg.iccg_set_wait_limit(S.ctx, 1)
     x = np.zeros(a.n)
     with pytest.raises(iccg.IccgError) as ei:
