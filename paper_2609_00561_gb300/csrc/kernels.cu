@@ -1269,6 +1269,49 @@ __device__ __forceinline__ void unit_coef(const PT *v, const uint32_t *sw, int o
   for (int w = 0; w < (S + 3) / 4; ++w) src[w] = 4 * w < M ? __ldg(sw + soff + w * kWarp + lane) : 0u;
 }
 
+// the lane's chain coefficients into its column of the warp's shared-memory
+// buffer (cp.async, only the steps its mask has: no registers held while the
+// copies fly) and its source lanes into registers
+template <typename PT>
+__device__ __forceinline__ void cp_async_elem(PT *smem, const PT *gmem);
+template <> __device__ __forceinline__ void cp_async_elem<double>(double *smem, const double *gmem) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(a), "l"(gmem) : "memory");
+}
+template <> __device__ __forceinline__ void cp_async_elem<float>(float *smem, const float *gmem) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(gmem) : "memory");
+}
+
+template <typename PT, int S>
+__device__ __forceinline__ void unit_coef_smem(const PT *v, const uint32_t *sw, int off, int soff, int M,
+                                               uint32_t mask, int lane, PT *cfs, uint32_t (&src)[(S + 3) / 4]) {
+#pragma unroll
+  for (int k = 0; k < S; ++k)
+    if ((mask >> k) & 1u) cp_async_elem<PT>(cfs + k * kWarp + lane, v + off + k * kWarp + lane);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+#pragma unroll
+  for (int w = 0; w < (S + 3) / 4; ++w) src[w] = 4 * w < M ? __ldg(sw + soff + w * kWarp + lane) : 0u;
+}
+
+// phase B with the coefficients in shared memory (the lane's own column)
+template <typename PT, int S>
+__device__ __forceinline__ PT unit_chain_smem(PT t, int M, uint32_t mask, uint32_t wmask, const PT *cfs, int lane,
+                                              const uint32_t (&src)[(S + 3) / 4]) {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    if (k < M) {
+      const int sl = int((src[k / 4] >> (8 * (k % 4))) & 0xffu);
+      const PT tk = __shfl_sync(0xffffffffu, t, sl);
+      if ((wmask >> k) & 1u) {
+        if ((mask >> k) & 1u) t -= cfs[k * kWarp + lane] * tk;
+      }
+    }
+  }
+  return t;
+}
+
 // phase B of a unit: M chain steps; at step k every lane with a term
 // subtracts coefficient x the (final) value of its source lane; wmask = OR
 // of the warp's lane masks (a step no lane uses issues no FP64 instruction)
@@ -1290,13 +1333,22 @@ __device__ __forceinline__ PT unit_chain(PT t, int M, uint32_t mask, uint32_t wm
 
 constexpr int kUnitWarps = 8;   // warps (units in flight) per CTA of the warp-unit kernels
 
+// chain coefficients of segments of at least kUnitSmemS steps sit in shared
+// memory (S x 32 values per warp) instead of registers
+constexpr int kUnitSmemS = 16;
+
+inline int unit_smem_bytes(int S, int elem) { return S >= kUnitSmemS ? kUnitWarps * S * kWarp * elem : 0; }
+
 template <typename PT, int MODE, bool UPDATE, int S>
 __global__ void __launch_bounds__(kUnitWarps * kWarp)
 unit_kernel(Params P, int u0, int u1, int fin, SlotArgs sa) {
   pdl_trigger();
   __shared__ double red[kMaxWarpsPerCta];
   __shared__ int flag;
+  extern __shared__ __align__(16) unsigned char usm[];
+  constexpr bool SM = S >= kUnitSmemS;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  PT *cfs = reinterpret_cast<PT *>(usm) + (SM ? wid * S * kWarp : 0);
   const int step = lane & (S - 1);
   constexpr bool FWD = MODE != M_BWD;
   PT *yv = reinterpret_cast<PT *>(P.y);
@@ -1317,10 +1369,15 @@ unit_kernel(Params P, int u0, int u1, int fin, SlotArgs sa) {
     const bool on = row >= 0;
     const uint32_t mf = FWD ? __ldg(P.wl_mask + size_t(u) * kWarp + lane) : 0u;
     const uint32_t mb = MODE != M_FWD ? __ldg(P.wu_mask + size_t(u) * kWarp + lane) : 0u;
-    PT cf[S];
+    PT cf[SM ? 1 : S];
     uint32_t src[(S + 3) / 4];
-    if (FWD) unit_coef<PT, S>(wlv<PT>(P), P.wl_src, d.li, d.ls, d.lm, mf, lane, cf, src);
-    else unit_coef<PT, S>(wuv<PT>(P), P.wu_src, d.ui, d.us, d.um, mb, lane, cf, src);
+    if constexpr (SM) {
+      if (FWD) unit_coef_smem<PT, S>(wlv<PT>(P), P.wl_src, d.li, d.ls, d.lm, mf, lane, cfs, src);
+      else unit_coef_smem<PT, S>(wuv<PT>(P), P.wu_src, d.ui, d.us, d.um, mb, lane, cfs, src);
+    } else {
+      if (FWD) unit_coef<PT, S>(wlv<PT>(P), P.wl_src, d.li, d.ls, d.lm, mf, lane, cf, src);
+      else unit_coef<PT, S>(wuv<PT>(P), P.wu_src, d.ui, d.us, d.um, mb, lane, cf, src);
+    }
     const PT dv = on ? __ldg(dvg + row) : PT(0);
     if (!waited) {
       pdl_wait();
@@ -1342,20 +1399,23 @@ unit_kernel(Params P, int u0, int u1, int fin, SlotArgs sa) {
       }
       t = unit_ext<PT>(P.sl_col, slv<PT>(P), d.lo + lane, d.lw, t, yv);
       // B, C
-      t = unit_chain<PT, S>(t, d.lm, mf, __reduce_or_sync(0xffffffffu, mf), cf, src);
+      if constexpr (SM) t = unit_chain_smem<PT, S>(t, d.lm, mf, __reduce_or_sync(0xffffffffu, mf), cfs, lane, src);
+      else t = unit_chain<PT, S>(t, d.lm, mf, __reduce_or_sync(0xffffffffu, mf), cf, src);
       const PT y = t * dv;
       if (MODE == M_FWD) {
         if (on) yv[row] = y;
         continue;
       }
       // the last color: its backward sweep at once (y stays in registers)
-      unit_coef<PT, S>(wuv<PT>(P), P.wu_src, d.ui, d.us, d.um, mb, lane, cf, src);
+      if constexpr (SM) unit_coef_smem<PT, S>(wuv<PT>(P), P.wu_src, d.ui, d.us, d.um, mb, lane, cfs, src);
+      else unit_coef<PT, S>(wuv<PT>(P), P.wu_src, d.ui, d.us, d.um, mb, lane, cf, src);
       t = y;
     } else {
       if (on) t = __ldcg(yv + row);
     }
     t = unit_ext<PT>(P.su_col, suv<PT>(P), d.uo + lane, d.uw, t, zv);
-    t = unit_chain<PT, S>(t, d.um, mb, __reduce_or_sync(0xffffffffu, mb), cf, src);
+    if constexpr (SM) t = unit_chain_smem<PT, S>(t, d.um, mb, __reduce_or_sync(0xffffffffu, mb), cfs, lane, src);
+    else t = unit_chain<PT, S>(t, d.um, mb, __reduce_or_sync(0xffffffffu, mb), cf, src);
     const PT z = t * dv;
     if (on) {
       zv[row] = z;
@@ -2324,13 +2384,14 @@ cudaError_t launch_pair(const Params &P, const Plan &L, int c, int mode, bool up
 template <typename PT, int S>
 cudaError_t launch_unit_s(const Params &P, const Plan &L, int c, int mode, bool update, int fin, const SlotArgs &sa) {
   const int g = L.grid_c[c], t0 = L.unit0[c], t1 = L.unit1[c], th = kUnitWarps * kWarp;
-  if (mode == M_BWD) return launch(unit_kernel<PT, M_BWD, false, S>, g, th, 0, L, P, t0, t1, fin, sa);
+  const int sm = unit_smem_bytes(S, int(sizeof(PT)));
+  if (mode == M_BWD) return launch(unit_kernel<PT, M_BWD, false, S>, g, th, sm, L, P, t0, t1, fin, sa);
   if (update) {
-    if (mode == M_FUSED) return launch(unit_kernel<PT, M_FUSED, true, S>, g, th, 0, L, P, t0, t1, fin, sa);
-    return launch(unit_kernel<PT, M_FWD, true, S>, g, th, 0, L, P, t0, t1, fin, sa);
+    if (mode == M_FUSED) return launch(unit_kernel<PT, M_FUSED, true, S>, g, th, sm, L, P, t0, t1, fin, sa);
+    return launch(unit_kernel<PT, M_FWD, true, S>, g, th, sm, L, P, t0, t1, fin, sa);
   }
-  if (mode == M_FUSED) return launch(unit_kernel<PT, M_FUSED, false, S>, g, th, 0, L, P, t0, t1, fin, sa);
-  return launch(unit_kernel<PT, M_FWD, false, S>, g, th, 0, L, P, t0, t1, fin, sa);
+  if (mode == M_FUSED) return launch(unit_kernel<PT, M_FUSED, false, S>, g, th, sm, L, P, t0, t1, fin, sa);
+  return launch(unit_kernel<PT, M_FWD, false, S>, g, th, sm, L, P, t0, t1, fin, sa);
 }
 
 template <typename PT>
@@ -2482,6 +2543,11 @@ cudaError_t configure_pt() {
   if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_FUSED, false>);
   if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_FWD, false>);
   if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_BWD, false>);
+  if (e == cudaSuccess) e = allow_smem(unit_kernel<PT, M_FWD, true, 32>);
+  if (e == cudaSuccess) e = allow_smem(unit_kernel<PT, M_FWD, false, 32>);
+  if (e == cudaSuccess) e = allow_smem(unit_kernel<PT, M_FUSED, true, 32>);
+  if (e == cudaSuccess) e = allow_smem(unit_kernel<PT, M_FUSED, false, 32>);
+  if (e == cudaSuccess) e = allow_smem(unit_kernel<PT, M_BWD, false, 32>);
   return e;
 }
 
@@ -2541,12 +2607,13 @@ int coop_sweep_resident_ctas(bool fp32) {
 int unit_resident_ctas(bool fp32, int S, int threads) {
   int nb = 0;
   cudaError_t e;
+  const size_t sm = size_t(unit_smem_bytes(S <= 8 ? 8 : 32, fp32 ? 4 : 8));
   if (fp32) {
-    e = S <= 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, unit_kernel<float, M_FWD, true, 8>, threads, 0)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, unit_kernel<float, M_FWD, true, 32>, threads, 0);
+    e = S <= 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, unit_kernel<float, M_FWD, true, 8>, threads, sm)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, unit_kernel<float, M_FWD, true, 32>, threads, sm);
   } else {
-    e = S <= 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, unit_kernel<double, M_FWD, true, 8>, threads, 0)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, unit_kernel<double, M_FWD, true, 32>, threads, 0);
+    e = S <= 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, unit_kernel<double, M_FWD, true, 8>, threads, sm)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, unit_kernel<double, M_FWD, true, 32>, threads, sm);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -356,16 +356,23 @@ def iccg_dev_block_leiden(gptr, gadj, quality, gamma, n_iter=2, stream=None):
     return block_of[:n], nb.value
 
 
-def dev_blocking(a, method="leiden_cpm", gamma=0.5, n_iter=2, stream=None):
+def dev_blocking(a, method="leiden_cpm", gamma=0.5, n_iter=2, block_size=32, stream=None):
     """The blocking pipeline on the device (graph -> Leiden -> size order ->
-    greedy coloring -> ordering); returns the host dict of `blocking`."""
+    greedy coloring -> ordering); returns the host dict of `blocking`.
+    method "abmc": the graph and the coloring / ordering on the device, the
+    ABMC blocks themselves by the host code (a sequential breadth-first
+    construction by its definition)."""
     import torch
     rp = torch.as_tensor(np.asarray(a.rowptr, dtype=np.int64)).cuda()
     ci = torch.as_tensor(np.asarray(a.colind, dtype=np.int32)).cuda()
     gptr, gadj = iccg_dev_graph(rp, ci, stream)
-    q = {"leiden_md": "modularity", "leiden_cpm": "cpm"}[method]
-    block_of, nb = iccg_dev_block_leiden(gptr, gadj, q, gamma, n_iter, stream)
-    iccg_dev_sort_blocks_desc(nb, block_of, stream)
+    if method == "abmc":
+        bo, nb = iccg_block_abmc(a.n, gptr.cpu().numpy(), gadj.cpu().numpy(), block_size)
+        block_of = torch.as_tensor(bo).cuda()
+    else:
+        q = {"leiden_md": "modularity", "leiden_cpm": "cpm"}[method]
+        block_of, nb = iccg_dev_block_leiden(gptr, gadj, q, gamma, n_iter, stream)
+        iccg_dev_sort_blocks_desc(nb, block_of, stream)
     color_of, nc, perm, bptr, cptr = iccg_dev_color_order(gptr, gadj, nb, block_of, stream)
     return {"perm": perm.cpu().numpy(), "block_ptr": bptr.cpu().numpy(), "color_ptr": cptr.cpu().numpy(),
             "n_b": nb, "n_c": nc, "block_of": block_of.cpu().numpy(), "color_of": color_of.cpu().numpy()}

@@ -278,3 +278,15 @@ def test_device_leiden_full_size_cpm05():
     q_one = oracle.quality_cpm(n, gp, ga, np.arange(n), 0.5)
     assert q_dev - q_one >= 0.9 * (q_host - q_one)
     assert _connected(a, bd["block_of"], bd["n_b"])
+
+
+@pytest.mark.parametrize("s", [1, 2, 8, 32])
+def test_device_pipeline_abmc_equals_oracle(s):
+    """ABMC through the device pipeline (device graph, host ABMC blocks,
+    device coloring and ordering) gives the oracle's ordering exactly."""
+    a = gen.diffusion3d_27pt(14, seed=2)
+    bd = iccg.dev_blocking(a, "abmc", block_size=s)
+    bo = oracle.blocking(a, "abmc", s)
+    assert bd["n_b"] == bo["n_b"] and bd["n_c"] == bo["n_c"]
+    for k in ("perm", "block_ptr", "color_ptr", "color_of"):
+        assert np.array_equal(np.asarray(bd[k]), np.asarray(bo[k])), k
