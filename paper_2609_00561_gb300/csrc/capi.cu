@@ -581,8 +581,33 @@ iccg_status iccg_factor(iccg_ctx *ctx) {
   DeviceGuard g(ctx->device);
   ctx->factored = false;
   if (ctx->H.n == 0) { ctx->factored = true; return ICCG_OK; }
-  CK(cudaMemsetAsync(ctx->P.err_row, 0xff, sizeof(unsigned long long), ctx->stream), "factor");
-  CK(launch_factor(ctx->P, ctx->plan, int(ctx->H.nL)), "factor launch");
+  // the factorization's launches (one per in-block level of every color)
+  // are captured once into a graph and replayed: no host launch cost per level
+  if (ctx->opts.no_graph == 0 && !ctx->fexec && !ctx->fgraph_failed) {
+    cudaGraph_t fg = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = cudaMemsetAsync(ctx->P.err_row, 0xff, sizeof(unsigned long long), ctx->stream);
+      if (e1 == cudaSuccess) e1 = launch_factor(ctx->P, ctx->plan, int(ctx->H.nL));
+      e = cudaStreamEndCapture(ctx->stream, &fg);
+      if (e == cudaSuccess) e = e1;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->fexec, fg, 0);
+    if (fg) cudaGraphDestroy(fg);
+    if (e != cudaSuccess) {
+      // e.g. the legacy default stream, which cannot be captured
+      cudaGetLastError();
+      if (ctx->fexec) cudaGraphExecDestroy(ctx->fexec);
+      ctx->fexec = nullptr;
+      ctx->fgraph_failed = true;
+    }
+  }
+  if (ctx->fexec) {
+    CK(cudaGraphLaunch(ctx->fexec, ctx->stream), "factor graph launch");
+  } else {
+    CK(cudaMemsetAsync(ctx->P.err_row, 0xff, sizeof(unsigned long long), ctx->stream), "factor");
+    CK(launch_factor(ctx->P, ctx->plan, int(ctx->H.nL)), "factor launch");
+  }
   unsigned long long row = 0;
   CK(cudaMemcpyAsync(&row, ctx->P.err_row, sizeof(row), cudaMemcpyDeviceToHost, ctx->stream), "factor");
   CK(cudaStreamSynchronize(ctx->stream), "factor sync");
@@ -1015,6 +1040,8 @@ void iccg_destroy(iccg_ctx *ctx) {
     DeviceGuard guard(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     destroy_graph(ctx);
+    if (ctx->fexec) cudaGraphExecDestroy(ctx->fexec);
+    ctx->fexec = nullptr;
     for (void *p : ctx->allocs) cudaFree(p);
     if (ctx->sc_host) cudaFreeHost(ctx->sc_host);
     if (ctx->hist_host) cudaFreeHost(ctx->hist_host);

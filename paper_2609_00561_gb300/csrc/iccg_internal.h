@@ -411,6 +411,8 @@ struct iccg_ctx {
   int32_t hist_host_cap = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  cudaGraphExec_t fexec = nullptr;      // IC(0): its launch sequence as one graph
+  bool fgraph_failed = false;
   unsigned long long cond_handle = 0;
   // error record
   int64_t err_index = -1;
