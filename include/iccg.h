@@ -256,19 +256,22 @@ void iccg_destroy(iccg_ctx *ctx);
  *                      past its last iteration).  Returns ICCG_OK when every
  *                      right-hand side converged, else the worst status.
  *   iccg_batch_tune    re-runs the shape search: every candidate (warps per
- *                      CTA x CTAs per SM x CTA-split exponent) solves B (as in iccg_batch_solve,
- *                      from x0 = 0, to tol / maxit; host or device), or, with
- *                      B = NULL, random right-hand sides for 20 iterations;
- *                      the fastest is kept and *best_ms (may be NULL) gets
- *                      its time.
+ *                      CTA x CTAs per SM x CTA-split exponent, then rows per
+ *                      thread 1 / 2 / 4 at the best of those) solves B (as in
+ *                      iccg_batch_solve, from x0 = 0, to tol / maxit; host or
+ *                      device), or, with B = NULL, random right-hand sides for
+ *                      20 iterations; the fastest is kept and *best_ms (may be
+ *                      NULL) gets its time.
  *   iccg_batch_set_wait_limit  wall-time limit (ns) of the per-system barrier
  *                      waits inside the batched kernel (0: the default, 4 s);
  *                      a system whose wait runs out stops and its right-hand
  *                      sides report ICCG_ERR_TIMEOUT; the batch stays usable.
- *   iccg_batch_info    out[6]: warps per CTA, CTAs per SM, grid, padded nrhs,
+ *   iccg_batch_info    out[7]: warps per CTA, CTAs per SM, grid, padded nrhs,
  *                      largest block, 3 x the exponent e of the CTA split
  *                      (CTAs per system proportional to n^e; e = 1 or 4/3,
- *                      chosen by the tuner with the shape).
+ *                      chosen by the tuner with the shape), rows per thread
+ *                      (consecutive rows a chain of right-hand-side lanes takes
+ *                      per pass of the SpMV and the p update).
  * The paper has no batched solver; this serves many independent systems
  * (e.g. the learned-blocking sweep) and multiple right-hand sides.
  * ------------------------------------------------------------------------ */
@@ -277,7 +280,8 @@ typedef struct {
   int32_t warps_per_cta;
   int32_t ctas_per_sm;
   int32_t autotune;
-  int32_t reserved[5];
+  int32_t rows_per_thread;    /* 0 (1), 1, 2 or 4 */
+  int32_t reserved[4];
 } iccg_batch_opts;
 
 iccg_status iccg_batch_create(iccg_batch **batch, iccg_ctx *const *ctxs, int32_t nsys, int32_t nrhs,
@@ -287,7 +291,7 @@ iccg_status iccg_batch_solve(iccg_batch *batch, const double *const *B, double *
 iccg_status iccg_batch_tune(iccg_batch *batch, const double *const *B, double tol, int32_t maxit,
                             double *best_ms);
 iccg_status iccg_batch_set_wait_limit(iccg_batch *batch, uint64_t wait_ns);
-iccg_status iccg_batch_info(const iccg_batch *batch, int32_t out[6]);
+iccg_status iccg_batch_info(const iccg_batch *batch, int32_t out[7]);
 iccg_status iccg_batch_last_error(const iccg_batch *batch, const char **msg);
 void iccg_batch_destroy(iccg_batch *batch);
 

@@ -219,7 +219,8 @@ __device__ __forceinline__ bool batch_precond(const BatchSys &S, PT *w, int kp, 
   return true;
 }
 
-template <typename PT>
+// R: rows per chain and pass of the SpMV and the p update (1, 2 or 4)
+template <typename PT, int R>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp, 1)
 batch_kernel(const BatchSys *sys, const int32_t *cta_sys, int k, int kp, int smax, int maxit, double tol) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -317,13 +318,28 @@ batch_kernel(const BatchSys *sys, const int32_t *cta_sys, int k, int kp, int sma
     const double beta = st_beta[j];
     // p = z + beta p
     const PT *z = reinterpret_cast<const PT *>(S.z);
-    if (act)
+    // R consecutive rows per chain and pass: their loads are issued together
+    if (act && R == 1) {
       for (int i = gc; i < n; i += total)
         S.p[size_t(i) * kp + j] = double(__ldcg(z + size_t(i) * kp + j)) + beta * __ldcg(S.p + size_t(i) * kp + j);
+    } else if (act) {
+      for (int i0 = gc * R; i0 < n; i0 += total * R) {
+        double zz[R], pp[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+          if (i0 + u < n) {
+            zz[u] = double(__ldcg(z + size_t(i0 + u) * kp + j));
+            pp[u] = __ldcg(S.p + size_t(i0 + u) * kp + j);
+          }
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+          if (i0 + u < n) S.p[size_t(i0 + u) * kp + j] = zz[u] + beta * pp[u];
+      }
+    }
     if (!(ok = sys_sync(S.bar, nct, gen, &flag, S.wait_ns))) break;
     // q = A p, <p, q>
     acc = 0.0;
-    if (act) {
+    if (act && R == 1) {
       for (int i = gc; i < n; i += total) {
         double s = 0.0;
         const int e1 = __ldg(S.arp + i + 1);
@@ -331,6 +347,33 @@ batch_kernel(const BatchSys *sys, const int32_t *cta_sys, int k, int kp, int sma
           s += __ldg(S.aval + e) * __ldcg(S.p + size_t(__ldg(S.acol + e)) * kp + j);
         S.q[size_t(i) * kp + j] = s;
         acc += __ldcg(S.p + size_t(i) * kp + j) * s;
+      }
+    } else if (act) {
+      for (int i0 = gc * R; i0 < n; i0 += total * R) {
+        int e0[R], e1[R];
+        double sq[R];
+        int len = 0;
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          const bool v = i0 + u < n;
+          e0[u] = v ? __ldg(S.arp + i0 + u) : 0;
+          e1[u] = v ? __ldg(S.arp + i0 + u + 1) : 0;
+          sq[u] = 0.0;
+          len = max(len, e1[u] - e0[u]);
+        }
+        // the rows' t-th entries together (each row's sum in entry order)
+        for (int t = 0; t < len; ++t) {
+#pragma unroll
+          for (int u = 0; u < R; ++u)
+            if (e0[u] + t < e1[u])
+              sq[u] += __ldg(S.aval + e0[u] + t) * __ldcg(S.p + size_t(__ldg(S.acol + e0[u] + t)) * kp + j);
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+          if (i0 + u < n) {
+            S.q[size_t(i0 + u) * kp + j] = sq[u];
+            acc += __ldcg(S.p + size_t(i0 + u) * kp + j) * sq[u];
+          }
       }
     }
     cta_rhs_sum(acc, red, kp, nchain, mypart + 2 * kp);
@@ -403,6 +446,13 @@ cudaError_t allow_smem_b(K kernel) {
                               optin - int(fa.sharedSizeBytes) - 256);
 }
 
+using BatchKernel = void (*)(const BatchSys *, const int32_t *, int, int, int, int, double);
+
+template <typename PT>
+BatchKernel batch_kernel_of(int R) {
+  return R == 4 ? batch_kernel<PT, 4> : (R == 2 ? batch_kernel<PT, 2> : batch_kernel<PT, 1>);
+}
+
 }  // namespace
 }  // namespace iccg
 
@@ -426,6 +476,7 @@ struct iccg_batch {
   int hist_cap = 0;
   // launch shape
   int W = 8, cps = 1, grid = 0, smem = 0, max_part_ctas = 0;
+  int R = 1;             // rows per chain and pass (SpMV, p update)
   double wexp = 1.0;     // CTAs per system proportional to n^wexp
   std::vector<int32_t> cta0;
   cudaGraph_t graph = nullptr;
@@ -455,8 +506,8 @@ int batch_smem(const iccg_batch *b, int W) {
 int batch_occupancy(const iccg_batch *b, int W, int smem) {
   int nb = 0;
   const cudaError_t e =
-      b->fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<float>, W * kWarp, size_t(smem))
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<double>, W * kWarp, size_t(smem));
+      b->fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel_of<float>(b->R), W * kWarp, size_t(smem))
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel_of<double>(b->R), W * kWarp, size_t(smem));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -573,8 +624,8 @@ cudaError_t batch_launch(iccg_batch *b, cudaStream_t s, int maxit, double tol) {
   cfg.numAttrs = 1;
   const BatchSys *sys = b->d_sys;
   const int32_t *cts = b->d_cta_sys;
-  if (b->fp32) return cudaLaunchKernelEx(&cfg, batch_kernel<float>, sys, cts, b->k, b->kp, b->smax, maxit, tol);
-  return cudaLaunchKernelEx(&cfg, batch_kernel<double>, sys, cts, b->k, b->kp, b->smax, maxit, tol);
+  if (b->fp32) return cudaLaunchKernelEx(&cfg, batch_kernel_of<float>(b->R), sys, cts, b->k, b->kp, b->smax, maxit, tol);
+  return cudaLaunchKernelEx(&cfg, batch_kernel_of<double>(b->R), sys, cts, b->k, b->kp, b->smax, maxit, tol);
 }
 
 iccg_status set_shape(iccg_batch *b, int W, int cps, int sms) {
@@ -675,9 +726,11 @@ iccg_status iccg_batch_create(iccg_batch **out, iccg_ctx *const *ctxs, int32_t n
   if (!ctxs || nsys < 1 || nrhs < 1 || nrhs > 32) return ICCG_ERR_ARG;
   iccg_batch_opts o{};
   if (opts) o = *opts;
-  for (int k = 0; k < 5; ++k)
+  for (int k = 0; k < 4; ++k)
     if (o.reserved[k] != 0) return ICCG_ERR_ARG;
   if (o.warps_per_cta < 0 || o.warps_per_cta > kMaxWarpsPerCta || o.ctas_per_sm < 0) return ICCG_ERR_ARG;
+  if (o.rows_per_thread != 0 && o.rows_per_thread != 1 && o.rows_per_thread != 2 && o.rows_per_thread != 4)
+    return ICCG_ERR_ARG;
   for (int s = 0; s < nsys; ++s) {
     const iccg_ctx *c = ctxs[s];
     if (!c || !c->factored || c->H.n < 1) return ICCG_ERR_STATE;
@@ -699,10 +752,8 @@ iccg_status iccg_batch_create(iccg_batch **out, iccg_ctx *const *ctxs, int32_t n
   cudaGetDevice(&prev);
   if (prev != b->device) cudaSetDevice(b->device);
   cudaError_t e = cudaSuccess;
-  if (b->fp32) {
-    if (e == cudaSuccess) e = allow_smem_b(batch_kernel<float>);
-  } else if (e == cudaSuccess) {
-    e = allow_smem_b(batch_kernel<double>);
+  for (int R : {1, 2, 4}) {
+    if (e == cudaSuccess) e = b->fp32 ? allow_smem_b(batch_kernel_of<float>(R)) : allow_smem_b(batch_kernel_of<double>(R));
   }
   const size_t pe = b->fp32 ? 4 : 8;
   int sms = 152;
@@ -758,6 +809,7 @@ iccg_status iccg_batch_create(iccg_batch **out, iccg_ctx *const *ctxs, int32_t n
     b->err_msg = "cooperative launch not supported";
     return ICCG_ERR_CUDA;
   }
+  b->R = o.rows_per_thread > 0 ? o.rows_per_thread : 1;
   iccg_status st = set_shape(b, o.warps_per_cta > 0 ? o.warps_per_cta : 8, o.ctas_per_sm, sms);
   if (st != ICCG_OK) return st;
   if (o.autotune) {
@@ -877,8 +929,25 @@ iccg_status iccg_batch_tune(iccg_batch *b, const double *const *B, double tol, i
       if (ms < best) { best = ms; bW = W; bC = cps; bE = E; }
     }
   }
-  if (best_ms) *best_ms = best;
+  // rows per thread at the best shape
   b->wexp = bE;
+  int bR = b->R;
+  const int R0 = b->R;
+  for (int R : {1, 2, 4}) {
+    if (R == R0) continue;
+    b->R = R;   // the shape's occupancy is that of this R's kernel
+    if (set_shape(b, bW, bC, sms) != ICCG_OK) continue;
+    for (auto &x : hx) std::fill(x.begin(), x.end(), 0.0);
+    if (iccg_batch_solve(b, Bp.data(), X.data(), ttol, tmax, nullptr, nullptr, nullptr) == ICCG_ERR_CUDA) continue;
+    for (auto &x : hx) std::fill(x.begin(), x.end(), 0.0);
+    const auto t0 = std::chrono::steady_clock::now();
+    const iccg_status r = iccg_batch_solve(b, Bp.data(), X.data(), ttol, tmax, nullptr, nullptr, nullptr);
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (r == ICCG_ERR_CUDA || r == ICCG_ERR_TIMEOUT) continue;
+    if (ms < best) { best = ms; bR = R; }
+  }
+  b->R = bR;
+  if (best_ms) *best_ms = best;
   return set_shape(b, bW, bC, sms);
 }
 
@@ -889,7 +958,7 @@ iccg_status iccg_batch_set_wait_limit(iccg_batch *b, uint64_t wait_ns) {
   return ICCG_OK;
 }
 
-iccg_status iccg_batch_info(const iccg_batch *b, int32_t out[6]) {
+iccg_status iccg_batch_info(const iccg_batch *b, int32_t out[7]) {
   if (!b || !out) return ICCG_ERR_ARG;
   out[0] = b->W;
   out[1] = b->cps;
@@ -897,6 +966,7 @@ iccg_status iccg_batch_info(const iccg_batch *b, int32_t out[6]) {
   out[3] = b->kp;
   out[4] = b->smax;
   out[5] = int32_t(b->wexp * 3.0 + 0.5);   // 3 x the CTA-split exponent (3: rows, 4: rows^(4/3))
+  out[6] = b->R;
   return ICCG_OK;
 }
 

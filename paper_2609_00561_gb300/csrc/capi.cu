@@ -430,7 +430,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
     int32_t *d_fr;
     CK(dev_upload(ctx, &d_fr, H.fac_rows), "alloc factor schedule");
     P.fac_rows = d_fr;
-    P.fp_ptr = nullptr; P.fp_b = nullptr; P.fp_pos = nullptr;
+    P.fp_ptr = nullptr; P.fp_b = nullptr; P.fp_pos = nullptr; P.fac_rec = nullptr;
     if (!H.fp_ptr.empty()) {
       int32_t *d_fp, *d_fb;
       uint8_t *d_fs;
@@ -438,6 +438,19 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
       CK(dev_upload(ctx, &d_fb, H.fp_b), "alloc factor pairs");
       CK(dev_upload(ctx, &d_fs, H.fp_pos), "alloc factor pairs");
       P.fp_ptr = d_fp; P.fp_b = d_fb; P.fp_pos = d_fs;
+      // one 16-byte record per scheduled row (no dependent index loads in
+      // the factor kernels); rows the record cannot describe take the
+      // general form (entries field 255)
+      std::vector<int4> rec(H.fac_rows.size());
+      for (size_t k = 0; k < rec.size(); ++k) {
+        const int32_t i = H.fac_rows[k], rb = H.lrp[i], ni = H.lrp[i + 1] - rb;
+        const int32_t q0 = H.fp_ptr[size_t(rb)], np = H.fp_ptr[size_t(rb + ni)] - q0;
+        const bool ok = ni < 255 && np < (1 << 23);
+        rec[k] = make_int4(i, rb, q0, ok ? (ni | (np << 8)) : 255);
+      }
+      int4 *d_rec;
+      CK(dev_upload(ctx, &d_rec, rec), "alloc factor schedule");
+      P.fac_rec = d_rec;
     }
     L.fac_ptr = H.fac_ptr;
     L.fac_lev0 = H.fac_lev0;

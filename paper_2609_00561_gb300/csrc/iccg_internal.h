@@ -240,6 +240,7 @@ struct Params {
   double *hist;
   unsigned long long *err_row;  // IC(0) breakdown row (new numbering), ~0 = none
   const int32_t *fac_rows;      // IC(0) rows of the lane-tile colors, level by level
+  const int4 *fac_rec;          // per fac_rows entry: row, first L entry, first pair, entries | pairs << 8
   const int32_t *fp_ptr, *fp_b;  // IC(0) update pairs (null: not built)
   const uint8_t *fp_pos;
   // warp units: descriptors, per-lane in-block masks, in-block coefficients

@@ -1693,10 +1693,19 @@ struct FacSmem {
   Strided<uint32_t> pw;   // fp_pos bytes, as the 4-byte words covering the pass
 };
 
-__device__ __forceinline__ void factor_row_pairs(const Params &P, int i, const FacSmem &m) {
-  const int rb = P.lrp[i], ni = P.lrp[i + 1] - rb;
+// STAGE: pairs per pass
+template <int STAGE>
+__device__ __forceinline__ void factor_row_pairs(const Params &P, int4 rec, const FacSmem &m) {
+  const int i = rec.x, rb = rec.y, q0 = rec.z, ni = rec.w & 0xff, np = rec.w >> 8;
   if (ni > kFacRow) { factor_row_merge(P, i); return; }
-  const int q0 = __ldg(P.fp_ptr + rb), np = ni > 0 ? __ldg(P.fp_ptr + rb + ni) - q0 : 0;
+  // the first pass's pair indices and position words, before anything else
+  const uint32_t *posw = reinterpret_cast<const uint32_t *>(P.fp_pos);
+  {
+    const int nq = min(STAGE, np), w0 = q0 >> 2, w1 = (q0 + nq + 3) >> 2;
+    for (int q = 0; q < nq; ++q) cp_async4(&m.pb[q], P.fp_b + q0 + q);
+    for (int w = w0; w < w1; ++w) cp_async4(&m.pw[w - w0], posw + w);
+    cp_commit();
+  }
   {
     int col[kFacRow];
 #pragma unroll
@@ -1720,14 +1729,16 @@ __device__ __forceinline__ void factor_row_pairs(const Params &P, int i, const F
     ++p;
   }
   if (p < ni) s = m.sv[p];
-  const uint32_t *posw = reinterpret_cast<const uint32_t *>(P.fp_pos);
-  for (int qa = 0; qa < np; qa += kFacStage) {
-    const int nq = min(kFacStage, np - qa);
-    // indices and the words holding the positions
+  for (int qa = 0; qa < np; qa += STAGE) {
+    const int nq = min(STAGE, np - qa);
+    // indices and the words holding the positions (the first pass's were
+    // issued at the start)
     const int g0 = q0 + qa, w0 = g0 >> 2, w1 = (g0 + nq + 3) >> 2;
-    for (int q = 0; q < nq; ++q) cp_async4(&m.pb[q], P.fp_b + g0 + q);
-    for (int w = w0; w < w1; ++w) cp_async4(&m.pw[w - w0], posw + w);
-    cp_commit();
+    if (qa > 0) {
+      for (int q = 0; q < nq; ++q) cp_async4(&m.pb[q], P.fp_b + g0 + q);
+      for (int w = w0; w < w1; ++w) cp_async4(&m.pw[w - w0], posw + w);
+      cp_commit();
+    }
     cp_wait_all();
     // the pair values
     for (int q = 0; q < nq; ++q) cp_async8(&m.pv[q], P.lval + m.pb[q]);
@@ -1749,6 +1760,7 @@ __device__ __forceinline__ void factor_row_pairs(const Params &P, int i, const F
       }
     }
   }
+  cp_wait_all();   // no copy of this row may land in the next row's buffers
   for (int t = 0; t < ni; ++t) P.lval[rb + t] = m.sv[t];
   if (!(d > 0.0) || !isfinite(d)) {
     atomicMin(P.err_row, (unsigned long long)i);
@@ -1782,9 +1794,8 @@ __global__ void __launch_bounds__(kFacRowThreads) factor_rows_kernel(Params P, i
   q += size_t(T) * kFacStage * 4;
   m.pw.base = reinterpret_cast<uint32_t *>(q) + t;
   for (int k = k0 + int(blockIdx.x * blockDim.x + threadIdx.x); k < k1; k += int(gridDim.x * blockDim.x)) {
-    const int i = __ldg(P.fac_rows + k);
-    if (P.fp_ptr) factor_row_pairs(P, i, m);
-    else factor_row_merge(P, i);
+    if (P.fac_rec) factor_row_pairs<kFacStage>(P, __ldg(P.fac_rec + k), m);
+    else factor_row_merge(P, __ldg(P.fac_rows + k));
   }
 }
 

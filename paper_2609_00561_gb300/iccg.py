@@ -42,7 +42,7 @@ TILE_MAPPINGS = {"auto": 0, "cta": 1, "warp": 2, "pair": 3, "units": 4}
 
 class iccg_batch_opts(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("rows_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 _lib = None
@@ -497,13 +497,14 @@ def _batch_check(st, where, h):
 class BatchSolver:
     """iccg_batch over factored Solvers (set up with lane_block_max=-1)."""
 
-    def __init__(self, solvers, nrhs, warps_per_cta=0, ctas_per_sm=0, autotune=False):
+    def __init__(self, solvers, nrhs, warps_per_cta=0, ctas_per_sm=0, autotune=False, rows_per_thread=0):
         self.solvers = list(solvers)
         self.nrhs = int(nrhs)
         self.ns = [s.n for s in self.solvers]
         arr = (ctypes.c_void_p * len(self.solvers))(*[s.ctx for s in self.solvers])
         o = iccg_batch_opts()
         o.warps_per_cta, o.ctas_per_sm, o.autotune = int(warps_per_cta), int(ctas_per_sm), int(bool(autotune))
+        o.rows_per_thread = int(rows_per_thread)
         h = ctypes.c_void_p()
         st = load().iccg_batch_create(ctypes.byref(h), arr, len(self.solvers), self.nrhs, ctypes.byref(o))
         self.h = h
@@ -519,9 +520,10 @@ class BatchSolver:
             raise err
 
     def info(self):
-        out = np.zeros(6, dtype=np.int32)
+        out = np.zeros(7, dtype=np.int32)
         _batch_check(load().iccg_batch_info(self.h, _ptr(out)), "iccg_batch_info", self.h)
-        return dict(zip(("warps_per_cta", "ctas_per_sm", "grid", "kp", "smax", "split_exp_x3"), out.tolist()))
+        return dict(zip(("warps_per_cta", "ctas_per_sm", "grid", "kp", "smax", "split_exp_x3", "rows_per_thread"),
+                        out.tolist()))
 
     def set_wait_limit(self, wait_ns):
         """iccg_batch_set_wait_limit: barrier wait limit (ns); 0 = default."""

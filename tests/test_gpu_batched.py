@@ -55,7 +55,8 @@ def _refs(systems, key):
 SMALL = dict(sides=[5, 9, 12, 7, 10], shifts=[1e-3, 1e-2, 1e-4, 5e-2, 0.0], nrhs=3, block=8, seed=3)
 
 
-@pytest.mark.parametrize("shape", [dict(), dict(warps_per_cta=4, ctas_per_sm=1), dict(warps_per_cta=16)])
+@pytest.mark.parametrize("shape", [dict(), dict(warps_per_cta=4, ctas_per_sm=1), dict(warps_per_cta=16),
+                                   dict(rows_per_thread=2), dict(rows_per_thread=4, warps_per_cta=4)])
 def test_batched_fp64_matches_oracle(shape):
     systems = _batch(**SMALL)
     refs = _refs(systems, "small")
@@ -128,6 +129,7 @@ def test_batched_device_buffers_and_autotune():
     bs = iccg.BatchSolver(solvers, 16, autotune=True)
     info = bs.info()
     assert info["kp"] == 16 and info["warps_per_cta"] in (4, 8, 16) and info["grid"] >= 3
+    assert info["rows_per_thread"] in (1, 2, 4)
     B = [torch.tensor(b, device="cuda") for _, _, b in systems]
     X = [torch.zeros_like(b) for b in B]
     st, it, stv, _ = bs.solve(B, X, 1e-8, 5000)
