@@ -1694,10 +1694,17 @@ struct FacSmem {
 };
 
 // STAGE: pairs per pass
+// The row's static data (its record, pair indices and positions, columns,
+// a_ij, pair ends) is read before griddepcontrol.wait, i.e. while the
+// previous level's launch still runs; 1/L_jj and the pair values L_jk after.
 template <int STAGE>
 __device__ __forceinline__ void factor_row_pairs(const Params &P, int4 rec, const FacSmem &m) {
   const int i = rec.x, rb = rec.y, q0 = rec.z, ni = rec.w & 0xff, np = rec.w >> 8;
-  if (ni > kFacRow) { factor_row_merge(P, i); return; }
+  if (ni > kFacRow) {
+    pdl_wait();
+    factor_row_merge(P, i);
+    return;
+  }
   // the first pass's pair indices and position words, before anything else
   const uint32_t *posw = reinterpret_cast<const uint32_t *>(P.fp_pos);
   {
@@ -1714,9 +1721,12 @@ __device__ __forceinline__ void factor_row_pairs(const Params &P, int4 rec, cons
     for (int p = 0; p < kFacRow; ++p)
       if (p < ni) {
         m.sv[p] = __ldg(P.ainit + rb + p);
-        m.ivj[p] = __ldcg(P.invd + col[p]);
         m.qe[p] = __ldg(P.fp_ptr + rb + p + 1) - q0;
       }
+    pdl_wait();
+#pragma unroll
+    for (int p = 0; p < kFacRow; ++p)
+      if (p < ni) m.ivj[p] = __ldcg(P.invd + col[p]);
   }
   double d = P.adiag[i];
   int p = 0;
@@ -1777,6 +1787,7 @@ constexpr int kFacSmem = kFacRowThreads * (kFacRow * 20 + kFacStage * 12 + kFacP
 // the rows of one in-block level of a lane-tile or warp-unit color, one row
 // per thread (dynamic shared memory, thread-interleaved)
 __global__ void __launch_bounds__(kFacRowThreads) factor_rows_kernel(Params P, int k0, int k1) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char fsm[];
   const int t = threadIdx.x;
   constexpr int T = kFacRowThreads;
@@ -1794,8 +1805,12 @@ __global__ void __launch_bounds__(kFacRowThreads) factor_rows_kernel(Params P, i
   q += size_t(T) * kFacStage * 4;
   m.pw.base = reinterpret_cast<uint32_t *>(q) + t;
   for (int k = k0 + int(blockIdx.x * blockDim.x + threadIdx.x); k < k1; k += int(gridDim.x * blockDim.x)) {
-    if (P.fac_rec) factor_row_pairs<kFacStage>(P, __ldg(P.fac_rec + k), m);
-    else factor_row_merge(P, __ldg(P.fac_rows + k));
+    if (P.fac_rec) {
+      factor_row_pairs<kFacStage>(P, __ldg(P.fac_rec + k), m);
+    } else {
+      pdl_wait();
+      factor_row_merge(P, __ldg(P.fac_rows + k));
+    }
   }
 }
 
@@ -1803,6 +1818,8 @@ __global__ void __launch_bounds__(kFacRowThreads) factor_rows_kernel(Params P, i
 // the general form (short merges), no staging, full CTAs
 constexpr int kFacShort = 8;
 __global__ void __launch_bounds__(kVecThreads) factor_short_kernel(Params P, int k0, int k1) {
+  pdl_trigger();
+  pdl_wait();
   for (int k = k0 + int(blockIdx.x * blockDim.x + threadIdx.x); k < k1; k += int(gridDim.x * blockDim.x))
     factor_row_merge(P, __ldg(P.fac_rows + k));
 }
@@ -2692,14 +2709,16 @@ cudaError_t launch_factor(const Params &P, const Plan &L, int nL) {
       // lane-tile and warp-unit colors: one launch per in-block level, a thread per row
       for (int v = 0; v < L.fac_nlev[c]; ++v) {
         const int k0 = L.fac_ptr[size_t(L.fac_lev0[c] + v)], k1 = L.fac_ptr[size_t(L.fac_lev0[c] + v + 1)];
+        // consecutive levels overlap through programmatic dependent launch:
+        // a level's static loads run while the previous level finishes
+        cudaError_t e;
         if (L.fac_wide[size_t(L.fac_lev0[c] + v)] <= kFacShort) {
           const int grid = std::max(1, std::min((k1 - k0 + kVecThreads - 1) / kVecThreads, L.grid_v));
-          factor_short_kernel<<<grid, kVecThreads, 0, L.stream>>>(P, k0, k1);
+          e = launch(factor_short_kernel, grid, kVecThreads, 0, L, P, k0, k1);
         } else {
           const int grid = std::max(1, std::min((k1 - k0 + kFacRowThreads - 1) / kFacRowThreads, 8 * L.grid_v));
-          factor_rows_kernel<<<grid, kFacRowThreads, kFacSmem, L.stream>>>(P, k0, k1);
+          e = launch(factor_rows_kernel, grid, kFacRowThreads, kFacSmem, L, P, k0, k1);
         }
-        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }
     } else {
