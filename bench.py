@@ -232,18 +232,21 @@ def hbm_peak():
     return float(peaks.get("hbm_gbs", 6800.0)), ("measured" if "hbm_gbs" in peaks else "fallback")
 
 
-def time_steps(step, steps, stream):
-    """Device time per step (CUDA events on the launching stream)."""
+def time_steps(step, steps, stream, per_step=None):
+    """Device time per step (CUDA events on the launching stream; an event
+    after every step, so `per_step`, when a list, receives each step's ms)."""
     import torch
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     torch.cuda.synchronize()
-    ev0.record(stream)
+    evs[0].record(stream)
     out = None
-    for _ in range(steps):
+    for k in range(steps):
         out = step()
-    ev1.record(stream)
+        evs[k + 1].record(stream)
     torch.cuda.synchronize()
-    return ev0.elapsed_time(ev1) / steps, out
+    if per_step is not None:
+        per_step.extend(evs[k].elapsed_time(evs[k + 1]) for k in range(steps))
+    return evs[0].elapsed_time(evs[steps]) / steps, out
 
 
 def run_gpu(args):
@@ -287,8 +290,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    step_ms = []
     with ClockSampler(local) as clk:
-        ms, (st, iters, _) = time_steps(step, args.steps, stream)
+        ms, (st, iters, _) = time_steps(step, args.steps, stream, step_ms)
     if world > 1:
         ms = max_over_ranks(ms, dev)
 
@@ -340,6 +344,7 @@ def run_gpu(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": round(ms, 4),
+        "ms_std": round(statistics.pstdev(step_ms), 4) if len(step_ms) > 1 else 0.0,
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
