@@ -535,8 +535,12 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
           const int32_t so = int32_t((pass ? H.wu_src : H.wl_src).size());
           std::vector<int32_t> &mp = pass ? H.wu_map : H.wl_map, &sr = pass ? H.wu_srow : H.wl_srow;
           std::vector<uint32_t> &swd = pass ? H.wu_src : H.wl_src, &mk = pass ? H.wu_mask : H.wl_mask;
-          mp.resize(size_t(co) + size_t(M) * kWarp, -1);
-          sr.resize(size_t(co) + size_t(M) * kWarp, -1);
+          // coefficients term-major: lane l's j-th term (in step order) at
+          // co + j * 32 + l, the block as deep as the lane with most terms
+          size_t T = 0;
+          for (int l = 0; l < kWarp; ++l) T = std::max(T, sched[size_t(l)].size());
+          mp.resize(size_t(co) + T * kWarp, -1);
+          sr.resize(size_t(co) + T * kWarp, -1);
           const int32_t nw = (M + 3) / 4;
           swd.resize(size_t(so) + size_t(nw) * kWarp, 0u);
           for (int l = 0; l < kWarp; ++l) {
@@ -545,11 +549,13 @@ iccg_status build_layout(int32_t n, int64_t nnz, const int64_t *rowptr, const in
               const size_t w = size_t(so) + size_t(m / 4) * kWarp + size_t(l);
               swd[w] |= uint32_t(l) << (8 * (m % 4));
             }
+            size_t j = 0;
             for (const auto &pr : sched[size_t(l)]) {
               const int32_t m = pr.first, x = pr.second;
               mask |= 1u << m;
-              mp[size_t(co) + size_t(m) * kWarp + size_t(l)] = tmap[size_t(l)][size_t(x)];
-              sr[size_t(co) + size_t(m) * kWarp + size_t(l)] = trow[size_t(l)][size_t(x)];
+              mp[size_t(co) + j * kWarp + size_t(l)] = tmap[size_t(l)][size_t(x)];
+              sr[size_t(co) + j * kWarp + size_t(l)] = trow[size_t(l)][size_t(x)];
+              ++j;
               const size_t w = size_t(so) + size_t(m / 4) * kWarp + size_t(l);
               swd[w] = (swd[w] & ~(0xffu << (8 * (m % 4)))) | (uint32_t(tsrc[size_t(l)][size_t(x)]) << (8 * (m % 4)));
             }
@@ -905,10 +911,14 @@ extern "C" iccg_status iccg_check_layout(int32_t n, int64_t nnz, const int64_t *
             if (cols[size_t(e)] >= H.block_ptr[size_t(b)] && cols[size_t(e)] < H.block_ptr[size_t(b) + 1])
               want.push_back(pass ? H.umap[size_t(e)] : e);
           std::vector<int32_t> got;
+          int32_t j = 0;
           for (int k = 0; k < M; ++k) {
-            const size_t e = size_t(off) + size_t(k) * kWarp + size_t(l);
             const uint32_t src = (swd[size_t(so) + size_t(k / 4) * kWarp + size_t(l)] >> (8 * (k % 4))) & 0xffu;
-            if (!((m >> k) & 1u)) { ck(mp[e] == -1, t, "chain padding"); continue; }
+            if (!((m >> k) & 1u)) continue;
+            // the lane's terms are stored term-major: its j-th term at off + j * 32 + l
+            const size_t e = size_t(off) + size_t(j++) * kWarp + size_t(l);
+            ck(e < mp.size(), t, "chain term slot");
+            if (e >= mp.size()) break;
             got.push_back(mp[e]);
             const int32_t srow = H.block_ptr[size_t(b)] + int32_t(src) % S;
             ck(int32_t(src) / S == l / S && sr[e] == srow && (pass ? srow > i : srow < i), t, "chain source");

@@ -1263,8 +1263,11 @@ __device__ __forceinline__ PT unit_ext(const int32_t *col, const PT *val, int e,
 template <typename PT, int S>
 __device__ __forceinline__ void unit_coef(const PT *v, const uint32_t *sw, int off, int soff, int M, uint32_t mask,
                                           int lane, PT (&cf)[S], uint32_t (&src)[(S + 3) / 4]) {
+  // the lane's terms are stored term-major (its j-th term at off + j * 32 +
+  // lane): the term of step k is number popc(mask below k)
 #pragma unroll
-  for (int k = 0; k < S; ++k) cf[k] = ((mask >> k) & 1u) ? __ldg(v + off + k * kWarp + lane) : PT(0);
+  for (int k = 0; k < S; ++k)
+    cf[k] = ((mask >> k) & 1u) ? __ldg(v + off + __popc(mask & ((1u << k) - 1u)) * kWarp + lane) : PT(0);
 #pragma unroll
   for (int w = 0; w < (S + 3) / 4; ++w) src[w] = 4 * w < M ? __ldg(sw + soff + w * kWarp + lane) : 0u;
 }
@@ -1288,7 +1291,8 @@ __device__ __forceinline__ void unit_coef_smem(const PT *v, const uint32_t *sw, 
                                                uint32_t mask, int lane, PT *cfs, uint32_t (&src)[(S + 3) / 4]) {
 #pragma unroll
   for (int k = 0; k < S; ++k)
-    if ((mask >> k) & 1u) cp_async_elem<PT>(cfs + k * kWarp + lane, v + off + k * kWarp + lane);
+    if ((mask >> k) & 1u)
+      cp_async_elem<PT>(cfs + k * kWarp + lane, v + off + __popc(mask & ((1u << k) - 1u)) * kWarp + lane);
   asm volatile("cp.async.commit_group;" ::: "memory");
 #pragma unroll
   for (int w = 0; w < (S + 3) / 4; ++w) src[w] = 4 * w < M ? __ldg(sw + soff + w * kWarp + lane) : 0u;
