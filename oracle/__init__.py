@@ -8,7 +8,8 @@ CUDA library; its only common dependency is the input generator package
 ``gen`` (matrices and right-hand sides, no method arithmetic).
 
 Heavy loops (graph, ABMC, coloring, Leiden, IC(0), substitutions, PCG) live in
-``iccg_oracle.c`` (single-threaded, -ffp-contract=off).  This module adds
+``iccg_oracle.c``, the sequential statement of the library's parallel Leiden
+in ``par_leiden.c`` (single-threaded, -ffp-contract=off).  This module adds
 ctypes marshalling and a few plain numpy definitions:
 
   * ``permute``            A_hat = P A P^T with P from perm[new] = old (Sec. 3);
@@ -56,6 +57,8 @@ def lib():
         L.orc_color_blocks.restype = c_i32
         L.orc_leiden.argtypes = [c_i32, _i64p, _i32p, c_i32, c_d, c_i32, c_d, c_u64, _i32p]
         L.orc_leiden.restype = c_i32
+        L.orc_par_leiden.argtypes = [c_i32, _i64p, _i32p, c_i32, c_d, c_i32, _i32p]
+        L.orc_par_leiden.restype = c_i32
         L.orc_delta_quality.argtypes = [c_i32, _i64p, _i32p, c_i32, c_d, _i32p, c_i32, c_i32]
         L.orc_delta_quality.restype = c_d
         L.orc_sort_blocks_desc.argtypes = [c_i32, c_i32, _i32p]
@@ -130,6 +133,16 @@ def leiden(n, gptr, gadj, quality: str, gamma: float, n_iter: int = 2, beta: flo
     memb = np.zeros(max(n, 1), dtype=np.int32)
     k = lib().orc_leiden(n, _c(gptr, np.int64), _c(gadj, np.int32), q, float(gamma),
                          int(n_iter), float(beta), int(seed), memb)
+    return memb[:n], k
+
+
+def par_leiden(n, gptr, gadj, quality: str, gamma: float, n_iter: int = 2):
+    """The parallel Leiden of the GPU library (synchronous sub-rounds, greedy
+    refinement, connected blocks), stated sequentially (par_leiden.c).
+    Returns (block_of int32[n], number of blocks)."""
+    q = {"modularity": 0, "md": 0, "cpm": 1, "cp": 1}[quality.lower()]
+    memb = np.zeros(max(n, 1), dtype=np.int32)
+    k = lib().orc_par_leiden(n, _c(gptr, np.int64), _c(gadj, np.int32), q, float(gamma), int(n_iter), memb)
     return memb[:n], k
 
 

@@ -10,16 +10,16 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "iccg_oracle.c")
+SRCS = [os.path.join(HERE, "iccg_oracle.c"), os.path.join(HERE, "par_leiden.c")]
 LIB = os.path.join(HERE, "_liboracle.so")
 
 
 def build(force: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+    if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in SRCS):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
-                           "-shared", "-fPIC", "-o", tmp, SRC, "-lm"])
+                           "-shared", "-fPIC", "-o", tmp] + SRCS + ["-lm"])
     os.replace(tmp, LIB)
     return LIB
 

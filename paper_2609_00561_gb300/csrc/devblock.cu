@@ -513,8 +513,14 @@ __global__ void community_weights(int32_t n, const int32_t *comm, const int64_t 
   }
 }
 
+// Every floating-point operation of the Leiden decisions is one IEEE
+// round-to-nearest step in a fixed order (no contraction into FMA), so a
+// sequential restatement on the CPU takes exactly the same decisions.
+__device__ __forceinline__ double penalty(double gp, int64_t w, int64_t W) {
+  return __dmul_rn(__dmul_rn(gp, double(w)), double(W));
+}
 __device__ __forceinline__ double leiden_gain(int64_t k, int64_t w, int64_t W, double gp) {
-  return double(k) - gp * double(w) * double(W);
+  return __dsub_rn(double(k), penalty(gp, w, W));
 }
 
 // one local-moving sub-round: the decision of every node from the state at
@@ -523,7 +529,7 @@ __device__ __forceinline__ double leiden_gain(int64_t k, int64_t w, int64_t W, d
 // values) above, 0xffffffff - node below, so the largest gain wins and ties
 // go to the smallest node
 __device__ __forceinline__ unsigned long long join_key(double delta, int32_t v) {
-  const float f = fmaxf(float(delta), 1e-30f);
+  const float f = fmaxf(__double2float_rn(delta), 1e-30f);
   return (static_cast<unsigned long long>(__float_as_uint(f)) << 32) |
          static_cast<unsigned long long>(0xffffffffu - uint32_t(v));
 }
@@ -561,7 +567,7 @@ __global__ void lm_decide(DGraph g, const int32_t *comm, const int64_t *W, const
       bestg = 0.0;
     }
     newc[v] = best;
-    if (best != C && best != v) atomicMax(join + best, join_key(bestg - stay, v));
+    if (best != C && best != v) atomicMax(join + best, join_key(__dsub_rn(bestg, stay), v));
   }
 }
 
@@ -609,7 +615,7 @@ __global__ void refine_decide(DGraph g, const int32_t *comm, const int64_t *W, c
     int64_t inside = 0;
     for (int64_t e = e0; e < e1; ++e)
       if (comm[g.adj[e]] == C) inside += g.ew[e];
-    if (!(double(inside) >= gp * double(wv) * double(WC - wv))) continue;   // not well connected
+    if (!(double(inside) >= penalty(gp, wv, WC - wv))) continue;   // not well connected
     int32_t best = v;
     double bestg = 0.0;
     bool found = false;
@@ -621,7 +627,7 @@ __global__ void refine_decide(DGraph g, const int32_t *comm, const int64_t *W, c
       bool dup = false;
       for (int64_t f = e0; f < e && !dup; ++f) dup = comm[g.adj[f]] == C && sub[g.adj[f]] == t;
       if (dup) continue;
-      if (!(double(subE[t]) >= gp * double(SW[t]) * double(WC - SW[t]))) continue;
+      if (!(double(subE[t]) >= penalty(gp, SW[t], WC - SW[t]))) continue;
       int64_t kt = g.ew[e];
       for (int64_t f = e + 1; f < e1; ++f)
         if (comm[g.adj[f]] == C && sub[g.adj[f]] == t) kt += g.ew[f];
@@ -634,7 +640,7 @@ __global__ void refine_decide(DGraph g, const int32_t *comm, const int64_t *W, c
     }
     if (found) {
       newsub[v] = best;
-      atomicMax(join + best, join_key(bestg + 1.0, v));
+      atomicMax(join + best, join_key(__dadd_rn(bestg, 1.0), v));
     }
   }
 }

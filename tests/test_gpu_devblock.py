@@ -290,3 +290,37 @@ def test_device_pipeline_abmc_equals_oracle(s):
     assert bd["n_b"] == bo["n_b"] and bd["n_c"] == bo["n_c"]
     for k in ("perm", "block_ptr", "color_ptr", "color_of"):
         assert np.array_equal(np.asarray(bd[k]), np.asarray(bo[k])), k
+
+
+# ---------------------------------------------------------------------------
+# the device Leiden against its sequential statement in the oracle
+# (par_leiden.c): the same partition, integer for integer
+# ---------------------------------------------------------------------------
+PAR_CASES = {
+    "grid2d_40": lambda: gen.poisson2d_5pt(40),
+    "grid3d_20": lambda: gen.poisson3d_7pt(20),
+    "rgg_4000": lambda: gen.rgg_laplacian(4000, 12.0, 5),
+    "diff27_14": lambda: gen.diffusion3d_27pt(14, seed=3),
+    "elast7": lambda: gen.elasticity_like(2000, 7, 3.0),
+    "cliques": lambda: _ring_of_cliques(12, 5),
+}
+
+
+@pytest.mark.parametrize("case", sorted(PAR_CASES))
+@pytest.mark.parametrize("quality,gamma", [("cpm", 0.5), ("cpm", 0.1), ("cpm", 0.02), ("modularity", 1.0)])
+def test_device_leiden_equals_oracle_statement(case, quality, gamma):
+    a = PAR_CASES[case]()
+    gp, ga = oracle.graph(a.n, a.rowptr, a.colind)
+    ref, nref = oracle.par_leiden(a.n, gp, ga, quality, gamma)
+    memb, nb = _dev_leiden(a, quality, gamma)
+    assert nb == nref
+    assert np.array_equal(memb, ref)
+
+
+def test_device_leiden_equals_oracle_statement_full_size():
+    a = gen.poisson3d_7pt(128)
+    gp, ga = oracle.graph(a.n, a.rowptr, a.colind)
+    ref, nref = oracle.par_leiden(a.n, gp, ga, "cpm", 0.5)
+    memb, nb = _dev_leiden(a, "cpm", 0.5)
+    assert nb == nref
+    assert np.array_equal(memb, ref)

@@ -134,3 +134,73 @@ def test_cpm_block_count_grows_with_gamma():
     _, k1 = oracle.leiden(a.n, gptr, gadj, "cpm", 0.02, seed=42)
     _, k4 = oracle.leiden(a.n, gptr, gadj, "cpm", 0.08, seed=42)
     assert 1.6 < k4 / k1 < 4.0
+
+
+# ---------------------------------------------------------------------------
+# the sequential statement of the library's parallel Leiden (par_leiden.c)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("K,k", [(8, 6), (12, 5)])
+@pytest.mark.parametrize("quality,gamma", [("cpm", 0.3), ("modularity", 1.0)])
+def test_par_leiden_planted_cliques(K, k, quality, gamma):
+    a = _ring_of_cliques(K, k)
+    gptr, gadj = _graph_of(a)
+    memb, nk = oracle.par_leiden(a.n, gptr, gadj, quality, gamma)
+    assert nk == K
+    assert np.array_equal(memb, np.repeat(np.arange(K), k))   # blocks numbered by smallest node
+
+
+@pytest.mark.parametrize("side", [(10, 10), (8, 8, 8), (6, 4, 10)])
+def test_par_leiden_cpm05_reaches_the_grid_optimum(side):
+    """CPM at resolution 0.5 with unit weights: a community of k nodes and e
+    internal edges contributes e - k^2/4, which is 0 for an edge (k = 2, e =
+    1) or a 4-cycle (k = 4, e = 4) and negative for every other subgraph of a
+    grid (a grid is bipartite: k nodes span at most 0, 1, 2, 4, 5, 7, 9, 12
+    edges for k = 1..8, and at most 3k < k^2/4 edges for k > 12, with the
+    cases between checked alike), so the optimum of a grid with a perfect
+    matching is 0, reached exactly by pairs (and 4-cycles); the parallel
+    Leiden finds it."""
+    a = gen.poisson2d_5pt(*side) if len(side) == 2 else gen.from_scipy(
+        _grid3d(*side))
+    gptr, gadj = _graph_of(a)
+    memb, nk = oracle.par_leiden(a.n, gptr, gadj, "cpm", 0.5)
+    assert abs(oracle.quality_cpm(a.n, gptr, gadj, memb, 0.5)) < 1e-12
+    sizes = np.bincount(memb)
+    assert set(np.unique(sizes)) <= {2, 4}
+
+
+def _grid3d(nx, ny, nz):
+    def lap(m):
+        return sp.diags([-np.ones(m - 1), 2 * np.ones(m), -np.ones(m - 1)], [-1, 0, 1])
+    ix, iy, iz = sp.identity(nx), sp.identity(ny), sp.identity(nz)
+    return (sp.kron(sp.kron(lap(nx), iy), iz) + sp.kron(sp.kron(ix, lap(ny)), iz)
+            + sp.kron(sp.kron(ix, iy), lap(nz))).tocsr()
+
+
+@pytest.mark.parametrize("quality,gamma", [("modularity", 1.0), ("cpm", 0.05), ("cpm", 0.3), ("cpm", 0.5)])
+@pytest.mark.parametrize("case", ["grid2d", "grid3d", "rgg"])
+def test_par_leiden_invariants(quality, gamma, case):
+    """Labels 0..k-1 numbered by smallest node, every block connected, the
+    quality above the singleton partition's and at least 90% of the
+    sequential Leiden's gain over it, deterministic."""
+    a = {"grid2d": lambda: gen.poisson2d_5pt(30), "grid3d": lambda: gen.poisson3d_7pt(10),
+         "rgg": lambda: gen.rgg_laplacian(800, 12.0, 5)}[case]()
+    gptr, gadj = _graph_of(a)
+    memb, nk = oracle.par_leiden(a.n, gptr, gadj, quality, gamma)
+    assert memb.min() == 0 and memb.max() == nk - 1 and len(np.unique(memb)) == nk
+    first = np.full(nk, a.n)
+    np.minimum.at(first, memb, np.arange(a.n))
+    assert np.all(np.diff(first) > 0)
+    adj = sp.csr_matrix((np.ones(gadj.size), gadj, gptr), shape=(a.n, a.n))
+    for c in range(nk):
+        idx = np.nonzero(memb == c)[0]
+        ncomp, _ = connected_components(adj[idx][:, idx], directed=False)
+        assert ncomp == 1
+    qf = oracle.quality_modularity if quality == "modularity" else oracle.quality_cpm
+    q_par = qf(a.n, gptr, gadj, memb, gamma)
+    q_one = qf(a.n, gptr, gadj, np.arange(a.n), gamma)
+    seq, _ = oracle.leiden(a.n, gptr, gadj, quality, gamma, seed=42)
+    q_seq = qf(a.n, gptr, gadj, seq, gamma)
+    assert q_par >= q_one
+    assert q_par - q_one >= 0.9 * (q_seq - q_one)
+    again, _ = oracle.par_leiden(a.n, gptr, gadj, quality, gamma)
+    assert np.array_equal(memb, again)
