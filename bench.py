@@ -183,6 +183,21 @@ def make_blocking(mod, a, args):
         bl = mod.blocking(a, "abmc", args.block_size)
     elif args.blocking == "levels":
         bl = mod.blocking(a, "levels")
+    elif args.blocking.endswith("_par"):
+        # the parallel Leiden: on the device in the GPU arm, its sequential
+        # statement in the oracle for the reference arm (the same partition)
+        method = args.blocking[:-4]
+        if hasattr(mod, "dev_blocking"):
+            bl = mod.dev_blocking(a, method, args.gamma)
+        else:
+            q = "cpm" if method == "leiden_cpm" else "modularity"
+            gptr, gadj = mod.graph(a.n, a.rowptr, a.colind)
+            raw, nb = mod.par_leiden(a.n, gptr, gadj, q, args.gamma)
+            block_of = mod.sort_blocks_desc(a.n, nb, raw)
+            color_of, nc = mod.color_blocks(a.n, gptr, gadj, nb, block_of)
+            perm, bptr, cptr = mod.order(a.n, nb, nc, block_of, color_of)
+            bl = {"perm": perm, "block_ptr": bptr, "color_ptr": cptr, "n_b": nb, "n_c": nc,
+                  "block_of": block_of, "color_of": color_of}
     else:
         bl = mod.blocking(a, args.blocking, gamma=args.gamma)
     if args.split_levels:
@@ -204,6 +219,10 @@ def _blocking_name(args):
         return "level sets of the natural order (level scheduling, a color per level)"
     if args.blocking == "leiden_cpm":
         return f"Leiden CPM resolution {args.gamma:g}"
+    if args.blocking == "leiden_cpm_par":
+        return f"parallel Leiden CPM resolution {args.gamma:g}"
+    if args.blocking == "leiden_md_par":
+        return f"parallel Leiden modularity resolution {args.gamma:g}"
     return f"Leiden modularity resolution {args.gamma:g}"
 
 
@@ -809,7 +828,8 @@ def main():
     p.add_argument("--workload", default="poisson128", choices=sorted(WORKLOADS))
     p.add_argument("--nx", type=int, default=None, help="grid side (default 128, or 96 for diffusion96)")
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--blocking", default=None, choices=["abmc", "leiden_cpm", "leiden_md", "levels"],
+    p.add_argument("--blocking", default=None,
+                   choices=["abmc", "leiden_cpm", "leiden_md", "leiden_cpm_par", "leiden_md_par", "levels"],
                    help="default: leiden_cpm for poisson128, abmc otherwise")
     p.add_argument("--gamma", type=float, default=0.5, help="Leiden resolution (CPM threshold or modularity gamma)")
     p.add_argument("--split-levels", type=int, default=0,

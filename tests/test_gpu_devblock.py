@@ -324,3 +324,22 @@ def test_device_leiden_equals_oracle_statement_full_size():
     memb, nb = _dev_leiden(a, "cpm", 0.5)
     assert nb == nref
     assert np.array_equal(memb, ref)
+
+
+@pytest.mark.parametrize("method,gamma", [("leiden_cpm", 0.5), ("leiden_cpm", 0.05), ("leiden_md", 1.0)])
+def test_device_pipeline_parallel_leiden_equals_oracle(method, gamma):
+    """The whole device blocking pipeline with the parallel Leiden (graph,
+    Leiden, size order, coloring, ordering) gives the ordering of the
+    oracle's pipeline with its sequential statement of that Leiden (the
+    reference arm of bench.py for the *_par blockings)."""
+    a = gen.diffusion3d_27pt(14, seed=2) if method == "leiden_md" else gen.poisson3d_7pt(24)
+    bd = iccg.dev_blocking(a, method, gamma)
+    gp, ga = oracle.graph(a.n, a.rowptr, a.colind)
+    raw, nb = oracle.par_leiden(a.n, gp, ga, "cpm" if method == "leiden_cpm" else "modularity", gamma)
+    block_of = oracle.sort_blocks_desc(a.n, nb, raw)
+    color_of, nc = oracle.color_blocks(a.n, gp, ga, nb, block_of)
+    perm, bptr, cptr = oracle.order(a.n, nb, nc, block_of, color_of)
+    assert bd["n_b"] == nb and bd["n_c"] == nc
+    assert np.array_equal(bd["perm"], perm)
+    assert np.array_equal(bd["block_ptr"], bptr)
+    assert np.array_equal(bd["color_ptr"], cptr)
