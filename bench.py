@@ -2,8 +2,11 @@
 problem (128^3, n = 2,097,152, 14.58M nonzeros, b ~ U[-1,1] from seed 0) with
 Leiden CPM blocking (resolution 0.5) and greedy block coloring: the fastest
 blocking on a GB300 of the swept set (ABMC block sizes 8..128, Leiden
-modularity, CPM resolutions 0.01..0.5); `--blocking abmc --block-size S`
-selects another.
+modularity, CPM resolutions 0.01..0.5).  The default computes the Leiden
+blocking on the device with the library's parallel Leiden (the reference arm
+computes the same partition with the oracle's sequential statement of it);
+`--blocking leiden_cpm` takes the sequential Leiden of the host instead, and
+`--blocking abmc --block-size S` an ABMC blocking.
 `--workload diffusion96 --fp32` runs the 27-point variable-coefficient
 diffusion problem (96^3, ABMC 32) with the FP32 preconditioner (extension 1).
 `--workload batch64` runs the batched extension: 64 shifted 7-point systems
@@ -414,6 +417,8 @@ def run_gpu(args):
     S.close()
     if not args.no_ext and world == 1 and args.blocking in ("leiden_cpm", "leiden_md") and not args.split_levels:
         result["ext_device_blocking"] = ext_device_blocking(args, a, b, ms, iters, stream, dev)
+    if not args.no_ext and world == 1 and args.blocking in ("leiden_cpm_par", "leiden_md_par"):
+        result["ext_sequential_leiden"] = ext_sequential_leiden(args, a, b, ms, iters, t_block, stream, dev)
     if not args.no_ext and world == 1 and args.workload == "poisson128":
         result["ext_batched"] = ext_batched(args, stream, dev)
     if world > 1:
@@ -454,6 +459,38 @@ def ext_device_blocking(args, a, b, ms_host, it_host, stream, dev):
             "true_relres": float(np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)),
             "vs_host_blocking": {"ms_per_step": round(ms_host, 4), "iterations": it_host},
             "how": "wall time of the device pipeline (synchronised), second call"}
+
+
+def ext_sequential_leiden(args, a, b, ms_par, it_par, t_par, stream, dev):
+    """The same resolution with the sequential Leiden on the host (the
+    published algorithm's order: random visiting queue, randomized
+    refinement): its blocking time and the step with its blocking, next to
+    the parallel Leiden's."""
+    import torch
+    from paper_2609_00561_gb300 import iccg
+    method = args.blocking[:-4]
+    t0 = time.perf_counter()
+    bl = iccg.blocking(a, method, gamma=args.gamma)
+    t_host = time.perf_counter() - t0
+    S = iccg.Solver(a, bl, stream=stream.cuda_stream, factor=False)
+    bd = torch.tensor(b, device=dev)
+    xd = torch.zeros_like(bd)
+
+    def step():
+        iccg.iccg_factor(S.ctx)
+        xd.zero_()
+        return iccg.iccg_solve(S.ctx, bd, xd, args.tol, args.maxit, want_hist=False)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    ms, (st, it, _) = time_steps(step, args.steps, stream)
+    x = xd.cpu().numpy()
+    S.close()
+    return {"blocking_s": round(t_host, 3), "n_b": int(bl["n_b"]), "n_c": int(bl["n_c"]),
+            "ms_per_step": round(ms, 4), "iterations": it, "status": iccg.STATUS.get(st, st),
+            "true_relres": float(np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)),
+            "vs_parallel_leiden": {"ms_per_step": round(ms_par, 4), "iterations": it_par,
+                                   "blocking_s": round(t_par, 3)}}
 
 
 def ext_fp32(args, a, b, bl, x64, ms64, stream, dev):
@@ -830,7 +867,7 @@ def main():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--blocking", default=None,
                    choices=["abmc", "leiden_cpm", "leiden_md", "leiden_cpm_par", "leiden_md_par", "levels"],
-                   help="default: leiden_cpm for poisson128, abmc otherwise")
+                   help="default: leiden_cpm_par for poisson128, abmc otherwise")
     p.add_argument("--gamma", type=float, default=0.5, help="Leiden resolution (CPM threshold or modularity gamma)")
     p.add_argument("--split-levels", type=int, default=0,
                    help="split blocks above this many rows into in-block levels (0: no)")
@@ -860,7 +897,7 @@ def main():
     if args.block_size is None:
         args.block_size = 32 if args.workload in ("diffusion96", "batch64") else 8
     if args.blocking is None:
-        args.blocking = "leiden_cpm" if args.workload == "poisson128" else "abmc"
+        args.blocking = "leiden_cpm_par" if args.workload == "poisson128" else "abmc"
     if args.steps < 1 or args.warmup < 0:
         raise SystemExit("steps >= 1, warmup >= 0")
     if args.impl == "reference":

@@ -1,6 +1,7 @@
 """GPU parity at the benchmark's full size: the 128^3 7-point Poisson problem
 (n = 2,097,152, nnz = 14,581,760, b ~ U[-1, 1] seed 0) in the layout bench.py
-times (Leiden CPM resolution 0.5 + greedy coloring, automatic tile mapping),
+times (the parallel Leiden at CPM resolution 0.5 on the device + greedy
+coloring, automatic tile mapping), with the sequential Leiden CPM 0.5 blocking
 and with ABMC s = 8.
 
   * blockings: the library's permutation, block and color pointers equal the
@@ -27,7 +28,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-LAYOUTS = {"cpm05": ("leiden_cpm", {"gamma": 0.5}), "abmc8": ("abmc", {"block_size": 8})}
+LAYOUTS = {"cpm05": ("leiden_cpm", {"gamma": 0.5}), "abmc8": ("abmc", {"block_size": 8}),
+           "cpm05par": ("leiden_cpm_par", {"gamma": 0.5})}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -44,18 +46,41 @@ def problem():
 _bl = {}
 
 
+def _oracle_par_blocking(a, gamma):
+    """The oracle's pipeline around its sequential statement of the parallel
+    Leiden (the bench default's blocking)."""
+    gp, ga = oracle.graph(a.n, a.rowptr, a.colind)
+    raw, nb = oracle.par_leiden(a.n, gp, ga, "cpm", gamma)
+    block_of = oracle.sort_blocks_desc(a.n, nb, raw)
+    color_of, nc = oracle.color_blocks(a.n, gp, ga, nb, block_of)
+    perm, bptr, cptr = oracle.order(a.n, nb, nc, block_of, color_of)
+    return {"perm": perm, "block_ptr": bptr, "color_ptr": cptr, "n_b": nb, "n_c": nc}
+
+
 def _blocking(a, name):
     if name not in _bl:
         method, kw = LAYOUTS[name]
-        _bl[name] = (oracle.blocking(a, method, **kw), iccg.blocking(a, method, **kw))
+        if method == "leiden_cpm_par":
+            _bl[name] = (_oracle_par_blocking(a, kw["gamma"]), iccg.dev_blocking(a, "leiden_cpm", kw["gamma"]))
+        else:
+            _bl[name] = (oracle.blocking(a, method, **kw), iccg.blocking(a, method, **kw))
     return _bl[name]
+
+
+_sol = {}
+
+
+def _oracle_solution(a, b, name):
+    if name not in _sol:
+        bo, _ = _blocking(a, name)
+        _sol[name] = oracle.iccg(a, b, bo["perm"], tol=1e-8, maxit=5000)
+    return _sol[name]
 
 
 @pytest.fixture(scope="module")
 def oracle_solve(problem):
     a, b = problem
-    bo, _ = _blocking(a, "cpm05")
-    return oracle.iccg(a, b, bo["perm"], tol=1e-8, maxit=5000)
+    return _oracle_solution(a, b, "cpm05")
 
 
 @pytest.mark.parametrize("name", sorted(LAYOUTS))
@@ -103,14 +128,15 @@ def test_factor_spmv_precond_at_full_size(problem, name):
     S.close()
 
 
-def test_solve_fp64_matches_oracle_at_full_size(problem, oracle_solve):
+@pytest.mark.parametrize("name", ["cpm05", "cpm05par"])
+def test_solve_fp64_matches_oracle_at_full_size(problem, name):
     a, b = problem
-    _, bl = _blocking(a, "cpm05")
+    _, bl = _blocking(a, name)
     S = iccg.Solver(a, bl)
     x = np.zeros(a.n)
     st, it, hist = iccg.iccg_solve(S.ctx, b, x, 1e-8, 5000)
     S.close()
-    ref = oracle_solve
+    ref = _oracle_solution(a, b, name)
     assert st == iccg.ICCG_OK
     assert abs(it - ref["iterations"]) <= 1, (it, ref["iterations"])
     err = float(np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]))
@@ -119,14 +145,15 @@ def test_solve_fp64_matches_oracle_at_full_size(problem, oracle_solve):
     assert true_rel <= 1e-8
 
 
-def test_solve_fp32_preconditioner_at_full_size(problem, oracle_solve):
+@pytest.mark.parametrize("name", ["cpm05", "cpm05par"])
+def test_solve_fp32_preconditioner_at_full_size(problem, name):
     a, b = problem
-    _, bl = _blocking(a, "cpm05")
+    _, bl = _blocking(a, name)
     S = iccg.Solver(a, bl, precond_fp32=True)
     x = np.zeros(a.n)
     st, it, hist = iccg.iccg_solve(S.ctx, b, x, 1e-8, 5000)
     S.close()
-    ref = oracle_solve
+    ref = _oracle_solution(a, b, name)
     assert st == iccg.ICCG_OK and abs(it - ref["iterations"]) <= 2, (it, ref["iterations"])
     assert np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b) <= 1e-8
     assert np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-6
