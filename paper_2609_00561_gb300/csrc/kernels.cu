@@ -65,6 +65,23 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
+// 4- and 8-byte copies (.ca: cached in L1 as well)
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+template <typename PT>
+__device__ __forceinline__ void cp_async_elem(PT *smem, const PT *gmem);
+template <> __device__ __forceinline__ void cp_async_elem<double>(double *smem, const double *gmem) {
+  cp_async8(smem, gmem);
+}
+template <> __device__ __forceinline__ void cp_async_elem<float>(float *smem, const float *gmem) {
+  cp_async4(smem, gmem);
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 // all but the most recently committed group
@@ -1181,19 +1198,209 @@ __device__ __forceinline__ void pair_tile(const Params &P, int t, int lane, doub
   }
 }
 
+// The pair kernel proper stages each tile's static data ahead of its
+// gathers: the descriptor, the pivots' reciprocals and in-block coefficient
+// in registers, and the first kPairStage entries of each step (the sums over
+// the other colors: lower for the forward sweep, upper for the backward) in
+// the warp's shared-memory buffer by cp.async.  The warp's first tile is
+// staged before griddepcontrol.wait, so these loads overlap the previous
+// launch; after the wait a tile's gathers of both steps and its row vectors
+// are in flight together.  Wider steps take their remaining entries from
+// global memory.
+constexpr int kPairStage = 6;   // a 7-point row has at most 6 entries to other blocks
+
+template <typename PT>
+struct PairStage {
+  int32_t col[2][kPairStage][kWarp];
+  PT val[2][kPairStage][kWarp];
+};
+
+template <typename PT>
+struct PairPre {
+  PairDesc d;
+  PT dv0, dv1, e;   // 1/L_00, 1/L_11 and the in-block coefficient of the sweep
+};
+
+template <typename PT, bool BWD>
+__device__ __forceinline__ PairPre<PT> pair_stage(const Params &P, int t, int lane, PairStage<PT> &s) {
+  PairPre<PT> q;
+  q.d = load_pair(P.pairs + t);
+  const PairDesc &d = q.d;
+  q.dv0 = q.dv1 = q.e = PT(0);
+  if (lane < d.c0) {
+    const bool a1 = lane < d.c1;
+    const PT *dvg = invds<PT>(P);
+    q.dv0 = __ldg(dvg + d.row0 + lane);
+    if (a1) q.dv1 = __ldg(dvg + d.row0 + d.c0 + lane);
+    const int32_t *col = BWD ? P.su_col : P.sl_col;
+    const PT *val = BWD ? suv<PT>(P) : slv<PT>(P);
+    const int b0 = BWD ? d.uo : d.lo, w0 = BWD ? d.uw0 : d.lw0, w1 = BWD ? d.uw1 : d.lw1;
+    const int n0 = min(w0, kPairStage), n1 = a1 ? min(w1, kPairStage) : 0;
+    for (int j = 0; j < n0; ++j) {
+      cp_async4(&s.col[0][j][lane], col + b0 + j * d.c0 + lane);
+      cp_async_elem<PT>(&s.val[0][j][lane], val + b0 + j * d.c0 + lane);
+    }
+    const int b1 = b0 + w0 * d.c0;
+    for (int j = 0; j < n1; ++j) {
+      cp_async4(&s.col[1][j][lane], col + b1 + j * d.c1 + lane);
+      cp_async_elem<PT>(&s.val[1][j][lane], val + b1 + j * d.c1 + lane);
+    }
+    // a block of two rows has at most one in-block entry per row: row 1's
+    // to row 0 forward, row 0's to row 1 backward
+    if (BWD) {
+      if (d.uiw0 > 0) q.e = __ldg(uiv<PT>(P) + d.ui + lane);
+    } else {
+      if (a1 && d.liw1 > 0) q.e = __ldg(siv<PT>(P) + d.li + lane);
+    }
+  }
+  cp_commit();
+  return q;
+}
+
+// the staged sums of both steps: every gather issued before the first
+// multiply-add; entries past kPairStage from global memory
+template <typename PT, bool BWD>
+__device__ __forceinline__ void pair_staged_sums(const Params &P, const PairDesc &d, const PairStage<PT> &s,
+                                                 int lane, bool a1, PT &acc0, PT &acc1) {
+  const PT *g = reinterpret_cast<const PT *>(BWD ? P.z : P.y);
+  const int pad = BWD ? P.n - 1 : 0;
+  const int w0 = BWD ? d.uw0 : d.lw0, w1 = BWD ? d.uw1 : d.lw1;
+  PT g0[kPairStage], g1[kPairStage];
+#pragma unroll
+  for (int j = 0; j < kPairStage; ++j) {
+    g0[j] = PT(0);
+    if (j < w0) {
+      const int c = s.col[0][j][lane];
+      g0[j] = __ldcg(g + (c == kPadCol ? pad : c));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kPairStage; ++j) {
+    g1[j] = PT(0);
+    if (a1 && j < w1) {
+      const int c = s.col[1][j][lane];
+      g1[j] = __ldcg(g + (c == kPadCol ? pad : c));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kPairStage; ++j)
+    if (j < w0) acc0 -= s.val[0][j][lane] * g0[j];
+#pragma unroll
+  for (int j = 0; j < kPairStage; ++j)
+    if (a1 && j < w1) acc1 -= s.val[1][j][lane] * g1[j];
+  if (w0 > kPairStage || w1 > kPairStage) {
+    const int32_t *col = BWD ? P.su_col : P.sl_col;
+    const PT *val = BWD ? suv<PT>(P) : slv<PT>(P);
+    const int b0 = BWD ? d.uo : d.lo, b1 = b0 + w0 * d.c0;
+    for (int j = kPairStage; j < w0; ++j) {
+      const int e = b0 + j * d.c0 + lane, c = __ldg(col + e);
+      acc0 -= __ldg(val + e) * __ldcg(g + (c == kPadCol ? pad : c));
+    }
+    if (a1)
+      for (int j = kPairStage; j < w1; ++j) {
+        const int e = b1 + j * d.c1 + lane, c = __ldg(col + e);
+        acc1 -= __ldg(val + e) * __ldcg(g + (c == kPadCol ? pad : c));
+      }
+  }
+}
+
+template <typename PT, int MODE, bool UPDATE>
+__device__ __forceinline__ void pair_tile_staged(const Params &P, const PairPre<PT> &q, const PairStage<PT> &s,
+                                                 int lane, double alpha, double &rr_acc, double &rz_acc) {
+  const PairDesc &d = q.d;
+  if (lane >= d.c0) return;
+  const bool a1 = lane < d.c1;
+  const int i0 = d.row0 + lane, i1 = d.row0 + d.c0 + lane;
+  cp_wait_all();   // the lane's own staged entries (it reads no other lane's)
+  if (MODE == M_BWD) {
+    const PT *yv = reinterpret_cast<const PT *>(P.y);
+    PT acc0 = __ldcg(yv + i0), acc1 = a1 ? __ldcg(yv + i1) : PT(0);
+    const double r0 = __ldcg(P.r + i0), r1 = a1 ? __ldcg(P.r + i1) : 0.0;
+    pair_staged_sums<PT, true>(P, d, s, lane, a1, acc0, acc1);
+    const PT z1 = acc1 * q.dv1;
+    acc0 -= q.e * z1;
+    for (int j = 1; j < d.uiw0; ++j) acc0 -= __ldg(uiv<PT>(P) + d.ui + j * d.c0 + lane) * z1;
+    const PT z0 = acc0 * q.dv0;
+    PT *zv = reinterpret_cast<PT *>(P.z);
+    zv[i0] = z0;
+    rz_acc += r0 * double(z0);
+    if (a1) {
+      zv[i1] = z1;
+      rz_acc += r1 * double(z1);
+    }
+  } else {
+    PT acc0, acc1 = PT(0);
+    double r0 = __ldcg(P.r + i0), r1 = a1 ? __ldcg(P.r + i1) : 0.0;
+    if (UPDATE) {
+      const double q0 = __ldcg(P.q + i0), x0 = __ldcg(P.xh + i0), p0 = __ldcg(P.p0 + i0);
+      double q1 = 0.0, x1 = 0.0, p1 = 0.0;
+      if (a1) {
+        q1 = __ldcg(P.q + i1);
+        x1 = __ldcg(P.xh + i1);
+        p1 = __ldcg(P.p0 + i1);
+      }
+      r0 -= alpha * q0;
+      rr_acc += r0 * r0;
+      if (a1) {
+        r1 -= alpha * q1;
+        rr_acc += r1 * r1;
+      }
+      acc0 = PT(r0);
+      acc1 = PT(r1);
+      pair_staged_sums<PT, false>(P, d, s, lane, a1, acc0, acc1);
+      P.r[i0] = r0;
+      P.xh[i0] = x0 + alpha * p0;
+      if (a1) {
+        P.r[i1] = r1;
+        P.xh[i1] = x1 + alpha * p1;
+      }
+    } else {
+      acc0 = PT(r0);
+      acc1 = PT(r1);
+      pair_staged_sums<PT, false>(P, d, s, lane, a1, acc0, acc1);
+    }
+    const PT y0 = acc0 * q.dv0;
+    PT y1 = PT(0);
+    if (a1) {
+      acc1 -= q.e * y0;
+      for (int j = 1; j < d.liw1; ++j) acc1 -= __ldg(siv<PT>(P) + d.li + j * d.c1 + lane) * y0;
+      y1 = acc1 * q.dv1;
+    }
+    PT *yv = reinterpret_cast<PT *>(P.y);
+    if (MODE == M_FWD) {
+      yv[i0] = y0;
+      if (a1) yv[i1] = y1;
+    } else {
+      pair_bwd<PT>(P, d, lane, a1, y0, y1, q.dv0, q.dv1, r0, r1, rz_acc);
+    }
+  }
+}
+
+template <typename PT>
+constexpr int pair_stage_bytes() { return int(sizeof(PairStage<PT>)); }
+
 template <typename PT, int MODE, bool UPDATE>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
 pair_kernel(Params P, int t0, int t1, int fin, SlotArgs sa) {
   pdl_trigger();
+  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[kMaxWarpsPerCta];
   __shared__ int flag;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = int(threadIdx.x >> 5);
   const int nw = int(blockDim.x >> 5), stride = int(gridDim.x) * nw;
+  PairStage<PT> &st = reinterpret_cast<PairStage<PT> *>(smem)[wid];
   double rr_acc = 0.0, rz_acc = 0.0;
+  int t = t0 + int(blockIdx.x) * nw + wid;
+  PairPre<PT> q;
+  if (t < t1) q = pair_stage<PT, MODE == M_BWD>(P, t, lane, st);
   pdl_wait();
   const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
-  for (int t = t0 + int(blockIdx.x) * nw + int(threadIdx.x >> 5); t < t1; t += stride)
-    pair_tile<PT, MODE, UPDATE>(P, t, lane, alpha, rr_acc, rz_acc);
+  while (t < t1) {
+    pair_tile_staged<PT, MODE, UPDATE>(P, q, st, lane, alpha, rr_acc, rz_acc);
+    t += stride;
+    __syncwarp();
+    if (t < t1) q = pair_stage<PT, MODE == M_BWD>(P, t, lane, st);
+  }
   launch_epilogue(P, fin, sa, MODE != M_BWD && UPDATE, MODE != M_FWD, rr_acc, rz_acc, red, &flag);
 }
 
@@ -1275,16 +1482,6 @@ __device__ __forceinline__ void unit_coef(const PT *v, const uint32_t *sw, int o
 // the lane's chain coefficients into its column of the warp's shared-memory
 // buffer (cp.async, only the steps its mask has: no registers held while the
 // copies fly) and its source lanes into registers
-template <typename PT>
-__device__ __forceinline__ void cp_async_elem(PT *smem, const PT *gmem);
-template <> __device__ __forceinline__ void cp_async_elem<double>(double *smem, const double *gmem) {
-  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(a), "l"(gmem) : "memory");
-}
-template <> __device__ __forceinline__ void cp_async_elem<float>(float *smem, const float *gmem) {
-  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(gmem) : "memory");
-}
 
 template <typename PT, int S>
 __device__ __forceinline__ void unit_coef_smem(const PT *v, const uint32_t *sw, int off, int soff, int M,
@@ -1682,14 +1879,6 @@ struct Strided {
   __device__ __forceinline__ T &operator[](int q) const { return base[q * kFacRowThreads]; }
 };
 
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
-}
 
 struct FacSmem {
   Strided<double> sv, ivj, pv;
@@ -2404,13 +2593,14 @@ cudaError_t launch_wtile(const Params &P, const Plan &L, int c, int mode, bool u
 template <typename PT>
 cudaError_t launch_pair(const Params &P, const Plan &L, int c, int mode, bool update, int fin, const SlotArgs &sa) {
   const int g = L.grid_c[c], t0 = L.tile0[c], t1 = L.tile1[c], th = L.Ww * kWarp;
-  if (mode == M_BWD) return launch(pair_kernel<PT, M_BWD, false>, g, th, 0, L, P, t0, t1, fin, sa);
+  const int sm = L.Ww * pair_stage_bytes<PT>();
+  if (mode == M_BWD) return launch(pair_kernel<PT, M_BWD, false>, g, th, sm, L, P, t0, t1, fin, sa);
   if (update) {
-    if (mode == M_FUSED) return launch(pair_kernel<PT, M_FUSED, true>, g, th, 0, L, P, t0, t1, fin, sa);
-    return launch(pair_kernel<PT, M_FWD, true>, g, th, 0, L, P, t0, t1, fin, sa);
+    if (mode == M_FUSED) return launch(pair_kernel<PT, M_FUSED, true>, g, th, sm, L, P, t0, t1, fin, sa);
+    return launch(pair_kernel<PT, M_FWD, true>, g, th, sm, L, P, t0, t1, fin, sa);
   }
-  if (mode == M_FUSED) return launch(pair_kernel<PT, M_FUSED, false>, g, th, 0, L, P, t0, t1, fin, sa);
-  return launch(pair_kernel<PT, M_FWD, false>, g, th, 0, L, P, t0, t1, fin, sa);
+  if (mode == M_FUSED) return launch(pair_kernel<PT, M_FUSED, false>, g, th, sm, L, P, t0, t1, fin, sa);
+  return launch(pair_kernel<PT, M_FWD, false>, g, th, sm, L, P, t0, t1, fin, sa);
 }
 
 template <typename PT, int S>
@@ -2570,6 +2760,11 @@ cudaError_t configure_pt() {
   if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_FUSED, false>);
   if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_FWD, false>);
   if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_BWD, false>);
+  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_FUSED, true>);
+  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_FWD, true>);
+  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_FUSED, false>);
+  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_FWD, false>);
+  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_BWD, false>);
   if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_FUSED, true>);
   if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_FWD, true>);
   if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_FUSED, false>);
@@ -2615,8 +2810,10 @@ int wtile_resident_ctas(bool fp32, int threads, int smem) {
 int pair_resident_ctas(bool fp32, int threads) {
   int nb = 0;
   const cudaError_t e =
-      fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<float, M_FWD, true>, threads, 0)
-           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<double, M_FWD, true>, threads, 0);
+      fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<float, M_FWD, true>, threads,
+                                                           size_t(threads / kWarp) * pair_stage_bytes<float>())
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<double, M_FWD, true>, threads,
+                                                           size_t(threads / kWarp) * pair_stage_bytes<double>());
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
