@@ -131,6 +131,7 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   if (o.lane_block_max > 32 || o.lane_block_max < -1) return ICCG_ERR_ARG;
   if (o.solver < ICCG_SOLVER_AUTO || o.solver > ICCG_SOLVER_PHASED) return ICCG_ERR_ARG;
   if (o.fuse_sweep < -1 || o.fuse_sweep > 2) return ICCG_ERR_ARG;
+  const bool w_auto = o.warps_per_cta == 0;
   if (o.warps_per_cta == 0) o.warps_per_cta = 8;
   if (o.rows_per_thread == 0) o.rows_per_thread = 1;
   if (o.warps_per_cta < 1 || o.warps_per_cta > kMaxWarpsPerCta) return ICCG_ERR_ARG;
@@ -277,7 +278,12 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
   L.smem_wt = L.Ww * L.cap_ws * kWarp * elem;
   const int wt_full =
       H.tile_colors > 0 ? sms * wtile_resident_ctas(ctx->fp32, L.Ww * kWarp, L.smem_wt) : 1;
-  const int pr_full = H.tile_colors > 0 ? sms * pair_resident_ctas(ctx->fp32, L.Ww * kWarp) : 1;
+  // pair kernels: 4 warps per CTA unless set (on a GB300 at 128^3 with two-row
+  // blocks 3% faster than 8, 16 slower)
+  L.Wp = w_auto ? 4 : W;
+  const int pr_full = H.tile_colors > 0 ? sms * pair_resident_ctas(ctx->fp32, L.Wp * kWarp) : 1;
+  L.pstage_f.assign(n_c, 0);
+  L.pstage_b.assign(n_c, 0);
   L.wtile.assign(n_c, 0);
   L.stage_ext.assign(n_c, 0);
   L.unit0.assign(n_c, 0);
@@ -320,7 +326,23 @@ iccg_status iccg_setup(iccg_ctx **out, int32_t n, int64_t nnz, const int64_t *ro
       const int full = sms * unit_resident_ctas(ctx->fp32, L.unit_S[c], L.Wu * kWarp);
       L.grid_c[c] = std::max(1, std::min((nu + L.Wu - 1) / L.Wu, full));
     } else if (L.wtile[c] == 1) L.grid_c[c] = std::min((nt + L.Ww - 1) / L.Ww, wt_full);
-    else if (L.wtile[c] == 2) L.grid_c[c] = std::min((nt + L.Ww - 1) / L.Ww, pr_full);
+    else if (L.wtile[c] == 2) {
+      L.grid_c[c] = std::min((nt + L.Wp - 1) / L.Wp, pr_full);
+      // a sweep stages its entries to other colors ahead of the gathers when
+      // its tiles have on average at least two (over both steps), and always
+      // with the FP32 preconditioner (on a GB300 at 128^3 with two-row blocks:
+      // FP64 41.2 ms with this rule against 43.5 with every color staged, where
+      // the staged kernel of a color without entries ran 50% longer; FP32 34.0
+      // ms with every color staged against 35.8 with this rule)
+      int64_t wf = 0, wb = 0;
+      for (int t = L.tile0[c]; t < L.tile1[c]; ++t) {
+        const PairDesc &d = H.pairs[size_t(t)];
+        wf += d.lw0 + d.lw1;
+        wb += d.uw0 + d.uw1;
+      }
+      L.pstage_f[c] = ctx->fp32 || wf >= 2 * int64_t(nt);
+      L.pstage_b[c] = ctx->fp32 || wb >= 2 * int64_t(nt);
+    }
     else L.grid_c[c] = nt > 0 ? std::min(nt, L.stage_ext[c] ? tile_full_x : tile_full)
                               : std::max(1, L.task1[c] - L.task0[c]);
     gbig = std::max(gbig, L.grid_c[c]);

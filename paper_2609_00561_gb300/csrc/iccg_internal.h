@@ -345,6 +345,8 @@ struct Plan {
   int32_t tail_c = 0;                   // > 0: colors tail_c.. of every sweep in one cooperative launch
   int32_t grid_tail = 0;                // CTAs of that launch (one per SM)
   int32_t Ww = 8;                       // warps per CTA of the warp-tile kernels
+  int32_t Wp = 4;                       // warps per CTA of the pair kernels
+  std::vector<char> pstage_f, pstage_b; // pair color c's forward / backward launches stage their entries
   int32_t smem_wt = 0;                  // bytes per CTA of the warp-tile kernels
   int32_t cap_ws = 0;                   // steps per tile held in a warp's buffer
   std::vector<int32_t> off_rr, off_rz;  // slot regions of the color-c forward / backward launches

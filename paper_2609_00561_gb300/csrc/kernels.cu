@@ -1379,7 +1379,7 @@ __device__ __forceinline__ void pair_tile_staged(const Params &P, const PairPre<
 template <typename PT>
 constexpr int pair_stage_bytes() { return int(sizeof(PairStage<PT>)); }
 
-template <typename PT, int MODE, bool UPDATE>
+template <typename PT, int MODE, bool UPDATE, bool STAGE>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kWarp)
 pair_kernel(Params P, int t0, int t1, int fin, SlotArgs sa) {
   pdl_trigger();
@@ -1388,18 +1388,24 @@ pair_kernel(Params P, int t0, int t1, int fin, SlotArgs sa) {
   __shared__ int flag;
   const int lane = threadIdx.x & 31, wid = int(threadIdx.x >> 5);
   const int nw = int(blockDim.x >> 5), stride = int(gridDim.x) * nw;
-  PairStage<PT> &st = reinterpret_cast<PairStage<PT> *>(smem)[wid];
   double rr_acc = 0.0, rz_acc = 0.0;
   int t = t0 + int(blockIdx.x) * nw + wid;
-  PairPre<PT> q;
-  if (t < t1) q = pair_stage<PT, MODE == M_BWD>(P, t, lane, st);
-  pdl_wait();
-  const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
-  while (t < t1) {
-    pair_tile_staged<PT, MODE, UPDATE>(P, q, st, lane, alpha, rr_acc, rz_acc);
-    t += stride;
-    __syncwarp();
+  if constexpr (STAGE) {
+    PairStage<PT> &st = reinterpret_cast<PairStage<PT> *>(smem)[wid];
+    PairPre<PT> q;
     if (t < t1) q = pair_stage<PT, MODE == M_BWD>(P, t, lane, st);
+    pdl_wait();
+    const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
+    while (t < t1) {
+      pair_tile_staged<PT, MODE, UPDATE>(P, q, st, lane, alpha, rr_acc, rz_acc);
+      t += stride;
+      __syncwarp();
+      if (t < t1) q = pair_stage<PT, MODE == M_BWD>(P, t, lane, st);
+    }
+  } else {
+    pdl_wait();
+    const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
+    for (; t < t1; t += stride) pair_tile<PT, MODE, UPDATE>(P, t, lane, alpha, rr_acc, rz_acc);
   }
   launch_epilogue(P, fin, sa, MODE != M_BWD && UPDATE, MODE != M_FWD, rr_acc, rz_acc, red, &flag);
 }
@@ -2590,17 +2596,25 @@ cudaError_t launch_wtile(const Params &P, const Plan &L, int c, int mode, bool u
   return launch(wtile_kernel<PT, M_FWD, false>, g, th, sm, L, P, t0, t1, cs, fin, sa);
 }
 
+template <typename PT, bool STAGE>
+cudaError_t launch_pair_s(const Params &P, const Plan &L, int c, int mode, bool update, int fin,
+                          const SlotArgs &sa) {
+  const int g = L.grid_c[c], t0 = L.tile0[c], t1 = L.tile1[c], th = L.Wp * kWarp;
+  const int sm = STAGE ? L.Wp * pair_stage_bytes<PT>() : 0;
+  if (mode == M_BWD) return launch(pair_kernel<PT, M_BWD, false, STAGE>, g, th, sm, L, P, t0, t1, fin, sa);
+  if (update) {
+    if (mode == M_FUSED) return launch(pair_kernel<PT, M_FUSED, true, STAGE>, g, th, sm, L, P, t0, t1, fin, sa);
+    return launch(pair_kernel<PT, M_FWD, true, STAGE>, g, th, sm, L, P, t0, t1, fin, sa);
+  }
+  if (mode == M_FUSED) return launch(pair_kernel<PT, M_FUSED, false, STAGE>, g, th, sm, L, P, t0, t1, fin, sa);
+  return launch(pair_kernel<PT, M_FWD, false, STAGE>, g, th, sm, L, P, t0, t1, fin, sa);
+}
+
 template <typename PT>
 cudaError_t launch_pair(const Params &P, const Plan &L, int c, int mode, bool update, int fin, const SlotArgs &sa) {
-  const int g = L.grid_c[c], t0 = L.tile0[c], t1 = L.tile1[c], th = L.Ww * kWarp;
-  const int sm = L.Ww * pair_stage_bytes<PT>();
-  if (mode == M_BWD) return launch(pair_kernel<PT, M_BWD, false>, g, th, sm, L, P, t0, t1, fin, sa);
-  if (update) {
-    if (mode == M_FUSED) return launch(pair_kernel<PT, M_FUSED, true>, g, th, sm, L, P, t0, t1, fin, sa);
-    return launch(pair_kernel<PT, M_FWD, true>, g, th, sm, L, P, t0, t1, fin, sa);
-  }
-  if (mode == M_FUSED) return launch(pair_kernel<PT, M_FUSED, false>, g, th, sm, L, P, t0, t1, fin, sa);
-  return launch(pair_kernel<PT, M_FWD, false>, g, th, sm, L, P, t0, t1, fin, sa);
+  const bool stage = mode == M_BWD ? L.pstage_b[c] != 0 : L.pstage_f[c] != 0;
+  return stage ? launch_pair_s<PT, true>(P, L, c, mode, update, fin, sa)
+               : launch_pair_s<PT, false>(P, L, c, mode, update, fin, sa);
 }
 
 template <typename PT, int S>
@@ -2760,11 +2774,11 @@ cudaError_t configure_pt() {
   if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_FUSED, false>);
   if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_FWD, false>);
   if (e == cudaSuccess) e = allow_smem(tile_kernel<PT, M_BWD, false>);
-  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_FUSED, true>);
-  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_FWD, true>);
-  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_FUSED, false>);
-  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_FWD, false>);
-  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_BWD, false>);
+  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_FUSED, true, true>);
+  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_FWD, true, true>);
+  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_FUSED, false, true>);
+  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_FWD, false, true>);
+  if (e == cudaSuccess) e = allow_smem(pair_kernel<PT, M_BWD, false, true>);
   if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_FUSED, true>);
   if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_FWD, true>);
   if (e == cudaSuccess) e = allow_smem(wtile_kernel<PT, M_FUSED, false>);
@@ -2810,9 +2824,9 @@ int wtile_resident_ctas(bool fp32, int threads, int smem) {
 int pair_resident_ctas(bool fp32, int threads) {
   int nb = 0;
   const cudaError_t e =
-      fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<float, M_FWD, true>, threads,
+      fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<float, M_FWD, true, true>, threads,
                                                            size_t(threads / kWarp) * pair_stage_bytes<float>())
-           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<double, M_FWD, true>, threads,
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<double, M_FWD, true, true>, threads,
                                                            size_t(threads / kWarp) * pair_stage_bytes<double>());
   if (e != cudaSuccess) {
     cudaGetLastError();
