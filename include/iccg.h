@@ -53,7 +53,8 @@ typedef struct {
                                  with FP32 accumulation; IC(0) itself, the CG dots,
                                  alpha/beta and the x/r updates stay FP64 */
   int32_t warps_per_cta;      /* warps per CTA of the substitution kernels (a lane-tile
-                                 CTA uses at most one warp per step); 1..16; 0 = 8 */
+                                 CTA uses at most one warp per step); 1..16; 0 = 8,
+                                 and 4 for the pair kernels (colors of two-row blocks) */
   int32_t rows_per_thread;    /* a group (the work of one CTA) holds up to
                                  32 * warps_per_cta * rows_per_thread rows of whole
                                  blocks; 1, 2, 4, 8, 16 or 32; 0 = 1 */
