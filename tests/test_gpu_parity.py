@@ -167,6 +167,41 @@ def test_solve_fp32_preconditioner(name, solver):
     S.close()
 
 
+@pytest.mark.parametrize("name", ["grid3d_abmc2", "grid3d_cpm_pairs", "rgg_levels"])
+@pytest.mark.parametrize("shape", [dict(tile_mapping="pair"), dict(tile_mapping="pair", warps_per_cta=16),
+                                   dict(tile_mapping="pair", no_graph=1)])
+def test_fp32_preconditioner_on_pair_tiles(name, shape):
+    """Extension 1 on the pair kernels, which in FP32 stage every color's
+    entries to other colors: two-row blocks (ABMC 2), one- and two-row
+    blocks mixed in a tile (CPM 0.5), and one-row blocks with up to a dozen
+    entries to earlier levels (a random geometric graph by level sets, past
+    the six entries per step staged in shared memory)."""
+    a, b, bl, ref = _case(name)
+    S = iccg.Solver(a, bl, precond_fp32=True, **shape)
+    assert iccg.iccg_info(S.ctx)["pair_tile_colors"] > 0
+    x = np.zeros(a.n)
+    st, it, hist = iccg.iccg_solve(S.ctx, b, x, 1e-8, 20000)
+    assert st == iccg.ICCG_OK and hist[-1] <= 1e-8
+    true_rel = np.linalg.norm(b - a.to_scipy() @ x) / np.linalg.norm(b)
+    assert true_rel <= 1e-7
+    err = _rel(x, ref["x"])
+    assert err <= 1e-6 * max(1.0, ref["iterations"] / 10.0), err
+    assert abs(it - ref["iterations"]) <= 3 + ref["iterations"] // 10
+    # the preconditioner apply alone against the oracle's FP64 substitutions:
+    # FP32 factors and accumulation give a relative error of order (entries
+    # per row) x 2^-24 x cond(L), well below 1e-4 for these matrices
+    z = np.zeros(a.n)
+    iccg.iccg_precond(S.ctx, b, z)
+    ah = oracle.permute(a, bl["perm"])
+    lptr, lcol, aval = oracle.tril_csr(ah)
+    lref, _ = oracle.ic0(lptr, lcol, aval)
+    zp = oracle.backward(lptr, lcol, lref, oracle.forward(lptr, lcol, lref, b[bl["perm"]]))
+    zref = np.zeros(a.n)
+    zref[bl["perm"]] = zp
+    assert _rel(z, zref) <= 1e-4
+    S.close()
+
+
 @pytest.mark.parametrize("solver", sorted(SOLVERS))
 def test_device_and_host_pointers_agree_and_are_deterministic(solver):
     a, b, bl, ref = _case("grid3d_abmc32")
