@@ -316,8 +316,8 @@ void iccg_batch_destroy(iccg_batch *batch);
  * that loads the library until the process exits.  All calls share it: the
  * counters are cleared at the start of every call, and two calls whose work
  * overlaps on the GPU race and give wrong results.  The first call on each
- * device looks up the array's address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  The sum is deterministic (fixed order).
+ * device looks up the array's address (cudaGetSymbolAddress) and caches it.
+ * The sum is deterministic (fixed order).
  * ICCG_ERR_CUDA when a CUDA call of this entry point failed (an error left
  * pending by earlier unrelated work is not consumed).
  * ------------------------------------------------------------------------ */

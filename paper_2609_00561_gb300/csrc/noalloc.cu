@@ -18,9 +18,9 @@
 // or different host threads) race on the array and give wrong results.
 //
 // The first call on each device looks up the array's device address with
-// cudaGetSymbolAddress (with that device current) and caches it; make that
-// first call before any stream capture starts.  The stream must belong to the
-// current device (the cached address is that device's copy of the array).
+// cudaGetSymbolAddress (with that device current) and caches it.  The stream
+// must belong to the current device (the cached address is that device's
+// copy of the array).
 #include <mutex>
 
 #include "iccg_internal.h"
