@@ -1109,9 +1109,11 @@ wtile_kernel(Params P, int t0, int t1, int cap_s, int fin, SlotArgs sa) {
 // Padding entries (kPadCol, 0) add 0 * an element the sweep has already
 // written: y_0 (first color) forward, z_{n-1} (last color) backward.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ PairDesc load_pair(const PairDesc *p) {
+// a descriptor whose first 16 bytes (first row, block counts) are already
+// in registers
+__device__ __forceinline__ PairDesc load_pair_rest(const PairDesc *p, int4 a) {
   const int4 *q = reinterpret_cast<const int4 *>(p);
-  const int4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+  const int4 b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
   PairDesc r;
   r.row0 = a.x; r.c0 = a.y; r.c1 = a.z; r.lo = a.w;
   r.lw0 = b.x; r.lw1 = b.y; r.li = b.z; r.liw1 = b.w;
@@ -1119,6 +1121,8 @@ __device__ __forceinline__ PairDesc load_pair(const PairDesc *p) {
   r.uiw0 = d.x; r.pad0 = r.pad1 = r.pad2 = 0;
   return r;
 }
+__device__ __forceinline__ int4 pair_head(const PairDesc *p) { return __ldg(reinterpret_cast<const int4 *>(p)); }
+__device__ __forceinline__ PairDesc load_pair(const PairDesc *p) { return load_pair_rest(p, pair_head(p)); }
 
 template <typename PT>
 __device__ __forceinline__ PT pair_sub(const int32_t *col, const PT *val, int e, int cnt, int w, PT acc,
@@ -1155,11 +1159,11 @@ __device__ __forceinline__ void pair_bwd(const Params &P, const PairDesc &d, int
 
 // one tile of a pair color, warp-wide (lanes beyond the tile's blocks idle)
 template <typename PT, int MODE, bool UPDATE>
-__device__ __forceinline__ void pair_tile(const Params &P, int t, int lane, double alpha, double &rr_acc,
-                                          double &rz_acc) {
+__device__ __forceinline__ void pair_tile_h(const Params &P, int t, int4 head, int lane, double alpha,
+                                            double &rr_acc, double &rz_acc) {
   PT *yv = reinterpret_cast<PT *>(P.y);
   const PT *dvg = invds<PT>(P);
-  const PairDesc d = load_pair(P.pairs + t);
+  const PairDesc d = load_pair_rest(P.pairs + t, head);
   if (lane >= d.c0) return;   // a lane active in step 1 is active in step 0
   const bool a1 = lane < d.c1;
   const int i0 = d.row0 + lane, i1 = d.row0 + d.c0 + lane;
@@ -1196,6 +1200,12 @@ __device__ __forceinline__ void pair_tile(const Params &P, int t, int lane, doub
       pair_bwd<PT>(P, d, lane, a1, y0, y1, dv0, dv1, r0, r1, rz_acc);
     }
   }
+}
+
+template <typename PT, int MODE, bool UPDATE>
+__device__ __forceinline__ void pair_tile(const Params &P, int t, int lane, double alpha, double &rr_acc,
+                                          double &rz_acc) {
+  pair_tile_h<PT, MODE, UPDATE>(P, t, pair_head(P.pairs + t), lane, alpha, rr_acc, rz_acc);
 }
 
 // The pair kernel proper stages each tile's static data ahead of its
@@ -1403,9 +1413,17 @@ pair_kernel(Params P, int t0, int t1, int fin, SlotArgs sa) {
       if (t < t1) q = pair_stage<PT, MODE == M_BWD>(P, t, lane, st);
     }
   } else {
+    // the next tile's first descriptor word (its rows) loads while the
+    // current tile runs, the first tile's before the wait
+    int4 hn = make_int4(0, 0, 0, 0);
+    if (t < t1) hn = pair_head(P.pairs + t);
     pdl_wait();
     const double alpha = UPDATE ? __ldcg(&P.sc->alpha) : 0.0;
-    for (; t < t1; t += stride) pair_tile<PT, MODE, UPDATE>(P, t, lane, alpha, rr_acc, rz_acc);
+    for (; t < t1; t += stride) {
+      const int4 h = hn;
+      if (t + stride < t1) hn = pair_head(P.pairs + t + stride);
+      pair_tile_h<PT, MODE, UPDATE>(P, t, h, lane, alpha, rr_acc, rz_acc);
+    }
   }
   launch_epilogue(P, fin, sa, MODE != M_BWD && UPDATE, MODE != M_FWD, rr_acc, rz_acc, red, &flag);
 }
