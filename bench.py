@@ -153,12 +153,23 @@ def workload_string(args, a, bl):
             f"IC(0) + PCG to {args.tol:g}" + (", FP32 preconditioner" if args.fp32 else ""))
 
 
+def code_only(src):
+    """C++ source without its comments, trailing blanks and empty lines (string
+    literals kept), so that a change of comments alone keeps the digest."""
+    import re
+    tok = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\\n])*"|\'(?:\\.|[^\'\\\n])*\'', re.S)
+    out = tok.sub(lambda m: "" if m.group(0)[0] == "/" else m.group(0), src)
+    return "\n".join(ln.rstrip() for ln in out.split("\n") if ln.strip())
+
+
 def kernels_sha():
-    """sha256 of the CUDA sources the substitution kernels are built from."""
+    """sha256 of the CUDA sources the substitution kernels are built from
+    (their code, comments left out)."""
     import hashlib
     h = hashlib.sha256()
     for f in ("kernels.cu", "iccg_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_2609_00561_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2609_00561_gb300", "csrc", f), encoding="utf-8").read()
+        h.update(code_only(src).encode())
     return h.hexdigest()
 
 

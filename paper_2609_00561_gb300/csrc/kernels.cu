@@ -1208,7 +1208,8 @@ __device__ __forceinline__ void pair_tile(const Params &P, int t, int lane, doub
   pair_tile_h<PT, MODE, UPDATE>(P, t, pair_head(P.pairs + t), lane, alpha, rr_acc, rz_acc);
 }
 
-// The pair kernel proper stages each tile's static data ahead of its
+// The staged pair kernel (pair_kernel<.., STAGE = true>, chosen per color
+// and sweep on the host) loads each tile's static data ahead of its
 // gathers: the descriptor, the pivots' reciprocals and in-block coefficient
 // in registers, and the first kPairStage entries of each step (the sums over
 // the other colors: lower for the forward sweep, upper for the backward) in
@@ -1216,7 +1217,8 @@ __device__ __forceinline__ void pair_tile(const Params &P, int t, int lane, doub
 // staged before griddepcontrol.wait, so these loads overlap the previous
 // launch; after the wait a tile's gathers of both steps and its row vectors
 // are in flight together.  Wider steps take their remaining entries from
-// global memory.
+// global memory.  The unstaged kernel (pair_tile_h) keeps the loads in the
+// order the recurrence uses them and serves sweeps with few such entries.
 constexpr int kPairStage = 6;   // a 7-point row has at most 6 entries to other blocks
 
 template <typename PT>
