@@ -61,3 +61,16 @@ def test_reference_arm_prints_on_rank_zero_only():
     wl = line["config"]["workload"]
     assert "n=4096" in wl and "n_b=" in wl and "n_c=" in wl and "Leiden CPM resolution 0.5" in wl
     assert line["iterations"] > 0
+
+
+def test_traffic_record_digest_ignores_comments_only():
+    """The committed DRAM-traffic record is keyed by the kernel sources' code:
+    a comment edit keeps the digest, any code edit changes it, and string
+    literals (inline PTX) count as code."""
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    src = 'int a = 1;  // one\n/* block\n comment */\nasm("ld.global // not a comment");\n'
+    assert bench.code_only(src) == 'int a = 1;\nasm("ld.global // not a comment");'
+    assert bench.code_only(src.replace("// one", "// two\n// three")) == bench.code_only(src)
+    assert bench.code_only(src.replace("a = 1", "a = 2")) != bench.code_only(src)
+    assert bench.code_only(src.replace("// not a comment", "")) != bench.code_only(src)
