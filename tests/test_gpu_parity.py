@@ -53,6 +53,10 @@ CASES = {
     "aniso27": (lambda: (gen.stencil_aniso("27pt", 3375, 4.0), gen.rhs_uniform(3375, 8), None), "abmc", {"block_size": 32}),
     "elast27": (lambda: (gen.elasticity_like(700, 27, 3.0), gen.rhs_uniform(2187, 9), None), "abmc", {"block_size": 24}),
     "diff27": (lambda: (gen.diffusion3d_27pt(14, seed=2), gen.rhs_uniform(2744, 10), None), "abmc", {"block_size": 32}),
+    # two-row blocks of a 27-point stencil: pair tiles whose steps have more
+    # entries to other colors than the pair kernels stage in shared memory
+    "aniso27_abmc2": (lambda: (gen.stencil_aniso("27pt", 3375, 4.0), gen.rhs_uniform(3375, 18), None), "abmc",
+                      {"block_size": 2}),
     # level scheduling of the natural order: one-row blocks, a color per level
     "grid3d_levels": (lambda: (gen.poisson3d_7pt(13), gen.rhs_uniform(2197, 16), None), "levels", {}),
     "rgg_levels": (lambda: (gen.rgg_laplacian(1500, 10.0, 5), gen.rhs_uniform(1500, 17), None), "levels", {}),
@@ -167,7 +171,7 @@ def test_solve_fp32_preconditioner(name, solver):
     S.close()
 
 
-@pytest.mark.parametrize("name", ["grid3d_abmc2", "grid3d_cpm_pairs", "rgg_levels"])
+@pytest.mark.parametrize("name", ["grid3d_abmc2", "grid3d_cpm_pairs", "rgg_levels", "aniso27_abmc2"])
 @pytest.mark.parametrize("shape", [dict(tile_mapping="pair"), dict(tile_mapping="pair", warps_per_cta=16),
                                    dict(tile_mapping="pair", no_graph=1)])
 def test_fp32_preconditioner_on_pair_tiles(name, shape):
